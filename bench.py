@@ -1,0 +1,330 @@
+#!/usr/bin/env python
+"""Throughput of the semi-regular Boltzmann step on GB300.
+
+One step = one pass of the whole hot path over the cavity: wall densities,
+the shared Monte Carlo sample set, and the fused per-cell kernel (upwind
+streaming, Jacobi Monte Carlo collision update, conservation correction,
+moments).  Workload: the 256x256-cell driven cavity with a 32^3 velocity grid
+on [-5, 5]^3, Kn 0.05, lid 0.05 sin(2 pi t / 50), 2x10^4 samples per step,
+FP32 state (8.6 GB per buffer, far larger than L2, so no flush is needed).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank advances an
+independent cavity instance (weak scaling, no collective on the data path);
+the timed region is bracketed by barriers and the max over ranks is used.
+`--impl reference` times the FP64 CPU oracle on the host cores instead, on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "phase-space node updates/s (256^2 x 32^3 FP32 cavity step)"
+UNIT = "node-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", default="cavity256_v32")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def problem(name):
+    from paper_1005_5405_gb300 import workloads
+    return getattr(workloads, name)()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    src = os.path.join(ROOT, "paper_1005_5405_gb300", "csrc")
+    for f in sorted(os.listdir(src)):
+        with open(os.path.join(src, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(config):
+    """DRAM bytes per launch of the per-cell kernel from the committed ncu
+    summary, or None when the summary is absent or the kernel source changed
+    since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"k_cell_fused_{config}.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(p, cells_per_side=32, steps=2):
+    """Time the FP64 oracle on a sub-cavity with the workload's cell size,
+    velocity grid and sample count (same work per node and per sample)."""
+    import numpy as np
+    import oracle
+    from paper_1005_5405_gb300 import workloads
+    s = cells_per_side
+    dx = (1.0 / p.kn) / p.nx
+    sub = workloads.Problem("sample", s, s, 1.0 / (s * dx), p.nv, p.vmax, p.nt, p.seed,
+                            lid_u0=p.lid_u0, lid_amp=p.lid_amp, lid_period=p.lid_period)
+    o = oracle.Oracle(**sub.kwargs())
+    h = np.zeros((sub.nr, sub.nvt))
+    o.step(h, 0)                       # first touch of the buffers
+    t0 = time.perf_counter()
+    for n in range(steps):
+        h, _ = o.step(h, n + 1)
+    dt = (time.perf_counter() - t0) / steps
+    return {
+        "value": sub.nodes / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+        "pairs_per_s": sub.nr * sub.nt / dt, "s_per_step": dt,
+        "sample": (f"{steps} steps of a {s}x{s}-cell sub-cavity, same cell size, {p.nv}^3 "
+                   f"velocities on [-{p.vmax},{p.vmax}]^3, {p.nt} samples/step, FP64 oracle"),
+    }
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    p = problem(args.config)
+    steps = max(1, min(args.steps, 3))
+    r = oracle_sample(p, 64, steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT,
+        "n_gpus": args.gpus, "steps": steps, "warmup": 1, "ms_per_step": r["s_per_step"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": p.name, "nx": p.nx, "ny": p.ny, "nv": p.nv,
+                                         "vmax": p.vmax, "kn": p.kn, "samples_per_step": p.nt},
+        "cpu_baseline": {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": r["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "mc_pairs_per_s": r["pairs_per_s"],
+    }
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    __graft_entry__.build()
+    from paper_1005_5405_gb300 import binding
+
+    p = problem(args.config)
+    p.instance = rank                      # independent replica per rank
+    cav = binding.Cavity(p)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    cav.step(args.warmup)
+    barrier()
+    launches0 = cav.stats()[4]
+    clocks = Clocks(local)
+    clocks.start()
+    cav.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cav.step(args.steps)
+    e1.record(stream)
+    barrier()
+    cav.profile(False)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    kms, kn = cav.profile_read()
+    launches = cav.stats()[4] - launches0
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+
+    # End to end through the C ABI with host buffers: per step the caller
+    # uploads the lid velocity of every lid face (pinned host -> device),
+    # advances one step and reads the macroscopic fields back to pinned host
+    # memory (device -> host, synchronised).
+    prof_h = torch.zeros(p.nx, dtype=torch.float64).pin_memory()
+    mom_h = torch.empty((p.nr, 11), dtype=torch.float64).pin_memory()
+    info = cav.get_info()
+    n0 = info.step
+
+    def lid_at(n):
+        tt = n * info.dt
+        u = p.lid_u0 + (p.lid_amp * np.sin(2 * np.pi * tt / p.lid_period) if p.lid_period > 0 else 0.0)
+        return np.full(p.nx, u)
+
+    barrier()
+    t0 = time.perf_counter()
+    args.e2e_steps = max(1, args.e2e_steps)
+    for k in range(args.e2e_steps):
+        prof_h.numpy()[:] = lid_at(n0 + k)
+        cav.set_lid(0.0, 0.0, 0.0, profile=prof_h.numpy())
+        cav.step(1)
+        cav.moments(out=mom_h)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_s = float(te.item())
+    cav.set_lid(p.lid_u0, p.lid_amp, p.lid_period, None)
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    nodes = p.nodes
+    value = world * nodes * args.steps / (ms_max / 1e3)
+    pairs = world * p.nr * p.nt * args.steps / (ms_max / 1e3)
+    cell_ms = kms[2] / max(1, kn[2])
+    esz = 8 if p.dtype == "f64" else 4
+    alg_bytes = 2 * esz * nodes + (16 + esz) * p.nt + 88 * p.nr
+    achieved = alg_bytes / (cell_ms / 1e3) / 1e9
+    peak, peak_src = peaks()
+    step_bytes = alg_bytes  # walls and sampling add < 0.1% (boundary reads, 20 B/sample)
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = oracle_sample(p, 64, 2)
+        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": p.dtype, "data": "synthetic",
+        "config": {"workload": p.name, "nx": p.nx, "ny": p.ny, "nv": p.nv, "vmax": p.vmax,
+                   "kn": p.kn, "samples_per_step": p.nt, "state_gb": nodes * esz / 1e9,
+                   "l2": f"state ({nodes * esz / 1e9:.2f} GB/buffer) exceeds L2 (129 MB); no flush needed",
+                   "parallelism": f"replicas x{world}"},
+        "mc_pairs_per_s": pairs,
+        "kernels_ms_per_step": {"walls": kms[0] / max(1, kn[0]), "sampling": kms[1] / max(1, kn[1]),
+                                "cell": cell_ms},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": profiled_traffic(p.name),
+                     "kernel": "k_cell<float,fused>", "peak_source": peak_src,
+                     "step_frac": (step_bytes / (ms_max / args.steps / 1e3) / 1e9) / peak},
+        "e2e": {"value": world * nodes * args.e2e_steps / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": 8 * p.nx, "d2h_bytes_per_step": 8 * 11 * p.nr},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

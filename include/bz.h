@@ -1,0 +1,210 @@
+/*
+ * bz.h -- C ABI of a GB300-native (sm_103a) semi-regular Boltzmann solver.
+ *
+ * Method: Frezzotti, Ghiroldi & Gibelli, "Solving the Boltzmann equation on
+ * GPUs".  The deviational distribution h, f = Phi0 (1 + eps h) (Sec. 2,
+ * Eq. definition), is advanced on a 2D driven cavity by time splitting
+ * (Sec. 3): first-order upwind free streaming with Maxwell diffuse walls
+ * (Eqs. streaming2D, bcMax), then a Monte Carlo evaluation of the hard-sphere
+ * collision integral on a Cartesian velocity grid (Eqs. coll8Dim,
+ * monteCarloInt, collision_step) and the Aristov-Tcheremissine conservation
+ * correction (Eqs. rinorm_a, correzione).
+ *
+ * Units: velocities in V0 = sqrt(2 R T0); lengths in lambda0 =
+ * (mu0/p0) V0 with mu0 the hard-sphere viscosity; times in lambda0/V0; n0 = 1;
+ * Phi0(v) = pi^{-3/2} exp(-|v|^2).  Geometry (Sec. 5.1): the cavity is
+ * [-L/2, L/2] x [0, L] with L = 1/kn; the lid y = L moves along +x; all
+ * walls are at T0.
+ *
+ * State layout (device memory, owned by the handle): h[cell][node] with
+ * cell = iy*nx + ix (x fastest) and node j = (jx*nv + jy)*nv + jz; element
+ * type float (BZ_F32) or double (BZ_F64).  Node velocities are the cell
+ * centres v = -vmax + (j + 1/2) dv, dv = 2 vmax / nv.
+ *
+ * Conventions:
+ *  - every call returns a bz_status; nothing is thrown across the ABI;
+ *  - a `stream` argument is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream); device work is enqueued on it asynchronously and errors
+ *    of that work surface at the next call that synchronises;
+ *  - pointer arguments documented as "host or device" may be either (the copy
+ *    uses unified addressing); all other pointers are as documented;
+ *  - inputs are copied at the call; the library never keeps caller pointers;
+ *  - a handle is not thread-safe; distinct handles are independent;
+ *  - bz_last_error() returns a thread-local message for the last failure.
+ */
+#ifndef BZ_H
+#define BZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bz_handle bz_handle;
+
+typedef enum {
+    BZ_OK = 0,
+    BZ_EINVAL = 1,        /* invalid argument (message says which) */
+    BZ_ENOMEM = 2,        /* device allocation failed */
+    BZ_ECUDA = 3,         /* a CUDA runtime call failed (message has the text) */
+    BZ_EDEVICE = 4,       /* a kernel reported an inconsistency (error word) */
+    BZ_ETIMEOUT = 5,      /* a bounded device wait gave up */
+    BZ_ENONFINITE = 6,    /* a non-finite moment was produced */
+    BZ_ESTATE = 7,        /* call not valid in the handle's current state */
+    BZ_EUNSUPPORTED = 8   /* configuration outside what the kernels support */
+} bz_status;
+
+enum { BZ_F32 = 0, BZ_F64 = 1 };             /* state element type */
+enum { BZ_SHARED = 0, BZ_PER_CELL = 1 };     /* Monte Carlo sample sets */
+
+/* Sub-step selection for bz_step_ex (tests and profiling). */
+enum {
+    BZ_DO_STREAM = 1u,     /* walls + free streaming into h~ (Eq. streaming2D) */
+    BZ_DO_COLLIDE = 2u,    /* sampling + collision + correction on the state */
+    BZ_SPLIT = 4u          /* full step as separate stream and collide kernels */
+};
+
+/* Spatial grid (Sec. 3, Sec. 5.1): nx x ny cells on the square cavity of
+ * side L = 1/kn (Knudsen number kn = 1/delta). */
+typedef struct {
+    int32_t nx, ny;
+    double kn;
+} bz_space;
+
+/* Velocity grid (Sec. 3): nv^3 nodes on the cube [-vmax, vmax]^3 (V0 units). */
+typedef struct {
+    int32_t nv;
+    double vmax;
+} bz_vel;
+
+/* Walls (Sec. 2 Eq. bcMax, Sec. 5.1): the lid speed of lid face ix at time
+ * t is U_ix(t) = base_ix + lid_amp sin(2 pi t / lid_period) (the sine term
+ * only when lid_period > 0), with base_ix = lid_profile[ix] when lid_profile
+ * is non-NULL (host pointer to nx doubles, copied) and lid_u0 otherwise.
+ * All other walls are at rest; every wall is at T0. */
+typedef struct {
+    double lid_u0, lid_amp, lid_period;
+    const double *lid_profile;
+} bz_walls;
+
+/* Method parameters.
+ *   n_pairs     Monte Carlo samples per step, Nt of Eq. monteCarloInt (>= 1)
+ *   seed        Philox4x32-10 key word 0; instance = key word 1
+ *   eps         deviation parameter of Eq. definition; 0 => max |U| (1 if
+ *               the lid never moves)
+ *   cfl         maximum Courant number per direction (Sec. 5.1); 0 => 0.5
+ *   kcoll       K = n0 sigma^2 lambda0; 0 => hard-sphere value
+ *               (5 * 1.016034 / 16) sqrt(2/pi) (Sec. 5.1, lambda0)
+ *   dtype       BZ_F32 or BZ_F64 state
+ *   sample_mode BZ_SHARED: one sample set per step for all cells (Sec. 3,
+ *               "the same set of collisions"); BZ_PER_CELL: independent sets */
+typedef struct {
+    int64_t n_pairs;
+    uint32_t seed, instance;
+    double eps, cfl, kcoll;
+    int32_t dtype;
+    int32_t sample_mode;
+} bz_params;
+
+/* Derived quantities of a handle. */
+typedef struct {
+    double dt, dx, dy, dv, eps, kcoll;
+    int64_t nodes;          /* nx*ny*nv^3 */
+    int64_t state_bytes;    /* one state buffer */
+    int64_t step;           /* steps taken so far (time t = step * dt) */
+    int32_t nr, nvt;        /* cells, velocity nodes */
+    int32_t dtype;
+    int32_t threads_per_cell, smem_bytes;  /* collision kernel launch shape */
+} bz_info;
+
+/* Create a solver for the driven cavity.  Validates every argument
+ * (BZ_EINVAL), rejects grids whose velocity slab does not fit one SM's
+ * shared memory (BZ_EUNSUPPORTED), allocates two state buffers and the
+ * per-step scratch on the current device (BZ_ENOMEM), and sets h = 0, the
+ * uniform equilibrium n0, T0 of Sec. 5.1.  *out is NULL on failure. */
+bz_status bz_create(const bz_space *space, const bz_vel *vel, const bz_walls *walls,
+                    const bz_params *params, bz_handle **out);
+
+/* Release a handle and all device memory it owns (NULL is accepted). */
+bz_status bz_destroy(bz_handle *h);
+
+/* Advance nsteps >= 0 time steps (Sec. 3 time splitting): per step the
+ * wall densities from h^n (Eq. bcMax), the shared sample set (Sec. 4.2,
+ * Algorithm 2), and one fused kernel that streams (Eq. streaming2D),
+ * collides (Eq. collision_step), corrects (Eqs. rinorm_a, correzione) and
+ * reduces the moments.  Asynchronous on `stream`. */
+bz_status bz_step(bz_handle *h, int32_t nsteps, void *stream);
+
+/* Like bz_step with the sub-steps chosen by `flags` (BZ_DO_STREAM,
+ * BZ_DO_COLLIDE, BZ_SPLIT).  BZ_DO_STREAM alone replaces the state by h~
+ * without advancing the step counter; BZ_DO_COLLIDE alone applies the
+ * relaxation of step `step` to the current state and advances the counter;
+ * both (or BZ_SPLIT) take one full step with separate kernels. */
+bz_status bz_step_ex(bz_handle *h, int32_t nsteps, uint32_t flags, void *stream);
+
+/* Macroscopic quantities of every cell (Eqs. densita..sforzi, written in V0
+ * units): out[cell*11 + k], k = rho, ux, uy, uz, theta, Pxx, Pyy, Pzz, Pxy,
+ * Pxz, Pyz, as doubles; `out` (nx*ny*11 doubles, host or device) is written
+ * on `stream` (synchronously when it is pageable host memory).
+ * BZ_ENONFINITE if any value is not finite (the values are still written). */
+bz_status bz_moments(bz_handle *h, double *out, void *stream);
+
+/* Wall shear on the lid (D of Sec. 5.2): out[ix] for ix < nx is the
+ * x-momentum flux 2 sum_j w_j v_x v_y h_face,j through lid face ix of the
+ * current state, with h_face the cell value for v_y > 0 and the diffusely
+ * emitted value for v_y < 0; out[nx] is their mean D.  out: nx+1 doubles,
+ * host or device. */
+bz_status bz_lid_shear(bz_handle *h, double *out, void *stream);
+
+/* Copy the state out of / into the handle (layout above; dtype of the
+ * handle).  dst/src: host or device, nx*ny*nv^3 elements.  get returns the
+ * step counter in *step (nullable); set overwrites it with `step`. */
+bz_status bz_get_state(bz_handle *h, void *dst, int64_t *step, void *stream);
+bz_status bz_set_state(bz_handle *h, const void *src, int64_t step, void *stream);
+
+/* Replace the lid motion (same meaning as bz_walls; profile host, copied).
+ * The deviation parameter eps is not changed. */
+bz_status bz_set_lid(bz_handle *h, double lid_u0, double lid_amp, double lid_period,
+                     const double *lid_profile);
+
+bz_status bz_get_info(const bz_handle *h, bz_info *out);
+
+/* Counters since creation: [0] steps, [1] samples with a node outside the
+ * velocity box, [2] samples within 1e-9 dv of a cell face, [3] correction
+ * solves that fell back from Cholesky to pivoted elimination, [4] kernel
+ * launches issued, [5..7] reserved (0).  Synchronises the device. */
+bz_status bz_stats(bz_handle *h, int64_t out[8]);
+
+/* The Monte Carlo sample set of step `step` (Sec. 4.2, Algorithm 2) as the
+ * device computes it: idx[4*l + q] = node of v, v1, v*, v1* (q = 0..3; -1
+ * outside the box) and W[l] = pi K dt |(v1 - v).k| / Nt (Eq. monteCarloInt
+ * times dt) in double.  Both outputs host or device (4*Nt int32, Nt double).
+ * For parity checks; the step path keeps its own copy in device scratch. */
+bz_status bz_sample_plan(bz_handle *h, int64_t step, int32_t *idx, double *W, void *stream);
+
+/* Device Philox4x32-10 (Salmon et al., SC'11) words for n counters
+ * (ctr: 4*n uint32, host or device) under key (k0, k1); out: 4*n uint32,
+ * host or device.  Synchronous.  For cross-checks of the generator. */
+bz_status bz_philox(uint32_t k0, uint32_t k1, const uint32_t *ctr, int64_t n, uint32_t *out);
+
+/* Per-kernel timing with CUDA events recorded on the launching stream around
+ * every kernel the handle launches while enabled (enable != 0); disabling
+ * keeps what was recorded.  bz_profile_read synchronises, returns per kernel
+ * class k (0 walls, 1 sampling, 2 per-cell step or collision, 3 streaming)
+ * the summed device time ms[k] and the launch count launches[k] since the
+ * last read, and clears the record.  No counterpart in the paper (its timings
+ * are host-side, Sec. 5.2); used by the benchmark. */
+bz_status bz_profile(bz_handle *h, int32_t enable);
+bz_status bz_profile_read(bz_handle *h, double ms[4], int64_t launches[4]);
+
+/* Thread-local text of the last failure on this thread ("" if none). */
+const char *bz_last_error(void);
+
+/* Library version string. */
+const char *bz_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BZ_H */

@@ -114,6 +114,7 @@ def lib():
                 "bzo_collide": (None, [_P, C.c_int64, C.c_void_p, _D, _D, _D, _D]),
                 "bzo_step": (None, [_P, C.c_int64, _D, _D, _D]),
                 "bzo_moments": (None, [_P, _D, _D]),
+                "bzo_step_cell": (None, [_P, C.c_int64, C.c_int32, _D, _D, _D, _D, _D, _D, _D]),
                 "bzo_lid_shear": (None, [_P, C.c_int64, _D, _D]),
                 "bzo_mc_dNdt": (None, [_P, C.c_int64, _D, _D, _D]),
                 "bzo_num_threads": (C.c_int32, []),
@@ -242,6 +243,21 @@ class Oracle:
         out = np.empty_like(h)
         mom = np.empty((self.nr, 11))
         self.L.bzo_step(C.byref(self.p), step, _dptr(h), _dptr(out), _dptr(mom))
+        return out, mom
+
+    def step_cell(self, c, own, left=None, right=None, below=None, above=None, step=0):
+        """One step of cell c from its own and neighbouring slabs (None at walls)."""
+        def arr(a):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            assert a.shape == (self.nvt,)
+            return a
+        sl = [arr(x) for x in (own, left, right, below, above)]
+        out = np.empty(self.nvt)
+        mom = np.empty(11)
+        self.L.bzo_step_cell(C.byref(self.p), step, c, *[(_dptr(a) if a is not None else None)
+                                                         for a in sl], _dptr(out), _dptr(mom))
         return out, mom
 
     def run(self, h, nsteps, step0=0):

@@ -242,24 +242,33 @@ static double wall_maxwellian(const double v[3], const double vw[3])
 
 /* n_w from zero net mass flux through the face; integrals become sums over the
  * velocity nodes with the same weights as everywhere else. */
+static double face_density(const bzo_problem *p, int64_t step, int32_t f, const double *hcell)
+{
+    int32_t nvt = p->nv * p->nv * p->nv;
+    double dv = bzo_dv(p), dV = dv * dv * dv;
+    int32_t cell;
+    double nrm[3], vw[3], v[3];
+    face_info(p, step, f, &cell, nrm, vw);
+    double out = 0.0, in = 0.0;
+    for (int32_t j = 0; j < nvt; ++j) {
+        node_velocity(p, j, v);
+        double vn = v[0] * nrm[0] + v[1] * nrm[1] + v[2] * nrm[2];
+        if (vn < 0.0)
+            out += -vn * bzo_weight(p, j) * (1.0 + p->eps * hcell[j]);
+        else if (vn > 0.0)
+            in += vn * dV * wall_maxwellian(v, vw);
+    }
+    return out / in;
+}
+
 void bzo_wall_density(const bzo_problem *p, int64_t step, const double *h, double *nw)
 {
     int32_t nf = bzo_num_faces(p), nvt = p->nv * p->nv * p->nv;
-    double dv = bzo_dv(p), dV = dv * dv * dv;
     for (int32_t f = 0; f < nf; ++f) {
         int32_t cell;
-        double nrm[3], vw[3], v[3];
+        double nrm[3], vw[3];
         face_info(p, step, f, &cell, nrm, vw);
-        double out = 0.0, in = 0.0;
-        for (int32_t j = 0; j < nvt; ++j) {
-            node_velocity(p, j, v);
-            double vn = v[0] * nrm[0] + v[1] * nrm[1] + v[2] * nrm[2];
-            if (vn < 0.0)
-                out += -vn * bzo_weight(p, j) * (1.0 + p->eps * h[(int64_t)cell * nvt + j]);
-            else if (vn > 0.0)
-                in += vn * dV * wall_maxwellian(v, vw);
-        }
-        nw[f] = out / in;
+        nw[f] = face_density(p, step, f, h + (int64_t)cell * nvt);
     }
 }
 
@@ -277,42 +286,55 @@ double bzo_ghost(const bzo_problem *p, int64_t step, int32_t f, double nw, int32
 /* Free streaming: first-order explicit upwind scheme (Eq. streaming2D) */
 /* ------------------------------------------------------------------ */
 
+/* Eq. streaming2D for every node of cell c.  nb[0] is the cell's own slab,
+ * nb[1..4] the left, right, lower and upper neighbours (NULL at a wall, where
+ * the diffusely emitted ghost value of that face is used). */
+static void stream_cell(const bzo_problem *p, int64_t step, int32_t c, const double *nb[5],
+                        const double *nw, double *out)
+{
+    int32_t nx = p->nx, ny = p->ny, n = p->nv;
+    int32_t ix = c % nx, iy = c / nx;
+    int64_t nvt = (int64_t)n * n * n;
+    double dt = bzo_dt(p), dx = bzo_dx(p), dy = bzo_dy(p);
+    for (int64_t j = 0; j < nvt; ++j) {
+        double v[3];
+        node_velocity(p, (int32_t)j, v);
+        double cux = v[0] * dt / dx, cuy = v[1] * dt / dy;
+        double h0 = nb[0][j];
+        double hx = h0, hy = h0;
+        if (v[0] > 0.0) {           /* upwind neighbour on the left */
+            hx = nb[1] ? nb[1][j] : bzo_ghost(p, step, iy, nw[iy], (int32_t)j);
+        } else if (v[0] < 0.0) {    /* upwind neighbour on the right */
+            hx = nb[2] ? nb[2][j] : bzo_ghost(p, step, ny + iy, nw[ny + iy], (int32_t)j);
+        }
+        if (v[1] > 0.0) {           /* upwind neighbour below */
+            hy = nb[3] ? nb[3][j] : bzo_ghost(p, step, 2 * ny + ix, nw[2 * ny + ix], (int32_t)j);
+        } else if (v[1] < 0.0) {    /* upwind neighbour above (lid) */
+            hy = nb[4] ? nb[4][j]
+                       : bzo_ghost(p, step, 2 * ny + nx + ix, nw[2 * ny + nx + ix], (int32_t)j);
+        }
+        double ax = fabs(cux), ay = fabs(cuy);
+        out[j] = (1.0 - ax - ay) * h0 + ax * hx + ay * hy;
+    }
+}
+
 void bzo_stream(const bzo_problem *p, int64_t step, const double *h, double *ht)
 {
     int32_t nx = p->nx, ny = p->ny, n = p->nv;
     int64_t nvt = (int64_t)n * n * n;
-    double dt = bzo_dt(p), dx = bzo_dx(p), dy = bzo_dy(p);
     int32_t nf = bzo_num_faces(p);
     double *nw = (double *)malloc(sizeof(double) * nf);
     bzo_wall_density(p, step, h, nw);
 
 #pragma omp parallel for schedule(static)
     for (int32_t c = 0; c < nx * ny; ++c) {
-        int32_t ix = c % nx, iy = c / nx;
-        for (int64_t j = 0; j < nvt; ++j) {
-            double v[3];
-            node_velocity(p, (int32_t)j, v);
-            double cux = v[0] * dt / dx, cuy = v[1] * dt / dy;
-            double h0 = h[(int64_t)c * nvt + j];
-            double hx = h0, hy = h0;
-            if (v[0] > 0.0) {           /* upwind neighbour on the left */
-                hx = ix > 0 ? h[(int64_t)(c - 1) * nvt + j]
-                            : bzo_ghost(p, step, iy, nw[iy], (int32_t)j);
-            } else if (v[0] < 0.0) {    /* upwind neighbour on the right */
-                hx = ix < nx - 1 ? h[(int64_t)(c + 1) * nvt + j]
-                                 : bzo_ghost(p, step, ny + iy, nw[ny + iy], (int32_t)j);
-            }
-            if (v[1] > 0.0) {           /* upwind neighbour below */
-                hy = iy > 0 ? h[(int64_t)(c - nx) * nvt + j]
-                            : bzo_ghost(p, step, 2 * ny + ix, nw[2 * ny + ix], (int32_t)j);
-            } else if (v[1] < 0.0) {    /* upwind neighbour above (lid) */
-                hy = iy < ny - 1 ? h[(int64_t)(c + nx) * nvt + j]
-                                 : bzo_ghost(p, step, 2 * ny + nx + ix,
-                                             nw[2 * ny + nx + ix], (int32_t)j);
-            }
-            double ax = fabs(cux), ay = fabs(cuy);
-            ht[(int64_t)c * nvt + j] = (1.0 - ax - ay) * h0 + ax * hx + ay * hy;
-        }
+        const double *nb[5];
+        nb[0] = h + (int64_t)c * nvt;
+        nb[1] = c % nx > 0 ? h + (int64_t)(c - 1) * nvt : NULL;
+        nb[2] = c % nx < nx - 1 ? h + (int64_t)(c + 1) * nvt : NULL;
+        nb[3] = c / nx > 0 ? h + (int64_t)(c - nx) * nvt : NULL;
+        nb[4] = c / nx < ny - 1 ? h + (int64_t)(c + nx) * nvt : NULL;
+        stream_cell(p, step, c, nb, nw, ht + (int64_t)c * nvt);
     }
     free(nw);
 }
@@ -416,12 +438,64 @@ void bzo_moments(const bzo_problem *p, const double *h, double *mom)
     free(vel);
 }
 
+/* Relaxation of one cell (Eqs. monteCarloInt, collision_step, rinorm_a,
+ * correzione) from h (= h~) into o, with scratch dN, hc of nv^3 doubles. */
+static void collide_cell(const bzo_problem *p, const bzo_sample_t *smp, const double *w,
+                         const double *vel, const double *h, double *o, double *stage,
+                         double *dN, double *hc)
+{
+    int64_t nvt = (int64_t)p->nv * p->nv * p->nv;
+    double eps = p->eps;
+    /* Moments of h~ to be preserved (Eq. correzione, right side). */
+    double pre[5] = {0, 0, 0, 0, 0}, phi[5];
+    for (int64_t j = 0; j < nvt; ++j) {
+        invariants(vel + 3 * j, phi);
+        for (int a = 0; a < 5; ++a) pre[a] += w[j] * h[j] * phi[a];
+    }
+    /* Eq. monteCarloInt evaluated on h~ (Eq. collision_step). */
+    memset(dN, 0, sizeof(double) * nvt);
+    for (int64_t l = 0; l < p->nt; ++l) {
+        const bzo_sample_t *q = smp + l;
+        double ha = q->idx[0] >= 0 ? h[q->idx[0]] : 0.0;
+        double hb = q->idx[1] >= 0 ? h[q->idx[1]] : 0.0;
+        double g = ha + hb + eps * ha * hb;
+        double r = q->W * g;
+        if (q->idx[2] >= 0) dN[q->idx[2]] += r;
+        if (q->idx[3] >= 0) dN[q->idx[3]] += r;
+        if (q->idx[0] >= 0) dN[q->idx[0]] -= r;
+        if (q->idx[1] >= 0) dN[q->idx[1]] -= r;
+    }
+    for (int64_t j = 0; j < nvt; ++j) hc[j] = h[j] + dN[j] / w[j];
+    if (stage) memcpy(stage, hc, sizeof(double) * nvt);
+
+    /* Correction of the full distribution (Eqs. rinorm_a, correzione):
+     * Phi0 (1 + eps h^{n+1}) = Phi0 (1 + eps h_c) (1 + eps mu.psi), so
+     * sum_b [sum_j w (1 + eps h_c) psi_a psi_b] mu_b = -(post_a - pre_a). */
+    double G[5][5] = {{0}}, R[5] = {0, 0, 0, 0, 0}, mu[5];
+    for (int64_t j = 0; j < nvt; ++j) {
+        invariants(vel + 3 * j, phi);
+        double f = w[j] * (1.0 + eps * hc[j]);
+        for (int a = 0; a < 5; ++a) {
+            R[a] += w[j] * hc[j] * phi[a];
+            for (int b = 0; b < 5; ++b) G[a][b] += f * phi[a] * phi[b];
+        }
+    }
+    double rhs[5];
+    for (int a = 0; a < 5; ++a) rhs[a] = -(R[a] - pre[a]);
+    if (solve5(G, rhs, mu) != 0) mu[0] = mu[1] = mu[2] = mu[3] = mu[4] = 0.0;
+    for (int64_t j = 0; j < nvt; ++j) {
+        invariants(vel + 3 * j, phi);
+        double corr = mu[0] * phi[0] + mu[1] * phi[1] + mu[2] * phi[2] +
+                      mu[3] * phi[3] + mu[4] * phi[4];
+        o[j] = hc[j] + (1.0 + eps * hc[j]) * corr;
+    }
+}
+
 void bzo_collide(const bzo_problem *p, int64_t step, const bzo_sample_t *samples,
                  const double *ht, double *hout, double *mom, double *stage)
 {
     int32_t nr = p->nx * p->ny;
     int64_t nvt = (int64_t)p->nv * p->nv * p->nv;
-    double eps = p->eps;
     double *w, *vel;
     tables(p, &w, &vel);
 
@@ -440,57 +514,14 @@ void bzo_collide(const bzo_problem *p, int64_t step, const bzo_sample_t *samples
         if (!samples) own = (bzo_sample_t *)malloc(sizeof(bzo_sample_t) * p->nt);
 #pragma omp for schedule(static)
         for (int32_t c = 0; c < nr; ++c) {
-            const double *h = ht + (int64_t)c * nvt;
             const bzo_sample_t *smp = samples;
             if (!smp) {
                 bzo_sample_all(p, step, (uint32_t)c, own);
                 smp = own;
             }
-            /* Moments of h~ to be preserved (Eq. correzione, right side). */
-            double pre[5] = {0, 0, 0, 0, 0}, phi[5];
-            for (int64_t j = 0; j < nvt; ++j) {
-                invariants(vel + 3 * j, phi);
-                for (int a = 0; a < 5; ++a) pre[a] += w[j] * h[j] * phi[a];
-            }
-            /* Eq. monteCarloInt evaluated on h~ (Eq. collision_step). */
-            memset(dN, 0, sizeof(double) * nvt);
-            for (int64_t l = 0; l < p->nt; ++l) {
-                const bzo_sample_t *q = smp + l;
-                double ha = q->idx[0] >= 0 ? h[q->idx[0]] : 0.0;
-                double hb = q->idx[1] >= 0 ? h[q->idx[1]] : 0.0;
-                double g = ha + hb + eps * ha * hb;
-                double r = q->W * g;
-                if (q->idx[2] >= 0) dN[q->idx[2]] += r;
-                if (q->idx[3] >= 0) dN[q->idx[3]] += r;
-                if (q->idx[0] >= 0) dN[q->idx[0]] -= r;
-                if (q->idx[1] >= 0) dN[q->idx[1]] -= r;
-            }
-            for (int64_t j = 0; j < nvt; ++j) hc[j] = h[j] + dN[j] / w[j];
-            if (stage) memcpy(stage + (int64_t)c * nvt, hc, sizeof(double) * nvt);
-
-            /* Correction of the full distribution (Eqs. rinorm_a, correzione):
-             * Phi0 (1 + eps h^{n+1}) = Phi0 (1 + eps h_c) (1 + eps mu.psi), so
-             * sum_b [sum_j w (1 + eps h_c) psi_a psi_b] mu_b = -(post_a - pre_a). */
-            double G[5][5] = {{0}}, R[5] = {0, 0, 0, 0, 0}, mu[5];
-            for (int64_t j = 0; j < nvt; ++j) {
-                invariants(vel + 3 * j, phi);
-                double f = w[j] * (1.0 + eps * hc[j]);
-                for (int a = 0; a < 5; ++a) {
-                    R[a] += w[j] * hc[j] * phi[a];
-                    for (int b = 0; b < 5; ++b) G[a][b] += f * phi[a] * phi[b];
-                }
-            }
-            double rhs[5];
-            for (int a = 0; a < 5; ++a) rhs[a] = -(R[a] - pre[a]);
-            if (solve5(G, rhs, mu) != 0) mu[0] = mu[1] = mu[2] = mu[3] = mu[4] = 0.0;
-            double *o = hout + (int64_t)c * nvt;
-            for (int64_t j = 0; j < nvt; ++j) {
-                invariants(vel + 3 * j, phi);
-                double corr = mu[0] * phi[0] + mu[1] * phi[1] + mu[2] * phi[2] +
-                              mu[3] * phi[3] + mu[4] * phi[4];
-                o[j] = hc[j] + (1.0 + eps * hc[j]) * corr;
-            }
-            if (mom) cell_moments(p, o, w, vel, mom + 11 * (int64_t)c);
+            collide_cell(p, smp, w, vel, ht + (int64_t)c * nvt, hout + (int64_t)c * nvt,
+                         stage ? stage + (int64_t)c * nvt : NULL, dN, hc);
+            if (mom) cell_moments(p, hout + (int64_t)c * nvt, w, vel, mom + 11 * (int64_t)c);
         }
         free(dN);
         free(hc);
@@ -510,6 +541,37 @@ void bzo_step(const bzo_problem *p, int64_t step, const double *h, double *hnext
     bzo_stream(p, step, h, ht);
     bzo_collide(p, step, NULL, ht, hnext, mom, NULL);
     free(ht);
+}
+
+/* One full step of a single cell from its own slab and its four neighbours
+ * (NULL where the cell touches a wall): the wall densities of its own
+ * boundary faces, Eq. streaming2D, and the relaxation with the step's sample
+ * set.  Gives the same values as bzo_step for that cell. */
+void bzo_step_cell(const bzo_problem *p, int64_t step, int32_t c, const double *own,
+                   const double *left, const double *right, const double *below,
+                   const double *above, double *out, double *mom)
+{
+    int32_t nx = p->nx, ny = p->ny, nf = bzo_num_faces(p);
+    int64_t nvt = (int64_t)p->nv * p->nv * p->nv;
+    int32_t ix = c % nx, iy = c / nx;
+    double *nw = (double *)calloc((size_t)nf, sizeof(double));
+    if (ix == 0) nw[iy] = face_density(p, step, iy, own);
+    if (ix == nx - 1) nw[ny + iy] = face_density(p, step, ny + iy, own);
+    if (iy == 0) nw[2 * ny + ix] = face_density(p, step, 2 * ny + ix, own);
+    if (iy == ny - 1) nw[2 * ny + nx + ix] = face_density(p, step, 2 * ny + nx + ix, own);
+    const double *nb[5] = {own, ix > 0 ? left : NULL, ix < nx - 1 ? right : NULL,
+                           iy > 0 ? below : NULL, iy < ny - 1 ? above : NULL};
+    double *ht = (double *)malloc(sizeof(double) * nvt);
+    stream_cell(p, step, c, nb, nw, ht);
+    double *w, *vel;
+    tables(p, &w, &vel);
+    bzo_sample_t *smp = (bzo_sample_t *)malloc(sizeof(bzo_sample_t) * p->nt);
+    bzo_sample_all(p, step, p->per_cell ? (uint32_t)c : 0xFFFFFFFFu, smp);
+    double *dN = (double *)malloc(sizeof(double) * nvt);
+    double *hc = (double *)malloc(sizeof(double) * nvt);
+    collide_cell(p, smp, w, vel, ht, out, NULL, dN, hc);
+    if (mom) cell_moments(p, out, w, vel, mom);
+    free(nw); free(ht); free(w); free(vel); free(smp); free(dN); free(hc);
 }
 
 /* Wall shear on the lid (D of Sec. 5.2): x-momentum flux through each lid

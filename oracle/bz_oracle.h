@@ -96,6 +96,13 @@ void bzo_collide(const bzo_problem *p, int64_t step, const bzo_sample_t *samples
 void bzo_step(const bzo_problem *p, int64_t step, const double *h, double *hnext,
               double *mom);
 
+/* One full step of the single cell c (same values as bzo_step for it) from
+ * its own slab and its left/right/lower/upper neighbours (NULL at walls).
+ * out: nv^3 values; mom (nullable): 11 moments. */
+void bzo_step_cell(const bzo_problem *p, int64_t step, int32_t c, const double *own,
+                   const double *left, const double *right, const double *below,
+                   const double *above, double *out, double *mom);
+
 /* Macroscopic quantities of every cell (Eqs. densita..sforzi, V0 units):
  * [rho, ux, uy, uz, theta, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz]. */
 void bzo_moments(const bzo_problem *p, const double *h, double *mom);

@@ -1,0 +1,665 @@
+// bz_api.cu -- host side of the C ABI declared in include/bz.h.
+//
+// Owns device memory, derives the discretisation of the paper's problem
+// statement (Sec. 3, Sec. 5.1), and sequences the kernels of one time step on
+// the caller's stream.  No host computation is on the step path: the host only
+// validates arguments, builds per-axis tables once at creation and launches.
+#include "bz.h"
+#include "bz_kernels.cuh"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using bzk::Geo;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+bz_status fail(bz_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+#define BZ_CUDA(call)                                                                  \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(e_ == cudaErrorMemoryAllocation ? BZ_ENOMEM : BZ_ECUDA,        \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));               \
+    } while (0)
+
+#define BZ_LAUNCHED(hd)                                                                \
+    do {                                                                               \
+        cudaError_t e_ = cudaGetLastError();                                           \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(BZ_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e_)); \
+        (hd)->launches++;                                                              \
+    } while (0)
+
+bool fault_injected(const char *what)
+{
+    const char *f = getenv("BZ_FAULT");
+    return f && strcmp(f, what) == 0;
+}
+
+}  // namespace
+
+struct bz_handle {
+    Geo g{};
+    int dtype = BZ_F32;
+    size_t esz = 4;
+    void *h[2] = {nullptr, nullptr};
+    int cur = 0;
+    int64_t step = 0;
+    void *ht = nullptr;                 // h~ for the unfused path (lazy)
+    void *pidx = nullptr;               // sample plan: node indices (16- or 32-bit)
+    bool idx16 = true;
+    void *pW = nullptr;                 // sample plan: weights (state type)
+    void *ghost = nullptr;              // emitted ghost values per face
+    double *nw = nullptr;               // wall densities per face
+    double *shear = nullptr;            // lid face shear (nx)
+    double *mom = nullptr;              // nr * 11
+    bool mom_valid = false;
+    void *gw_global = nullptr;          // per-CTA product scratch when it does not fit smem
+    int gw_in_smem = 1;
+    unsigned long long *stats = nullptr;
+    int *flag = nullptr;
+    double *axv = nullptr, *axA = nullptr, *profile = nullptr;
+    std::vector<double> host_profile;
+    int dev = 0, nsm = 0, smem_optin = 0;
+    int threads = 0, grid_cell = 0, grid_cell_fused = 0;
+    size_t smem_cell = 0;
+    long long launches = 0;
+    bool prof = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
+};
+
+namespace {
+
+template <typename T>
+bz_status dalloc(T **p, size_t bytes)
+{
+    if (fault_injected("alloc"))
+        return fail(BZ_ENOMEM, "device allocation of %zu bytes failed (BZ_FAULT=alloc)", bytes);
+    cudaError_t e = cudaMalloc((void **)p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? BZ_ENOMEM : BZ_ECUDA,
+                    "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    return BZ_OK;
+}
+
+#define BZ_TRY(x)                          \
+    do {                                   \
+        bz_status s_ = (x);                \
+        if (s_ != BZ_OK) return s_;        \
+    } while (0)
+
+double lid_eps(double u0, double amp, const double *profile, int nx)
+{
+    double m = std::fabs(u0);
+    if (profile) {
+        m = 0.0;
+        for (int i = 0; i < nx; ++i) m = std::max(m, std::fabs(profile[i]));
+    }
+    m += std::fabs(amp);
+    return m > 0.0 ? m : 1.0;
+}
+
+// Event pair around one launch of kernel class k when profiling is enabled.
+struct ProfScope {
+    bz_handle *H;
+    int k;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    ProfScope(bz_handle *H_, int k_, cudaStream_t s_) : H(H_), k(k_), s(s_)
+    {
+        if (H->prof && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+            cudaEventRecord(a, s);
+    }
+    ~ProfScope()
+    {
+        if (a && b) {
+            cudaEventRecord(b, s);
+            H->ev[k].push_back({a, b});
+        }
+    }
+};
+
+template <typename R, typename I>
+bz_status launch_step(bz_handle *H, cudaStream_t s, bool fused, bool do_stream, bool do_collide)
+{
+    using V4 = typename bzk::Idx4<I>::type;
+    Geo &g = H->g;
+    R *hin = (R *)H->h[H->cur];
+    R *hout = (R *)H->h[H->cur ^ 1];
+    if (do_stream || fused) {
+        ProfScope ps(H, 0, s);
+        bzk::k_walls<R><<<g.nfaces, 256, 0, s>>>(g, H->step, hin, (R *)H->ghost, H->nw, nullptr);
+        BZ_LAUNCHED(H);
+    }
+    if (do_collide || fused) {
+        ProfScope ps(H, 1, s);
+        int pb = 256, pg = (g.nt + pb - 1) / pb;
+        bzk::k_plan<R, I><<<pg, pb, 0, s>>>(g, H->step, (V4 *)H->pidx, (R *)H->pW, nullptr, H->stats);
+        BZ_LAUNCHED(H);
+    }
+    if (fused) {
+        ProfScope ps(H, 2, s);
+        bzk::k_cell<R, true, I><<<H->grid_cell_fused, H->threads, H->smem_cell, s>>>(
+            g, H->step, hin, (const R *)H->ghost, (const V4 *)H->pidx, (const R *)H->pW,
+            (R *)H->gw_global, hout, H->mom, H->stats, H->gw_in_smem);
+        BZ_LAUNCHED(H);
+        H->cur ^= 1;
+        H->mom_valid = true;
+        return BZ_OK;
+    }
+    if (do_stream) {
+        R *dst = do_collide ? (R *)H->ht : hout;
+        int grid = std::min(g.nr, H->nsm * 16);
+        {
+            ProfScope ps(H, 3, s);
+            bzk::k_stream<R><<<grid, 256, 0, s>>>(g, hin, (const R *)H->ghost, dst);
+            BZ_LAUNCHED(H);
+        }
+        if (!do_collide) {
+            H->cur ^= 1;
+            H->mom_valid = false;
+            return BZ_OK;
+        }
+        hin = dst;
+    }
+    if (do_collide) {
+        ProfScope ps(H, 2, s);
+        bzk::k_cell<R, false, I><<<H->grid_cell, H->threads, H->smem_cell, s>>>(
+            g, H->step, hin, (const R *)H->ghost, (const V4 *)H->pidx, (const R *)H->pW,
+            (R *)H->gw_global, hout, H->mom, H->stats, H->gw_in_smem);
+        BZ_LAUNCHED(H);
+        H->cur ^= 1;
+        H->mom_valid = true;
+    }
+    return BZ_OK;
+}
+
+template <typename R, typename I>
+bz_status configure_kernels(bz_handle *H, int *occ_f, int *occ_c)
+{
+    BZ_CUDA(cudaFuncSetAttribute(bzk::k_cell<R, true, I>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)H->smem_cell));
+    BZ_CUDA(cudaFuncSetAttribute(bzk::k_cell<R, false, I>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)H->smem_cell));
+    BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_f, bzk::k_cell<R, true, I>,
+                                                          H->threads, H->smem_cell));
+    BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_c, bzk::k_cell<R, false, I>,
+                                                          H->threads, H->smem_cell));
+    return BZ_OK;
+}
+
+template <typename R>
+bz_status configure_cell_kernel(bz_handle *H)
+{
+    Geo &g = H->g;
+    int n2 = g.nv * g.nv;
+    H->threads = std::min(bzk::kMaxThreads, (n2 + 31) / 32 * 32);
+    size_t with_gw = bzk::cell_smem_bytes<R>(g.nv, g.nvt, g.nt, true);
+    size_t without = bzk::cell_smem_bytes<R>(g.nv, g.nvt, g.nt, false);
+    if (without > (size_t)H->smem_optin)
+        return fail(BZ_EUNSUPPORTED,
+                    "velocity slab of %d nodes needs %zu bytes of shared memory; the device "
+                    "offers %d per block", g.nvt, without, H->smem_optin);
+    H->gw_in_smem = with_gw <= (size_t)H->smem_optin;
+    H->smem_cell = H->gw_in_smem ? with_gw : without;
+    int occ_f = 0, occ_c = 0;
+    if (H->idx16) {
+        BZ_TRY((configure_kernels<R, uint16_t>(H, &occ_f, &occ_c)));
+    } else {
+        BZ_TRY((configure_kernels<R, int>(H, &occ_f, &occ_c)));
+    }
+    if (occ_f < 1 || occ_c < 1)
+        return fail(BZ_EUNSUPPORTED, "cell kernel cannot be resident (%d threads, %zu bytes)",
+                    H->threads, H->smem_cell);
+    H->grid_cell_fused = std::min(g.nr, H->nsm * occ_f);
+    H->grid_cell = std::min(g.nr, H->nsm * occ_c);
+    if (!H->gw_in_smem) {
+        int grid = std::max(H->grid_cell, H->grid_cell_fused);
+        BZ_TRY(dalloc(&H->gw_global, sizeof(R) * (size_t)g.nt * grid));
+    }
+    return BZ_OK;
+}
+
+void clear_events(bz_handle *H)
+{
+    for (auto &v : H->ev) {
+        for (auto &p : v) {
+            cudaEventDestroy(p.first);
+            cudaEventDestroy(p.second);
+        }
+        v.clear();
+    }
+}
+
+void release(bz_handle *H)
+{
+    clear_events(H);
+    void *ptrs[] = {H->h[0], H->h[1], H->ht, H->pidx, H->pW, H->ghost, H->nw, H->shear,
+                    H->mom, H->gw_global, H->stats, H->flag, H->axv, H->axA, H->profile};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *bz_last_error(void) { return g_last_error.c_str(); }
+
+const char *bz_version(void) { return "bz 0.1 (sm_103a)"; }
+
+bz_status bz_create(const bz_space *space, const bz_vel *vel, const bz_walls *walls,
+                    const bz_params *params, bz_handle **out)
+{
+    g_last_error.clear();
+    if (!out) return fail(BZ_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!space || !vel || !walls || !params) return fail(BZ_EINVAL, "NULL argument");
+    if (space->nx < 1 || space->ny < 1) return fail(BZ_EINVAL, "nx, ny must be >= 1");
+    if ((int64_t)space->nx * space->ny > (1 << 30)) return fail(BZ_EINVAL, "too many cells");
+    if (!(space->kn > 0.0) || !std::isfinite(space->kn)) return fail(BZ_EINVAL, "kn must be > 0");
+    if (vel->nv < 2 || vel->nv > bzk::kMaxN)
+        return fail(BZ_EINVAL, "nv must be in [2, %d]", bzk::kMaxN);
+    if (!(vel->vmax > 0.0) || !std::isfinite(vel->vmax)) return fail(BZ_EINVAL, "vmax must be > 0");
+    if (params->n_pairs < 1 || params->n_pairs > 0x7FFFFFFF)
+        return fail(BZ_EINVAL, "n_pairs must be in [1, 2^31-1]");
+    if (params->dtype != BZ_F32 && params->dtype != BZ_F64)
+        return fail(BZ_EINVAL, "dtype must be BZ_F32 or BZ_F64");
+    if (params->sample_mode != BZ_SHARED && params->sample_mode != BZ_PER_CELL)
+        return fail(BZ_EINVAL, "unknown sample_mode");
+    if (params->sample_mode == BZ_PER_CELL)
+        return fail(BZ_EUNSUPPORTED, "per-cell sample sets are not implemented");
+    if (!(params->cfl >= 0.0 && params->cfl <= 1.0)) return fail(BZ_EINVAL, "cfl must be in [0, 1]");
+    if (!(params->eps >= 0.0) || !std::isfinite(params->eps)) return fail(BZ_EINVAL, "eps must be >= 0");
+    if (!(params->kcoll >= 0.0) || !std::isfinite(params->kcoll))
+        return fail(BZ_EINVAL, "kcoll must be >= 0");
+    if (!std::isfinite(walls->lid_u0) || !std::isfinite(walls->lid_amp) ||
+        !(walls->lid_period >= 0.0) || !std::isfinite(walls->lid_period))
+        return fail(BZ_EINVAL, "invalid lid motion");
+    if (walls->lid_profile)
+        for (int i = 0; i < space->nx; ++i)
+            if (!std::isfinite(walls->lid_profile[i])) return fail(BZ_EINVAL, "lid_profile[%d]", i);
+    if (fault_injected("alloc"))
+        return fail(BZ_ENOMEM, "device allocation failed (BZ_FAULT=alloc)");
+
+    bz_handle *H = new bz_handle();
+    auto bail = [&](bz_status st) {
+        release(H);
+        delete H;
+        return st;
+    };
+    Geo &g = H->g;
+    const int N = vel->nv;
+    g.nx = space->nx;
+    g.ny = space->ny;
+    g.nv = N;
+    g.nvt = N * N * N;
+    g.nr = g.nx * g.ny;
+    g.nfaces = 2 * g.nx + 2 * g.ny;
+    g.nt = (int)params->n_pairs;
+    g.vmax = vel->vmax;
+    g.dv = (2.0 * vel->vmax) / (double)N;
+    g.dx = (1.0 / space->kn) / (double)g.nx;
+    g.dy = (1.0 / space->kn) / (double)g.ny;
+    const double cfl = params->cfl > 0.0 ? params->cfl : 0.5;
+    const double vtop = -g.vmax + ((double)(N - 1) + 0.5) * g.dv;
+    g.dt = cfl * std::min(g.dx, g.dy) / vtop;
+    const double kcoll =
+        params->kcoll > 0.0 ? params->kcoll : 5.0 * 1.016034 / 16.0 * std::sqrt(2.0 / M_PI);
+    g.cw = M_PI * kcoll * g.dt / (double)g.nt;
+    g.eps = params->eps > 0.0 ? params->eps
+                              : lid_eps(walls->lid_u0, walls->lid_amp, walls->lid_profile, g.nx);
+    g.seed = params->seed;
+    g.instance = params->instance;
+    g.lid_u0 = walls->lid_u0;
+    g.lid_amp = walls->lid_amp;
+    g.lid_period = walls->lid_period;
+    H->dtype = params->dtype;
+    H->esz = params->dtype == BZ_F64 ? 8 : 4;
+
+    // Per-axis tables (host, FP64) and the constants of the wall fluxes.
+    std::vector<double> axv(N), axA(N);
+    for (int j = 0; j < N; ++j) {
+        axv[j] = -g.vmax + ((double)j + 0.5) * g.dv;
+        axA[j] = g.dv * (1.0 / std::sqrt(M_PI)) * std::exp(-axv[j] * axv[j]);
+    }
+    double hn = 0.0, zsum = 0.0;
+    for (int j = 0; j < N; ++j) {
+        zsum += axA[j];
+        if (axv[j] > 0.0) hn += axv[j] * axA[j];
+    }
+    g.hn = hn;
+    g.zsum = zsum;
+    g.cout = hn * zsum * zsum;
+    // Gram matrix of the equilibrium, sum_j w_j psi_a psi_b.
+    for (int a = 0; a < 25; ++a) g.G0[a] = 0.0;
+    for (int jx = 0; jx < N; ++jx)
+        for (int jy = 0; jy < N; ++jy)
+            for (int jz = 0; jz < N; ++jz) {
+                double w = axA[jx] * axA[jy] * axA[jz];
+                double p[5] = {1.0, axv[jx], axv[jy], axv[jz],
+                               axv[jx] * axv[jx] + axv[jy] * axv[jy] + axv[jz] * axv[jz]};
+                for (int a = 0; a < 5; ++a)
+                    for (int b = 0; b < 5; ++b) g.G0[a * 5 + b] += w * p[a] * p[b];
+            }
+
+    cudaError_t e = cudaGetDevice(&H->dev);
+    if (e != cudaSuccess) {
+        fail(BZ_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+        return bail(BZ_ECUDA);
+    }
+    cudaDeviceGetAttribute(&H->nsm, cudaDevAttrMultiProcessorCount, H->dev);
+    cudaDeviceGetAttribute(&H->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, H->dev);
+
+    bz_status st = BZ_OK;
+    const size_t nodes = (size_t)g.nr * g.nvt;
+#define BZ_STEP(x)                   \
+    do {                             \
+        st = (x);                    \
+        if (st != BZ_OK) return bail(st); \
+    } while (0)
+    BZ_STEP(dalloc(&H->h[0], nodes * H->esz));
+    BZ_STEP(dalloc(&H->h[1], nodes * H->esz));
+    H->idx16 = g.nvt < 65535;
+    BZ_STEP(dalloc(&H->pidx, (H->idx16 ? sizeof(ushort4) : sizeof(int4)) * (size_t)g.nt));
+    BZ_STEP(dalloc(&H->pW, H->esz * (size_t)g.nt));
+    BZ_STEP(dalloc(&H->ghost, H->esz * (size_t)g.nfaces * N));
+    BZ_STEP(dalloc(&H->nw, sizeof(double) * g.nfaces));
+    BZ_STEP(dalloc(&H->shear, sizeof(double) * (g.nx + 1)));
+    BZ_STEP(dalloc(&H->mom, sizeof(double) * 11 * (size_t)g.nr));
+    BZ_STEP(dalloc(&H->stats, sizeof(unsigned long long) * 8));
+    BZ_STEP(dalloc(&H->flag, sizeof(int)));
+    BZ_STEP(dalloc(&H->axv, sizeof(double) * N));
+    BZ_STEP(dalloc(&H->axA, sizeof(double) * N));
+    BZ_STEP(dalloc(&H->profile, sizeof(double) * g.nx));
+    if (H->dtype == BZ_F64)
+        BZ_STEP(configure_cell_kernel<double>(H));
+    else
+        BZ_STEP(configure_cell_kernel<float>(H));
+#undef BZ_STEP
+    e = cudaMemcpy(H->axv, axv.data(), sizeof(double) * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(H->axA, axA.data(), sizeof(double) * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && walls->lid_profile) {
+        H->host_profile.assign(walls->lid_profile, walls->lid_profile + g.nx);
+        e = cudaMemcpy(H->profile, walls->lid_profile, sizeof(double) * g.nx, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemset(H->h[0], 0, nodes * H->esz);
+    if (e == cudaSuccess) e = cudaMemset(H->h[1], 0, nodes * H->esz);
+    if (e == cudaSuccess) e = cudaMemset(H->stats, 0, sizeof(unsigned long long) * 8);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        fail(BZ_ECUDA, "initialisation failed: %s", cudaGetErrorString(e));
+        return bail(BZ_ECUDA);
+    }
+    g.axv = H->axv;
+    g.axA = H->axA;
+    g.lid_profile = walls->lid_profile ? H->profile : nullptr;
+    *out = H;
+    return BZ_OK;
+}
+
+bz_status bz_destroy(bz_handle *H)
+{
+    if (!H) return BZ_OK;
+    cudaDeviceSynchronize();
+    release(H);
+    delete H;
+    return BZ_OK;
+}
+
+bz_status bz_step_ex(bz_handle *H, int32_t nsteps, uint32_t flags, void *stream)
+{
+    if (!H) return fail(BZ_EINVAL, "handle is NULL");
+    if (nsteps < 0) return fail(BZ_EINVAL, "nsteps must be >= 0");
+    if (flags & ~(uint32_t)(BZ_DO_STREAM | BZ_DO_COLLIDE | BZ_SPLIT))
+        return fail(BZ_EINVAL, "unknown flags 0x%x", flags);
+    if (fault_injected("launch")) return fail(BZ_ECUDA, "kernel launch failed (BZ_FAULT=launch)");
+    cudaStream_t s = (cudaStream_t)stream;
+    bool fused = flags == 0;
+    bool ds = (flags & BZ_DO_STREAM) || (flags & BZ_SPLIT);
+    bool dc = (flags & BZ_DO_COLLIDE) || (flags & BZ_SPLIT);
+    if (ds && dc && !H->ht) BZ_TRY(dalloc(&H->ht, H->esz * (size_t)H->g.nr * H->g.nvt));
+    for (int32_t n = 0; n < nsteps; ++n) {
+        bz_status st;
+        if (H->dtype == BZ_F64)
+            st = H->idx16 ? launch_step<double, uint16_t>(H, s, fused, ds, dc)
+                          : launch_step<double, int>(H, s, fused, ds, dc);
+        else
+            st = H->idx16 ? launch_step<float, uint16_t>(H, s, fused, ds, dc)
+                          : launch_step<float, int>(H, s, fused, ds, dc);
+        if (st != BZ_OK) return st;
+        if (fused || dc) H->step++;
+    }
+    return BZ_OK;
+}
+
+bz_status bz_step(bz_handle *H, int32_t nsteps, void *stream)
+{
+    return bz_step_ex(H, nsteps, 0u, stream);
+}
+
+bz_status bz_moments(bz_handle *H, double *out, void *stream)
+{
+    if (!H || !out) return fail(BZ_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Geo &g = H->g;
+    if (!H->mom_valid) {
+        int grid = std::min(g.nr, H->nsm * 8);
+        if (H->dtype == BZ_F64)
+            bzk::k_moments<double><<<grid, 256, 0, s>>>(g, (const double *)H->h[H->cur], H->mom);
+        else
+            bzk::k_moments<float><<<grid, 256, 0, s>>>(g, (const float *)H->h[H->cur], H->mom);
+        BZ_LAUNCHED(H);
+        H->mom_valid = true;
+    }
+    size_t n = (size_t)g.nr * 11;
+    BZ_CUDA(cudaMemsetAsync(H->flag, 0, sizeof(int), s));
+    bzk::k_nonfinite<<<std::max(1, std::min(H->nsm, (int)((n + 255) / 256))), 256, 0, s>>>(
+        H->mom, (int64_t)n, H->flag);
+    BZ_LAUNCHED(H);
+    BZ_CUDA(cudaMemcpyAsync(out, H->mom, sizeof(double) * n, cudaMemcpyDefault, s));
+    int flag = 0;
+    BZ_CUDA(cudaMemcpyAsync(&flag, H->flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BZ_CUDA(cudaStreamSynchronize(s));
+    if (flag) return fail(BZ_ENONFINITE, "non-finite macroscopic quantity");
+    return BZ_OK;
+}
+
+bz_status bz_lid_shear(bz_handle *H, double *out, void *stream)
+{
+    if (!H || !out) return fail(BZ_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Geo &g = H->g;
+    if (H->dtype == BZ_F64)
+        bzk::k_walls<double><<<g.nfaces, 256, 0, s>>>(g, H->step, (const double *)H->h[H->cur],
+                                                      (double *)H->ghost, H->nw, H->shear);
+    else
+        bzk::k_walls<float><<<g.nfaces, 256, 0, s>>>(g, H->step, (const float *)H->h[H->cur],
+                                                     (float *)H->ghost, H->nw, H->shear);
+    BZ_LAUNCHED(H);
+    double *tmp = H->mom;  // reuse: nr*11 >= nx+1 always (ny >= 1)
+    if ((size_t)g.nr * 11 < (size_t)g.nx + 1) return fail(BZ_EINVAL, "internal size");
+    bzk::k_shear_mean<<<1, 256, 0, s>>>(H->shear, g.nx, tmp);
+    BZ_LAUNCHED(H);
+    H->mom_valid = false;
+    BZ_CUDA(cudaMemcpyAsync(out, tmp, sizeof(double) * (g.nx + 1), cudaMemcpyDefault, s));
+    return BZ_OK;
+}
+
+bz_status bz_get_state(bz_handle *H, void *dst, int64_t *step, void *stream)
+{
+    if (!H || !dst) return fail(BZ_EINVAL, "NULL argument");
+    BZ_CUDA(cudaMemcpyAsync(dst, H->h[H->cur], H->esz * (size_t)H->g.nr * H->g.nvt,
+                            cudaMemcpyDefault, (cudaStream_t)stream));
+    if (step) *step = H->step;
+    return BZ_OK;
+}
+
+bz_status bz_set_state(bz_handle *H, const void *src, int64_t step, void *stream)
+{
+    if (!H || !src) return fail(BZ_EINVAL, "NULL argument");
+    if (step < 0) return fail(BZ_EINVAL, "step must be >= 0");
+    BZ_CUDA(cudaMemcpyAsync(H->h[H->cur], src, H->esz * (size_t)H->g.nr * H->g.nvt,
+                            cudaMemcpyDefault, (cudaStream_t)stream));
+    H->step = step;
+    H->mom_valid = false;
+    return BZ_OK;
+}
+
+bz_status bz_set_lid(bz_handle *H, double lid_u0, double lid_amp, double lid_period,
+                     const double *lid_profile)
+{
+    if (!H) return fail(BZ_EINVAL, "handle is NULL");
+    if (!std::isfinite(lid_u0) || !std::isfinite(lid_amp) || !(lid_period >= 0.0) ||
+        !std::isfinite(lid_period))
+        return fail(BZ_EINVAL, "invalid lid motion");
+    Geo &g = H->g;
+    if (lid_profile) {
+        for (int i = 0; i < g.nx; ++i)
+            if (!std::isfinite(lid_profile[i])) return fail(BZ_EINVAL, "lid_profile[%d]", i);
+        // Ordered after earlier work on the legacy stream semantics of cudaMemcpy.
+        BZ_CUDA(cudaMemcpy(H->profile, lid_profile, sizeof(double) * g.nx, cudaMemcpyHostToDevice));
+        g.lid_profile = H->profile;
+    } else {
+        g.lid_profile = nullptr;
+    }
+    g.lid_u0 = lid_u0;
+    g.lid_amp = lid_amp;
+    g.lid_period = lid_period;
+    return BZ_OK;
+}
+
+bz_status bz_get_info(const bz_handle *H, bz_info *o)
+{
+    if (!H || !o) return fail(BZ_EINVAL, "NULL argument");
+    const Geo &g = H->g;
+    o->dt = g.dt;
+    o->dx = g.dx;
+    o->dy = g.dy;
+    o->dv = g.dv;
+    o->eps = g.eps;
+    o->kcoll = g.cw * g.nt / (M_PI * g.dt);
+    o->nodes = (int64_t)g.nr * g.nvt;
+    o->state_bytes = o->nodes * (int64_t)H->esz;
+    o->step = H->step;
+    o->nr = g.nr;
+    o->nvt = g.nvt;
+    o->dtype = H->dtype;
+    o->threads_per_cell = H->threads;
+    o->smem_bytes = (int32_t)H->smem_cell;
+    return BZ_OK;
+}
+
+bz_status bz_stats(bz_handle *H, int64_t out[8])
+{
+    if (!H || !out) return fail(BZ_EINVAL, "NULL argument");
+    unsigned long long d[8];
+    BZ_CUDA(cudaDeviceSynchronize());
+    BZ_CUDA(cudaMemcpy(d, H->stats, sizeof(d), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 8; ++i) out[i] = (int64_t)d[i];
+    out[0] = H->step;
+    out[4] = H->launches;
+    return BZ_OK;
+}
+
+bz_status bz_sample_plan(bz_handle *H, int64_t step, int32_t *idx, double *W, void *stream)
+{
+    if (!H || !idx || !W) return fail(BZ_EINVAL, "NULL argument");
+    if (step < 0) return fail(BZ_EINVAL, "step must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Geo &g = H->g;
+    int4 *di = nullptr;
+    double *dw = nullptr;
+    BZ_TRY(dalloc(&di, sizeof(int4) * (size_t)g.nt));
+    bz_status st = dalloc(&dw, sizeof(double) * (size_t)g.nt);
+    if (st != BZ_OK) {
+        cudaFree(di);
+        return st;
+    }
+    int pb = 256, pg = (g.nt + pb - 1) / pb;
+    if (H->dtype == BZ_F64)
+        bzk::k_plan<double, int><<<pg, pb, 0, s>>>(g, step, di, (double *)nullptr, dw, nullptr);
+    else
+        bzk::k_plan<float, int><<<pg, pb, 0, s>>>(g, step, di, (float *)nullptr, dw, nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(idx, di, sizeof(int4) * (size_t)g.nt, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(W, dw, sizeof(double) * (size_t)g.nt, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(di);
+    cudaFree(dw);
+    if (e != cudaSuccess) return fail(BZ_ECUDA, "sample plan failed: %s", cudaGetErrorString(e));
+    H->launches++;
+    return BZ_OK;
+}
+
+bz_status bz_profile(bz_handle *H, int32_t enable)
+{
+    if (!H) return fail(BZ_EINVAL, "handle is NULL");
+    H->prof = enable != 0;
+    return BZ_OK;
+}
+
+bz_status bz_profile_read(bz_handle *H, double ms[4], int64_t launches[4])
+{
+    if (!H || !ms || !launches) return fail(BZ_EINVAL, "NULL argument");
+    for (int k = 0; k < 4; ++k) {
+        ms[k] = 0.0;
+        launches[k] = (int64_t)H->ev[k].size();
+        for (auto &p : H->ev[k]) {
+            BZ_CUDA(cudaEventSynchronize(p.second));
+            float t = 0.f;
+            BZ_CUDA(cudaEventElapsedTime(&t, p.first, p.second));
+            ms[k] += t;
+        }
+    }
+    clear_events(H);
+    return BZ_OK;
+}
+
+bz_status bz_philox(uint32_t k0, uint32_t k1, const uint32_t *ctr, int64_t n, uint32_t *out)
+{
+    if (!ctr || !out || n < 0) return fail(BZ_EINVAL, "invalid argument");
+    if (n == 0) return BZ_OK;
+    uint4 *dc = nullptr, *dout = nullptr;
+    BZ_TRY(dalloc(&dc, sizeof(uint4) * (size_t)n));
+    bz_status st = dalloc(&dout, sizeof(uint4) * (size_t)n);
+    if (st != BZ_OK) {
+        cudaFree(dc);
+        return st;
+    }
+    cudaError_t e = cudaMemcpy(dc, ctr, sizeof(uint4) * (size_t)n, cudaMemcpyDefault);
+    if (e == cudaSuccess) {
+        bzk::k_philox<<<(unsigned)((n + 255) / 256), 256>>>(make_uint2(k0, k1), dc, dout, n);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, sizeof(uint4) * (size_t)n, cudaMemcpyDefault);
+    cudaFree(dc);
+    cudaFree(dout);
+    if (e != cudaSuccess) return fail(BZ_ECUDA, "philox failed: %s", cudaGetErrorString(e));
+    return BZ_OK;
+}
+
+}  // extern "C"

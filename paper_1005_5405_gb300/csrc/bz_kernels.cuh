@@ -1,0 +1,861 @@
+// bz_kernels.cuh -- sm_103a kernels of the semi-regular Boltzmann step.
+//
+// Method: Frezzotti, Ghiroldi & Gibelli, "Solving the Boltzmann equation on
+// GPUs" (Secs. 2-4).  One time step is
+//   k_walls   wall densities n_w and emitted ghost values (Eq. bcMax)
+//   k_plan    the shared Monte Carlo sample set (Sec. 4.2, Algorithm 2)
+//   k_fused   per spatial cell: upwind streaming into a shared-memory slab
+//             (Eq. streaming2D), Jacobi Monte Carlo collision update
+//             (Eqs. monteCarloInt, collision_step), conservation correction
+//             (Eqs. rinorm_a, correzione) and the moments (Eqs. densita..sforzi)
+// with k_stream + k_collide as the unfused equivalent.
+//
+// Layout: h[cell][j], j = (jx*N + jy)*N + jz.  A CTA owns one cell at a time;
+// thread t owns the velocity "pairs" p = jy*N + jz with p = t (mod T) and
+// walks jx, so a warp touches 32 consecutive nodes (coalesced global access,
+// conflict-free shared access) and every per-node weight factorises as
+// A[jx] * A[jy] * A[jz] with A(v) = dv pi^{-1/2} e^{-v^2}.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bzk {
+
+constexpr int kMaxThreads = 1024;
+constexpr int kMaxWarps = kMaxThreads / 32;
+constexpr int kMaxN = 64;          // velocity nodes per axis
+constexpr int kRedSlots = 20;      // values per block reduction
+
+// Problem description shared by every kernel (by value).
+struct Geo {
+    int nx, ny, nv, nvt, nr, nfaces;
+    int nt;                     // Monte Carlo samples per step
+    double vmax, dv, dt, dx, dy, eps, cw;   // cw = pi K dt / Nt
+    uint32_t seed, instance;
+    double lid_u0, lid_amp, lid_period;
+    const double *lid_profile;  // device, nx, or nullptr
+    const double *axv;          // device, nv: node velocity per axis
+    const double *axA;          // device, nv: dv pi^{-1/2} exp(-v^2)
+    // Wall flux constants (Eq. bcMax with discrete sums):
+    double cout;                // sum_{v_n<0} |v_n| w_j (same for all walls)
+    double hn;                  // sum_{v_n>0} v_n A(v_n)
+    double zsum;                // sum_z A(v_z)
+    double G0[25];              // sum_j w_j psi_a psi_b, psi = (1, v, v^2)
+};
+
+// ---------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11)
+// ---------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        uint32_t lo0 = m0 * c.x, hi0 = __umulhi(m0, c.x);
+        uint32_t lo1 = m1 * c.z, hi1 = __umulhi(m1, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+__global__ void k_philox(uint2 key, const uint4 *__restrict__ ctr, uint4 *__restrict__ out,
+                         int64_t n)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = philox4x32_10(ctr[i], key);
+}
+
+// ---------------------------------------------------------------------
+// Sampling (Eq. coll8Dim; Sec. 4.2).  All arithmetic that decides a node
+// index is IEEE double with explicit rounding intrinsics (no contraction).
+// ---------------------------------------------------------------------
+__device__ __forceinline__ double u01(uint32_t x)
+{
+    return __dmul_rn(__dadd_rn((double)x, 0.5), 2.3283064365386962890625e-10);
+}
+
+__device__ __forceinline__ int node_axis(double v, double vmax, double dv, int n, int *near)
+{
+    double t = __ddiv_rn(__dadd_rn(v, vmax), dv);
+    double fl = floor(t);
+    double fr = __dsub_rn(t, fl);
+    if (fr < 1e-9 || fr > 1.0 - 1e-9) *near = 1;
+    if (!(t >= 0.0) || fl >= (double)n) return -1;
+    return (int)fl;
+}
+
+__device__ __forceinline__ int node_of(const double v[3], double vmax, double dv, int n,
+                                       int *near)
+{
+    int a = node_axis(v[0], vmax, dv, n, near);
+    int b = node_axis(v[1], vmax, dv, n, near);
+    int c = node_axis(v[2], vmax, dv, n, near);
+    if (a < 0 || b < 0 || c < 0) return -1;
+    return (a * n + b) * n + c;
+}
+
+struct SampleOut {
+    int idx[4];
+    double W;
+    int near, outside;
+};
+
+__device__ __forceinline__ SampleOut draw_sample(const Geo &g, int64_t step, uint32_t cellword,
+                                                 uint32_t l)
+{
+    uint2 key = make_uint2(g.seed, g.instance);
+    uint4 a = philox4x32_10(make_uint4(l, (uint32_t)step, cellword, 0u), key);
+    uint4 b = philox4x32_10(make_uint4(l, (uint32_t)step, cellword, 1u), key);
+    const double twopi = 6.283185307179586;
+    // Box-Muller pairs: normals of variance 1/2 match Phi0 = pi^{-3/2} e^{-v^2}.
+    double r0 = __dsqrt_rn(-log(u01(a.x))), t0 = __dmul_rn(twopi, u01(a.y));
+    double r1 = __dsqrt_rn(-log(u01(a.z))), t1 = __dmul_rn(twopi, u01(a.w));
+    double r2 = __dsqrt_rn(-log(u01(b.x))), t2 = __dmul_rn(twopi, u01(b.y));
+    double v[3], v1[3], k[3];
+    v[0] = __dmul_rn(r0, cos(t0));
+    v[1] = __dmul_rn(r0, sin(t0));
+    v[2] = __dmul_rn(r1, cos(t1));
+    v1[0] = __dmul_rn(r1, sin(t1));
+    v1[1] = __dmul_rn(r2, cos(t2));
+    v1[2] = __dmul_rn(r2, sin(t2));
+    // Unit vector on the sphere through (k_z, phi).
+    double kz = __dsub_rn(1.0, __dmul_rn(2.0, u01(b.z)));
+    double ph = __dmul_rn(twopi, u01(b.w));
+    double st = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(kz, kz)));
+    k[0] = __dmul_rn(st, cos(ph));
+    k[1] = __dmul_rn(st, sin(ph));
+    k[2] = kz;
+    // v* = v + (v_r.k) k, v1* = v1 - (v_r.k) k with v_r = v1 - v (Algorithm 2).
+    double vr0 = __dsub_rn(v1[0], v[0]), vr1 = __dsub_rn(v1[1], v[1]),
+           vr2 = __dsub_rn(v1[2], v[2]);
+    double s = __dadd_rn(__dadd_rn(__dmul_rn(vr0, k[0]), __dmul_rn(vr1, k[1])),
+                         __dmul_rn(vr2, k[2]));
+    double vs[3], v1s[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double sk = __dmul_rn(s, k[c]);
+        vs[c] = __dadd_rn(v[c], sk);
+        v1s[c] = __dsub_rn(v1[c], sk);
+    }
+    SampleOut o;
+    int near = 0;
+    o.idx[0] = node_of(v, g.vmax, g.dv, g.nv, &near);
+    o.idx[1] = node_of(v1, g.vmax, g.dv, g.nv, &near);
+    o.idx[2] = node_of(vs, g.vmax, g.dv, g.nv, &near);
+    o.idx[3] = node_of(v1s, g.vmax, g.dv, g.nv, &near);
+    o.near = near;
+    o.outside = (o.idx[0] < 0) | (o.idx[1] < 0) | (o.idx[2] < 0) | (o.idx[3] < 0);
+    o.W = __dmul_rn(g.cw, fabs(s));
+    return o;
+}
+
+// Node indices of a sample (v, v1, v*, v1*).  Grids with fewer than 65535
+// nodes use 16-bit indices (0xFFFF = outside the box) to halve the bytes every
+// CTA streams from L2 per cell; larger grids use 32-bit indices (-1 outside).
+template <typename I> struct Idx4;
+template <> struct Idx4<int> {
+    using type = int4;
+    static __device__ __forceinline__ type make(const int *q) { return make_int4(q[0], q[1], q[2], q[3]); }
+};
+template <> struct Idx4<uint16_t> {
+    using type = ushort4;
+    static __device__ __forceinline__ type make(const int *q)
+    {
+        return make_ushort4((unsigned short)q[0], (unsigned short)q[1], (unsigned short)q[2],
+                            (unsigned short)q[3]);
+    }
+};
+__device__ __forceinline__ int idx_of(int v) { return v; }
+__device__ __forceinline__ int idx_of(unsigned short v) { return v == 0xFFFFu ? -1 : (int)v; }
+
+// One thread per sample; the set is shared by every cell of the step.
+template <typename R, typename I>
+__global__ void k_plan(Geo g, int64_t step, typename Idx4<I>::type *__restrict__ idx,
+                       R *__restrict__ W, double *__restrict__ Wd,
+                       unsigned long long *__restrict__ stats)
+{
+    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    SampleOut o = {};
+    bool act = l < g.nt;
+    if (act) {
+        o = draw_sample(g, step, 0xFFFFFFFFu, (uint32_t)l);
+        idx[l] = Idx4<I>::make(o.idx);
+        if (W) W[l] = (R)o.W;
+        if (Wd) Wd[l] = o.W;
+    }
+    if (stats) {
+        unsigned mo = __ballot_sync(0xFFFFFFFFu, act && o.outside);
+        unsigned mn = __ballot_sync(0xFFFFFFFFu, act && o.near);
+        if ((threadIdx.x & 31) == 0) {
+            if (mo) atomicAdd(stats + 1, (unsigned long long)__popc(mo));
+            if (mn) atomicAdd(stats + 2, (unsigned long long)__popc(mn));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------
+// Block reductions (per-thread partials -> per-warp -> double totals)
+// ---------------------------------------------------------------------
+template <int K, typename A>
+__device__ __forceinline__ void block_reduce(A (&v)[K], double *red /* kMaxWarps*kRedSlots */,
+                                             double *tot /* K */)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        A x = v[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+        if (lane == 0) red[warp * kRedSlots + k] = (double)x;
+    }
+    __syncthreads();
+    if (threadIdx.x < K) {
+        double s = 0.0;
+        for (int w = 0; w < nwarps; ++w) s += red[w * kRedSlots + threadIdx.x];
+        tot[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------
+// Diffuse walls (Eq. bcMax): one CTA per boundary face.
+// Faces: [0,ny) left, [ny,2ny) right, [2ny,2ny+nx) bottom, then the lid.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ double lid_speed(const Geo &g, int ix, int64_t step)
+{
+    double base = g.lid_profile ? g.lid_profile[ix] : g.lid_u0;
+    if (g.lid_period > 0.0) {
+        double t = (double)step * g.dt;
+        base += g.lid_amp * sin(6.283185307179586 * t / g.lid_period);
+    }
+    return base;
+}
+
+struct Face {
+    int cell, nax;   // boundary cell, normal axis (0 = x, 1 = y)
+    double nsign;    // inward normal = nsign * e_nax
+    double U;        // wall speed along the tangential axis (x for the lid)
+};
+
+__device__ __forceinline__ Face face_of(const Geo &g, int f, int64_t step)
+{
+    Face F;
+    F.U = 0.0;
+    if (f < g.ny) {
+        F.cell = f * g.nx; F.nax = 0; F.nsign = 1.0;
+    } else if (f < 2 * g.ny) {
+        F.cell = (f - g.ny) * g.nx + g.nx - 1; F.nax = 0; F.nsign = -1.0;
+    } else if (f < 2 * g.ny + g.nx) {
+        F.cell = f - 2 * g.ny; F.nax = 1; F.nsign = 1.0;
+    } else {
+        int ix = f - 2 * g.ny - g.nx;
+        F.cell = (g.ny - 1) * g.nx + ix; F.nax = 1; F.nsign = -1.0;
+        F.U = lid_speed(g, ix, step);
+    }
+    return F;
+}
+
+// ghost[f*nv + jt]: emitted h for inflow nodes of face f, indexed by the
+// tangential velocity index (jy for side walls, jx for bottom and lid).
+// shear[ix]: x-momentum flux through lid face ix (lid faces only).
+template <typename R>
+__global__ void k_walls(Geo g, int64_t step, const R *__restrict__ h, R *__restrict__ ghost,
+                        double *__restrict__ nw_out, double *__restrict__ shear)
+{
+    __shared__ double red[kMaxWarps * kRedSlots];
+    __shared__ double tot[4];
+    __shared__ double s_nw;
+    const int f = blockIdx.x;
+    const Face F = face_of(g, f, step);
+    const int N = g.nv, N2 = N * N;
+    __shared__ R sA[kMaxN], sv[kMaxN];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        sA[i] = (R)g.axA[i];
+        sv[i] = (R)g.axv[i];
+    }
+    __syncthreads();
+    const R *hc = h + (int64_t)F.cell * g.nvt;
+    const bool lid = f >= 2 * g.ny + g.nx;
+    const R ns = (R)F.nsign;
+    // Outgoing flux sum_{v_n<0} |v_n| w_j h_j and, on the lid, the cell part
+    // of the shear, sum_{v_y>0} w_j v_x v_y h_j (per-thread sums in the state
+    // precision, combined in double).
+    R acc[2] = {R(0), R(0)};
+    for (int j = threadIdx.x; j < g.nvt; j += blockDim.x) {
+        int jx = j / N2, jy = (j / N) % N, jz = j % N;
+        R vx = sv[jx], vy = sv[jy];
+        R vn = (F.nax == 0 ? vx : vy) * ns;
+        if (vn < R(0)) {
+            R w = sA[jx] * sA[jy] * sA[jz];
+            R hv = hc[j];
+            acc[0] -= vn * w * hv;
+            if (lid) acc[1] += w * vx * vy * hv;
+        }
+    }
+    block_reduce<2, R>(acc, red, tot);
+    if (threadIdx.x == 0) {
+        // D_in = sum_{v_n>0} v_n dV Phi_w(v_j), separable in the three axes.
+        double tsum = 0.0;
+        for (int jt = 0; jt < N; ++jt) {
+            double d = g.axv[jt] - F.U;
+            tsum += g.dv * 0.5641895835477563 * exp(-d * d);
+        }
+        double din = g.hn * tsum * g.zsum;
+        double nw = (g.cout + g.eps * tot[0]) / din;
+        s_nw = nw;
+        if (nw_out) nw_out[f] = nw;
+    }
+    __syncthreads();
+    const double nw = s_nw, lnw = log(nw), U = F.U;
+    for (int jt = threadIdx.x; jt < N; jt += blockDim.x) {
+        double vt = g.axv[jt];
+        // n_w Phi_w / Phi0 - 1 = expm1(ln n_w + 2 v_t U - U^2)
+        double gh = expm1(lnw + 2.0 * vt * U - U * U) / g.eps;
+        ghost[f * N + jt] = (R)gh;
+    }
+    if (lid && shear && threadIdx.x == 0) {
+        // Emitted part: sum over v_y < 0 of w v_x v_y h_w(jx), separable.
+        double sx = 0.0, sy = 0.0;
+        for (int jx = 0; jx < N; ++jx) {
+            double d = g.axv[jx] - U;
+            double gh = expm1(lnw + 2.0 * g.axv[jx] * U - U * U) / g.eps;
+            sx += g.axA[jx] * g.axv[jx] * gh;
+            (void)d;
+        }
+        for (int jy = 0; jy < N; ++jy)
+            if (g.axv[jy] < 0.0) sy += g.axA[jy] * g.axv[jy];
+        shear[f - 2 * g.ny - g.nx] = 2.0 * (tot[1] + sx * sy * g.zsum);
+    }
+}
+
+__global__ void k_shear_mean(const double *__restrict__ shear, int nx, double *__restrict__ out)
+{
+    __shared__ double red[kMaxWarps * kRedSlots];
+    __shared__ double tot[1];
+    double a[1] = {0.0};
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        a[0] += shear[i];
+        out[i] = shear[i];
+    }
+    block_reduce<1, double>(a, red, tot);
+    if (threadIdx.x == 0) out[nx] = tot[0] / nx;
+}
+
+// ---------------------------------------------------------------------
+// Free streaming (Eq. streaming2D), first-order upwind, conservative.
+// ---------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R upwind_node(const Geo &g, const R *__restrict__ h,
+                                         const R *__restrict__ ghost, int c, int ix, int iy,
+                                         int64_t j, int jx, int jy, R cux, R cuy)
+{
+    const int64_t nvt = g.nvt;
+    R h0 = h[(int64_t)c * nvt + j];
+    R hx = h0, hy = h0;
+    if (cux > R(0)) {
+        hx = ix > 0 ? h[(int64_t)(c - 1) * nvt + j] : ghost[iy * g.nv + jy];
+    } else if (cux < R(0)) {
+        hx = ix < g.nx - 1 ? h[(int64_t)(c + 1) * nvt + j] : ghost[(g.ny + iy) * g.nv + jy];
+    }
+    if (cuy > R(0)) {
+        hy = iy > 0 ? h[(int64_t)(c - g.nx) * nvt + j] : ghost[(2 * g.ny + ix) * g.nv + jx];
+    } else if (cuy < R(0)) {
+        hy = iy < g.ny - 1 ? h[(int64_t)(c + g.nx) * nvt + j]
+                           : ghost[(2 * g.ny + g.nx + ix) * g.nv + jx];
+    }
+    R ax = fabs(cux), ay = fabs(cuy);
+    return h0 - ax * (h0 - hx) - ay * (h0 - hy);
+}
+
+// One CTA per cell, threads over the slab.
+template <typename R>
+__global__ void k_stream(Geo g, const R *__restrict__ h, const R *__restrict__ ghost,
+                         R *__restrict__ ht)
+{
+    __shared__ R cu[kMaxN];
+    const int N = g.nv, N2 = N * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) cu[i] = (R)(g.axv[i] * g.dt / g.dx);
+    __syncthreads();
+    const R ry = (R)(g.dx / g.dy);
+    for (int c = blockIdx.x; c < g.nr; c += gridDim.x) {
+        const int ix = c % g.nx, iy = c / g.nx;
+        for (int j = threadIdx.x; j < g.nvt; j += blockDim.x) {
+            int jx = j / N2, jy = (j / N) % N;
+            ht[(int64_t)c * g.nvt + j] =
+                upwind_node<R>(g, h, ghost, c, ix, iy, j, jx, jy, cu[jx], cu[jy] * ry);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------
+// Per-cell relaxation (Eqs. monteCarloInt, collision_step, rinorm_a,
+// correzione) and moments, optionally with streaming fused into the load.
+// ---------------------------------------------------------------------
+template <typename R>
+struct AxisTab {       // per-axis tables in shared memory, N entries each
+    R *A, *IA, *v, *v2, *v3, *v4, *Av, *Av2, *cx, *cu;
+};
+
+__device__ __noinline__ void chol_or_ge(double G[5][5], double b[5], double x[5], int *fallback)
+{
+    double L[5][5];
+    bool ok = true;
+    for (int i = 0; i < 5 && ok; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double s = G[i][j];
+            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+            if (i == j) {
+                if (!(s > 0.0)) { ok = false; break; }
+                L[i][i] = sqrt(s);
+            } else {
+                L[i][j] = s / L[j][j];
+            }
+        }
+    }
+    if (ok) {
+        double y[5];
+        for (int i = 0; i < 5; ++i) {
+            double s = b[i];
+            for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
+            y[i] = s / L[i][i];
+        }
+        for (int i = 4; i >= 0; --i) {
+            double s = y[i];
+            for (int k = i + 1; k < 5; ++k) s -= L[k][i] * x[k];
+            x[i] = s / L[i][i];
+        }
+        return;
+    }
+    *fallback = 1;
+    // Gaussian elimination with partial pivoting.
+    double A[5][6];
+    for (int i = 0; i < 5; ++i) {
+        for (int j = 0; j < 5; ++j) A[i][j] = G[i][j];
+        A[i][5] = b[i];
+    }
+    for (int k = 0; k < 5; ++k) {
+        int p = k;
+        for (int i = k + 1; i < 5; ++i)
+            if (fabs(A[i][k]) > fabs(A[p][k])) p = i;
+        if (A[p][k] == 0.0) {
+            for (int i = 0; i < 5; ++i) x[i] = 0.0;
+            return;
+        }
+        for (int j = 0; j < 6; ++j) {
+            double t = A[k][j]; A[k][j] = A[p][j]; A[p][j] = t;
+        }
+        for (int i = k + 1; i < 5; ++i) {
+            double m = A[i][k] / A[k][k];
+            for (int j = k; j < 6; ++j) A[i][j] -= m * A[k][j];
+        }
+    }
+    for (int i = 4; i >= 0; --i) {
+        double s = A[i][5];
+        for (int j = i + 1; j < 5; ++j) s -= A[i][j] * x[j];
+        x[i] = s / A[i][i];
+    }
+}
+
+// Correction of Eqs. rinorm_a / correzione for one cell.  P holds the reduced
+// sums: P[0..13] moments of the post-collision N_c over the monomials
+// 1, vx, vy, vz, vx2, vy2, vz2, vxvy, vxvz, vyvz, vx v2, vy v2, vz v2, v4 and
+// P[14..18] the invariants 1, vx, vy, vz, v2 of the pre-collision N.  Solves
+// G mu = -(post - pre) with G = sum_j w_j (1 + eps h_c,j) psi psi^T.
+__device__ __noinline__ void correction_solve(const Geo &g, const double *P, double *mu,
+                                              int *fallback)
+{
+    const double e = g.eps;
+    double post[5] = {P[0], P[1], P[2], P[3], P[4] + P[5] + P[6]};
+    double rhs[5];
+    for (int a = 0; a < 5; ++a) rhs[a] = -(post[a] - P[14 + a]);
+    const double m[5][5] = {
+        {P[0], P[1], P[2], P[3], post[4]},
+        {P[1], P[4], P[7], P[8], P[10]},
+        {P[2], P[7], P[5], P[9], P[11]},
+        {P[3], P[8], P[9], P[6], P[12]},
+        {post[4], P[10], P[11], P[12], P[13]}};
+    double M[5][5];
+    for (int a = 0; a < 5; ++a)
+        for (int b = 0; b < 5; ++b) M[a][b] = g.G0[a * 5 + b] + e * m[a][b];
+    double x[5];
+    chol_or_ge(M, rhs, x, fallback);
+    for (int a = 0; a < 5; ++a) mu[a] = x[a];
+}
+
+// Dynamic shared memory layout of the per-cell kernels.
+template <typename R>
+struct CellSmem {
+    R *slab;           // nvt
+    R *gw;             // nt (or nullptr when the products live in global scratch)
+    AxisTab<R> tab;    // 10 * N
+    double *red;       // kMaxWarps * kRedSlots
+    double *tot;       // kRedSlots
+    double *mu;        // 8
+};
+
+template <typename R>
+__device__ __forceinline__ CellSmem<R> carve(char *base, const Geo &g, bool gw_in_smem)
+{
+    CellSmem<R> s;
+    size_t off = 0;
+    s.red = (double *)(base + off); off += sizeof(double) * kMaxWarps * kRedSlots;
+    s.tot = (double *)(base + off); off += sizeof(double) * kRedSlots;
+    s.mu = (double *)(base + off); off += sizeof(double) * 8;
+    R *t = (R *)(base + off);
+    const int N = g.nv;
+    s.tab.A = t; s.tab.IA = t + N; s.tab.v = t + 2 * N; s.tab.v2 = t + 3 * N;
+    s.tab.v3 = t + 4 * N; s.tab.v4 = t + 5 * N; s.tab.Av = t + 6 * N; s.tab.Av2 = t + 7 * N;
+    s.tab.cx = t + 8 * N; s.tab.cu = t + 9 * N;
+    off += sizeof(R) * 10 * N;
+    off = (off + 15) & ~(size_t)15;
+    s.slab = (R *)(base + off); off += sizeof(R) * g.nvt;
+    off = (off + 15) & ~(size_t)15;
+    s.gw = gw_in_smem ? (R *)(base + off) : nullptr;
+    return s;
+}
+
+template <typename R>
+__host__ __device__ inline size_t cell_smem_bytes(int nv, int nvt, int nt, bool gw_in_smem)
+{
+    size_t off = sizeof(double) * (kMaxWarps * kRedSlots + kRedSlots + 8) + sizeof(R) * 10 * nv;
+    off = (off + 15) & ~(size_t)15;
+    off += sizeof(R) * nvt;
+    off = (off + 15) & ~(size_t)15;
+    if (gw_in_smem) off += sizeof(R) * nt;
+    return off;
+}
+
+// FUSED: the slab is filled by streaming h^n (Eq. streaming2D) instead of
+// loading h~ from global memory.
+template <typename R, bool FUSED, typename I>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+k_cell(Geo g, int64_t step, const R *__restrict__ hin, const R *__restrict__ ghost,
+       const typename Idx4<I>::type *__restrict__ pidx, const R *__restrict__ pW,
+       R *__restrict__ gw_global,
+       R *__restrict__ hout, double *__restrict__ mom, unsigned long long *__restrict__ stats,
+       int gw_in_smem)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    CellSmem<R> S = carve<R>(smem_raw, g, gw_in_smem != 0);
+    const int N = g.nv, N2 = N * N, nvt = g.nvt, T = blockDim.x, t = threadIdx.x;
+    const R eps = (R)g.eps;
+    R *gw = S.gw ? S.gw : gw_global + (int64_t)blockIdx.x * g.nt;
+
+    for (int i = t; i < N; i += T) {
+        double v = g.axv[i], A = g.axA[i];
+        S.tab.A[i] = (R)A;
+        S.tab.IA[i] = (R)(1.0 / A);
+        S.tab.v[i] = (R)v;
+        S.tab.v2[i] = (R)(v * v);
+        S.tab.v3[i] = (R)(v * v * v);
+        S.tab.v4[i] = (R)(v * v * v * v);
+        S.tab.Av[i] = (R)(A * v);
+        S.tab.Av2[i] = (R)(A * v * v);
+        S.tab.cu[i] = (R)(v * g.dt / g.dx);
+    }
+    __syncthreads();
+    const R ry = (R)(g.dx / g.dy);
+    int fallback = 0;
+
+    for (int c = blockIdx.x; c < g.nr; c += gridDim.x) {
+        const int ix = c % g.nx, iy = c / g.nx;
+        // ---- fill the slab with h~ ----------------------------------------
+        if (FUSED) {
+            // Eq. streaming2D with the upwind sources hoisted per thread: the
+            // sign of v_x changes once along jx (negative half reads the right
+            // neighbour, positive half the left one), the sign of v_y is fixed
+            // per thread; at a wall the source is the face's ghost value.
+            const int64_t nvt64 = nvt;
+            const R *own = hin + (int64_t)c * nvt64;
+            const int nneg = N / 2, npos = (N + 1) / 2;
+            for (int p = t; p < N2; p += T) {
+                const int jy = p / N;
+                const R cuy = S.tab.cu[jy] * ry, ay = fabs(cuy);
+                const R *ys = own;
+                int ystr = N2, yoff = p;
+                if (cuy > R(0)) {
+                    if (iy > 0) ys = own - (int64_t)g.nx * nvt64;
+                    else { ys = ghost + (2 * g.ny + ix) * N; ystr = 1; yoff = 0; }
+                } else if (cuy < R(0)) {
+                    if (iy < g.ny - 1) ys = own + (int64_t)g.nx * nvt64;
+                    else { ys = ghost + (2 * g.ny + g.nx + ix) * N; ystr = 1; yoff = 0; }
+                }
+                // v_x < 0: right neighbour or right-wall ghost (constant in jx)
+                const R *xs = ix < g.nx - 1 ? own + nvt64 + p : ghost + (g.ny + iy) * N + jy;
+                int xstr = ix < g.nx - 1 ? N2 : 0;
+#pragma unroll 4
+                for (int jx = 0; jx < nneg; ++jx) {
+                    const int j = jx * N2 + p;
+                    R h0 = own[j], hx = xs[jx * xstr], hy = ys[jx * ystr + yoff];
+                    R ax = fabs(S.tab.cu[jx]);
+                    S.slab[j] = h0 - ax * (h0 - hx) - ay * (h0 - hy);
+                }
+                for (int jx = nneg; jx < npos; ++jx) {       // v_x = 0 (odd N)
+                    const int j = jx * N2 + p;
+                    R h0 = own[j], hy = ys[jx * ystr + yoff];
+                    S.slab[j] = h0 - ay * (h0 - hy);
+                }
+                // v_x > 0: left neighbour or left-wall ghost
+                xs = ix > 0 ? own - nvt64 + p : ghost + iy * N + jy;
+                xstr = ix > 0 ? N2 : 0;
+#pragma unroll 4
+                for (int jx = npos; jx < N; ++jx) {
+                    const int j = jx * N2 + p;
+                    R h0 = own[j], hx = xs[jx * xstr], hy = ys[jx * ystr + yoff];
+                    R ax = fabs(S.tab.cu[jx]);
+                    S.slab[j] = h0 - ax * (h0 - hx) - ay * (h0 - hy);
+                }
+            }
+        } else {
+            const R *src = hin + (int64_t)c * nvt;
+            for (int j = t; j < nvt; j += T) S.slab[j] = src[j];
+        }
+        __syncthreads();
+
+        // ---- phase A: g_l W_l from the pre-collision values (Jacobi) -------
+        // Plan entries are loaded four at a time to keep L2 requests in flight.
+        {
+            using V4 = typename Idx4<I>::type;
+            int l = t;
+            for (; l + 3 * T < g.nt; l += 4 * T) {
+                V4 q[4];
+                R w[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    q[u] = pidx[l + u * T];
+                    w[u] = pW[l + u * T];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int a = idx_of(q[u].x), b = idx_of(q[u].y);
+                    R ha = a >= 0 ? S.slab[a] : R(0);
+                    R hb = b >= 0 ? S.slab[b] : R(0);
+                    gw[l + u * T] = (ha + hb + eps * ha * hb) * w[u];
+                }
+            }
+            for (; l < g.nt; l += T) {
+                V4 q = pidx[l];
+                const int a = idx_of(q.x), b = idx_of(q.y);
+                R ha = a >= 0 ? S.slab[a] : R(0);
+                R hb = b >= 0 ? S.slab[b] : R(0);
+                gw[l] = (ha + hb + eps * ha * hb) * pW[l];
+            }
+        }
+        __syncthreads();
+
+        // ---- N = w h~ in place, and the conserved moments of h~ ------------
+        R pre[5] = {R(0), R(0), R(0), R(0), R(0)};
+        for (int p = t; p < N2; p += T) {
+            const int jy = p / N, jz = p % N;
+            const R Ayz = S.tab.A[jy] * S.tab.A[jz];
+            R s0 = R(0), s1 = R(0), s2 = R(0);
+            for (int jx = 0; jx < N; ++jx) {
+                const int j = jx * N2 + p;
+                R n = S.slab[j] * S.tab.A[jx] * Ayz;
+                S.slab[j] = n;
+                s0 += n;
+                s1 += n * S.tab.v[jx];
+                s2 += n * S.tab.v2[jx];
+            }
+            const R vy = S.tab.v[jy], vz = S.tab.v[jz], q = vy * vy + vz * vz;
+            pre[0] += s0;
+            pre[1] += s1;
+            pre[2] += vy * s0;
+            pre[3] += vz * s0;
+            pre[4] += s2 + q * s0;
+        }
+        __syncthreads();
+
+        // ---- phase B: scatter the gains and losses (Eq. monteCarloInt) -----
+        {
+            using V4 = typename Idx4<I>::type;
+            auto scatter = [&](const V4 &q, R r) {
+                if (r != R(0)) {
+                    const int a = idx_of(q.x), b = idx_of(q.y), as = idx_of(q.z), bs = idx_of(q.w);
+                    if (as >= 0) atomicAdd(S.slab + as, r);
+                    if (bs >= 0) atomicAdd(S.slab + bs, r);
+                    if (a >= 0) atomicAdd(S.slab + a, -r);
+                    if (b >= 0) atomicAdd(S.slab + b, -r);
+                }
+            };
+            int l = t;
+            for (; l + 3 * T < g.nt; l += 4 * T) {
+                V4 q[4];
+                R r[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    q[u] = pidx[l + u * T];
+                    r[u] = gw[l + u * T];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) scatter(q[u], r[u]);
+            }
+            for (; l < g.nt; l += T) scatter(pidx[l], gw[l]);
+        }
+        __syncthreads();
+
+        // ---- moments of the post-collision N_c for the correction ----------
+        R acc[19];
+#pragma unroll
+        for (int k = 0; k < 19; ++k) acc[k] = R(0);
+        for (int p = t; p < N2; p += T) {
+            const int jy = p / N, jz = p % N;
+            R s0 = R(0), s1 = R(0), s2 = R(0), s3 = R(0), s4 = R(0);
+            for (int jx = 0; jx < N; ++jx) {
+                R n = S.slab[jx * N2 + p];
+                s0 += n;
+                s1 += n * S.tab.v[jx];
+                s2 += n * S.tab.v2[jx];
+                s3 += n * S.tab.v3[jx];
+                s4 += n * S.tab.v4[jx];
+            }
+            const R vy = S.tab.v[jy], vz = S.tab.v[jz], q = vy * vy + vz * vz;
+            acc[0] += s0;                  // 1
+            acc[1] += s1;                  // vx
+            acc[2] += vy * s0;             // vy
+            acc[3] += vz * s0;             // vz
+            acc[4] += s2;                  // vx^2
+            acc[5] += vy * vy * s0;        // vy^2
+            acc[6] += vz * vz * s0;        // vz^2
+            acc[7] += vy * s1;             // vx vy
+            acc[8] += vz * s1;             // vx vz
+            acc[9] += vy * vz * s0;        // vy vz
+            acc[10] += s3 + q * s1;        // vx v^2
+            acc[11] += vy * (s2 + q * s0); // vy v^2
+            acc[12] += vz * (s2 + q * s0); // vz v^2
+            acc[13] += s4 + R(2) * q * s2 + q * q * s0;   // v^4
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) acc[14 + k] = pre[k];
+        block_reduce<19, R>(acc, S.red, S.tot);
+
+        // ---- 5x5 solve: G mu = -(post - pre), G = sum w (1 + eps h_c) psi psi
+        if (t == 0) correction_solve(g, S.tot, S.mu, &fallback);
+        __syncthreads();
+        {
+            const double mx = S.mu[1], m4 = S.mu[4];
+            for (int i = t; i < N; i += T) {
+                double v = g.axv[i];
+                S.tab.cx[i] = (R)(mx * v + m4 * v * v);
+            }
+        }
+        __syncthreads();
+
+        // ---- corrected write-back and output moments ----------------------
+        R mo[10];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) mo[k] = R(0);
+        R *dst = hout + (int64_t)c * nvt;
+        for (int p = t; p < N2; p += T) {
+            const int jy = p / N, jz = p % N;
+            const R IAyz = S.tab.IA[jy] * S.tab.IA[jz];
+            const R vy = S.tab.v[jy], vz = S.tab.v[jz];
+            const R ct = (R)(S.mu[0] + S.mu[2] * (double)vy + S.mu[3] * (double)vz +
+                             S.mu[4] * ((double)vy * vy + (double)vz * vz));
+            R t0 = R(0), t1 = R(0), t2 = R(0);
+            for (int jx = 0; jx < N; ++jx) {
+                const int j = jx * N2 + p;
+                R hc = S.slab[j] * S.tab.IA[jx] * IAyz;
+                R corr = ct + S.tab.cx[jx];
+                R hn = hc + (R(1) + eps * hc) * corr;
+                dst[j] = hn;
+                t0 += hn * S.tab.A[jx];
+                t1 += hn * S.tab.Av[jx];
+                t2 += hn * S.tab.Av2[jx];
+            }
+            const R Ayz = S.tab.A[jy] * S.tab.A[jz];
+            mo[0] += Ayz * t0;
+            mo[1] += Ayz * t1;
+            mo[2] += Ayz * vy * t0;
+            mo[3] += Ayz * vz * t0;
+            mo[4] += Ayz * t2;
+            mo[5] += Ayz * vy * vy * t0;
+            mo[6] += Ayz * vz * vz * t0;
+            mo[7] += Ayz * vy * t1;
+            mo[8] += Ayz * vz * t1;
+            mo[9] += Ayz * vy * vz * t0;
+        }
+        block_reduce<10, R>(mo, S.red, S.tot);
+        if (t == 0 && mom) {
+            const double *m = S.tot, e = g.eps;
+            double rho = m[0], n = 1.0 + e * rho;
+            double u[3] = {m[1] / n, m[2] / n, m[3] / n};
+            double *o = mom + (int64_t)c * 11;
+            o[0] = rho;
+            o[1] = u[0];
+            o[2] = u[1];
+            o[3] = u[2];
+            o[4] = ((2.0 / 3.0) * (m[4] + m[5] + m[6]) - rho) / n -
+                   (2.0 * e / 3.0) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
+            const double m2[6] = {m[4], m[5], m[6], m[7], m[8], m[9]};
+            for (int k = 0; k < 6; ++k) o[5 + k] = 2.0 * m2[k] - 2.0 * e * n * u[pa[k]] * u[pb[k]];
+        }
+        // red/tot reuse is protected by the barriers inside block_reduce; the
+        // next cell's first writes to the slab happen after this point only.
+        __syncthreads();
+    }
+    if (fallback && stats) atomicAdd(stats + 3, 1ull);
+}
+
+// Moments of an arbitrary state (Eqs. densita..sforzi), one CTA per cell.
+template <typename R>
+__global__ void k_moments(Geo g, const R *__restrict__ h, double *__restrict__ mom)
+{
+    __shared__ double red[kMaxWarps * kRedSlots];
+    __shared__ double tot[kRedSlots];
+    const int N = g.nv, N2 = N * N;
+    for (int c = blockIdx.x; c < g.nr; c += gridDim.x) {
+        double mo[10];
+        for (int k = 0; k < 10; ++k) mo[k] = 0.0;
+        const R *src = h + (int64_t)c * g.nvt;
+        for (int j = threadIdx.x; j < g.nvt; j += blockDim.x) {
+            int jx = j / N2, jy = (j / N) % N, jz = j % N;
+            double vx = g.axv[jx], vy = g.axv[jy], vz = g.axv[jz];
+            double wh = g.axA[jx] * g.axA[jy] * g.axA[jz] * (double)src[j];
+            mo[0] += wh;
+            mo[1] += wh * vx;
+            mo[2] += wh * vy;
+            mo[3] += wh * vz;
+            mo[4] += wh * vx * vx;
+            mo[5] += wh * vy * vy;
+            mo[6] += wh * vz * vz;
+            mo[7] += wh * vx * vy;
+            mo[8] += wh * vx * vz;
+            mo[9] += wh * vy * vz;
+        }
+        block_reduce<10, double>(mo, red, tot);
+        if (threadIdx.x == 0) {
+            const double *m = tot, e = g.eps;
+            double rho = m[0], n = 1.0 + e * rho;
+            double u[3] = {m[1] / n, m[2] / n, m[3] / n};
+            double *o = mom + (int64_t)c * 11;
+            o[0] = rho;
+            o[1] = u[0];
+            o[2] = u[1];
+            o[3] = u[2];
+            o[4] = ((2.0 / 3.0) * (m[4] + m[5] + m[6]) - rho) / n -
+                   (2.0 * e / 3.0) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
+            const double m2[6] = {m[4], m[5], m[6], m[7], m[8], m[9]};
+            for (int k = 0; k < 6; ++k) o[5 + k] = 2.0 * m2[k] - 2.0 * e * n * u[pa[k]] * u[pb[k]];
+        }
+        __syncthreads();
+    }
+}
+
+// Count of non-finite values in an array of doubles (flag only).
+__global__ void k_nonfinite(const double *__restrict__ x, int64_t n, int *__restrict__ flag)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(x[i])) *flag = 1;
+}
+
+}  // namespace bzk

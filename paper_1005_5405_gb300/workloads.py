@@ -80,6 +80,13 @@ def cavity256_v32() -> Problem:
                    lid_amp=0.05, lid_period=50.0, steps=1000)
 
 
+def cavity64_v32() -> Problem:
+    """64x64 cells with the cell size, velocity grid and samples of
+    cavity256_v32 (state 0.54 GB, above L2): the profiling case."""
+    return Problem("cavity64_v32", 64, 64, 0.2, 32, 5.0, 20_000, 3, lid_u0=0.0,
+                   lid_amp=0.05, lid_period=50.0, steps=1000)
+
+
 def adjoint128_v20(seed: int = 4) -> Problem:
     rng = np.random.default_rng(seed)
     prof = 0.1 + 0.01 * rng.standard_normal(128)

@@ -1,0 +1,276 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: node selection is integer work and must agree exactly (samples
+whose velocity lies within 1e-9 dv of a cell face may legitimately differ,
+since libm and CUDA's log/cos/sin may differ by an ulp; both sides flag them).
+Floating point: max |f_gpu - f_oracle| / max f <= 1e-5 per step with
+f = Phi0 (1 + eps h); macroscopic fields within 1e-4 of their range after
+200 steps.
+"""
+import os
+import subprocess
+import tempfile
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1005_5405_gb300 import binding, workloads
+from tests.gpu_helpers import f_metric, make, state
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    yield
+
+
+# ---------------------------------------------------------------- Philox
+def test_device_philox_matches_oracle():
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2 ** 32, size=(20000, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:16] = np.arange(64).reshape(16, 4)
+    for key in [(0, 0), (1, 2), (0xDEADBEEF, 0x12345678)]:
+        dev = binding.philox(key, ctr)
+        ref = np.array([oracle.philox(c, key) for c in ctr[:4000]], dtype=np.uint32)
+        assert np.array_equal(dev[:4000], ref)
+
+
+def test_device_philox_matches_curand():
+    """Cross-check against cuRAND's Philox4x32-10 device function."""
+    nvcc = "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    d = tempfile.mkdtemp()
+    so = os.path.join(d, "curand_ref.so")
+    subprocess.run([nvcc, "-gencode=arch=compute_103a,code=sm_103a", "-shared", "-Xcompiler",
+                    "-fPIC", "-cudart", "shared", "-o", so, os.path.join(HERE, "_curand_ref.cu")],
+                   check=True)
+    L = C.CDLL(so)
+    rng = np.random.default_rng(2)
+    ctr = rng.integers(0, 2 ** 32, size=(50000, 4), dtype=np.uint64).astype(np.uint32)
+    for key in [(7, 9), (0xFFFFFFFF, 0), (3, 0xCAFEF00D)]:
+        out = np.zeros_like(ctr)
+        assert L.curand_philox_ref(C.c_uint32(key[0]), C.c_uint32(key[1]),
+                                   C.c_void_p(ctr.ctypes.data), C.c_int(len(ctr)),
+                                   C.c_void_p(out.ctypes.data)) == 0
+        assert np.array_equal(out, binding.philox(key, ctr))
+        ref = np.array([oracle.philox(c, key) for c in ctr[:2000]], dtype=np.uint32)
+        assert np.array_equal(out[:2000], ref)
+
+
+# ---------------------------------------------------------------- sampling
+@pytest.mark.parametrize("nv,vmax,nt,dtype", [(12, 4.0, 1000, "f64"), (24, 4.5, 10000, "f32"),
+                                              (32, 5.0, 20000, "f32"), (8, 2.0, 5000, "f32")])
+def test_sample_plan_matches_oracle(nv, vmax, nt, dtype):
+    p = workloads.small(nx=2, ny=2, nv=nv, vmax=vmax, nt=nt, seed=3, dtype=dtype)
+    cav = binding.Cavity(p)
+    o = oracle.Oracle(**p.kwargs())
+    for step in (0, 1, 57):
+        idx, W = cav.sample_plan(step)
+        s = o.samples(step)
+        same = (idx == s["idx"]).all(1)
+        bad = ~same & (s["near_face"] == 0)
+        assert bad.sum() == 0, np.nonzero(bad)
+        # s = v_r.k suffers cancellation, so ulp-level differences of libm and
+        # CUDA cos/sin/log show up relative to the largest weight only
+        assert np.max(np.abs(W - s["W"])) <= 1e-12 * np.max(s["W"])
+
+
+# ---------------------------------------------------------------- sub-steps
+CASES = [
+    workloads.small(nx=6, ny=5, nv=12, vmax=4.0, nt=1000, seed=1, dtype="f64"),
+    workloads.small(nx=6, ny=5, nv=12, vmax=4.0, nt=3000, seed=2, dtype="f32"),
+    workloads.small(nx=7, ny=3, nv=16, vmax=4.0, nt=4000, seed=3, dtype="f32", lid_u0=0.2),
+    workloads.small(nx=1, ny=1, nv=10, vmax=4.0, nt=2000, seed=4, dtype="f32"),
+    workloads.small(nx=4, ny=4, nv=5, vmax=3.0, nt=700, seed=5, dtype="f32"),
+    workloads.small(nx=3, ny=4, nv=24, vmax=4.5, nt=10000, seed=6, dtype="f32", kn=0.1),
+    workloads.small(nx=3, ny=3, nv=8, vmax=2.0, nt=3000, seed=7, dtype="f32"),  # many out-of-box
+]
+IDS = ["f64_12", "f32_12", "f32_16_rect", "single_cell", "odd_nv5", "f32_24", "outbox"]
+
+
+@pytest.mark.parametrize("p", CASES, ids=IDS)
+def test_stream_matches_oracle(p):
+    cav, o, h0 = make(p)
+    cav.step_ex(1, binding.BZ_DO_STREAM)
+    assert f_metric(o, state(cav), o.stream(h0, 0)) < 1e-6
+
+
+@pytest.mark.parametrize("p", CASES, ids=IDS)
+def test_collide_matches_oracle(p):
+    cav, o, h0 = make(p)
+    cav.step_ex(1, binding.BZ_DO_COLLIDE)
+    h_o, mom_o = o.collide(h0, step=0)
+    assert f_metric(o, state(cav), h_o) < 1e-5
+    mom_g = cav.moments().cpu().numpy()
+    assert np.allclose(mom_g, mom_o, rtol=1e-4, atol=1e-6 * (1 + np.abs(mom_o).max()))
+
+
+@pytest.mark.parametrize("p", CASES, ids=IDS)
+def test_fused_step_matches_oracle(p):
+    cav, o, h0 = make(p)
+    h_o = h0
+    for n in range(3):
+        cav.step(1)
+        h_o, mom_o = o.step(h_o, n)
+        assert f_metric(o, state(cav), h_o) < 1e-5 * (n + 1)
+    mom_g = cav.moments().cpu().numpy()
+    assert np.allclose(mom_g, mom_o, rtol=1e-4, atol=1e-5 * (1 + np.abs(mom_o).max()))
+
+
+def test_split_path_matches_fused_path():
+    p = CASES[2]
+    a, o, h0 = make(p)
+    b, _, _ = make(p)
+    a.step(2)
+    b.step_ex(2, binding.BZ_SPLIT)
+    assert f_metric(o, state(a), state(b)) < 1e-6
+
+
+def test_gw_in_global_scratch_path():
+    """Enough samples that the per-sample products do not fit in shared
+    memory next to a 32^3 slab: the kernel keeps them in global scratch."""
+    p = workloads.small(nx=2, ny=2, nv=32, vmax=5.0, nt=40000, seed=9)
+    cav, o, h0 = make(p)
+    cav.step(1)
+    h_o, _ = o.step(h0, 0)
+    assert f_metric(o, state(cav), h_o) < 1e-5
+
+
+def test_zero_state_stays_at_rest():
+    p = workloads.small(nx=4, ny=4, nv=12, vmax=4.0, nt=2000, seed=1, lid_u0=0.0)
+    cav, o, h0 = make(p, h0=np.zeros((16, 12 ** 3)))
+    cav.step(5)
+    assert np.max(np.abs(state(cav))) < 1e-10
+
+
+def test_200_steps_fp64_cavity16_v12():
+    """16x16 cavity, 12^3 velocities, FP64 state: macroscopic fields after 200
+    steps from rest (the lid drives the flow)."""
+    p = workloads.cavity16_v12()
+    cav, o, h0 = make(p, h0=np.zeros((p.nr, p.nvt)))
+    cav.step(200)
+    h_o, mom_o = o.run(h0, 200)
+    mom_g = cav.moments().cpu().numpy()
+    for k in range(5):
+        rng_ = np.abs(mom_o[:, k]).max()
+        assert np.max(np.abs(mom_g[:, k] - mom_o[:, k])) <= 1e-4 * rng_, k
+    assert f_metric(o, state(cav), h_o) < 1e-9
+
+
+def test_200_steps_fp32_v24():
+    """FP32 state, 24^3 velocities on [-4.5, 4.5]^3, 10^4 samples, with the cell
+    size and time step of the 64x64 Kn 0.1 cavity (8x8 cells of side 10/64)."""
+    p = workloads.small(nx=8, ny=8, nv=24, vmax=4.5, nt=10000, seed=2, kn=1.0 / (8 * 10.0 / 64))
+    cav, o, h0 = make(p, h0=np.zeros((p.nr, p.nvt)))
+    cav.step(200)
+    h_o, mom_o = o.run(h0, 200)
+    mom_g = cav.moments().cpu().numpy()
+    for k in range(5):
+        rng_ = np.abs(mom_o[:, k]).max()
+        assert np.max(np.abs(mom_g[:, k] - mom_o[:, k])) <= 1e-4 * rng_, k
+
+
+def test_full_size_cavity256_v32_sampled_cells():
+    """256x256 cells x 32^3 velocities, FP32, 2x10^4 samples: the launch
+    configuration of the benchmark.  One step from a seeded warm state; the
+    oracle recomputes sampled cells one by one from their input slabs."""
+    import torch
+    p = workloads.cavity256_v32()
+    rng = np.random.default_rng(7)
+    coef = torch.from_numpy(0.3 * rng.standard_normal((p.nr, 6)).astype(np.float32)).cuda()
+    a = torch.from_numpy(workloads.axis_nodes(p.nv, p.vmax).astype(np.float32)).cuda()
+    vx, vy, vz = torch.meshgrid(a, a, a, indexing="ij")
+    vx, vy, vz = vx.reshape(-1), vy.reshape(-1), vz.reshape(-1)
+    basis = torch.stack([torch.ones_like(vx), vx, vy, vz, vx * vx + vy * vy + vz * vz - 1.5,
+                         vx * vy])
+    h0 = coef @ basis
+    g = torch.Generator(device="cuda").manual_seed(7)
+    h0 += 0.01 * torch.randn(h0.shape, generator=g, device="cuda")
+    cav = binding.Cavity(p)
+    cav.set_state(h0, step=3)
+    cav.step(1)
+    out, step = cav.get_state()
+    assert step == 4
+    mom = cav.moments().cpu().numpy()
+    o = oracle.Oracle(**p.kwargs())
+    nx, ny = p.nx, p.ny
+    cells = [0, nx - 1, (ny - 1) * nx, nx * ny - 1, nx // 2, (ny - 1) * nx + nx // 3,
+             (ny // 2) * nx, (ny // 2) * nx + nx - 1] + list(rng.integers(0, nx * ny, 6))
+    for c in cells:
+        c = int(c)
+        ix, iy = c % nx, c // nx
+        sl = lambda cc: h0[cc].double().cpu().numpy()
+        ref, m = o.step_cell(c, sl(c), sl(c - 1) if ix > 0 else None,
+                             sl(c + 1) if ix < nx - 1 else None, sl(c - nx) if iy > 0 else None,
+                             sl(c + nx) if iy < ny - 1 else None, step=3)
+        got = out[c].double().cpu().numpy()
+        assert f_metric(o, got, ref) < 1e-5, c
+        assert np.allclose(mom[c], m, rtol=1e-4, atol=1e-5 * (1 + np.abs(m).max())), c
+
+
+# ---------------------------------------------------------------- API
+def test_moments_of_arbitrary_state():
+    p = CASES[1]
+    cav, o, h0 = make(p)
+    assert np.allclose(cav.moments().cpu().numpy(), o.moments(h0), rtol=1e-5, atol=1e-6)
+
+
+def test_lid_shear_matches_oracle():
+    p = CASES[2]
+    cav, o, h0 = make(p)
+    d = cav.lid_shear().cpu().numpy()
+    ref = o.lid_shear(h0, 0)
+    assert np.allclose(d, ref, rtol=1e-5, atol=1e-6 * np.abs(ref).max())
+
+
+def test_checkpoint_resume():
+    p = CASES[1]
+    a, o, h0 = make(p)
+    a.step(4)
+    b, _, _ = make(p)
+    b.step(2)
+    snap, st = b.get_state()
+    c = binding.Cavity(p)
+    c.set_state(snap.clone(), step=st)
+    c.step(2)
+    assert f_metric(o, state(a), state(c)) < 1e-6
+
+
+def test_stats_and_info():
+    p = CASES[6]
+    cav, o, h0 = make(p)
+    cav.step(3)
+    st = cav.stats()
+    assert st[0] == 3 and st[1] > 0 and st[4] >= 9
+    info = cav.get_info()
+    assert abs(info.dt - o.dt) <= 1e-15 * o.dt and info.nodes == p.nodes
+
+
+def test_errors_are_reported():
+    with pytest.raises(binding.BzError) as e:
+        binding.Cavity(workloads.small(nv=48, vmax=5.0))      # 48^3 slab > shared memory
+    assert e.value.status == binding.BZ_EUNSUPPORTED
+    with pytest.raises(binding.BzError) as e:
+        binding.Cavity(workloads.small(nt=0))
+    assert e.value.status == binding.BZ_EINVAL
+    cav = binding.Cavity(workloads.small())
+    os.environ["BZ_FAULT"] = "launch"
+    try:
+        with pytest.raises(binding.BzError) as e:
+            cav.step(1)
+        assert e.value.status == binding.BZ_ECUDA
+    finally:
+        del os.environ["BZ_FAULT"]
+    cav.step(1)

@@ -111,3 +111,18 @@ def test_lid_shear_closed_form():
         errs.append(abs(d[-1] - exact) / abs(exact))
     assert errs[0] < 0.04 and errs[2] < 0.003
     assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+def test_single_cell_step_matches_full_step():
+    """The per-cell oracle entry (used to check sampled cells of large runs)
+    reproduces the whole-cavity step bit for bit."""
+    o = oracle.Oracle(nx=5, ny=4, kn=1.0, nv=8, vmax=4.0, nt=300, seed=3, lid_u0=0.1)
+    p = workloads.small(nx=5, ny=4, nv=8)
+    h = workloads.warm_state(p, seed=2)
+    full, mom = o.step(h, 2)
+    for c in range(o.nr):
+        ix, iy = c % 5, c // 5
+        out, m = o.step_cell(c, h[c], h[c - 1] if ix > 0 else None, h[c + 1] if ix < 4 else None,
+                             h[c - 5] if iy > 0 else None, h[c + 5] if iy < 3 else None, step=2)
+        assert np.array_equal(out, full[c])
+        assert np.allclose(m, mom[c], rtol=1e-13, atol=1e-15)
