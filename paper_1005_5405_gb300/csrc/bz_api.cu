@@ -69,7 +69,7 @@ struct bz_handle {
     void *ht = nullptr;                 // h~ for the unfused path (lazy)
     void *pidx = nullptr;               // sample plan: node indices (16- or 32-bit)
     bool idx16 = true;
-    void *pW = nullptr;                 // sample plan: weights (state type)
+    void *pa = nullptr;                 // sample plan: (a, b, W) records of the gather phase
     void *ghost = nullptr;              // emitted ghost values per face
     double *nw = nullptr;               // wall densities per face
     double *shear = nullptr;            // lid face shear (nx)
@@ -146,6 +146,7 @@ template <typename R, typename I>
 bz_status launch_step(bz_handle *H, cudaStream_t s, bool fused, bool do_stream, bool do_collide)
 {
     using V4 = typename bzk::Idx4<I>::type;
+    using PA = bzk::PlanA<R, I>;
     Geo &g = H->g;
     R *hin = (R *)H->h[H->cur];
     R *hout = (R *)H->h[H->cur ^ 1];
@@ -157,13 +158,13 @@ bz_status launch_step(bz_handle *H, cudaStream_t s, bool fused, bool do_stream, 
     if (do_collide || fused) {
         ProfScope ps(H, 1, s);
         int pb = 256, pg = (g.nt + pb - 1) / pb;
-        bzk::k_plan<R, I><<<pg, pb, 0, s>>>(g, H->step, (V4 *)H->pidx, (R *)H->pW, nullptr, H->stats);
+        bzk::k_plan<R, I><<<pg, pb, 0, s>>>(g, H->step, (V4 *)H->pidx, (PA *)H->pa, nullptr, H->stats);
         BZ_LAUNCHED(H);
     }
     if (fused) {
         ProfScope ps(H, 2, s);
         bzk::k_cell<R, true, I><<<H->grid_cell_fused, H->threads, H->smem_cell, s>>>(
-            g, H->step, hin, (const R *)H->ghost, (const V4 *)H->pidx, (const R *)H->pW,
+            g, H->step, hin, (const R *)H->ghost, (const V4 *)H->pidx, (const PA *)H->pa,
             (R *)H->gw_global, hout, H->mom, H->stats, H->gw_in_smem);
         BZ_LAUNCHED(H);
         H->cur ^= 1;
@@ -188,7 +189,7 @@ bz_status launch_step(bz_handle *H, cudaStream_t s, bool fused, bool do_stream, 
     if (do_collide) {
         ProfScope ps(H, 2, s);
         bzk::k_cell<R, false, I><<<H->grid_cell, H->threads, H->smem_cell, s>>>(
-            g, H->step, hin, (const R *)H->ghost, (const V4 *)H->pidx, (const R *)H->pW,
+            g, H->step, hin, (const R *)H->ghost, (const V4 *)H->pidx, (const PA *)H->pa,
             (R *)H->gw_global, hout, H->mom, H->stats, H->gw_in_smem);
         BZ_LAUNCHED(H);
         H->cur ^= 1;
@@ -257,7 +258,7 @@ void clear_events(bz_handle *H)
 void release(bz_handle *H)
 {
     clear_events(H);
-    void *ptrs[] = {H->h[0], H->h[1], H->ht, H->pidx, H->pW, H->ghost, H->nw, H->shear,
+    void *ptrs[] = {H->h[0], H->h[1], H->ht, H->pidx, H->pa, H->ghost, H->nw, H->shear,
                     H->mom, H->gw_global, H->stats, H->flag, H->axv, H->axA, H->profile};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -365,6 +366,7 @@ bz_status bz_create(const bz_space *space, const bz_vel *vel, const bz_walls *wa
                 for (int a = 0; a < 5; ++a)
                     for (int b = 0; b < 5; ++b) g.G0[a * 5 + b] += w * p[a] * p[b];
             }
+    for (int a = 0; a < 25; ++a) g.G0f[a] = (float)g.G0[a];
 
     cudaError_t e = cudaGetDevice(&H->dev);
     if (e != cudaSuccess) {
@@ -385,7 +387,7 @@ bz_status bz_create(const bz_space *space, const bz_vel *vel, const bz_walls *wa
     BZ_STEP(dalloc(&H->h[1], nodes * H->esz));
     H->idx16 = g.nvt < 65535;
     BZ_STEP(dalloc(&H->pidx, (H->idx16 ? sizeof(ushort4) : sizeof(int4)) * (size_t)g.nt));
-    BZ_STEP(dalloc(&H->pW, H->esz * (size_t)g.nt));
+    BZ_STEP(dalloc(&H->pa, 16 * (size_t)g.nt));
     BZ_STEP(dalloc(&H->ghost, H->esz * (size_t)g.nfaces * N));
     BZ_STEP(dalloc(&H->nw, sizeof(double) * g.nfaces));
     BZ_STEP(dalloc(&H->shear, sizeof(double) * (g.nx + 1)));
@@ -601,9 +603,9 @@ bz_status bz_sample_plan(bz_handle *H, int64_t step, int32_t *idx, double *W, vo
     }
     int pb = 256, pg = (g.nt + pb - 1) / pb;
     if (H->dtype == BZ_F64)
-        bzk::k_plan<double, int><<<pg, pb, 0, s>>>(g, step, di, (double *)nullptr, dw, nullptr);
+        bzk::k_plan<double, int><<<pg, pb, 0, s>>>(g, step, di, (bzk::PlanA<double, int> *)nullptr, dw, nullptr);
     else
-        bzk::k_plan<float, int><<<pg, pb, 0, s>>>(g, step, di, (float *)nullptr, dw, nullptr);
+        bzk::k_plan<float, int><<<pg, pb, 0, s>>>(g, step, di, (bzk::PlanA<float, int> *)nullptr, dw, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(idx, di, sizeof(int4) * (size_t)g.nt, cudaMemcpyDefault, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(W, dw, sizeof(double) * (size_t)g.nt, cudaMemcpyDefault, s);

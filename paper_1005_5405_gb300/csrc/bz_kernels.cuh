@@ -42,6 +42,7 @@ struct Geo {
     double hn;                  // sum_{v_n>0} v_n A(v_n)
     double zsum;                // sum_z A(v_z)
     double G0[25];              // sum_j w_j psi_a psi_b, psi = (1, v, v^2)
+    float G0f[25];              // the same, rounded to float
 };
 
 // ---------------------------------------------------------------------
@@ -173,10 +174,53 @@ template <> struct Idx4<uint16_t> {
 __device__ __forceinline__ int idx_of(int v) { return v; }
 __device__ __forceinline__ int idx_of(unsigned short v) { return v == 0xFFFFu ? -1 : (int)v; }
 
+// What the gather phase of a cell needs per sample: the nodes of v and v1 and
+// the weight W (8 bytes for FP32 state with 16-bit indices).
+template <typename R, typename I> struct PlanA;
+template <> struct __align__(8) PlanA<float, uint16_t> {
+    uint32_t ab;
+    float W;
+    __device__ __forceinline__ int a() const { return idx_of((unsigned short)(ab & 0xFFFFu)); }
+    __device__ __forceinline__ int b() const { return idx_of((unsigned short)(ab >> 16)); }
+};
+template <> struct __align__(16) PlanA<double, uint16_t> {
+    uint32_t ab, pad;
+    double W;
+    __device__ __forceinline__ int a() const { return idx_of((unsigned short)(ab & 0xFFFFu)); }
+    __device__ __forceinline__ int b() const { return idx_of((unsigned short)(ab >> 16)); }
+};
+template <> struct __align__(16) PlanA<float, int> {
+    int ia, ib;
+    float W;
+    int pad;
+    __device__ __forceinline__ int a() const { return ia; }
+    __device__ __forceinline__ int b() const { return ib; }
+};
+template <> struct __align__(16) PlanA<double, int> {
+    int ia, ib;
+    double W;
+    __device__ __forceinline__ int a() const { return ia; }
+    __device__ __forceinline__ int b() const { return ib; }
+};
+
+template <typename R, typename I>
+__device__ __forceinline__ PlanA<R, I> make_plan_a(int a, int b, double W)
+{
+    PlanA<R, I> o;
+    if constexpr (sizeof(I) == 2) {
+        o.ab = (uint32_t)(a & 0xFFFF) | ((uint32_t)(b & 0xFFFF) << 16);
+    } else {
+        o.ia = a;
+        o.ib = b;
+    }
+    o.W = (R)W;
+    return o;
+}
+
 // One thread per sample; the set is shared by every cell of the step.
 template <typename R, typename I>
 __global__ void k_plan(Geo g, int64_t step, typename Idx4<I>::type *__restrict__ idx,
-                       R *__restrict__ W, double *__restrict__ Wd,
+                       PlanA<R, I> *__restrict__ pa, double *__restrict__ Wd,
                        unsigned long long *__restrict__ stats)
 {
     int l = blockIdx.x * blockDim.x + threadIdx.x;
@@ -185,7 +229,7 @@ __global__ void k_plan(Geo g, int64_t step, typename Idx4<I>::type *__restrict__
     if (act) {
         o = draw_sample(g, step, 0xFFFFFFFFu, (uint32_t)l);
         idx[l] = Idx4<I>::make(o.idx);
-        if (W) W[l] = (R)o.W;
+        if (pa) pa[l] = make_plan_a<R, I>(o.idx[0], o.idx[1], o.W);
         if (Wd) Wd[l] = o.W;
     }
     if (stats) {
@@ -205,6 +249,10 @@ template <int K, typename A>
 __device__ __forceinline__ void block_reduce(A (&v)[K], double *red /* kMaxWarps*kRedSlots */,
                                              double *tot /* K */)
 {
+    // Per-warp shuffle sums, then one thread per value adds the warp partials
+    // in the accumulator precision (no FP64 on the FP32 path: GB300's FP64
+    // rate is a small fraction of FP32) and stores the total as double.
+    A *ra = reinterpret_cast<A *>(red);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = (blockDim.x + 31) >> 5;
 #pragma unroll
@@ -212,13 +260,13 @@ __device__ __forceinline__ void block_reduce(A (&v)[K], double *red /* kMaxWarps
         A x = v[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
-        if (lane == 0) red[warp * kRedSlots + k] = (double)x;
+        if (lane == 0) ra[warp * kRedSlots + k] = x;
     }
     __syncthreads();
     if (threadIdx.x < K) {
-        double s = 0.0;
-        for (int w = 0; w < nwarps; ++w) s += red[w * kRedSlots + threadIdx.x];
-        tot[threadIdx.x] = s;
+        A s = A(0);
+        for (int w = 0; w < nwarps; ++w) s += ra[w * kRedSlots + threadIdx.x];
+        tot[threadIdx.x] = (double)s;
     }
     __syncthreads();
 }
@@ -402,16 +450,17 @@ struct AxisTab {       // per-axis tables in shared memory, N entries each
     R *A, *IA, *v, *v2, *v3, *v4, *Av, *Av2, *cx, *cu;
 };
 
-__device__ __noinline__ void chol_or_ge(double G[5][5], double b[5], double x[5], int *fallback)
+template <typename R>
+__device__ __noinline__ void chol_or_ge(R G[5][5], R b[5], R x[5], int *fallback)
 {
-    double L[5][5];
+    R L[5][5];
     bool ok = true;
     for (int i = 0; i < 5 && ok; ++i) {
         for (int j = 0; j <= i; ++j) {
-            double s = G[i][j];
+            R s = G[i][j];
             for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
             if (i == j) {
-                if (!(s > 0.0)) { ok = false; break; }
+                if (!(s > R(0))) { ok = false; break; }
                 L[i][i] = sqrt(s);
             } else {
                 L[i][j] = s / L[j][j];
@@ -419,14 +468,14 @@ __device__ __noinline__ void chol_or_ge(double G[5][5], double b[5], double x[5]
         }
     }
     if (ok) {
-        double y[5];
+        R y[5];
         for (int i = 0; i < 5; ++i) {
-            double s = b[i];
+            R s = b[i];
             for (int k = 0; k < i; ++k) s -= L[i][k] * y[k];
             y[i] = s / L[i][i];
         }
         for (int i = 4; i >= 0; --i) {
-            double s = y[i];
+            R s = y[i];
             for (int k = i + 1; k < 5; ++k) s -= L[k][i] * x[k];
             x[i] = s / L[i][i];
         }
@@ -434,7 +483,7 @@ __device__ __noinline__ void chol_or_ge(double G[5][5], double b[5], double x[5]
     }
     *fallback = 1;
     // Gaussian elimination with partial pivoting.
-    double A[5][6];
+    R A[5][6];
     for (int i = 0; i < 5; ++i) {
         for (int j = 0; j < 5; ++j) A[i][j] = G[i][j];
         A[i][5] = b[i];
@@ -443,20 +492,20 @@ __device__ __noinline__ void chol_or_ge(double G[5][5], double b[5], double x[5]
         int p = k;
         for (int i = k + 1; i < 5; ++i)
             if (fabs(A[i][k]) > fabs(A[p][k])) p = i;
-        if (A[p][k] == 0.0) {
-            for (int i = 0; i < 5; ++i) x[i] = 0.0;
+        if (A[p][k] == R(0)) {
+            for (int i = 0; i < 5; ++i) x[i] = R(0);
             return;
         }
         for (int j = 0; j < 6; ++j) {
-            double t = A[k][j]; A[k][j] = A[p][j]; A[p][j] = t;
+            R t = A[k][j]; A[k][j] = A[p][j]; A[p][j] = t;
         }
         for (int i = k + 1; i < 5; ++i) {
-            double m = A[i][k] / A[k][k];
+            R m = A[i][k] / A[k][k];
             for (int j = k; j < 6; ++j) A[i][j] -= m * A[k][j];
         }
     }
     for (int i = 4; i >= 0; --i) {
-        double s = A[i][5];
+        R s = A[i][5];
         for (int j = i + 1; j < 5; ++j) s -= A[i][j] * x[j];
         x[i] = s / A[i][i];
     }
@@ -467,25 +516,50 @@ __device__ __noinline__ void chol_or_ge(double G[5][5], double b[5], double x[5]
 // 1, vx, vy, vz, vx2, vy2, vz2, vxvy, vxvz, vyvz, vx v2, vy v2, vz v2, v4 and
 // P[14..18] the invariants 1, vx, vy, vz, v2 of the pre-collision N.  Solves
 // G mu = -(post - pre) with G = sum_j w_j (1 + eps h_c,j) psi psi^T.
-__device__ __noinline__ void correction_solve(const Geo &g, const double *P, double *mu,
+template <typename R>
+__device__ __noinline__ void correction_solve(const Geo &g, const double *Pd, double *mu,
                                               int *fallback)
 {
-    const double e = g.eps;
-    double post[5] = {P[0], P[1], P[2], P[3], P[4] + P[5] + P[6]};
-    double rhs[5];
+    // Solved in the state precision: G is close to the equilibrium Gram matrix
+    // (condition number ~30), so FP32 keeps the correction to ~1e-6 of itself.
+    R P[19];
+    for (int k = 0; k < 19; ++k) P[k] = (R)Pd[k];
+    const R e = (R)g.eps;
+    R post[5] = {P[0], P[1], P[2], P[3], P[4] + P[5] + P[6]};
+    R rhs[5];
     for (int a = 0; a < 5; ++a) rhs[a] = -(post[a] - P[14 + a]);
-    const double m[5][5] = {
+    const R m[5][5] = {
         {P[0], P[1], P[2], P[3], post[4]},
         {P[1], P[4], P[7], P[8], P[10]},
         {P[2], P[7], P[5], P[9], P[11]},
         {P[3], P[8], P[9], P[6], P[12]},
         {post[4], P[10], P[11], P[12], P[13]}};
-    double M[5][5];
+    R M[5][5];
     for (int a = 0; a < 5; ++a)
-        for (int b = 0; b < 5; ++b) M[a][b] = g.G0[a * 5 + b] + e * m[a][b];
-    double x[5];
-    chol_or_ge(M, rhs, x, fallback);
-    for (int a = 0; a < 5; ++a) mu[a] = x[a];
+        for (int b = 0; b < 5; ++b)
+            M[a][b] = (sizeof(R) == 8 ? (R)g.G0[a * 5 + b] : (R)g.G0f[a * 5 + b]) + e * m[a][b];
+    R x[5];
+    chol_or_ge<R>(M, rhs, x, fallback);
+    for (int a = 0; a < 5; ++a) mu[a] = (double)x[a];
+}
+
+// Eqs. densita..sforzi in V0 units from the ten sums m = sum w h {1, v_x,
+// v_y, v_z, v_x^2, v_y^2, v_z^2, v_x v_y, v_x v_z, v_y v_z}.
+template <typename R>
+__device__ __noinline__ void finalize_moments(const double *md, R e, double *o)
+{
+    R m[10];
+    for (int k = 0; k < 10; ++k) m[k] = (R)md[k];
+    R rho = m[0], n = R(1) + e * rho;
+    R u[3] = {m[1] / n, m[2] / n, m[3] / n};
+    o[0] = rho;
+    o[1] = u[0];
+    o[2] = u[1];
+    o[3] = u[2];
+    o[4] = ((R(2) / R(3)) * (m[4] + m[5] + m[6]) - rho) / n -
+           (R(2) * e / R(3)) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
+    for (int k = 0; k < 6; ++k) o[5 + k] = R(2) * m[4 + k] - R(2) * e * n * u[pa[k]] * u[pb[k]];
 }
 
 // Dynamic shared memory layout of the per-cell kernels.
@@ -536,7 +610,7 @@ __host__ __device__ inline size_t cell_smem_bytes(int nv, int nvt, int nt, bool 
 template <typename R, bool FUSED, typename I>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 k_cell(Geo g, int64_t step, const R *__restrict__ hin, const R *__restrict__ ghost,
-       const typename Idx4<I>::type *__restrict__ pidx, const R *__restrict__ pW,
+       const typename Idx4<I>::type *__restrict__ pidx, const PlanA<R, I> *__restrict__ pa,
        R *__restrict__ gw_global,
        R *__restrict__ hout, double *__restrict__ mom, unsigned long long *__restrict__ stats,
        int gw_in_smem)
@@ -621,30 +695,25 @@ k_cell(Geo g, int64_t step, const R *__restrict__ hin, const R *__restrict__ gho
         // ---- phase A: g_l W_l from the pre-collision values (Jacobi) -------
         // Plan entries are loaded four at a time to keep L2 requests in flight.
         {
-            using V4 = typename Idx4<I>::type;
             int l = t;
             for (; l + 3 * T < g.nt; l += 4 * T) {
-                V4 q[4];
-                R w[4];
+                PlanA<R, I> q[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) q[u] = pa[l + u * T];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    q[u] = pidx[l + u * T];
-                    w[u] = pW[l + u * T];
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int a = idx_of(q[u].x), b = idx_of(q[u].y);
+                    const int a = q[u].a(), b = q[u].b();
                     R ha = a >= 0 ? S.slab[a] : R(0);
                     R hb = b >= 0 ? S.slab[b] : R(0);
-                    gw[l + u * T] = (ha + hb + eps * ha * hb) * w[u];
+                    gw[l + u * T] = (ha + hb + eps * ha * hb) * q[u].W;
                 }
             }
             for (; l < g.nt; l += T) {
-                V4 q = pidx[l];
-                const int a = idx_of(q.x), b = idx_of(q.y);
+                const PlanA<R, I> q = pa[l];
+                const int a = q.a(), b = q.b();
                 R ha = a >= 0 ? S.slab[a] : R(0);
                 R hb = b >= 0 ? S.slab[b] : R(0);
-                gw[l] = (ha + hb + eps * ha * hb) * pW[l];
+                gw[l] = (ha + hb + eps * ha * hb) * q.W;
             }
         }
         __syncthreads();
@@ -736,13 +805,13 @@ k_cell(Geo g, int64_t step, const R *__restrict__ hin, const R *__restrict__ gho
         block_reduce<19, R>(acc, S.red, S.tot);
 
         // ---- 5x5 solve: G mu = -(post - pre), G = sum w (1 + eps h_c) psi psi
-        if (t == 0) correction_solve(g, S.tot, S.mu, &fallback);
+        if (t == 0) correction_solve<R>(g, S.tot, S.mu, &fallback);
         __syncthreads();
         {
-            const double mx = S.mu[1], m4 = S.mu[4];
+            const R mx = (R)S.mu[1], m4 = (R)S.mu[4];
             for (int i = t; i < N; i += T) {
-                double v = g.axv[i];
-                S.tab.cx[i] = (R)(mx * v + m4 * v * v);
+                const R v = S.tab.v[i];
+                S.tab.cx[i] = mx * v + m4 * S.tab.v2[i];
             }
         }
         __syncthreads();
@@ -756,8 +825,8 @@ k_cell(Geo g, int64_t step, const R *__restrict__ hin, const R *__restrict__ gho
             const int jy = p / N, jz = p % N;
             const R IAyz = S.tab.IA[jy] * S.tab.IA[jz];
             const R vy = S.tab.v[jy], vz = S.tab.v[jz];
-            const R ct = (R)(S.mu[0] + S.mu[2] * (double)vy + S.mu[3] * (double)vz +
-                             S.mu[4] * ((double)vy * vy + (double)vz * vz));
+            const R ct = (R)S.mu[0] + (R)S.mu[2] * vy + (R)S.mu[3] * vz +
+                         (R)S.mu[4] * (vy * vy + vz * vz);
             R t0 = R(0), t1 = R(0), t2 = R(0);
             for (int jx = 0; jx < N; ++jx) {
                 const int j = jx * N2 + p;
@@ -782,21 +851,7 @@ k_cell(Geo g, int64_t step, const R *__restrict__ hin, const R *__restrict__ gho
             mo[9] += Ayz * vy * vz * t0;
         }
         block_reduce<10, R>(mo, S.red, S.tot);
-        if (t == 0 && mom) {
-            const double *m = S.tot, e = g.eps;
-            double rho = m[0], n = 1.0 + e * rho;
-            double u[3] = {m[1] / n, m[2] / n, m[3] / n};
-            double *o = mom + (int64_t)c * 11;
-            o[0] = rho;
-            o[1] = u[0];
-            o[2] = u[1];
-            o[3] = u[2];
-            o[4] = ((2.0 / 3.0) * (m[4] + m[5] + m[6]) - rho) / n -
-                   (2.0 * e / 3.0) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-            const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
-            const double m2[6] = {m[4], m[5], m[6], m[7], m[8], m[9]};
-            for (int k = 0; k < 6; ++k) o[5 + k] = 2.0 * m2[k] - 2.0 * e * n * u[pa[k]] * u[pb[k]];
-        }
+        if (t == 0 && mom) finalize_moments<R>(S.tot, (R)g.eps, mom + (int64_t)c * 11);
         // red/tot reuse is protected by the barriers inside block_reduce; the
         // next cell's first writes to the slab happen after this point only.
         __syncthreads();
