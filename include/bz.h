@@ -115,7 +115,8 @@ typedef struct {
     int64_t step;           /* steps taken so far (time t = step * dt) */
     int32_t nr, nvt;        /* cells, velocity nodes */
     int32_t dtype;
-    int32_t threads_per_cell, smem_bytes;  /* collision kernel launch shape */
+    int32_t threads_per_cell, smem_bytes;  /* per-cell kernel launch shape */
+    int32_t kernel_variant;  /* 0: generic per-cell kernel; 1: FP32 4-node-vector kernel */
 } bz_info;
 
 /* Create a solver for the driven cavity.  Validates every argument
@@ -197,6 +198,13 @@ bz_status bz_philox(uint32_t k0, uint32_t k1, const uint32_t *ctr, int64_t n, ui
  * are host-side, Sec. 5.2); used by the benchmark. */
 bz_status bz_profile(bz_handle *h, int32_t enable);
 bz_status bz_profile_read(bz_handle *h, double ms[4], int64_t launches[4]);
+
+/* Phase trace of the FP32 per-cell kernel, recorded while bz_profile(h, 2)
+ * is on: SM clock (clock64) at the 9 phase barriers (cell start, after
+ * streaming, gather, N = w h~, scatter, correction sums, solve, write-back,
+ * cell end) of the first 8 cells of CTA 0 in the latest launch.  out: at
+ * least 72 int64, host; row-major [cell][phase].  BZ_ESTATE if not enabled. */
+bz_status bz_phase_clocks(bz_handle *h, int64_t *out, int32_t n);
 
 /* Thread-local text of the last failure on this thread ("" if none). */
 const char *bz_last_error(void);

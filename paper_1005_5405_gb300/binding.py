@@ -59,7 +59,8 @@ class bz_info(C.Structure):
                 ("dv", C.c_double), ("eps", C.c_double), ("kcoll", C.c_double),
                 ("nodes", C.c_int64), ("state_bytes", C.c_int64), ("step", C.c_int64),
                 ("nr", C.c_int32), ("nvt", C.c_int32), ("dtype", C.c_int32),
-                ("threads_per_cell", C.c_int32), ("smem_bytes", C.c_int32)]
+                ("threads_per_cell", C.c_int32), ("smem_bytes", C.c_int32),
+                ("kernel_variant", C.c_int32)]
 
 
 _H = C.c_void_p
@@ -81,6 +82,7 @@ _SIGNATURES = {
     "bz_philox": [C.c_uint32, C.c_uint32, _V, C.c_int64, _V],
     "bz_profile": [_H, C.c_int32],
     "bz_profile_read": [_H, C.POINTER(C.c_double), C.POINTER(C.c_int64)],
+    "bz_phase_clocks": [_H, C.POINTER(C.c_int64), C.c_int32],
 }
 
 _lib = None
@@ -228,8 +230,14 @@ class Cavity:
         check(load().bz_stats(self.h, out), "bz_stats")
         return list(out)
 
-    def profile(self, enable: bool):
-        check(load().bz_profile(self.h, 1 if enable else 0), "bz_profile")
+    def profile(self, enable):
+        """0 off; 1 (or True) per-kernel event timing; 2 also the phase trace."""
+        check(load().bz_profile(self.h, int(enable)), "bz_profile")
+
+    def phase_clocks(self):
+        out = (C.c_int64 * 72)()
+        check(load().bz_phase_clocks(self.h, out, 72), "bz_phase_clocks")
+        return np.array(list(out), dtype=np.int64).reshape(8, 9)
 
     def profile_read(self):
         """(ms, launches) per kernel class: walls, sampling, per-cell, streaming."""

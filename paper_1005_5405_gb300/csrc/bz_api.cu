@@ -6,6 +6,7 @@
 // validates arguments, builds per-axis tables once at creation and launches.
 #include "bz.h"
 #include "bz_kernels.cuh"
+#include "bz_cell4.cuh"
 
 #include <cuda_runtime.h>
 
@@ -87,6 +88,14 @@ struct bz_handle {
     long long launches = 0;
     bool prof = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
+    // FP32 fast path (bz_cell4.cuh)
+    bool fast = false;
+    long long *prof_clk = nullptr;      // phase trace of the per-cell kernel (bz_profile level 2)
+    bzk::Map4 map{};
+    int threads4 = 0, grid4f = 0, grid4c = 0;
+    size_t smem4 = 0;
+    int *sc_count = nullptr, *sc_cursor = nullptr, *sc_meta = nullptr;  // scatter-list sort
+    uint32_t *sc_ent = nullptr;
 };
 
 namespace {
@@ -142,6 +151,86 @@ struct ProfScope {
     }
 };
 
+// Launch the FP32 fast-path cell kernel; false when the handle does not use it.
+template <typename R>
+bool launch_cell4(bz_handle *H, cudaStream_t s, bool fused, const R *hin, R *hout)
+{
+    if constexpr (sizeof(R) != 4) {
+        return false;
+    } else {
+        if (!H->fast) return false;
+        const Geo &g = H->g;
+        const float *gh = (const float *)H->ghost;
+        const ushort4 *pi = (const ushort4 *)H->pidx;
+        const bzk::PlanA<float, uint16_t> *pa = (const bzk::PlanA<float, uint16_t> *)H->pa;
+        // Destination-sorted scatter list of this step's sample set.
+        {
+            ProfScope ps1(H, 1, s);
+            const int pb = 256, pg = (g.nt + pb - 1) / pb;
+            if (cudaMemsetAsync(H->sc_count, 0, sizeof(int) * g.nvt, s) != cudaSuccess) return true;
+            bzk::k_scatter_count<<<pg, pb, 0, s>>>(g.nt, pi, H->sc_count);
+            bzk::k_scatter_scan<<<1, 1024, 0, s>>>(g.nvt, H->threads4, H->sc_count, H->sc_cursor,
+                                                   H->sc_meta);
+            bzk::k_scatter_fill<<<pg, pb, 0, s>>>(g.nt, H->threads4, pi, H->sc_cursor, H->sc_meta,
+                                                  H->sc_ent);
+            H->launches += 3;
+        }
+        ProfScope ps(H, 2, s);
+        const int grid = fused ? H->grid4f : H->grid4c;
+        if (fused)
+            bzk::k_cell4<true><<<grid, H->threads4, H->smem4, s>>>(
+                g, H->map, hin, gh, pa, H->sc_ent, H->sc_meta, hout, H->mom, H->stats, H->prof_clk);
+        else
+            bzk::k_cell4<false><<<grid, H->threads4, H->smem4, s>>>(
+                g, H->map, hin, gh, pa, H->sc_ent, H->sc_meta, hout, H->mom, H->stats, H->prof_clk);
+        return true;
+    }
+}
+
+template <bool F>
+bz_status setup_cell4_kernel(bz_handle *H, int *occ)
+{
+    BZ_CUDA(cudaFuncSetAttribute(bzk::k_cell4<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)H->smem4));
+    BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, bzk::k_cell4<F>, H->threads4,
+                                                          H->smem4));
+    return BZ_OK;
+}
+
+// Decide whether the FP32 fast path applies and size its launch.
+bz_status configure_cell4(bz_handle *H)
+{
+    const Geo &g = H->g;
+    const int N = g.nv;
+    const char *force = getenv("BZ_KERNEL");
+    H->fast = false;
+    if (force && strcmp(force, "generic") == 0) return BZ_OK;
+    if (H->dtype != BZ_F32 || !H->idx16 || N % 4 != 0 || N < 12) return BZ_OK;
+    if (g.nt > 32768) return BZ_OK;                 // 15-bit sample index in the scatter list
+    if (bzk::cell4_smem_bytes(N, g.nvt, g.nt) > (size_t)H->smem_optin) return BZ_OK;
+    const int Q = N * N / 4;
+    int K = 1;
+    for (int k = 1; k <= N; ++k)
+        if (N % k == 0 && Q * k <= bzk::kMaxThreads) K = k;
+    const int T = (Q * K + 31) / 32 * 32;
+    H->map = bzk::Map4{Q, K, N / K};
+    H->threads4 = T;
+    H->smem4 = bzk::cell4_smem_bytes(N, g.nvt, g.nt);
+    int of = 0, oc = 0;
+    BZ_TRY(setup_cell4_kernel<true>(H, &of));
+    BZ_TRY(setup_cell4_kernel<false>(H, &oc));
+    if (of < 1 || oc < 1) return BZ_OK;
+    H->grid4f = std::min(g.nr, H->nsm * of);
+    H->grid4c = std::min(g.nr, H->nsm * oc);
+    BZ_TRY(dalloc(&H->sc_count, sizeof(int) * g.nvt));
+    BZ_TRY(dalloc(&H->sc_cursor, sizeof(int) * g.nvt));
+    BZ_TRY(dalloc(&H->sc_meta, sizeof(int) * 2));
+    BZ_TRY(dalloc(&H->sc_ent, sizeof(uint32_t) * ((size_t)4 * g.nt + T)));
+    H->fast = true;
+    H->g.swz = 1;
+    return BZ_OK;
+}
+
 template <typename R, typename I>
 bz_status launch_step(bz_handle *H, cudaStream_t s, bool fused, bool do_stream, bool do_collide)
 {
@@ -160,6 +249,12 @@ bz_status launch_step(bz_handle *H, cudaStream_t s, bool fused, bool do_stream, 
         int pb = 256, pg = (g.nt + pb - 1) / pb;
         bzk::k_plan<R, I><<<pg, pb, 0, s>>>(g, H->step, (V4 *)H->pidx, (PA *)H->pa, nullptr, H->stats);
         BZ_LAUNCHED(H);
+    }
+    if (fused && launch_cell4(H, s, true, hin, hout)) {
+        BZ_LAUNCHED(H);
+        H->cur ^= 1;
+        H->mom_valid = true;
+        return BZ_OK;
     }
     if (fused) {
         ProfScope ps(H, 2, s);
@@ -185,6 +280,12 @@ bz_status launch_step(bz_handle *H, cudaStream_t s, bool fused, bool do_stream, 
             return BZ_OK;
         }
         hin = dst;
+    }
+    if (do_collide && launch_cell4(H, s, false, hin, hout)) {
+        BZ_LAUNCHED(H);
+        H->cur ^= 1;
+        H->mom_valid = true;
+        return BZ_OK;
     }
     if (do_collide) {
         ProfScope ps(H, 2, s);
@@ -258,7 +359,7 @@ void clear_events(bz_handle *H)
 void release(bz_handle *H)
 {
     clear_events(H);
-    void *ptrs[] = {H->h[0], H->h[1], H->ht, H->pidx, H->pa, H->ghost, H->nw, H->shear,
+    void *ptrs[] = {H->sc_count, H->sc_cursor, H->sc_meta, H->sc_ent, H->prof_clk, H->h[0], H->h[1], H->ht, H->pidx, H->pa, H->ghost, H->nw, H->shear,
                     H->mom, H->gw_global, H->stats, H->flag, H->axv, H->axA, H->profile};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -401,6 +502,7 @@ bz_status bz_create(const bz_space *space, const bz_vel *vel, const bz_walls *wa
         BZ_STEP(configure_cell_kernel<double>(H));
     else
         BZ_STEP(configure_cell_kernel<float>(H));
+    BZ_STEP(configure_cell4(H));
 #undef BZ_STEP
     e = cudaMemcpy(H->axv, axv.data(), sizeof(double) * N, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(H->axA, axA.data(), sizeof(double) * N, cudaMemcpyHostToDevice);
@@ -570,8 +672,9 @@ bz_status bz_get_info(const bz_handle *H, bz_info *o)
     o->nr = g.nr;
     o->nvt = g.nvt;
     o->dtype = H->dtype;
-    o->threads_per_cell = H->threads;
-    o->smem_bytes = (int32_t)H->smem_cell;
+    o->threads_per_cell = H->fast ? H->threads4 : H->threads;
+    o->smem_bytes = (int32_t)(H->fast ? H->smem4 : H->smem_cell);
+    o->kernel_variant = H->fast ? 1 : 0;
     return BZ_OK;
 }
 
@@ -602,10 +705,12 @@ bz_status bz_sample_plan(bz_handle *H, int64_t step, int32_t *idx, double *W, vo
         return st;
     }
     int pb = 256, pg = (g.nt + pb - 1) / pb;
+    Geo gl = g;
+    gl.swz = 0;                       // logical node order for the caller
     if (H->dtype == BZ_F64)
-        bzk::k_plan<double, int><<<pg, pb, 0, s>>>(g, step, di, (bzk::PlanA<double, int> *)nullptr, dw, nullptr);
+        bzk::k_plan<double, int><<<pg, pb, 0, s>>>(gl, step, di, (bzk::PlanA<double, int> *)nullptr, dw, nullptr);
     else
-        bzk::k_plan<float, int><<<pg, pb, 0, s>>>(g, step, di, (bzk::PlanA<float, int> *)nullptr, dw, nullptr);
+        bzk::k_plan<float, int><<<pg, pb, 0, s>>>(gl, step, di, (bzk::PlanA<float, int> *)nullptr, dw, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(idx, di, sizeof(int4) * (size_t)g.nt, cudaMemcpyDefault, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(W, dw, sizeof(double) * (size_t)g.nt, cudaMemcpyDefault, s);
@@ -621,6 +726,24 @@ bz_status bz_profile(bz_handle *H, int32_t enable)
 {
     if (!H) return fail(BZ_EINVAL, "handle is NULL");
     H->prof = enable != 0;
+    if (enable >= 2 && !H->prof_clk) {
+        BZ_TRY(dalloc(&H->prof_clk, sizeof(long long) * bzk::kClkCells * bzk::kClkPhases));
+        BZ_CUDA(cudaMemset(H->prof_clk, 0, sizeof(long long) * bzk::kClkCells * bzk::kClkPhases));
+    } else if (enable < 2 && H->prof_clk) {
+        cudaDeviceSynchronize();
+        cudaFree(H->prof_clk);
+        H->prof_clk = nullptr;
+    }
+    return BZ_OK;
+}
+
+bz_status bz_phase_clocks(bz_handle *H, int64_t *out, int32_t n)
+{
+    if (!H || !out || n < bzk::kClkCells * bzk::kClkPhases) return fail(BZ_EINVAL, "invalid argument");
+    if (!H->prof_clk) return fail(BZ_ESTATE, "phase trace not enabled (bz_profile(h, 2))");
+    BZ_CUDA(cudaDeviceSynchronize());
+    BZ_CUDA(cudaMemcpy(out, H->prof_clk, sizeof(long long) * bzk::kClkCells * bzk::kClkPhases,
+                       cudaMemcpyDeviceToHost));
     return BZ_OK;
 }
 

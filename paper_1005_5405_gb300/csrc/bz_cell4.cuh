@@ -1,0 +1,587 @@
+// bz_cell4.cuh -- per-cell relaxation kernel, FP32 fast path.
+//
+// Same mathematics as k_cell (Eqs. streaming2D, monteCarloInt,
+// collision_step, rinorm_a, correzione, densita..sforzi) for FP32 states whose
+// velocity axis has a multiple of 4 nodes.  Thread t owns a "quad" of four
+// consecutive jz nodes of one (jy) row and a contiguous range of J jx-planes:
+//   q = t mod Q (Q = N^2/4 quads per plane), k = t div Q, jx in [kJ, kJ + J).
+// All slab traffic (global and shared) is 16-byte vectors and the per-jx
+// tables are read as broadcast float4s shared by the quad's four nodes.  The
+// scatter of Eq. monteCarloInt walks a destination-sorted list of the step's
+// terms (built once per step by k_scatter_*), so a thread adds the sum of a
+// node's terms with one shared-memory atomic instead of one per term.
+#pragma once
+
+#include "bz_kernels.cuh"
+
+namespace bzk {
+
+constexpr int kClkCells = 8;    // cells traced per launch (CTA 0)
+constexpr int kClkPhases = 9;   // stamps per cell
+
+struct Map4 {
+    int Q;   // quads per jx-plane (N^2 / 4)
+    int K;   // jx chunks
+    int J;   // jx planes per chunk (N / K)
+};
+
+// Shared-memory layout of k_cell4.
+struct Cell4Smem {
+    float *red;      // kMaxWarps * 32
+    double *tot;     // 32 (totf aliases its first 128 bytes)
+    double *mu;      // 8
+    float4 *conv;    // N: {A, v, v^2, 0}
+    float4 *gram;    // N: {v, v^2, v^3, v^4}
+    float4 *fin;     // N: {1/A, cx, A, A v}   (cx = mu_x v + mu_4 v^2, per cell)
+    float *Av2;      // N: A v^2
+    float *cu;       // N: v dt/dx
+    float *v;        // N
+    float *A;        // N
+    float *IA;       // N
+    int *rot;        // N: jx mod (N/4), the quad rotation of plane jx
+    float4 *slab4;   // N^3 / 4
+    float *gw;       // Nt: g_l W_l of the gather phase
+};
+
+__host__ __device__ inline size_t cell4_smem_bytes(int nv, int nvt, int nt)
+{
+    size_t off = sizeof(float) * kMaxWarps * 32 + sizeof(double) * (32 + 8);
+    off += sizeof(float4) * 3 * nv + sizeof(float) * 5 * nv + sizeof(int) * nv;
+    off = (off + 15) & ~(size_t)15;
+    off += sizeof(float) * nvt;
+    off += sizeof(float) * nt;
+    return off;
+}
+
+__device__ __forceinline__ Cell4Smem carve4(char *base, int N, int nvt)
+{
+    Cell4Smem s;
+    size_t off = 0;
+    s.red = (float *)(base + off); off += sizeof(float) * kMaxWarps * 32;
+    s.tot = (double *)(base + off); off += sizeof(double) * 32;
+    s.mu = (double *)(base + off); off += sizeof(double) * 8;
+    s.conv = (float4 *)(base + off); off += sizeof(float4) * N;
+    s.gram = (float4 *)(base + off); off += sizeof(float4) * N;
+    s.fin = (float4 *)(base + off); off += sizeof(float4) * N;
+    s.Av2 = (float *)(base + off); off += sizeof(float) * N;
+    s.cu = (float *)(base + off); off += sizeof(float) * N;
+    s.v = (float *)(base + off); off += sizeof(float) * N;
+    s.A = (float *)(base + off); off += sizeof(float) * N;
+    s.IA = (float *)(base + off); off += sizeof(float) * N;
+    s.rot = (int *)(base + off); off += sizeof(int) * N;
+    off = (off + 15) & ~(size_t)15;
+    s.slab4 = (float4 *)(base + off);
+    off += sizeof(float) * nvt;
+    s.gw = (float *)(base + off);
+    return s;
+}
+
+// Destination-sorted scatter list of a step (shared by every cell): every
+// valid (node, sample, sign) term of Eq. monteCarloInt as one 32-bit word
+// node << 16 | loss << 15 | l, sorted by node by a counting sort, and stored
+// so that thread t of the cell kernel reads its contiguous run of C words at
+// stride T (coalesced).  meta[0] = number of words E, meta[1] = C.
+__global__ void k_scatter_count(int nt, const ushort4 *__restrict__ pidx, int *__restrict__ count)
+{
+    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nt) return;
+    ushort4 q = pidx[l];
+    if (q.x != 0xFFFF) atomicAdd(count + q.x, 1);
+    if (q.y != 0xFFFF) atomicAdd(count + q.y, 1);
+    if (q.z != 0xFFFF) atomicAdd(count + q.z, 1);
+    if (q.w != 0xFFFF) atomicAdd(count + q.w, 1);
+}
+
+// Exclusive scan of the per-node counts (one CTA of 1024 threads).
+__global__ void __launch_bounds__(1024) k_scatter_scan(int nvt, int T, const int *__restrict__ count,
+                                                      int *__restrict__ cursor, int *__restrict__ meta)
+{
+    __shared__ int part[1024];
+    const int t = threadIdx.x, per = (nvt + 1023) / 1024;
+    const int b = t * per, e = min(nvt, b + per);
+    int s = 0;
+    for (int j = b; j < e; ++j) s += count[j];
+    part[t] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {       // Hillis-Steele inclusive scan
+        int v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int run = part[t] - s;
+    for (int j = b; j < e; ++j) {
+        cursor[j] = run;
+        run += count[j];
+    }
+    if (t == 1023) {
+        meta[0] = part[1023];
+        meta[1] = (part[1023] + T - 1) / T;
+    }
+}
+
+__global__ void k_scatter_fill(int nt, int T, const ushort4 *__restrict__ pidx,
+                               int *__restrict__ cursor, const int *__restrict__ meta,
+                               uint32_t *__restrict__ ent)
+{
+    int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nt) return;
+    const int C = meta[1];
+    const ushort4 q = pidx[l];
+    const unsigned short d[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (d[k] == 0xFFFF) continue;
+        const int pos = atomicAdd(cursor + d[k], 1);
+        const int tt = pos / C, i = pos - tt * C;
+        ent[(int64_t)i * T + tt] = ((uint32_t)d[k] << 16) | (k < 2 ? 0x8000u : 0u) | (uint32_t)l;
+    }
+}
+
+// G mu = -(post - pre) (Eqs. rinorm_a, correzione) solved in registers by
+// Gaussian elimination without pivoting, which is stable for the symmetric
+// positive definite Gram matrix; false if a pivot is not positive.
+__device__ __forceinline__ bool correction_spd(const Geo &g, const float *P, float *mu)
+{
+    const float e = (float)g.eps;
+    const float p4 = P[4] + P[5] + P[6];
+    const float m[5][5] = {
+        {P[0], P[1], P[2], P[3], p4},
+        {P[1], P[4], P[7], P[8], P[10]},
+        {P[2], P[7], P[5], P[9], P[11]},
+        {P[3], P[8], P[9], P[6], P[12]},
+        {p4, P[10], P[11], P[12], P[13]}};
+    const float post[5] = {P[0], P[1], P[2], P[3], p4};
+    float A[5][6];
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+#pragma unroll
+        for (int b = 0; b < 5; ++b) A[a][b] = g.G0f[a * 5 + b] + e * m[a][b];
+        A[a][5] = -(post[a] - P[14 + a]);
+    }
+#pragma unroll
+    for (int kk = 0; kk < 5; ++kk) {
+        const float piv = A[kk][kk];
+        if (!(piv > 0.f)) return false;
+        const float ip = 1.f / piv;
+#pragma unroll
+        for (int i = kk + 1; i < 5; ++i) {
+            const float f = A[i][kk] * ip;
+#pragma unroll
+            for (int j = kk + 1; j < 6; ++j) A[i][j] -= f * A[kk][j];
+        }
+    }
+#pragma unroll
+    for (int i = 4; i >= 0; --i) {
+        float s = A[i][5];
+#pragma unroll
+        for (int j = i + 1; j < 5; ++j) s -= A[i][j] * A[j][5];
+        A[i][5] = s / A[i][i];
+    }
+#pragma unroll
+    for (int a = 0; a < 5; ++a) mu[a] = A[a][5];
+    return true;
+}
+
+// Sum K (<= 32) per-thread values over the block.  Inside a warp the values
+// are transposed while being added (31 shuffles for any K <= 32, lane i ends
+// with the warp total of value i); one thread per value then adds the warp
+// totals.  Totals are stored in tot[0..K).
+template <int K>
+__device__ __forceinline__ void block_reduce4(float (&v)[K], float *red, float *tot)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+    float x[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) x[i] = i < K ? v[i] : 0.f;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const bool up = (lane & w) != 0;
+#pragma unroll
+        for (int i = 0; i < w; ++i) {
+            float send = up ? x[i] : x[i + w];
+            float keep = up ? x[i + w] : x[i];
+            x[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, w);
+        }
+    }
+    if (lane < K) red[warp * 32 + lane] = x[0];
+    __syncthreads();
+    if (threadIdx.x < K) {
+        float s = 0.f;
+        for (int w = 0; w < nwarps; ++w) s += red[w * 32 + threadIdx.x];
+        tot[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ float4 f4(float a) { return make_float4(a, a, a, a); }
+
+// One upwind update of a quad (Eq. streaming2D, both signs handled by |Cu|).
+__device__ __forceinline__ float4 upwind4(float4 h0, float4 hx, float4 hy, float ax, float ay)
+{
+    float4 o;
+    o.x = h0.x - ax * (h0.x - hx.x) - ay * (h0.x - hy.x);
+    o.y = h0.y - ax * (h0.y - hx.y) - ay * (h0.y - hy.y);
+    o.z = h0.z - ax * (h0.z - hx.z) - ay * (h0.z - hy.z);
+    o.w = h0.w - ax * (h0.w - hx.w) - ay * (h0.w - hy.w);
+    return o;
+}
+
+// Eqs. densita..sforzi from float sums (see finalize_moments).
+__device__ __noinline__ void finalize_moments_f(const float *m, float e, double *o)
+{
+    const float rho = m[0], n = 1.f + e * rho;
+    const float u[3] = {m[1] / n, m[2] / n, m[3] / n};
+    o[0] = rho;
+    o[1] = u[0];
+    o[2] = u[1];
+    o[3] = u[2];
+    o[4] = ((2.f / 3.f) * (m[4] + m[5] + m[6]) - rho) / n -
+           (2.f * e / 3.f) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const int pa[6] = {0, 1, 2, 0, 0, 1}, pb[6] = {0, 1, 2, 1, 2, 2};
+    for (int k = 0; k < 6; ++k) o[5 + k] = 2.f * m[4 + k] - 2.f * e * n * u[pa[k]] * u[pb[k]];
+}
+
+template <bool FUSED>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+k_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ ghost,
+        const PlanA<float, uint16_t> *__restrict__ pa, const uint32_t *__restrict__ ent,
+        const int *__restrict__ meta, float *__restrict__ hout, double *__restrict__ mom,
+        unsigned long long *__restrict__ stats, long long *__restrict__ clk)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    const int N = g.nv, N2 = N * N, nvt = g.nvt, T = blockDim.x, t = threadIdx.x;
+    Cell4Smem S = carve4(smem_raw, N, nvt);
+    (void)N2;
+    // Phase trace: SM clock at the barriers of the first kClkCells cells of CTA 0.
+    int ncell = 0;
+    auto stamp = [&](int ph) {
+        if (clk && blockIdx.x == 0 && t == 0 && ncell < kClkCells)
+            clk[ncell * kClkPhases + ph] = clock64();
+    };
+    const float eps = (float)g.eps;
+
+    for (int i = t; i < N; i += T) {
+        const double v = g.axv[i], A = g.axA[i];
+        S.conv[i] = make_float4((float)A, (float)v, (float)(v * v), 0.f);
+        S.gram[i] = make_float4((float)v, (float)(v * v), (float)(v * v * v), (float)(v * v * v * v));
+        S.fin[i] = make_float4((float)(1.0 / A), 0.f, (float)A, (float)(A * v));
+        S.Av2[i] = (float)(A * v * v);
+        S.cu[i] = (float)(v * g.dt / g.dx);
+        S.v[i] = (float)v;
+        S.A[i] = (float)A;
+        S.IA[i] = (float)(1.0 / A);
+        S.rot[i] = i % (N / 4);
+    }
+    __syncthreads();
+    float *totf = reinterpret_cast<float *>(S.tot);
+
+    // Quad of this thread.
+    const int Q = m.Q, nq = N / 4;
+    const int q = t % Q, kchunk = t / Q;
+    const bool active = kchunk < m.K;
+    const int jy = q / nq, jz0 = 4 * (q % nq);
+    const int jx0 = active ? kchunk * m.J : 0, jx1 = active ? jx0 + m.J : 0;
+    const float vy = S.v[jy];
+    float vz[4], Ayz[4], IAyz[4], qq[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        vz[i] = S.v[jz0 + i];
+        Ayz[i] = S.A[jy] * S.A[jz0 + i];
+        IAyz[i] = S.IA[jy] * S.IA[jz0 + i];
+        qq[i] = vy * vy + vz[i] * vz[i];
+    }
+    const float ry = (float)(g.dx / g.dy);
+    const int half = N / 2;
+    const int Q4 = Q;   // float4 stride of one jx-plane
+    // Shared-memory position of this thread's quad in plane jx: quads of a row
+    // are rotated by jx so that the jz-concentrated sample gathers spread over
+    // all banks (the plan's node indices use the same order).
+    const int qz = q % nq, rowq = jy * nq;
+    auto phys = [&](int jx) {
+        int r = qz + S.rot[jx];
+        r -= r >= nq ? nq : 0;
+        return jx * Q4 + rowq + r;
+    };
+    int fallback = 0;
+
+    for (int c = blockIdx.x; c < g.nr; c += gridDim.x, ++ncell) {
+        const int ix = c % g.nx, iy = c / g.nx;
+        const float4 *own4 = reinterpret_cast<const float4 *>(hin + (int64_t)c * nvt);
+        stamp(0);
+
+        // ---- slab <- h~ ------------------------------------------------------
+        if (active) {
+            if (FUSED) {
+                const float cuy = S.cu[jy] * ry, ay = fabsf(cuy);
+                const int64_t plane = (int64_t)nvt / 4;
+                if (ix > 0 && ix < g.nx - 1 && iy > 0 && iy < g.ny - 1) {
+                    // Interior cell: all upwind sources are neighbour slabs.
+                    const float4 *ys = cuy > 0.f ? own4 - (int64_t)g.nx * plane
+                                                 : own4 + (int64_t)g.nx * plane;
+                    const float4 *xr = own4 + plane, *xl = own4 - plane;
+                    const int e = min(jx1, half), b = max(jx0, half);
+#pragma unroll 4
+                    for (int jx = jx0; jx < e; ++jx) {
+                        const int o = jx * Q4 + q;
+                        const float4 h0 = own4[o], hx = xr[o], hy = ys[o];
+                        S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]), ay);
+                    }
+#pragma unroll 4
+                    for (int jx = b; jx < jx1; ++jx) {
+                        const int o = jx * Q4 + q;
+                        const float4 h0 = own4[o], hx = xl[o], hy = ys[o];
+                        S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]), ay);
+                    }
+                } else {
+                    const float4 *ys = nullptr;
+                    const float *yg = nullptr;
+                    if (cuy > 0.f) {
+                        if (iy > 0) ys = own4 - (int64_t)g.nx * plane;
+                        else yg = ghost + (2 * g.ny + ix) * N;
+                    } else {
+                        if (iy < g.ny - 1) ys = own4 + (int64_t)g.nx * plane;
+                        else yg = ghost + (2 * g.ny + g.nx + ix) * N;
+                    }
+                    for (int jx = jx0; jx < jx1; ++jx) {
+                        const int o = jx * Q4 + q;
+                        const float4 h0 = own4[o];
+                        float4 hx;
+                        if (jx < half)   // v_x < 0: right neighbour or right-wall ghost
+                            hx = ix < g.nx - 1 ? own4[plane + o] : f4(ghost[(g.ny + iy) * N + jy]);
+                        else             // v_x > 0: left neighbour or left-wall ghost
+                            hx = ix > 0 ? own4[o - plane] : f4(ghost[iy * N + jy]);
+                        const float4 hy = ys ? ys[o] : f4(yg[jx]);
+                        S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]), ay);
+                    }
+                }
+            } else {
+#pragma unroll 4
+                for (int jx = jx0; jx < jx1; ++jx) S.slab4[phys(jx)] = own4[jx * Q4 + q];
+            }
+        }
+        __syncthreads();
+
+        stamp(1);
+        // ---- phase A: g_l W_l on h~ (Jacobi) into shared memory ---------------
+        {
+            const float *slab = reinterpret_cast<const float *>(S.slab4);
+            int l = t;
+            for (; l + 15 * T < g.nt; l += 16 * T) {
+                PlanA<float, uint16_t> rec[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) rec[u] = pa[l + u * T];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int a = rec[u].a(), b = rec[u].b();
+                    const float ha = a >= 0 ? slab[a] : 0.f;
+                    const float hb = b >= 0 ? slab[b] : 0.f;
+                    S.gw[l + u * T] = (ha + hb + eps * ha * hb) * rec[u].W;
+                }
+            }
+            for (; l < g.nt; l += T) {
+                const PlanA<float, uint16_t> r = pa[l];
+                const int a = r.a(), b = r.b();
+                const float ha = a >= 0 ? slab[a] : 0.f;
+                const float hb = b >= 0 ? slab[b] : 0.f;
+                S.gw[l] = (ha + hb + eps * ha * hb) * r.W;
+            }
+        }
+        __syncthreads();
+
+        stamp(2);
+        // ---- N = w h~ in place, with the invariants of h~ ----------------------
+        float p0 = 0.f, p1 = 0.f, p3 = 0.f, p4 = 0.f;
+        if (active) {
+#pragma unroll 4
+            for (int jx = jx0; jx < jx1; ++jx) {
+                const int o = phys(jx);
+                float4 h = S.slab4[o];
+                const float4 cv = S.conv[jx];        // {A, v, v^2, -}
+                float n0 = h.x * (cv.x * Ayz[0]), n1 = h.y * (cv.x * Ayz[1]);
+                float n2 = h.z * (cv.x * Ayz[2]), n3 = h.w * (cv.x * Ayz[3]);
+                S.slab4[o] = make_float4(n0, n1, n2, n3);
+                const float sn = (n0 + n1) + (n2 + n3);
+                p0 += sn;
+                p1 += sn * cv.y;
+                p3 += n0 * vz[0] + n1 * vz[1] + n2 * vz[2] + n3 * vz[3];
+                p4 += n0 * (cv.z + qq[0]) + n1 * (cv.z + qq[1]) + n2 * (cv.z + qq[2]) +
+                      n3 * (cv.z + qq[3]);
+            }
+        }
+        __syncthreads();
+
+        stamp(3);
+        // ---- phase B: gains and losses (Eq. monteCarloInt) --------------------
+        // Each thread walks its run of the destination-sorted list, sums the
+        // terms of one node in a register and adds the sum with one atomic.
+        {
+            float *slabw = reinterpret_cast<float *>(S.slab4);
+            const int E = meta[0], C = meta[1];
+            const int base = t * C, n = max(0, min(C, E - base));
+            // Only the first and the last node of a run can be shared with the
+            // neighbouring runs; they are added atomically, the others plainly.
+            int cur = -1;
+            bool first = true;
+            float acc = 0.f;
+            auto flush = [&](bool shared) {
+                if (cur >= 0 && acc != 0.f) {
+                    if (shared) atomicAdd(slabw + cur, acc);
+                    else slabw[cur] += acc;
+                }
+            };
+            auto term = [&](uint32_t w) {
+                const int dest = (int)(w >> 16);
+                const float r = S.gw[w & 0x7FFFu];
+                if (dest != cur) {
+                    flush(first);
+                    first = cur < 0;
+                    cur = dest;
+                    acc = 0.f;
+                }
+                acc += (w & 0x8000u) ? -r : r;
+            };
+            int i = 0;
+            for (; i + 7 < n; i += 8) {
+                uint32_t w[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) w[u] = ent[(int64_t)(i + u) * T + t];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) term(w[u]);
+            }
+            for (; i < n; ++i) term(ent[(int64_t)i * T + t]);
+            flush(true);
+        }
+        __syncthreads();
+
+        stamp(4);
+        // ---- moments of N_c for the correction (post pass) --------------------
+        float acc[19];
+        {
+            float s[4][5];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int k = 0; k < 5; ++k) s[i][k] = 0.f;
+            if (active) {
+#pragma unroll 2
+                for (int jx = jx0; jx < jx1; ++jx) {
+                    float4 n = S.slab4[phys(jx)];
+                    const float4 gv = S.gram[jx];   // v, v^2, v^3, v^4
+                    const float nn[4] = {n.x, n.y, n.z, n.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        s[i][0] += nn[i];
+                        s[i][1] += nn[i] * gv.x;
+                        s[i][2] += nn[i] * gv.y;
+                        s[i][3] += nn[i] * gv.z;
+                        s[i][4] += nn[i] * gv.w;
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 19; ++k) acc[k] = 0.f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float z = vz[i], qi = qq[i];
+                const float s0 = s[i][0], s1 = s[i][1], s2 = s[i][2], s3 = s[i][3], s4 = s[i][4];
+                acc[0] += s0;
+                acc[1] += s1;
+                acc[2] += vy * s0;
+                acc[3] += z * s0;
+                acc[4] += s2;
+                acc[5] += vy * vy * s0;
+                acc[6] += z * z * s0;
+                acc[7] += vy * s1;
+                acc[8] += z * s1;
+                acc[9] += vy * z * s0;
+                acc[10] += s3 + qi * s1;
+                acc[11] += vy * (s2 + qi * s0);
+                acc[12] += z * (s2 + qi * s0);
+                acc[13] += s4 + 2.f * qi * s2 + qi * qi * s0;
+            }
+            acc[14] = p0;
+            acc[15] = p1;
+            acc[16] = vy * p0;
+            acc[17] = p3;
+            acc[18] = p4;
+        }
+        block_reduce4<19>(acc, S.red, totf);
+        stamp(5);
+
+        // ---- correction solve (thread 0) and per-cell tables --------------------
+        float *muf = reinterpret_cast<float *>(S.mu);
+        if (t == 0) {
+            if (!correction_spd(g, totf, muf)) {
+                double m8[5], Pd[19];
+                for (int a = 0; a < 19; ++a) Pd[a] = (double)totf[a];
+                correction_solve<float>(g, Pd, m8, &fallback);
+                for (int a = 0; a < 5; ++a) muf[a] = (float)m8[a];
+            }
+        }
+        __syncthreads();
+        const float mu0 = muf[0], mux = muf[1], muy = muf[2], muz = muf[3], mu4 = muf[4];
+        for (int i = t; i < N; i += T) S.fin[i].y = mux * S.v[i] + mu4 * S.v[i] * S.v[i];
+        __syncthreads();
+        stamp(6);
+
+        // ---- corrected write-back and output moments ---------------------------
+        float mo[10];
+        {
+            float tt[4][3];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) tt[i][0] = tt[i][1] = tt[i][2] = 0.f;
+            float ct[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ct[i] = mu0 + muy * vy + muz * vz[i] + mu4 * qq[i];
+            if (active) {
+                float4 *dst4 = reinterpret_cast<float4 *>(hout + (int64_t)c * nvt);
+#pragma unroll 2
+                for (int jx = jx0; jx < jx1; ++jx) {
+                    const int o = jx * Q4 + q;
+                    float4 n = S.slab4[phys(jx)];
+                    const float4 fv = S.fin[jx];        // 1/A, cx, A, A v
+                    const float av2 = S.Av2[jx];
+                    const float nn[4] = {n.x, n.y, n.z, n.w};
+                    float hn[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float hc = nn[i] * (fv.x * IAyz[i]);
+                        const float corr = ct[i] + fv.y;
+                        hn[i] = hc + (1.f + eps * hc) * corr;
+                        tt[i][0] += hn[i] * fv.z;
+                        tt[i][1] += hn[i] * fv.w;
+                        tt[i][2] += hn[i] * av2;
+                    }
+                    dst4[o] = make_float4(hn[0], hn[1], hn[2], hn[3]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 10; ++k) mo[k] = 0.f;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float a = Ayz[i], z = vz[i];
+                const float t0 = a * tt[i][0], t1 = a * tt[i][1], t2 = a * tt[i][2];
+                mo[0] += t0;
+                mo[1] += t1;
+                mo[2] += vy * t0;
+                mo[3] += z * t0;
+                mo[4] += t2;
+                mo[5] += vy * vy * t0;
+                mo[6] += z * z * t0;
+                mo[7] += vy * t1;
+                mo[8] += z * t1;
+                mo[9] += vy * z * t0;
+            }
+        }
+        stamp(7);
+        block_reduce4<10>(mo, S.red, totf);
+        if (t == 0 && mom) finalize_moments_f(totf, eps, mom + (int64_t)c * 11);
+        __syncthreads();
+        stamp(8);
+    }
+    if (fallback && stats) atomicAdd(stats + 3, 1ull);
+}
+
+}  // namespace bzk

@@ -43,6 +43,7 @@ struct Geo {
     double zsum;                // sum_z A(v_z)
     double G0[25];              // sum_j w_j psi_a psi_b, psi = (1, v, v^2)
     float G0f[25];              // the same, rounded to float
+    int swz;                    // plan node indices in the quad-rotated shared-memory order
 };
 
 // ---------------------------------------------------------------------
@@ -228,6 +229,20 @@ __global__ void k_plan(Geo g, int64_t step, typename Idx4<I>::type *__restrict__
     bool act = l < g.nt;
     if (act) {
         o = draw_sample(g, step, 0xFFFFFFFFu, (uint32_t)l);
+        if (g.swz) {
+            // Shared-memory order of the FP32 vector kernel: within each
+            // (jx, jy) row the quads of four jz nodes are rotated by jx.
+            const int N = g.nv, nq = N / 4;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int j = o.idx[k];
+                if (j < 0) continue;
+                const int jx = j / (N * N), jz = j % N, row = j - jz;
+                int r = jz / 4 + jx % nq;
+                if (r >= nq) r -= nq;
+                o.idx[k] = row + 4 * r + (jz & 3);
+            }
+        }
         idx[l] = Idx4<I>::make(o.idx);
         if (pa) pa[l] = make_plan_a<R, I>(o.idx[0], o.idx[1], o.W);
         if (Wd) Wd[l] = o.W;

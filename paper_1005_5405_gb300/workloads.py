@@ -105,6 +105,28 @@ def axis_nodes(nv: int, vmax: float) -> np.ndarray:
     return -vmax + (np.arange(nv) + 0.5) * dv
 
 
+def warm_state_device(p: Problem, seed: int = 7, noise: float = 0.01, torch=None):
+    """The same kind of state as `warm_state`, built on the current CUDA
+    device with PyTorch (for grids too large to build on the host).  The
+    per-cell coefficients come from numpy's seeded generator; the per-node
+    noise from a seeded torch generator.  Returns a (nr, nv^3) tensor in the
+    problem's state dtype."""
+    if torch is None:
+        import torch
+    dt = torch.float64 if p.dtype == "f64" else torch.float32
+    rng = np.random.default_rng(seed)
+    coef = torch.from_numpy(0.3 * rng.standard_normal((p.nr, 6))).to(dt).cuda()
+    a = torch.from_numpy(axis_nodes(p.nv, p.vmax)).to(dt).cuda()
+    vx, vy, vz = torch.meshgrid(a, a, a, indexing="ij")
+    vx, vy, vz = vx.reshape(-1), vy.reshape(-1), vz.reshape(-1)
+    basis = torch.stack([torch.ones_like(vx), vx, vy, vz, vx * vx + vy * vy + vz * vz - 1.5,
+                         vx * vy])
+    h = coef @ basis
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    h += noise * torch.randn(h.shape, generator=gen, device="cuda", dtype=dt)
+    return h
+
+
 def warm_state(p: Problem, seed: int = 7, noise: float = 0.01) -> np.ndarray:
     """Seeded smooth-plus-noise deviational state h0[cell, node] (float64).
 

@@ -108,7 +108,7 @@ def test_stream_matches_oracle(p):
 
 
 @pytest.mark.parametrize("p", CASES, ids=IDS)
-def test_collide_matches_oracle(p):
+def test_collide_matches_oracle(p, kernel):
     cav, o, h0 = make(p)
     cav.step_ex(1, binding.BZ_DO_COLLIDE)
     h_o, mom_o = o.collide(h0, step=0)
@@ -117,9 +117,22 @@ def test_collide_matches_oracle(p):
     assert np.allclose(mom_g, mom_o, rtol=1e-4, atol=1e-6 * (1 + np.abs(mom_o).max()))
 
 
+@pytest.fixture(params=["auto", "generic"])
+def kernel(request, monkeypatch):
+    """Run a test with the library's own choice of per-cell kernel (the FP32
+    4-node-vector kernel where it applies) and with the generic kernel."""
+    if request.param == "generic":
+        monkeypatch.setenv("BZ_KERNEL", "generic")
+    else:
+        monkeypatch.delenv("BZ_KERNEL", raising=False)
+    return request.param
+
+
 @pytest.mark.parametrize("p", CASES, ids=IDS)
-def test_fused_step_matches_oracle(p):
+def test_fused_step_matches_oracle(p, kernel):
     cav, o, h0 = make(p)
+    if kernel == "generic":
+        assert cav.get_info().kernel_variant == 0
     h_o = h0
     for n in range(3):
         cav.step(1)
@@ -246,6 +259,13 @@ def test_checkpoint_resume():
     c.set_state(snap.clone(), step=st)
     c.step(2)
     assert f_metric(o, state(a), state(c)) < 1e-6
+
+
+def test_fast_kernel_is_selected_for_fp32_quads():
+    for nv, expect in ((32, 1), (24, 1), (16, 1), (12, 1), (10, 0), (8, 0)):
+        p = workloads.small(nx=2, ny=2, nv=nv, vmax=4.0, nt=2000)
+        assert binding.Cavity(p).get_info().kernel_variant == expect, nv
+    assert binding.Cavity(workloads.small(nv=12, dtype="f64")).get_info().kernel_variant == 0
 
 
 def test_stats_and_info():
