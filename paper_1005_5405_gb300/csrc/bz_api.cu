@@ -92,7 +92,7 @@ struct bz_handle {
     bool fast = false;
     long long *prof_clk = nullptr;      // phase trace of the per-cell kernel (bz_profile level 2)
     bzk::Map4 map{};
-    int threads4 = 0, grid4f = 0, grid4c = 0;
+    int threads4 = 0, grid4f = 0, grid4c = 0, maxt4 = 1024;
     size_t smem4 = 0;
     int *sc_count = nullptr, *sc_cursor = nullptr, *sc_meta = nullptr;  // scatter-list sort
     uint32_t *sc_ent = nullptr;
@@ -177,22 +177,26 @@ bool launch_cell4(bz_handle *H, cudaStream_t s, bool fused, const R *hin, R *hou
         }
         ProfScope ps(H, 2, s);
         const int grid = fused ? H->grid4f : H->grid4c;
-        if (fused)
-            bzk::k_cell4<true><<<grid, H->threads4, H->smem4, s>>>(
-                g, H->map, hin, gh, pa, H->sc_ent, H->sc_meta, hout, H->mom, H->stats, H->prof_clk);
-        else
-            bzk::k_cell4<false><<<grid, H->threads4, H->smem4, s>>>(
-                g, H->map, hin, gh, pa, H->sc_ent, H->sc_meta, hout, H->mom, H->stats, H->prof_clk);
+#define BZ_C4(F, M)                                                                           \
+    bzk::k_cell4<F, M><<<grid, H->threads4, H->smem4, s>>>(g, H->map, hin, gh, pa, H->sc_ent, \
+                                                          H->sc_meta, hout, H->mom, H->stats,   \
+                                                          H->prof_clk)
+        if (H->maxt4 == 512) {
+            if (fused) BZ_C4(true, 512); else BZ_C4(false, 512);
+        } else {
+            if (fused) BZ_C4(true, 1024); else BZ_C4(false, 1024);
+        }
+#undef BZ_C4
         return true;
     }
 }
 
-template <bool F>
+template <bool F, int M>
 bz_status setup_cell4_kernel(bz_handle *H, int *occ)
 {
-    BZ_CUDA(cudaFuncSetAttribute(bzk::k_cell4<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    BZ_CUDA(cudaFuncSetAttribute(bzk::k_cell4<F, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)H->smem4));
-    BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, bzk::k_cell4<F>, H->threads4,
+    BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, bzk::k_cell4<F, M>, H->threads4,
                                                           H->smem4));
     return BZ_OK;
 }
@@ -208,17 +212,28 @@ bz_status configure_cell4(bz_handle *H)
     if (H->dtype != BZ_F32 || !H->idx16 || N % 4 != 0 || N < 12) return BZ_OK;
     if (g.nt > 32768) return BZ_OK;                 // 15-bit sample index in the scatter list
     if (bzk::cell4_smem_bytes(N, g.nvt, g.nt) > (size_t)H->smem_optin) return BZ_OK;
+    // Threads per CTA: up to 1024 (64 registers each) or, with
+    // BZ_CELL_THREADS=512, up to 512 with twice the registers per thread.
+    const char *ct = getenv("BZ_CELL_THREADS");
+    const int maxt = (ct && atoi(ct) == 512) ? 512 : 1024;
     const int Q = N * N / 4;
+    if (Q > maxt) return BZ_OK;
     int K = 1;
     for (int k = 1; k <= N; ++k)
-        if (N % k == 0 && Q * k <= bzk::kMaxThreads) K = k;
+        if (N % k == 0 && Q * k <= maxt) K = k;
     const int T = (Q * K + 31) / 32 * 32;
     H->map = bzk::Map4{Q, K, N / K};
     H->threads4 = T;
+    H->maxt4 = maxt;
     H->smem4 = bzk::cell4_smem_bytes(N, g.nvt, g.nt);
     int of = 0, oc = 0;
-    BZ_TRY(setup_cell4_kernel<true>(H, &of));
-    BZ_TRY(setup_cell4_kernel<false>(H, &oc));
+    if (maxt == 512) {
+        BZ_TRY((setup_cell4_kernel<true, 512>(H, &of)));
+        BZ_TRY((setup_cell4_kernel<false, 512>(H, &oc)));
+    } else {
+        BZ_TRY((setup_cell4_kernel<true, 1024>(H, &of)));
+        BZ_TRY((setup_cell4_kernel<false, 1024>(H, &oc)));
+    }
     if (of < 1 || oc < 1) return BZ_OK;
     H->grid4f = std::min(g.nr, H->nsm * of);
     H->grid4c = std::min(g.nr, H->nsm * oc);
@@ -439,6 +454,7 @@ bz_status bz_create(const bz_space *space, const bz_vel *vel, const bz_walls *wa
     g.lid_u0 = walls->lid_u0;
     g.lid_amp = walls->lid_amp;
     g.lid_period = walls->lid_period;
+    g.strip = g.nx >= 16 ? 8 : g.nx;
     H->dtype = params->dtype;
     H->esz = params->dtype == BZ_F64 ? 8 : 4;
 

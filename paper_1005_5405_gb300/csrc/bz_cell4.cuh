@@ -39,6 +39,9 @@ struct Cell4Smem {
     float *A;        // N
     float *IA;       // N
     int *rot;        // N: jx mod (N/4), the quad rotation of plane jx
+    float4 *vzq;     // N/4: v of the four jz nodes of quad column qz
+    float4 *Azq;     // N/4: A of those nodes
+    float4 *IAzq;    // N/4: 1/A of those nodes
     float4 *slab4;   // N^3 / 4
     float *gw;       // Nt: g_l W_l of the gather phase
 };
@@ -48,6 +51,7 @@ __host__ __device__ inline size_t cell4_smem_bytes(int nv, int nvt, int nt)
     size_t off = sizeof(float) * kMaxWarps * 32 + sizeof(double) * (32 + 8);
     off += sizeof(float4) * 3 * nv + sizeof(float) * 5 * nv + sizeof(int) * nv;
     off = (off + 15) & ~(size_t)15;
+    off += sizeof(float4) * 3 * (nv / 4);
     off += sizeof(float) * nvt;
     off += sizeof(float) * nt;
     return off;
@@ -70,6 +74,9 @@ __device__ __forceinline__ Cell4Smem carve4(char *base, int N, int nvt)
     s.IA = (float *)(base + off); off += sizeof(float) * N;
     s.rot = (int *)(base + off); off += sizeof(int) * N;
     off = (off + 15) & ~(size_t)15;
+    s.vzq = (float4 *)(base + off); off += sizeof(float4) * (N / 4);
+    s.Azq = (float4 *)(base + off); off += sizeof(float4) * (N / 4);
+    s.IAzq = (float4 *)(base + off); off += sizeof(float4) * (N / 4);
     s.slab4 = (float4 *)(base + off);
     off += sizeof(float) * nvt;
     s.gw = (float *)(base + off);
@@ -243,8 +250,8 @@ __device__ __noinline__ void finalize_moments_f(const float *m, float e, double 
     for (int k = 0; k < 6; ++k) o[5 + k] = 2.f * m[4 + k] - 2.f * e * n * u[pa[k]] * u[pb[k]];
 }
 
-template <bool FUSED>
-__global__ void __launch_bounds__(kMaxThreads, 1)
+template <bool FUSED, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
 k_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ ghost,
         const PlanA<float, uint16_t> *__restrict__ pa, const uint32_t *__restrict__ ent,
         const int *__restrict__ meta, float *__restrict__ hout, double *__restrict__ mom,
@@ -275,6 +282,12 @@ k_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ 
         S.rot[i] = i % (N / 4);
     }
     __syncthreads();
+    for (int i = t; i < N / 4; i += T) {
+        S.vzq[i] = make_float4(S.v[4 * i], S.v[4 * i + 1], S.v[4 * i + 2], S.v[4 * i + 3]);
+        S.Azq[i] = make_float4(S.A[4 * i], S.A[4 * i + 1], S.A[4 * i + 2], S.A[4 * i + 3]);
+        S.IAzq[i] = make_float4(S.IA[4 * i], S.IA[4 * i + 1], S.IA[4 * i + 2], S.IA[4 * i + 3]);
+    }
+    __syncthreads();
     float *totf = reinterpret_cast<float *>(S.tot);
 
     // Quad of this thread.
@@ -283,15 +296,22 @@ k_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ 
     const bool active = kchunk < m.K;
     const int jy = q / nq, jz0 = 4 * (q % nq);
     const int jx0 = active ? kchunk * m.J : 0, jx1 = active ? jx0 + m.J : 0;
-    const float vy = S.v[jy];
-    float vz[4], Ayz[4], IAyz[4], qq[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        vz[i] = S.v[jz0 + i];
-        Ayz[i] = S.A[jy] * S.A[jz0 + i];
-        IAyz[i] = S.IA[jy] * S.IA[jz0 + i];
-        qq[i] = vy * vy + vz[i] * vz[i];
-    }
+    (void)jz0;
+    // Per-node constants of the quad (v_z, A_y A_z, 1/(A_y A_z), v_y^2 + v_z^2)
+    // are re-read from shared tables inside each pass rather than kept live
+    // across the whole cell: registers are the binding limit at 1024 threads.
+#define QUAD_CONSTS                                                                  \
+    const float vy = S.v[jy];                                                        \
+    float vz[4], Ayz[4], IAyz[4], qq[4];                                             \
+    {                                                                                \
+        const float4 z4 = S.vzq[qz], a4 = S.Azq[qz], i4 = S.IAzq[qz];                \
+        const float ay_ = S.A[jy], iay_ = S.IA[jy];                                  \
+        vz[0] = z4.x; vz[1] = z4.y; vz[2] = z4.z; vz[3] = z4.w;                      \
+        Ayz[0] = ay_ * a4.x; Ayz[1] = ay_ * a4.y; Ayz[2] = ay_ * a4.z; Ayz[3] = ay_ * a4.w; \
+        IAyz[0] = iay_ * i4.x; IAyz[1] = iay_ * i4.y; IAyz[2] = iay_ * i4.z; IAyz[3] = iay_ * i4.w; \
+        for (int i_ = 0; i_ < 4; ++i_) qq[i_] = vy * vy + vz[i_] * vz[i_];          \
+    }                                                                                \
+    (void)IAyz; (void)Ayz; (void)qq; (void)vz
     const float ry = (float)(g.dx / g.dy);
     const int half = N / 2;
     const int Q4 = Q;   // float4 stride of one jx-plane
@@ -306,7 +326,8 @@ k_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ 
     };
     int fallback = 0;
 
-    for (int c = blockIdx.x; c < g.nr; c += gridDim.x, ++ncell) {
+    for (int kc = blockIdx.x; kc < g.nr; kc += gridDim.x, ++ncell) {
+        const int c = cell_of(g, kc);
         const int ix = c % g.nx, iy = c / g.nx;
         const float4 *own4 = reinterpret_cast<const float4 *>(hin + (int64_t)c * nvt);
         stamp(0);
@@ -394,6 +415,7 @@ k_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ 
         // ---- N = w h~ in place, with the invariants of h~ ----------------------
         float p0 = 0.f, p1 = 0.f, p3 = 0.f, p4 = 0.f;
         if (active) {
+            QUAD_CONSTS;
 #pragma unroll 4
             for (int jx = jx0; jx < jx1; ++jx) {
                 const int o = phys(jx);
@@ -431,9 +453,8 @@ k_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ 
                     else slabw[cur] += acc;
                 }
             };
-            auto term = [&](uint32_t w) {
+            auto term = [&](uint32_t w, float r) {
                 const int dest = (int)(w >> 16);
-                const float r = S.gw[w & 0x7FFFu];
                 if (dest != cur) {
                     flush(first);
                     first = cur < 0;
@@ -445,12 +466,18 @@ k_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ 
             int i = 0;
             for (; i + 7 < n; i += 8) {
                 uint32_t w[8];
+                float r[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) w[u] = ent[(int64_t)(i + u) * T + t];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) term(w[u]);
+                for (int u = 0; u < 8; ++u) r[u] = S.gw[w[u] & 0x7FFFu];   // before any flush
+#pragma unroll
+                for (int u = 0; u < 8; ++u) term(w[u], r[u]);
             }
-            for (; i < n; ++i) term(ent[(int64_t)i * T + t]);
+            for (; i < n; ++i) {
+                const uint32_t w = ent[(int64_t)i * T + t];
+                term(w, S.gw[w & 0x7FFFu]);
+            }
             flush(true);
         }
         __syncthreads();
@@ -459,6 +486,7 @@ k_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ 
         // ---- moments of N_c for the correction (post pass) --------------------
         float acc[19];
         {
+            QUAD_CONSTS;
             float s[4][5];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
@@ -529,6 +557,7 @@ k_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ 
         // ---- corrected write-back and output moments ---------------------------
         float mo[10];
         {
+            QUAD_CONSTS;
             float tt[4][3];
 #pragma unroll
             for (int i = 0; i < 4; ++i) tt[i][0] = tt[i][1] = tt[i][2] = 0.f;

@@ -44,7 +44,23 @@ struct Geo {
     double G0[25];              // sum_j w_j psi_a psi_b, psi = (1, v, v^2)
     float G0f[25];              // the same, rounded to float
     int swz;                    // plan node indices in the quad-rotated shared-memory order
+    int strip;                  // cells are visited in column strips of this width
 };
+
+// Visiting order of the cells by the persistent per-cell kernels: column
+// strips of width g.strip, row by row inside a strip, so that the cells in
+// flight at any time form a compact block and the upwind neighbour slabs
+// (left/right and below/above) are read from L2 rather than HBM.
+__device__ __forceinline__ int cell_of(const Geo &g, int k)
+{
+    const int S = g.strip, full = g.nx / S, inFull = full * S * g.ny;
+    if (k < inFull) {
+        const int s = k / (S * g.ny), r = k - s * S * g.ny;
+        return (r / S) * g.nx + s * S + r % S;
+    }
+    const int R = g.nx - full * S, kk = k - inFull;
+    return (kk / R) * g.nx + full * S + kk % R;
+}
 
 // ---------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11)
@@ -652,7 +668,8 @@ k_cell(Geo g, int64_t step, const R *__restrict__ hin, const R *__restrict__ gho
     const R ry = (R)(g.dx / g.dy);
     int fallback = 0;
 
-    for (int c = blockIdx.x; c < g.nr; c += gridDim.x) {
+    for (int kc = blockIdx.x; kc < g.nr; kc += gridDim.x) {
+        const int c = cell_of(g, kc);
         const int ix = c % g.nx, iy = c / g.nx;
         // ---- fill the slab with h~ ----------------------------------------
         if (FUSED) {

@@ -117,14 +117,17 @@ def test_collide_matches_oracle(p, kernel):
     assert np.allclose(mom_g, mom_o, rtol=1e-4, atol=1e-6 * (1 + np.abs(mom_o).max()))
 
 
-@pytest.fixture(params=["auto", "generic"])
+@pytest.fixture(params=["auto", "t512", "generic"])
 def kernel(request, monkeypatch):
     """Run a test with the library's own choice of per-cell kernel (the FP32
-    4-node-vector kernel where it applies) and with the generic kernel."""
+    4-node-vector kernel where it applies), with that kernel in its 512-thread
+    shape, and with the generic kernel."""
+    monkeypatch.delenv("BZ_KERNEL", raising=False)
+    monkeypatch.delenv("BZ_CELL_THREADS", raising=False)
     if request.param == "generic":
         monkeypatch.setenv("BZ_KERNEL", "generic")
-    else:
-        monkeypatch.delenv("BZ_KERNEL", raising=False)
+    elif request.param == "t512":
+        monkeypatch.setenv("BZ_CELL_THREADS", "512")
     return request.param
 
 
