@@ -206,6 +206,41 @@ bz_status bz_profile_read(bz_handle *h, double ms[4], int64_t launches[4]);
  * least 72 int64, host; row-major [cell][phase].  BZ_ESTATE if not enabled. */
 bz_status bz_phase_clocks(bz_handle *h, int64_t *out, int32_t n);
 
+/* ---------------------------------------------------------------------
+ * Collision step without device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc, such as
+ * applications whose device memory is owned entirely by their own pool
+ * allocator, and latency-critical loops in which cudaMalloc/cudaFree would
+ * synchronise the device.
+ *
+ * Applies the relaxation of step `step` (the shared Monte Carlo sample set of
+ * that step, the Jacobi collision update, the conservation correction; Eqs.
+ * monteCarloInt, collision_step, rinorm_a, correzione) to the caller's state
+ * h_in and writes the result to h_out and, when mom is non-NULL, the moments
+ * of the result to mom (nx*ny*11 doubles, as bz_moments).  h_in and h_out
+ * are device arrays of nx*ny*nv^3 elements of params->dtype in the layout
+ * above and must not overlap.  walls are not needed; params->eps must be
+ * given (> 0); cfl and kcoll keep their defaults at 0.  The result equals
+ * bz_step_ex(h, 1, BZ_DO_COLLIDE, ...) on a handle holding h_in at `step`, up
+ * to floating-point summation order.
+ *
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  Its only
+ * scratch (the sample set and the per-axis velocity tables) is a file-scope
+ * device array of BZ_NOALLOC_SCRATCH_BYTES that every GPU which loads the
+ * library keeps until the process exits; hence n_pairs <= BZ_NOALLOC_MAX_PAIRS
+ * (larger values return BZ_EINVAL), and the per-sample products must fit in
+ * shared memory next to the velocity slab (else BZ_EUNSUPPORTED).  The first
+ * call on a device looks up the device address of that array (with the device
+ * current) and should come before any stream capture.  All calls share the
+ * array and it keeps the last call's contents: calls that overlap on the GPU
+ * (on different streams or devices' shared use) race and give wrong results;
+ * serialise them.  Asynchronous on `stream`; errors as elsewhere. */
+#define BZ_NOALLOC_MAX_PAIRS 65536
+#define BZ_NOALLOC_SCRATCH_BYTES ((2u << 20) + 4096u)
+bz_status bz_collide_noalloc(const bz_space *space, const bz_vel *vel, const bz_params *params,
+                             int64_t step, const void *h_in, void *h_out, double *mom,
+                             void *stream);
+
 /* Thread-local text of the last failure on this thread ("" if none). */
 const char *bz_last_error(void);
 

@@ -83,6 +83,8 @@ _SIGNATURES = {
     "bz_profile": [_H, C.c_int32],
     "bz_profile_read": [_H, C.POINTER(C.c_double), C.POINTER(C.c_int64)],
     "bz_phase_clocks": [_H, C.POINTER(C.c_int64), C.c_int32],
+    "bz_collide_noalloc": [C.POINTER(bz_space), C.POINTER(bz_vel), C.POINTER(bz_params),
+                           C.c_int64, _V, _V, _V, _V],
 }
 
 _lib = None
@@ -252,6 +254,24 @@ class Cavity:
         check(load().bz_sample_plan(self.h, step, idx.ctypes.data, W.ctypes.data,
                                     _stream_ptr(None)), "bz_sample_plan")
         return idx, W
+
+
+NOALLOC_MAX_PAIRS = 65536
+
+
+def collide_noalloc(p: Problem, step: int, h_in, h_out, mom=None, stream=None):
+    """bz_collide_noalloc: one relaxation step of the caller's state without
+    any device allocation by the library (see include/bz.h).  h_in/h_out are
+    CUDA tensors of shape (nr, nv^3) in the problem's dtype; mom is an
+    optional (nr, 11) float64 CUDA tensor; p.eps must be > 0."""
+    sp = bz_space(p.nx, p.ny, p.kn)
+    ve = bz_vel(p.nv, p.vmax)
+    pa = bz_params(p.nt, p.seed, p.instance, p.eps, p.cfl, 0.0,
+                   BZ_F64 if p.dtype == "f64" else BZ_F32,
+                   BZ_PER_CELL if p.per_cell else BZ_SHARED)
+    check(load().bz_collide_noalloc(C.byref(sp), C.byref(ve), C.byref(pa), step, _ptr(h_in),
+                                    _ptr(h_out), _ptr(mom) if mom is not None else None,
+                                    _stream_ptr(stream)), "bz_collide_noalloc")
 
 
 def philox(key, ctr):

@@ -48,17 +48,29 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     cuda_home = os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-cudart", "shared", f"-I{os.path.join(ROOT, 'include')}", f"-I{SRC}",
-           "-Xlinker", f"-rpath={os.path.join(cuda_home, 'lib64')}",
-           "-o", tmp, os.path.join(SRC, "bz_api.cu")]
+    common = [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+              f"-I{os.path.join(ROOT, 'include')}", f"-I{SRC}"]
     if verbose:
-        cmd.insert(3, "-Xptxas=-v")
-    r = subprocess.run(cmd, capture_output=True, text=True)
+        common.append("-Xptxas=-v")
+    units = ["bz_api.cu", "bz_noalloc.cu"]
+    objs = [os.path.join(OUT_DIR, u.replace(".cu", f".{os.getpid()}.o")) for u in units]
+    # The translation units compile in parallel, then link into one library.
+    procs = [subprocess.Popen(common + ["-c", "-o", o, os.path.join(SRC, u)],
+                              stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
+             for u, o in zip(units, objs)]
+    outs = [p.communicate()[0] for p in procs]
+    if any(p.returncode != 0 for p in procs):
+        raise RuntimeError("nvcc failed:\n" + "\n".join(outs))
+    if verbose:
+        print("\n".join(outs))
+    link = [nvcc, ARCH, "-shared", "-cudart", "shared",
+            "-Xlinker", f"-rpath={os.path.join(cuda_home, 'lib64')}", "-o", tmp] + objs
+    r = subprocess.run(link, capture_output=True, text=True)
+    for o in objs:
+        if os.path.exists(o):
+            os.remove(o)
     if r.returncode != 0:
-        raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
-    if verbose:
-        print(r.stdout + r.stderr)
+        raise RuntimeError("nvcc link failed:\n" + r.stdout + r.stderr)
     os.replace(tmp, LIB)
     return LIB
 

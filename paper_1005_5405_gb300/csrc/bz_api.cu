@@ -5,6 +5,7 @@
 // the caller's stream.  No host computation is on the step path: the host only
 // validates arguments, builds per-axis tables once at creation and launches.
 #include "bz.h"
+#include "bz_internal.h"
 #include "bz_kernels.cuh"
 #include "bz_cell4.cuh"
 
@@ -59,6 +60,8 @@ bool fault_injected(const char *what)
 }
 
 }  // namespace
+
+void bz_record_error(const char *msg) { g_last_error = msg; }
 
 struct bz_handle {
     Geo g{};

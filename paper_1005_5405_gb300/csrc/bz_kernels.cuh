@@ -81,7 +81,7 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
     return c;
 }
 
-__global__ void k_philox(uint2 key, const uint4 *__restrict__ ctr, uint4 *__restrict__ out,
+static __global__ void k_philox(uint2 key, const uint4 *__restrict__ ctr, uint4 *__restrict__ out,
                          int64_t n)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -413,7 +413,7 @@ __global__ void k_walls(Geo g, int64_t step, const R *__restrict__ h, R *__restr
     }
 }
 
-__global__ void k_shear_mean(const double *__restrict__ shear, int nx, double *__restrict__ out)
+static __global__ void k_shear_mean(const double *__restrict__ shear, int nx, double *__restrict__ out)
 {
     __shared__ double red[kMaxWarps * kRedSlots];
     __shared__ double tot[1];
@@ -938,7 +938,7 @@ __global__ void k_moments(Geo g, const R *__restrict__ h, double *__restrict__ m
 }
 
 // Count of non-finite values in an array of doubles (flag only).
-__global__ void k_nonfinite(const double *__restrict__ x, int64_t n, int *__restrict__ flag)
+static __global__ void k_nonfinite(const double *__restrict__ x, int64_t n, int *__restrict__ flag)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)

@@ -1,0 +1,194 @@
+// bz_noalloc.cu -- a collision step that allocates no device memory.
+//
+// Some callers cannot call cudaMalloc: applications whose device memory is
+// owned entirely by their own pool allocator and that forbid run-time
+// allocation, and latency-critical loops in which cudaMalloc/cudaFree would
+// synchronise the device.  bz_collide_noalloc serves them: the caller passes
+// the input and output states, and the only scratch the step needs (the Monte
+// Carlo sample set of the step and the per-axis velocity tables) lives in the
+// file-scope device array below, which every GPU that loads the library keeps
+// until the process exits.
+#include "bz.h"
+#include "bz_internal.h"
+#include "bz_kernels.cuh"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <mutex>
+#include <string>
+#include <vector>
+
+namespace {
+
+constexpr int kNoallocMaxPairs = BZ_NOALLOC_MAX_PAIRS;
+constexpr int kNoallocMaxDevices = 64;
+// Scratch layout: sample node indices (int4), gather records (16 bytes each),
+// per-axis velocity nodes and weights (kMaxN doubles each).
+constexpr size_t kIdxBytes = sizeof(int4) * (size_t)kNoallocMaxPairs;
+constexpr size_t kRecBytes = 16 * (size_t)kNoallocMaxPairs;
+constexpr size_t kTabBytes = sizeof(double) * bzk::kMaxN;
+constexpr size_t kScratchBytes = kIdxBytes + kRecBytes + 2 * kTabBytes;
+static_assert(kScratchBytes <= BZ_NOALLOC_SCRATCH_BYTES, "scratch size");
+
+// Shared by every call on a device; its contents are those of the last call.
+static __device__ __align__(256) unsigned char bz_noalloc_scratch[BZ_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_mutex;
+void *g_scratch[kNoallocMaxDevices] = {};
+
+bz_status err(bz_status st, const char *fmt, ...)
+{
+    char buf[400];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    bz_record_error(buf);
+    return st;
+}
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+bz_status scratch_address(int dev, unsigned char **out)
+{
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (dev < 0 || dev >= kNoallocMaxDevices) return err(BZ_EINVAL, "device %d out of range", dev);
+    if (!g_scratch[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, bz_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return err(BZ_ECUDA, "cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+        g_scratch[dev] = p;
+    }
+    *out = (unsigned char *)g_scratch[dev];
+    return BZ_OK;
+}
+
+template <typename R>
+bz_status run(const bzk::Geo &g0, unsigned char *scr, int64_t step, const void *hin, void *hout,
+              double *mom, cudaStream_t s)
+{
+    bzk::Geo g = g0;
+    int4 *pidx = (int4 *)scr;
+    bzk::PlanA<R, int> *pa = (bzk::PlanA<R, int> *)(scr + kIdxBytes);
+    double *axv = (double *)(scr + kIdxBytes + kRecBytes);
+    double *axA = axv + bzk::kMaxN;
+    g.axv = axv;
+    g.axA = axA;
+    int dev = 0, nsm = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t smem = bzk::cell_smem_bytes<R>(g.nv, g.nvt, g.nt, true);
+    if (smem > (size_t)optin)
+        return err(BZ_EUNSUPPORTED,
+                   "the velocity slab and the %d per-sample products need %zu bytes of shared "
+                   "memory; the device offers %d", g.nt, smem, optin);
+    const int threads = std::min(bzk::kMaxThreads, (g.nv * g.nv + 31) / 32 * 32);
+    cudaError_t e = cudaFuncSetAttribute(bzk::k_cell<R, false, int>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int occ = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bzk::k_cell<R, false, int>,
+                                                          threads, smem);
+    if (e != cudaSuccess) return err(BZ_ECUDA, "kernel set-up failed: %s", cudaGetErrorString(e));
+    if (occ < 1) return err(BZ_EUNSUPPORTED, "collision kernel cannot be resident");
+    const int grid = std::min(g.nr, nsm * occ);
+    const int pb = 256, pg = (g.nt + pb - 1) / pb;
+    bzk::k_plan<R, int><<<pg, pb, 0, s>>>(g, step, pidx, pa, nullptr, nullptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return err(BZ_ECUDA, "sampling launch failed: %s", cudaGetErrorString(e));
+    bzk::k_cell<R, false, int><<<grid, threads, smem, s>>>(g, step, (const R *)hin, nullptr, pidx,
+                                                           pa, nullptr, (R *)hout, mom, nullptr, 1);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return err(BZ_ECUDA, "collision launch failed: %s", cudaGetErrorString(e));
+    return BZ_OK;
+}
+
+}  // namespace
+
+extern "C" bz_status bz_collide_noalloc(const bz_space *space, const bz_vel *vel,
+                                        const bz_params *params, int64_t step, const void *h_in,
+                                        void *h_out, double *mom, void *stream)
+{
+    bz_record_error("");
+    if (!space || !vel || !params || !h_in || !h_out) return err(BZ_EINVAL, "NULL argument");
+    if (space->nx < 1 || space->ny < 1 || (int64_t)space->nx * space->ny > (1 << 30))
+        return err(BZ_EINVAL, "invalid spatial grid");
+    if (!(space->kn > 0.0) || !std::isfinite(space->kn)) return err(BZ_EINVAL, "kn must be > 0");
+    if (vel->nv < 2 || vel->nv > bzk::kMaxN) return err(BZ_EINVAL, "nv must be in [2, %d]", bzk::kMaxN);
+    if (!(vel->vmax > 0.0) || !std::isfinite(vel->vmax)) return err(BZ_EINVAL, "vmax must be > 0");
+    if (params->n_pairs < 1 || params->n_pairs > kNoallocMaxPairs)
+        return err(BZ_EINVAL, "n_pairs must be in [1, %d] (size of the static scratch)",
+                   kNoallocMaxPairs);
+    if (!(params->eps > 0.0) || !std::isfinite(params->eps))
+        return err(BZ_EINVAL, "eps must be given (> 0): there is no lid to derive it from");
+    if (!(params->cfl >= 0.0 && params->cfl <= 1.0)) return err(BZ_EINVAL, "cfl must be in [0, 1]");
+    if (!(params->kcoll >= 0.0) || !std::isfinite(params->kcoll))
+        return err(BZ_EINVAL, "kcoll must be >= 0");
+    if (params->dtype != BZ_F32 && params->dtype != BZ_F64) return err(BZ_EINVAL, "dtype");
+    if (params->sample_mode != BZ_SHARED)
+        return err(BZ_EUNSUPPORTED, "only the shared sample set is implemented");
+    if (step < 0) return err(BZ_EINVAL, "step must be >= 0");
+    if (h_in == h_out) return err(BZ_EINVAL, "h_in and h_out must not overlap");
+
+    // Discretisation (Sec. 3, Sec. 5.1), the same rules as bz_create.
+    bzk::Geo g{};
+    const int N = vel->nv;
+    g.nx = space->nx;
+    g.ny = space->ny;
+    g.nv = N;
+    g.nvt = N * N * N;
+    g.nr = g.nx * g.ny;
+    g.nfaces = 2 * g.nx + 2 * g.ny;
+    g.nt = (int)params->n_pairs;
+    g.vmax = vel->vmax;
+    g.dv = (2.0 * vel->vmax) / (double)N;
+    g.dx = (1.0 / space->kn) / (double)g.nx;
+    g.dy = (1.0 / space->kn) / (double)g.ny;
+    const double cfl = params->cfl > 0.0 ? params->cfl : 0.5;
+    const double vtop = -g.vmax + ((double)(N - 1) + 0.5) * g.dv;
+    g.dt = cfl * std::min(g.dx, g.dy) / vtop;
+    const double kcoll =
+        params->kcoll > 0.0 ? params->kcoll : 5.0 * 1.016034 / 16.0 * std::sqrt(2.0 / M_PI);
+    g.cw = M_PI * kcoll * g.dt / (double)g.nt;
+    g.eps = params->eps;
+    g.seed = params->seed;
+    g.instance = params->instance;
+    g.strip = g.nx >= 16 ? 8 : g.nx;
+    double tabs[2 * bzk::kMaxN];
+    for (int j = 0; j < N; ++j) {
+        const double v = -g.vmax + ((double)j + 0.5) * g.dv;
+        tabs[j] = v;
+        tabs[bzk::kMaxN + j] = g.dv * (1.0 / std::sqrt(M_PI)) * std::exp(-v * v);
+    }
+    for (int a = 0; a < 25; ++a) g.G0[a] = 0.0;
+    for (int jx = 0; jx < N; ++jx)
+        for (int jy = 0; jy < N; ++jy)
+            for (int jz = 0; jz < N; ++jz) {
+                const double *v = tabs, *A = tabs + bzk::kMaxN;
+                const double w = A[jx] * A[jy] * A[jz];
+                const double p[5] = {1.0, v[jx], v[jy], v[jz],
+                                     v[jx] * v[jx] + v[jy] * v[jy] + v[jz] * v[jz]};
+                for (int a = 0; a < 5; ++a)
+                    for (int b = 0; b < 5; ++b) g.G0[a * 5 + b] += w * p[a] * p[b];
+            }
+    for (int a = 0; a < 25; ++a) g.G0f[a] = (float)g.G0[a];
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return err(BZ_ECUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    unsigned char *scr = nullptr;
+    bz_status st = scratch_address(dev, &scr);
+    if (st != BZ_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    e = cudaMemcpyAsync(scr + kIdxBytes + kRecBytes, tabs, sizeof(tabs), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return err(BZ_ECUDA, "table upload failed: %s", cudaGetErrorString(e));
+    return params->dtype == BZ_F64 ? run<double>(g, scr, step, h_in, h_out, mom, s)
+                                   : run<float>(g, scr, step, h_in, h_out, mom, s);
+}
