@@ -249,6 +249,22 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
 
+    # Free streaming alone (walls + upwind stencil, Eq. streaming2D): the
+    # BASELINE's separate streaming target.  Timed by the library's events
+    # around each streaming-kernel launch.
+    barrier()
+    cav.profile(True)
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    cav.step_ex(args.steps, binding.BZ_DO_STREAM)
+    s1.record(stream)
+    barrier()
+    cav.profile(False)
+    sms, skn = cav.profile_read()
+    stream_step_ms = s0.elapsed_time(s1) / args.steps
+    stream_kernel_ms = sms[3] / max(1, skn[3])
+
     # End to end through the C ABI with host buffers: per step the caller
     # uploads the lid velocity of every lid face (pinned host -> device),
     # advances one step and reads the macroscopic fields back to pinned host
@@ -314,6 +330,13 @@ def run_ours(args):
                      "frac": achieved / peak, "traffic": profiled_traffic(p.name),
                      "kernel": "k_cell<float,fused>", "peak_source": peak_src,
                      "step_frac": (step_bytes / (ms_max / args.steps / 1e3) / 1e9) / peak},
+        "streaming": {
+            "node_updates_per_s": world * nodes / (stream_step_ms / 1e3),
+            "ms_per_step": stream_step_ms, "kernel_ms": stream_kernel_ms,
+            "kernel": "k_stream4" if cav.get_info().kernel_variant == 1 else "k_stream",
+            "achieved_gbs": 2 * esz * nodes / (stream_kernel_ms / 1e3) / 1e9,
+            "frac": 2 * esz * nodes / (stream_kernel_ms / 1e3) / 1e9 / peak,
+            "note": "8 B/node (read h once, write h~ once); walls kernel excluded"},
         "e2e": {"value": world * nodes * args.e2e_steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * p.nx, "d2h_bytes_per_step": 8 * 11 * p.nr},
         "gpu_launches": int(launches),

@@ -235,6 +235,55 @@ __device__ __forceinline__ float4 upwind4(float4 h0, float4 hx, float4 hy, float
     return o;
 }
 
+// Free streaming alone (Eq. streaming2D) for FP32 states with a multiple-of-4
+// velocity axis: each thread moves 16-byte quads of four jz nodes, one CTA
+// per cell at a time in the strip order, interior cells without branches.
+__global__ void __launch_bounds__(1024) k_stream4(Geo g, const float *__restrict__ hin,
+                                                  const float *__restrict__ ghost,
+                                                  float *__restrict__ hout)
+{
+    // blockDim.x is a multiple of Q: thread t keeps quad q = t mod Q of every
+    // plane and walks the planes jx = t div Q, t div Q + blockDim.x / Q, ...
+    __shared__ float scu[kMaxN];
+    const int N = g.nv, nq = N / 4, Q = N * N / 4, half = N / 2;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) scu[i] = (float)(g.axv[i] * g.dt / g.dx);
+    __syncthreads();
+    const int64_t plane = g.nvt / 4;
+    const float ry = (float)(g.dx / g.dy);
+    const int q = threadIdx.x % Q, jxs = threadIdx.x / Q, jstep = blockDim.x / Q;
+    const int jy = q / nq;
+    const float ay = fabsf(scu[jy] * ry);
+    for (int kc = blockIdx.x; kc < g.nr; kc += gridDim.x) {
+        const int c = cell_of(g, kc);
+        const int ix = c % g.nx, iy = c / g.nx;
+        const float4 *own = reinterpret_cast<const float4 *>(hin) + (int64_t)c * plane;
+        float4 *dst = reinterpret_cast<float4 *>(hout) + (int64_t)c * plane;
+        if (ix > 0 && ix < g.nx - 1 && iy > 0 && iy < g.ny - 1) {
+            const float4 *ys = jy < half ? own + (int64_t)g.nx * plane : own - (int64_t)g.nx * plane;
+            const float4 *xr = own + plane, *xl = own - plane;
+#pragma unroll 4
+            for (int jx = jxs; jx < N; jx += jstep) {
+                const int o = jx * Q + q;
+                const float4 hx = jx < half ? xr[o] : xl[o];
+                dst[o] = upwind4(own[o], hx, ys[o], fabsf(scu[jx]), ay);
+            }
+        } else {
+            for (int jx = jxs; jx < N; jx += jstep) {
+                const int o = jx * Q + q;
+                float4 hx, hy;
+                if (jx < half) hx = ix < g.nx - 1 ? own[o + plane] : f4(ghost[(g.ny + iy) * N + jy]);
+                else hx = ix > 0 ? own[o - plane] : f4(ghost[iy * N + jy]);
+                if (jy < half)
+                    hy = iy < g.ny - 1 ? own[o + (int64_t)g.nx * plane]
+                                       : f4(ghost[(2 * g.ny + g.nx + ix) * N + jx]);
+                else
+                    hy = iy > 0 ? own[o - (int64_t)g.nx * plane] : f4(ghost[(2 * g.ny + ix) * N + jx]);
+                dst[o] = upwind4(own[o], hx, hy, fabsf(scu[jx]), ay);
+            }
+        }
+    }
+}
+
 // Eqs. densita..sforzi from float sums (see finalize_moments).
 __device__ __noinline__ void finalize_moments_f(const float *m, float e, double *o)
 {
