@@ -58,6 +58,29 @@ def problem(name):
     return getattr(workloads, name)()
 
 
+def replica_problem(name, rank):
+    """The workload of one rank: an independent cavity instance (the Philox
+    instance word is the rank, so the ranks draw different sample sets)."""
+    p = problem(name)
+    p.instance = rank
+    return p
+
+
+def max_over_ranks(x, world, device):
+    """Largest value of x over the ranks (the timed region's wall time)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, steps, world, seconds):
+    """Whole-job throughput: the units every rank processed over the max time."""
+    return world * units_per_rank * steps / seconds
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -76,22 +99,23 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(config):
-    """DRAM bytes per launch of the per-cell kernel from the committed ncu
-    summary, or None when the summary is absent or the kernel source changed
-    since it was taken."""
-    path = os.path.join(ROOT, "profiles", f"k_cell_fused_{config}.md")
+def profiled_traffic(nr):
+    """DRAM bytes per launch of the per-cell kernel, from the committed ncu
+    summary of the 64x64-cell case scaled to `nr` cells (its traffic is
+    proportional to the cells processed: 8 B per node).  None when the summary
+    is absent or the kernel source has changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "k_cell_fused_cavity64_v32.md")
     if not os.path.exists(path):
         return None
     vals = {}
     for line in open(path):
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
-            vals[k.strip()] = v.strip()
+            vals[k.strip()] = v.strip().split()[0] if v.strip() else ""
     if vals.get("source_hash") != kernel_source_hash():
         return None
     try:
-        return float(vals["dram_bytes_per_launch"])
+        return float(vals["dram_bytes_per_cell"]) * nr
     except (KeyError, ValueError):
         return None
 
@@ -209,8 +233,7 @@ def run_ours(args):
     __graft_entry__.build()
     from paper_1005_5405_gb300 import binding
 
-    p = problem(args.config)
-    p.instance = rank                      # independent replica per rank
+    p = replica_problem(args.config, rank)     # independent replica per rank
     cav = binding.Cavity(p)
     stream = torch.cuda.current_stream()
     # Time a developed state: every cell starts from a seeded non-zero
@@ -244,10 +267,7 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     kms, kn = cav.profile_read()
     launches = cav.stats()[4] - launches0
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, "cuda")
 
     # Free streaming alone (walls + upwind stencil, Eq. streaming2D): the
     # BASELINE's separate streaming target.  Timed by the library's events
@@ -289,10 +309,7 @@ def run_ours(args):
         cav.moments(out=mom_h)
     barrier()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_s = float(te.item())
+    e2e_s = max_over_ranks(e2e_s, world, "cuda")
     cav.set_lid(p.lid_u0, p.lid_amp, p.lid_period, None)
 
     if rank != 0:
@@ -302,8 +319,8 @@ def run_ours(args):
         return
 
     nodes = p.nodes
-    value = world * nodes * args.steps / (ms_max / 1e3)
-    pairs = world * p.nr * p.nt * args.steps / (ms_max / 1e3)
+    value = job_throughput(nodes, args.steps, world, ms_max / 1e3)
+    pairs = job_throughput(p.nr * p.nt, args.steps, world, ms_max / 1e3)
     cell_ms = kms[2] / max(1, kn[2])
     esz = 8 if p.dtype == "f64" else 4
     alg_bytes = 2 * esz * nodes + (16 + esz) * p.nt + 88 * p.nr
@@ -327,8 +344,9 @@ def run_ours(args):
         "kernels_ms_per_step": {"walls": kms[0] / max(1, kn[0]), "sampling": kms[1] / max(1, kn[1]),
                                 "cell": cell_ms},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(p.name),
-                     "kernel": "k_cell<float,fused>", "peak_source": peak_src,
+                     "frac": achieved / peak, "traffic": profiled_traffic(p.nr),
+                     "kernel": "k_cell4<fused>" if cav.get_info().kernel_variant == 1 else "k_cell<fused>",
+                     "algorithmic_bytes": alg_bytes, "peak_source": peak_src,
                      "step_frac": (step_bytes / (ms_max / args.steps / 1e3) / 1e9) / peak},
         "streaming": {
             "node_updates_per_s": world * nodes / (stream_step_ms / 1e3),
@@ -337,7 +355,7 @@ def run_ours(args):
             "achieved_gbs": 2 * esz * nodes / (stream_kernel_ms / 1e3) / 1e9,
             "frac": 2 * esz * nodes / (stream_kernel_ms / 1e3) / 1e9 / peak,
             "note": "8 B/node (read h once, write h~ once); walls kernel excluded"},
-        "e2e": {"value": world * nodes * args.e2e_steps / e2e_s, "unit": UNIT,
+        "e2e": {"value": job_throughput(nodes, args.e2e_steps, world, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * p.nx, "d2h_bytes_per_step": 8 * 11 * p.nr},
         "gpu_launches": int(launches),
         "clocks": clk,
