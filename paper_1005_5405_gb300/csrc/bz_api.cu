@@ -69,7 +69,11 @@ struct bz_handle {
     size_t esz = 4;
     void *h[2] = {nullptr, nullptr};
     int cur = 0;
-    int64_t step = 0;
+    int64_t step = 0;                   // host mirror of the device step counter
+    int64_t *d_step = nullptr;          // device step counter read by the kernels
+    cudaStream_t cap_stream = nullptr;  // stream used to capture step graphs
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // two fused steps, by buffer parity
+    long long graph_launches = 0;
     void *ht = nullptr;                 // h~ for the unfused path (lazy)
     void *pidx = nullptr;               // sample plan: node indices (16- or 32-bit)
     bool idx16 = true;
@@ -153,6 +157,24 @@ struct ProfScope {
         }
     }
 };
+
+// End of a full step: the device step counter moves on (and its host mirror).
+bz_status advance(bz_handle *H, cudaStream_t s)
+{
+    bzk::k_advance<<<1, 1, 0, s>>>(H->d_step);
+    BZ_LAUNCHED(H);
+    H->step++;
+    return BZ_OK;
+}
+
+void drop_graphs(bz_handle *H)
+{
+    for (auto &g : H->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
 
 // Launch the FP32 fast-path cell kernel; false when the handle does not use it.
 template <typename R>
@@ -259,30 +281,30 @@ bz_status launch_step(bz_handle *H, cudaStream_t s, bool fused, bool do_stream, 
     R *hout = (R *)H->h[H->cur ^ 1];
     if (do_stream || fused) {
         ProfScope ps(H, 0, s);
-        bzk::k_walls<R><<<g.nfaces, 256, 0, s>>>(g, H->step, hin, (R *)H->ghost, H->nw, nullptr);
+        bzk::k_walls<R><<<g.nfaces, 256, 0, s>>>(g, H->d_step, hin, (R *)H->ghost, H->nw, nullptr);
         BZ_LAUNCHED(H);
     }
     if (do_collide || fused) {
         ProfScope ps(H, 1, s);
         int pb = 256, pg = (g.nt + pb - 1) / pb;
-        bzk::k_plan<R, I><<<pg, pb, 0, s>>>(g, H->step, (V4 *)H->pidx, (PA *)H->pa, nullptr, H->stats);
+        bzk::k_plan<R, I><<<pg, pb, 0, s>>>(g, H->d_step, (V4 *)H->pidx, (PA *)H->pa, nullptr, H->stats);
         BZ_LAUNCHED(H);
     }
     if (fused && launch_cell4(H, s, true, hin, hout)) {
         BZ_LAUNCHED(H);
         H->cur ^= 1;
         H->mom_valid = true;
-        return BZ_OK;
+        return advance(H, s);
     }
     if (fused) {
         ProfScope ps(H, 2, s);
         bzk::k_cell<R, true, I><<<H->grid_cell_fused, H->threads, H->smem_cell, s>>>(
-            g, H->step, hin, (const R *)H->ghost, (const V4 *)H->pidx, (const PA *)H->pa,
+            g, hin, (const R *)H->ghost, (const V4 *)H->pidx, (const PA *)H->pa,
             (R *)H->gw_global, hout, H->mom, H->stats, H->gw_in_smem);
         BZ_LAUNCHED(H);
         H->cur ^= 1;
         H->mom_valid = true;
-        return BZ_OK;
+        return advance(H, s);
     }
     if (do_stream) {
         R *dst = do_collide ? (R *)H->ht : hout;
@@ -315,16 +337,17 @@ bz_status launch_step(bz_handle *H, cudaStream_t s, bool fused, bool do_stream, 
         BZ_LAUNCHED(H);
         H->cur ^= 1;
         H->mom_valid = true;
-        return BZ_OK;
+        return advance(H, s);
     }
     if (do_collide) {
         ProfScope ps(H, 2, s);
         bzk::k_cell<R, false, I><<<H->grid_cell, H->threads, H->smem_cell, s>>>(
-            g, H->step, hin, (const R *)H->ghost, (const V4 *)H->pidx, (const PA *)H->pa,
+            g, hin, (const R *)H->ghost, (const V4 *)H->pidx, (const PA *)H->pa,
             (R *)H->gw_global, hout, H->mom, H->stats, H->gw_in_smem);
         BZ_LAUNCHED(H);
         H->cur ^= 1;
         H->mom_valid = true;
+        return advance(H, s);
     }
     return BZ_OK;
 }
@@ -389,7 +412,10 @@ void clear_events(bz_handle *H)
 void release(bz_handle *H)
 {
     clear_events(H);
-    void *ptrs[] = {H->sc_count, H->sc_cursor, H->sc_meta, H->sc_ent, H->prof_clk, H->h[0], H->h[1], H->ht, H->pidx, H->pa, H->ghost, H->nw, H->shear,
+    for (auto &g : H->graph)
+        if (g) cudaGraphExecDestroy(g);
+    if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
+    void *ptrs[] = {H->d_step, H->sc_count, H->sc_cursor, H->sc_meta, H->sc_ent, H->prof_clk, H->h[0], H->h[1], H->ht, H->pidx, H->pa, H->ghost, H->nw, H->shear,
                     H->mom, H->gw_global, H->stats, H->flag, H->axv, H->axA, H->profile};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -529,6 +555,7 @@ bz_status bz_create(const bz_space *space, const bz_vel *vel, const bz_walls *wa
     BZ_STEP(dalloc(&H->axv, sizeof(double) * N));
     BZ_STEP(dalloc(&H->axA, sizeof(double) * N));
     BZ_STEP(dalloc(&H->profile, sizeof(double) * g.nx));
+    BZ_STEP(dalloc(&H->d_step, sizeof(int64_t)));
     if (H->dtype == BZ_F64)
         BZ_STEP(configure_cell_kernel<double>(H));
     else
@@ -544,6 +571,8 @@ bz_status bz_create(const bz_space *space, const bz_vel *vel, const bz_walls *wa
     if (e == cudaSuccess) e = cudaMemset(H->h[0], 0, nodes * H->esz);
     if (e == cudaSuccess) e = cudaMemset(H->h[1], 0, nodes * H->esz);
     if (e == cudaSuccess) e = cudaMemset(H->stats, 0, sizeof(unsigned long long) * 8);
+    if (e == cudaSuccess) e = cudaMemset(H->d_step, 0, sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         fail(BZ_ECUDA, "initialisation failed: %s", cudaGetErrorString(e));
@@ -565,6 +594,57 @@ bz_status bz_destroy(bz_handle *H)
     return BZ_OK;
 }
 
+namespace {
+
+bz_status one_step(bz_handle *H, cudaStream_t s, bool fused, bool ds, bool dc)
+{
+    if (H->dtype == BZ_F64)
+        return H->idx16 ? launch_step<double, uint16_t>(H, s, fused, ds, dc)
+                        : launch_step<double, int>(H, s, fused, ds, dc);
+    return H->idx16 ? launch_step<float, uint16_t>(H, s, fused, ds, dc)
+                    : launch_step<float, int>(H, s, fused, ds, dc);
+}
+
+bool graphs_enabled()
+{
+    const char *e = getenv("BZ_GRAPH");
+    return !(e && strcmp(e, "0") == 0);
+}
+
+// Capture two fused steps (state buffer cur -> other -> cur) into a CUDA graph.
+// The kernels read the step number from device memory and k_advance moves it
+// on, so the graph can be replayed any number of times.
+bz_status capture_pair(bz_handle *H)
+{
+    const int cur0 = H->cur;
+    const int64_t step0 = H->step;
+    const long long l0 = H->launches;
+    const bool mv0 = H->mom_valid;
+    BZ_CUDA(cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal));
+    bz_status st = one_step(H, H->cap_stream, true, false, false);
+    if (st == BZ_OK) st = one_step(H, H->cap_stream, true, false, false);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(H->cap_stream, &graph);
+    H->graph_launches = H->launches - l0;
+    H->cur = cur0;
+    H->step = step0;
+    H->launches = l0;
+    H->mom_valid = mv0;
+    if (st != BZ_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(BZ_ECUDA, "step capture failed: %s", cudaGetErrorString(e));
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(BZ_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    H->graph[cur0] = ex;
+    return BZ_OK;
+}
+
+}  // namespace
+
 bz_status bz_step_ex(bz_handle *H, int32_t nsteps, uint32_t flags, void *stream)
 {
     if (!H) return fail(BZ_EINVAL, "handle is NULL");
@@ -577,17 +657,17 @@ bz_status bz_step_ex(bz_handle *H, int32_t nsteps, uint32_t flags, void *stream)
     bool ds = (flags & BZ_DO_STREAM) || (flags & BZ_SPLIT);
     bool dc = (flags & BZ_DO_COLLIDE) || (flags & BZ_SPLIT);
     if (ds && dc && !H->ht) BZ_TRY(dalloc(&H->ht, H->esz * (size_t)H->g.nr * H->g.nvt));
-    for (int32_t n = 0; n < nsteps; ++n) {
-        bz_status st;
-        if (H->dtype == BZ_F64)
-            st = H->idx16 ? launch_step<double, uint16_t>(H, s, fused, ds, dc)
-                          : launch_step<double, int>(H, s, fused, ds, dc);
-        else
-            st = H->idx16 ? launch_step<float, uint16_t>(H, s, fused, ds, dc)
-                          : launch_step<float, int>(H, s, fused, ds, dc);
-        if (st != BZ_OK) return st;
-        if (fused || dc) H->step++;
+    int32_t n = 0;
+    if (fused && nsteps >= 2 && !H->prof && graphs_enabled()) {
+        if (!H->graph[H->cur]) BZ_TRY(capture_pair(H));
+        for (; n + 1 < nsteps; n += 2) {
+            BZ_CUDA(cudaGraphLaunch(H->graph[H->cur], s));
+            H->step += 2;
+            H->launches += H->graph_launches;
+            H->mom_valid = true;
+        }
     }
+    for (; n < nsteps; ++n) BZ_TRY(one_step(H, s, fused, ds, dc));
     return BZ_OK;
 }
 
@@ -629,10 +709,10 @@ bz_status bz_lid_shear(bz_handle *H, double *out, void *stream)
     cudaStream_t s = (cudaStream_t)stream;
     const Geo &g = H->g;
     if (H->dtype == BZ_F64)
-        bzk::k_walls<double><<<g.nfaces, 256, 0, s>>>(g, H->step, (const double *)H->h[H->cur],
+        bzk::k_walls<double><<<g.nfaces, 256, 0, s>>>(g, H->d_step, (const double *)H->h[H->cur],
                                                       (double *)H->ghost, H->nw, H->shear);
     else
-        bzk::k_walls<float><<<g.nfaces, 256, 0, s>>>(g, H->step, (const float *)H->h[H->cur],
+        bzk::k_walls<float><<<g.nfaces, 256, 0, s>>>(g, H->d_step, (const float *)H->h[H->cur],
                                                      (float *)H->ghost, H->nw, H->shear);
     BZ_LAUNCHED(H);
     double *tmp = H->mom;  // reuse: nr*11 >= nx+1 always (ny >= 1)
@@ -659,6 +739,9 @@ bz_status bz_set_state(bz_handle *H, const void *src, int64_t step, void *stream
     if (step < 0) return fail(BZ_EINVAL, "step must be >= 0");
     BZ_CUDA(cudaMemcpyAsync(H->h[H->cur], src, H->esz * (size_t)H->g.nr * H->g.nvt,
                             cudaMemcpyDefault, (cudaStream_t)stream));
+    BZ_CUDA(cudaMemcpyAsync(H->d_step, &step, sizeof(int64_t), cudaMemcpyHostToDevice,
+                            (cudaStream_t)stream));
+    BZ_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     H->step = step;
     H->mom_valid = false;
     return BZ_OK;
@@ -684,6 +767,7 @@ bz_status bz_set_lid(bz_handle *H, double lid_u0, double lid_amp, double lid_per
     g.lid_u0 = lid_u0;
     g.lid_amp = lid_amp;
     g.lid_period = lid_period;
+    drop_graphs(H);   // the captured launches hold the old wall parameters
     return BZ_OK;
 }
 
@@ -729,25 +813,35 @@ bz_status bz_sample_plan(bz_handle *H, int64_t step, int32_t *idx, double *W, vo
     const Geo &g = H->g;
     int4 *di = nullptr;
     double *dw = nullptr;
+    int64_t *dstep = nullptr;
     BZ_TRY(dalloc(&di, sizeof(int4) * (size_t)g.nt));
     bz_status st = dalloc(&dw, sizeof(double) * (size_t)g.nt);
+    if (st == BZ_OK) st = dalloc(&dstep, sizeof(int64_t));
     if (st != BZ_OK) {
         cudaFree(di);
+        cudaFree(dw);
         return st;
+    }
+    if (cudaMemcpy(dstep, &step, sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(di);
+        cudaFree(dw);
+        cudaFree(dstep);
+        return fail(BZ_ECUDA, "step upload failed");
     }
     int pb = 256, pg = (g.nt + pb - 1) / pb;
     Geo gl = g;
     gl.swz = 0;                       // logical node order for the caller
     if (H->dtype == BZ_F64)
-        bzk::k_plan<double, int><<<pg, pb, 0, s>>>(gl, step, di, (bzk::PlanA<double, int> *)nullptr, dw, nullptr);
+        bzk::k_plan<double, int><<<pg, pb, 0, s>>>(gl, dstep, di, (bzk::PlanA<double, int> *)nullptr, dw, nullptr);
     else
-        bzk::k_plan<float, int><<<pg, pb, 0, s>>>(gl, step, di, (bzk::PlanA<float, int> *)nullptr, dw, nullptr);
+        bzk::k_plan<float, int><<<pg, pb, 0, s>>>(gl, dstep, di, (bzk::PlanA<float, int> *)nullptr, dw, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(idx, di, sizeof(int4) * (size_t)g.nt, cudaMemcpyDefault, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(W, dw, sizeof(double) * (size_t)g.nt, cudaMemcpyDefault, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(di);
     cudaFree(dw);
+    cudaFree(dstep);
     if (e != cudaSuccess) return fail(BZ_ECUDA, "sample plan failed: %s", cudaGetErrorString(e));
     H->launches++;
     return BZ_OK;
@@ -757,6 +851,7 @@ bz_status bz_profile(bz_handle *H, int32_t enable)
 {
     if (!H) return fail(BZ_EINVAL, "handle is NULL");
     H->prof = enable != 0;
+    drop_graphs(H);
     if (enable >= 2 && !H->prof_clk) {
         BZ_TRY(dalloc(&H->prof_clk, sizeof(long long) * bzk::kClkCells * bzk::kClkPhases));
         BZ_CUDA(cudaMemset(H->prof_clk, 0, sizeof(long long) * bzk::kClkCells * bzk::kClkPhases));

@@ -235,11 +235,14 @@ __device__ __forceinline__ PlanA<R, I> make_plan_a(int a, int b, double W)
 }
 
 // One thread per sample; the set is shared by every cell of the step.
+// The step number is read from device memory so that launches captured in a
+// CUDA graph stay correct when the graph is replayed (k_advance moves it on).
 template <typename R, typename I>
-__global__ void k_plan(Geo g, int64_t step, typename Idx4<I>::type *__restrict__ idx,
-                       PlanA<R, I> *__restrict__ pa, double *__restrict__ Wd,
-                       unsigned long long *__restrict__ stats)
+__global__ void k_plan(Geo g, const int64_t *__restrict__ stepp,
+                       typename Idx4<I>::type *__restrict__ idx, PlanA<R, I> *__restrict__ pa,
+                       double *__restrict__ Wd, unsigned long long *__restrict__ stats)
 {
+    const int64_t step = *stepp;
     int l = blockIdx.x * blockDim.x + threadIdx.x;
     SampleOut o = {};
     bool act = l < g.nt;
@@ -344,9 +347,11 @@ __device__ __forceinline__ Face face_of(const Geo &g, int f, int64_t step)
 // tangential velocity index (jy for side walls, jx for bottom and lid).
 // shear[ix]: x-momentum flux through lid face ix (lid faces only).
 template <typename R>
-__global__ void k_walls(Geo g, int64_t step, const R *__restrict__ h, R *__restrict__ ghost,
-                        double *__restrict__ nw_out, double *__restrict__ shear)
+__global__ void k_walls(Geo g, const int64_t *__restrict__ stepp, const R *__restrict__ h,
+                        R *__restrict__ ghost, double *__restrict__ nw_out,
+                        double *__restrict__ shear)
 {
+    const int64_t step = *stepp;
     __shared__ double red[kMaxWarps * kRedSlots];
     __shared__ double tot[4];
     __shared__ double s_nw;
@@ -412,6 +417,9 @@ __global__ void k_walls(Geo g, int64_t step, const R *__restrict__ h, R *__restr
         shear[f - 2 * g.ny - g.nx] = 2.0 * (tot[1] + sx * sy * g.zsum);
     }
 }
+
+// Advances the device step counter by one (the last launch of a step).
+static __global__ void k_advance(int64_t *__restrict__ stepp) { *stepp += 1; }
 
 static __global__ void k_shear_mean(const double *__restrict__ shear, int nx, double *__restrict__ out)
 {
@@ -640,7 +648,7 @@ __host__ __device__ inline size_t cell_smem_bytes(int nv, int nvt, int nt, bool 
 // loading h~ from global memory.
 template <typename R, bool FUSED, typename I>
 __global__ void __launch_bounds__(kMaxThreads, 1)
-k_cell(Geo g, int64_t step, const R *__restrict__ hin, const R *__restrict__ ghost,
+k_cell(Geo g, const R *__restrict__ hin, const R *__restrict__ ghost,
        const typename Idx4<I>::type *__restrict__ pidx, const PlanA<R, I> *__restrict__ pa,
        R *__restrict__ gw_global,
        R *__restrict__ hout, double *__restrict__ mom, unsigned long long *__restrict__ stats,

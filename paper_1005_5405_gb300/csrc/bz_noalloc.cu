@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -27,11 +28,11 @@ namespace {
 constexpr int kNoallocMaxPairs = BZ_NOALLOC_MAX_PAIRS;
 constexpr int kNoallocMaxDevices = 64;
 // Scratch layout: sample node indices (int4), gather records (16 bytes each),
-// per-axis velocity nodes and weights (kMaxN doubles each).
+// per-axis velocity nodes and weights (kMaxN doubles each), the step number.
 constexpr size_t kIdxBytes = sizeof(int4) * (size_t)kNoallocMaxPairs;
 constexpr size_t kRecBytes = 16 * (size_t)kNoallocMaxPairs;
 constexpr size_t kTabBytes = sizeof(double) * bzk::kMaxN;
-constexpr size_t kScratchBytes = kIdxBytes + kRecBytes + 2 * kTabBytes;
+constexpr size_t kScratchBytes = kIdxBytes + kRecBytes + 2 * kTabBytes + sizeof(int64_t);
 static_assert(kScratchBytes <= BZ_NOALLOC_SCRATCH_BYTES, "scratch size");
 
 // Shared by every call on a device; its contents are those of the last call.
@@ -78,6 +79,7 @@ bz_status run(const bzk::Geo &g0, unsigned char *scr, int64_t step, const void *
     bzk::PlanA<R, int> *pa = (bzk::PlanA<R, int> *)(scr + kIdxBytes);
     double *axv = (double *)(scr + kIdxBytes + kRecBytes);
     double *axA = axv + bzk::kMaxN;
+    const int64_t *stepp = (const int64_t *)(axA + bzk::kMaxN);
     g.axv = axv;
     g.axA = axA;
     int dev = 0, nsm = 0, optin = 0;
@@ -100,10 +102,11 @@ bz_status run(const bzk::Geo &g0, unsigned char *scr, int64_t step, const void *
     if (occ < 1) return err(BZ_EUNSUPPORTED, "collision kernel cannot be resident");
     const int grid = std::min(g.nr, nsm * occ);
     const int pb = 256, pg = (g.nt + pb - 1) / pb;
-    bzk::k_plan<R, int><<<pg, pb, 0, s>>>(g, step, pidx, pa, nullptr, nullptr);
+    bzk::k_plan<R, int><<<pg, pb, 0, s>>>(g, stepp, pidx, pa, nullptr, nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return err(BZ_ECUDA, "sampling launch failed: %s", cudaGetErrorString(e));
-    bzk::k_cell<R, false, int><<<grid, threads, smem, s>>>(g, step, (const R *)hin, nullptr, pidx,
+    (void)step;
+    bzk::k_cell<R, false, int><<<grid, threads, smem, s>>>(g, (const R *)hin, nullptr, pidx,
                                                            pa, nullptr, (R *)hout, mom, nullptr, 1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return err(BZ_ECUDA, "collision launch failed: %s", cudaGetErrorString(e));
@@ -161,7 +164,7 @@ extern "C" bz_status bz_collide_noalloc(const bz_space *space, const bz_vel *vel
     g.seed = params->seed;
     g.instance = params->instance;
     g.strip = g.nx >= 16 ? 8 : g.nx;
-    double tabs[2 * bzk::kMaxN];
+    double tabs[2 * bzk::kMaxN + 1];
     for (int j = 0; j < N; ++j) {
         const double v = -g.vmax + ((double)j + 0.5) * g.dv;
         tabs[j] = v;
@@ -179,6 +182,7 @@ extern "C" bz_status bz_collide_noalloc(const bz_space *space, const bz_vel *vel
                     for (int b = 0; b < 5; ++b) g.G0[a * 5 + b] += w * p[a] * p[b];
             }
     for (int a = 0; a < 25; ++a) g.G0f[a] = (float)g.G0[a];
+    std::memcpy(&tabs[2 * bzk::kMaxN], &step, sizeof(int64_t));   // read by the sampling kernel
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

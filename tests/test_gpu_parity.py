@@ -154,6 +154,33 @@ def test_split_path_matches_fused_path():
     assert f_metric(o, state(a), state(b)) < 1e-6
 
 
+def test_graph_replay_matches_plain_launches(monkeypatch):
+    """bz_step replays a captured two-step CUDA graph (the kernels read the
+    step number from device memory); the result must equal plain launches,
+    also across an odd step count, a lid change and a state reset."""
+    p = CASES[2]
+    monkeypatch.setenv("BZ_GRAPH", "0")
+    a, o, h0 = make(p)
+    a.step(5)
+    a.set_lid(0.05)
+    a.step(3)
+    monkeypatch.delenv("BZ_GRAPH")
+    b, _, _ = make(p)
+    b.step(5)
+    b.set_lid(0.05)
+    b.step(3)
+    assert a.get_state()[1] == b.get_state()[1] == 8
+    assert f_metric(o, state(a), state(b)) < 1e-6
+    st = b.stats()
+    assert st[0] == 8
+    b.set_state(h0.astype(np.float32), step=0)
+    b.step(4)
+    c, _, _ = make(p)
+    monkeypatch.setenv("BZ_GRAPH", "0")
+    c.step(4)
+    assert f_metric(o, state(b), state(c)) < 1e-6
+
+
 def test_gw_in_global_scratch_path():
     """Enough samples that the per-sample products do not fit in shared
     memory next to a 32^3 slab: the kernel keeps them in global scratch."""
