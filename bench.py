@@ -367,10 +367,74 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch(args):
+    """64 uneven cavity instances: the batched persistent launch (autotuned
+    schedule, one CUDA graph per step) against the same instances stepped as
+    64 single-instance handles, one launch sequence after another."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1005_5405_gb300 import binding, workloads
+    torch.cuda.set_device(0)
+    ps = workloads.batch64()
+    nodes = sum(p.nodes for p in ps)
+    batch = binding.Batch(ps)
+    for i, p in enumerate(ps):
+        batch.set_state(i, workloads.warm_state_device(p, seed=7 + i, torch=torch), step=0)
+    torch.cuda.empty_cache()
+    choice, tune_ms = batch.tune(trial_steps=2)
+    batch.step(args.warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    batch.step(args.steps)
+    e1.record()
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    sched = batch.schedule()
+    batch.close()
+    torch.cuda.empty_cache()
+    singles = []
+    for i, p in enumerate(ps):
+        c = binding.Cavity(p)
+        c.set_state(workloads.warm_state_device(p, seed=7 + i, torch=torch), step=0)
+        singles.append(c)
+    torch.cuda.empty_cache()
+    for _ in range(args.warmup):
+        for c in singles:
+            c.step(1)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        for c in singles:
+            c.step(1)
+    e1.record()
+    torch.cuda.synchronize()
+    t_single = e0.elapsed_time(e1) / 1e3
+    n = len(ps)
+    line = {
+        "metric": "instance steps/s (64 uneven cavities, FP32)", "value": n * args.steps / t_batch,
+        "unit": "instance-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_batch / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch64", "instances": n, "nodes": nodes,
+                   "samples_per_step": ps[0].nt, "schedule": sched, "tuner_choice": choice,
+                   "tuner_ms_per_step": tune_ms},
+        "node_updates_per_s": nodes * args.steps / t_batch,
+        "back_to_back": {"value": n * args.steps / t_single, "unit": "instance-steps/s",
+                         "ms_per_step": t_single / args.steps * 1e3,
+                         "how": "64 single-instance handles, one bz_step(1) each per step"},
+        "speedup_vs_back_to_back": t_single / t_batch,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "batch64":
+        run_batch(args)
     else:
         run_ours(args)
 

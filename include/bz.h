@@ -189,6 +189,36 @@ bz_status bz_sample_plan(bz_handle *h, int64_t step, int32_t *idx, double *W, vo
  * host or device.  Synchronous.  For cross-checks of the generator. */
 bz_status bz_philox(uint32_t k0, uint32_t k1, const uint32_t *ctr, int64_t n, uint32_t *out);
 
+/* ---------------------------------------------------------------------
+ * Batches: many independent cavity instances (each with its own grids, Kn,
+ * lid, sample count and Philox key) advanced together, one persistent launch
+ * per kernel class and step, the step captured once in a CUDA graph.  Every
+ * instance must be FP32 with nv a multiple of 4 and >= 12, and at most 32768
+ * samples per step (BZ_EUNSUPPORTED otherwise).  The batch owns its instances;
+ * instance i is addressed by its index.  The state of an instance at step n
+ * lives in one of its two buffers chosen by the parity of n, so the per-
+ * instance calls below are the way to read and write it. */
+typedef struct bz_batch bz_batch;
+
+bz_status bz_batch_create(int32_t n, const bz_space *spaces, const bz_vel *vels,
+                          const bz_walls *walls, const bz_params *params, bz_batch **out);
+bz_status bz_batch_destroy(bz_batch *b);
+/* Advance every instance by nsteps (asynchronous on stream). */
+bz_status bz_batch_step(bz_batch *b, int32_t nsteps, void *stream);
+bz_status bz_batch_set_state(bz_batch *b, int32_t i, const void *src, int64_t step, void *stream);
+bz_status bz_batch_get_state(bz_batch *b, int32_t i, void *dst, int64_t *step, void *stream);
+/* Moments of instance i's current state (as bz_moments). */
+bz_status bz_batch_moments(bz_batch *b, int32_t i, double *out, void *stream);
+/* Autotuner: times `trial_steps` recomputations of the current step (the
+ * state is not advanced) for every launch schedule (threads per CTA 512 or
+ * 1024, CTAs per SM, cell-strip width 4, 8 or 16), keeps the fastest and
+ * returns its index in *choice (nullable) and the milliseconds per step of
+ * every schedule in ms[0..ncand) (nullable, up to 12 entries). */
+bz_status bz_batch_tune(bz_batch *b, int32_t trial_steps, void *stream, int32_t *choice,
+                        double *ms, int32_t *ncand);
+/* Launch schedule in use: threads per CTA, persistent CTAs, strip width. */
+bz_status bz_batch_schedule(const bz_batch *b, int32_t out[3]);
+
 /* Per-kernel timing with CUDA events recorded on the launching stream around
  * every kernel the handle launches while enabled (enable != 0); disabling
  * keeps what was recorded.  bz_profile_read synchronises, returns per kernel

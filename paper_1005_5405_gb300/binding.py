@@ -85,6 +85,16 @@ _SIGNATURES = {
     "bz_phase_clocks": [_H, C.POINTER(C.c_int64), C.c_int32],
     "bz_collide_noalloc": [C.POINTER(bz_space), C.POINTER(bz_vel), C.POINTER(bz_params),
                            C.c_int64, _V, _V, _V, _V],
+    "bz_batch_create": [C.c_int32, C.POINTER(bz_space), C.POINTER(bz_vel), C.POINTER(bz_walls),
+                        C.POINTER(bz_params), C.POINTER(_H)],
+    "bz_batch_destroy": [_H],
+    "bz_batch_step": [_H, C.c_int32, _V],
+    "bz_batch_set_state": [_H, C.c_int32, _V, C.c_int64, _V],
+    "bz_batch_get_state": [_H, C.c_int32, _V, C.POINTER(C.c_int64), _V],
+    "bz_batch_moments": [_H, C.c_int32, _V, _V],
+    "bz_batch_tune": [_H, C.c_int32, _V, C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                      C.POINTER(C.c_int32)],
+    "bz_batch_schedule": [_H, C.POINTER(C.c_int32)],
 }
 
 _lib = None
@@ -272,6 +282,87 @@ def collide_noalloc(p: Problem, step: int, h_in, h_out, mom=None, stream=None):
     check(load().bz_collide_noalloc(C.byref(sp), C.byref(ve), C.byref(pa), step, _ptr(h_in),
                                     _ptr(h_out), _ptr(mom) if mom is not None else None,
                                     _stream_ptr(stream)), "bz_collide_noalloc")
+
+
+def _structs(p: Problem, kcoll: float = 0.0):
+    prof = None
+    if p.lid_profile is not None:
+        prof = np.ascontiguousarray(p.lid_profile, dtype=np.float64)
+    wa = bz_walls(p.lid_u0, p.lid_amp, p.lid_period,
+                  prof.ctypes.data_as(C.POINTER(C.c_double)) if prof is not None else None)
+    pa = bz_params(p.nt, p.seed, p.instance, p.eps, p.cfl, kcoll,
+                   BZ_F64 if p.dtype == "f64" else BZ_F32,
+                   BZ_PER_CELL if p.per_cell else BZ_SHARED)
+    return bz_space(p.nx, p.ny, p.kn), bz_vel(p.nv, p.vmax), wa, pa, prof
+
+
+class Batch:
+    """Independent cavity instances advanced together (bz_batch_*)."""
+
+    def __init__(self, problems):
+        L = load()
+        self.problems = list(problems)
+        n = len(self.problems)
+        st = [_structs(p) for p in self.problems]
+        self._keep = [s[4] for s in st]
+        sp = (bz_space * n)(*[s[0] for s in st])
+        ve = (bz_vel * n)(*[s[1] for s in st])
+        wa = (bz_walls * n)(*[s[2] for s in st])
+        pa = (bz_params * n)(*[s[3] for s in st])
+        h = _H()
+        check(L.bz_batch_create(n, sp, ve, wa, pa, C.byref(h)), "bz_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().bz_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1, stream=None):
+        check(load().bz_batch_step(self.h, n, _stream_ptr(stream)), "bz_batch_step")
+
+    def set_state(self, i, src, step=0, stream=None):
+        import torch
+        p = self.problems[i]
+        if isinstance(src, np.ndarray):
+            src = torch.from_numpy(np.ascontiguousarray(src, dtype=np.float32)).cuda()
+        assert src.dtype == torch.float32 and src.numel() == p.nr * p.nvt
+        check(load().bz_batch_set_state(self.h, i, _ptr(src.contiguous()), step,
+                                        _stream_ptr(stream)), "bz_batch_set_state")
+
+    def get_state(self, i, stream=None):
+        import torch
+        p = self.problems[i]
+        out = torch.empty((p.nr, p.nvt), dtype=torch.float32, device="cuda")
+        st = C.c_int64()
+        check(load().bz_batch_get_state(self.h, i, _ptr(out), C.byref(st), _stream_ptr(stream)),
+              "bz_batch_get_state")
+        return out, st.value
+
+    def moments(self, i, stream=None):
+        import torch
+        out = torch.empty((self.problems[i].nr, 11), dtype=torch.float64, device="cuda")
+        check(load().bz_batch_moments(self.h, i, _ptr(out), _stream_ptr(stream)), "bz_batch_moments")
+        return out
+
+    def tune(self, trial_steps=2, stream=None):
+        choice = C.c_int32()
+        ms = (C.c_double * 12)()
+        nc = C.c_int32()
+        check(load().bz_batch_tune(self.h, trial_steps, _stream_ptr(stream), C.byref(choice), ms,
+                                   C.byref(nc)), "bz_batch_tune")
+        return choice.value, list(ms)[: nc.value]
+
+    def schedule(self):
+        out = (C.c_int32 * 3)()
+        check(load().bz_batch_schedule(self.h, out), "bz_batch_schedule")
+        return {"threads": out[0], "ctas": out[1], "strip": out[2]}
 
 
 def philox(key, ctr):

@@ -8,6 +8,7 @@
 #include "bz_internal.h"
 #include "bz_kernels.cuh"
 #include "bz_cell4.cuh"
+#include "bz_batch.cuh"
 
 #include <cuda_runtime.h>
 
@@ -265,7 +266,7 @@ bz_status configure_cell4(bz_handle *H)
     BZ_TRY(dalloc(&H->sc_count, sizeof(int) * g.nvt));
     BZ_TRY(dalloc(&H->sc_cursor, sizeof(int) * g.nvt));
     BZ_TRY(dalloc(&H->sc_meta, sizeof(int) * 2));
-    BZ_TRY(dalloc(&H->sc_ent, sizeof(uint32_t) * ((size_t)4 * g.nt + T)));
+    BZ_TRY(dalloc(&H->sc_ent, sizeof(uint32_t) * ((size_t)4 * g.nt + bzk::kMaxThreads)));
     H->fast = true;
     H->g.swz = 1;
     return BZ_OK;
@@ -910,6 +911,319 @@ bz_status bz_philox(uint32_t k0, uint32_t k1, const uint32_t *ctr, int64_t n, ui
     cudaFree(dc);
     cudaFree(dout);
     if (e != cudaSuccess) return fail(BZ_ECUDA, "philox failed: %s", cudaGetErrorString(e));
+    return BZ_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------
+// Batches
+// ---------------------------------------------------------------------
+struct bz_batch {
+    int n = 0;
+    std::vector<bz_handle *> inst;
+    std::vector<bzk::BInst> hinst;
+    bzk::BInst *d_inst = nullptr;
+    int *d_cell_pre = nullptr, *d_face_pre = nullptr, *d_samp_pre = nullptr;
+    int tot_cells = 0, tot_faces = 0, tot_samples = 0;
+    int nsm = 0;
+    int maxt = 1024, grid = 0, strip = 8;
+    size_t smem = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    std::vector<int64_t> step;
+};
+
+namespace {
+
+bzk::Map4 map_for(int N, int maxt)
+{
+    const int Q = N * N / 4;
+    int K = 1;
+    for (int k = 1; k <= N; ++k)
+        if (N % k == 0 && Q * k <= maxt) K = k;
+    return bzk::Map4{Q, K, N / K};
+}
+
+void batch_free(bz_batch *B)
+{
+    if (B->graph) cudaGraphExecDestroy(B->graph);
+    if (B->cap) cudaStreamDestroy(B->cap);
+    void *ptrs[] = {B->d_inst, B->d_cell_pre, B->d_face_pre, B->d_samp_pre};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (bz_handle *h : B->inst) bz_destroy(h);
+}
+
+template <int M>
+bz_status batch_occupancy(bz_batch *B, int *occ)
+{
+    BZ_CUDA(cudaFuncSetAttribute(bzk::kb_cell4<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)B->smem));
+    BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, bzk::kb_cell4<M>, M, B->smem));
+    return BZ_OK;
+}
+
+// Apply a schedule: strip width into every instance's geometry, block size.
+bz_status batch_apply(bz_batch *B, int maxt, int ctas_per_sm, int strip)
+{
+    int occ = 0;
+    if (maxt == 512) BZ_TRY(batch_occupancy<512>(B, &occ));
+    else BZ_TRY(batch_occupancy<1024>(B, &occ));
+    if (occ < 1) return fail(BZ_EUNSUPPORTED, "batched cell kernel cannot be resident");
+    B->maxt = maxt;
+    B->grid = std::min(B->tot_cells, B->nsm * std::min(occ, ctas_per_sm));
+    B->strip = strip;
+    for (int i = 0; i < B->n; ++i) {
+        B->hinst[i].g.strip = std::min(strip, B->hinst[i].g.nx);
+    }
+    BZ_CUDA(cudaMemcpy(B->d_inst, B->hinst.data(), sizeof(bzk::BInst) * B->n,
+                       cudaMemcpyHostToDevice));
+    if (B->graph) {
+        cudaGraphExecDestroy(B->graph);
+        B->graph = nullptr;
+    }
+    return BZ_OK;
+}
+
+// One step of every instance; advance = false recomputes the current step.
+bz_status batch_launch(bz_batch *B, cudaStream_t s, bool advance)
+{
+    const int pb = 256;
+    bzk::kb_walls<<<B->tot_faces, 256, 0, s>>>(B->d_inst, B->d_face_pre, B->n);
+    bzk::kb_plan<<<(B->tot_samples + pb - 1) / pb, pb, 0, s>>>(B->d_inst, B->d_samp_pre, B->n);
+    bzk::kb_scatter_scan<<<B->n, 1024, 0, s>>>(B->d_inst, B->maxt);
+    bzk::kb_scatter_fill<<<(B->tot_samples + pb - 1) / pb, pb, 0, s>>>(B->d_inst, B->d_samp_pre,
+                                                                        B->n, B->maxt);
+    if (B->maxt == 512)
+        bzk::kb_cell4<512><<<B->grid, 512, B->smem, s>>>(B->d_inst, B->d_cell_pre, B->n);
+    else
+        bzk::kb_cell4<1024><<<B->grid, 1024, B->smem, s>>>(B->d_inst, B->d_cell_pre, B->n);
+    if (advance) bzk::kb_advance<<<(B->n + 127) / 128, 128, 0, s>>>(B->d_inst, B->n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(BZ_ECUDA, "batch launch failed: %s", cudaGetErrorString(e));
+    return BZ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bz_status bz_batch_create(int32_t n, const bz_space *spaces, const bz_vel *vels,
+                          const bz_walls *walls, const bz_params *params, bz_batch **out)
+{
+    g_last_error.clear();
+    if (!out) return fail(BZ_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 4096) return fail(BZ_EINVAL, "n must be in [1, 4096]");
+    if (!spaces || !vels || !walls || !params) return fail(BZ_EINVAL, "NULL argument");
+    for (int i = 0; i < n; ++i) {
+        if (params[i].dtype != BZ_F32) return fail(BZ_EUNSUPPORTED, "instance %d: batches are FP32", i);
+        if (vels[i].nv % 4 != 0 || vels[i].nv < 12)
+            return fail(BZ_EUNSUPPORTED, "instance %d: nv must be a multiple of 4, >= 12", i);
+        if (params[i].n_pairs > 32768)
+            return fail(BZ_EUNSUPPORTED, "instance %d: at most 32768 samples per step", i);
+    }
+    bz_batch *B = new bz_batch();
+    auto bail = [&](bz_status st) {
+        std::string msg = g_last_error;
+        batch_free(B);
+        delete B;
+        g_last_error = msg;
+        return st;
+    };
+    B->n = n;
+    size_t smem = 0;
+    std::vector<int> cpre(n + 1, 0), fpre(n + 1, 0), spre(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        bz_handle *h = nullptr;
+        bz_status st = bz_create(spaces + i, vels + i, walls + i, params + i, &h);
+        if (st != BZ_OK) return bail(st);
+        B->inst.push_back(h);
+        if (!h->fast) {
+            fail(BZ_EUNSUPPORTED, "instance %d does not fit the FP32 per-cell kernel", i);
+            return bail(BZ_EUNSUPPORTED);
+        }
+        bzk::BInst b{};
+        b.g = h->g;
+        b.map[0] = map_for(h->g.nv, 512);
+        b.map[1] = map_for(h->g.nv, 1024);
+        b.h[0] = (float *)h->h[0];
+        b.h[1] = (float *)h->h[1];
+        b.ghost = (float *)h->ghost;
+        b.nw = h->nw;
+        b.pidx = (ushort4 *)h->pidx;
+        b.pa = (bzk::PlanA<float, uint16_t> *)h->pa;
+        b.sc_count = h->sc_count;
+        b.sc_cursor = h->sc_cursor;
+        b.sc_meta = h->sc_meta;
+        b.sc_ent = h->sc_ent;
+        b.mom = h->mom;
+        b.step = h->d_step;
+        B->hinst.push_back(b);
+        cpre[i + 1] = cpre[i] + h->g.nr;
+        fpre[i + 1] = fpre[i] + h->g.nfaces;
+        spre[i + 1] = spre[i] + h->g.nt;
+        smem = std::max(smem, bzk::cell4_smem_bytes(h->g.nv, h->g.nvt, h->g.nt));
+        if (cudaMemset(h->sc_count, 0, sizeof(int) * h->g.nvt) != cudaSuccess) {
+            fail(BZ_ECUDA, "memset failed");
+            return bail(BZ_ECUDA);
+        }
+    }
+    B->tot_cells = cpre[n];
+    B->tot_faces = fpre[n];
+    B->tot_samples = spre[n];
+    B->nsm = B->inst[0]->nsm;
+    B->smem = smem;
+    B->step.assign(n, 0);
+    bz_status st = dalloc(&B->d_inst, sizeof(bzk::BInst) * n);
+    if (st == BZ_OK) st = dalloc(&B->d_cell_pre, sizeof(int) * (n + 1));
+    if (st == BZ_OK) st = dalloc(&B->d_face_pre, sizeof(int) * (n + 1));
+    if (st == BZ_OK) st = dalloc(&B->d_samp_pre, sizeof(int) * (n + 1));
+    if (st != BZ_OK) return bail(st);
+    cudaError_t e = cudaMemcpy(B->d_cell_pre, cpre.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(B->d_face_pre, fpre.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(B->d_samp_pre, spre.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        fail(BZ_ECUDA, "batch set-up failed: %s", cudaGetErrorString(e));
+        return bail(BZ_ECUDA);
+    }
+    // Default schedule: two 512-thread CTAs per SM when they fit, else one of 1024.
+    int occ512 = 0;
+    st = batch_occupancy<512>(B, &occ512);
+    if (st == BZ_OK) st = occ512 >= 2 ? batch_apply(B, 512, 2, 8) : batch_apply(B, 1024, 1, 8);
+    if (st != BZ_OK) return bail(st);
+    *out = B;
+    return BZ_OK;
+}
+
+bz_status bz_batch_destroy(bz_batch *B)
+{
+    if (!B) return BZ_OK;
+    cudaDeviceSynchronize();
+    batch_free(B);
+    delete B;
+    return BZ_OK;
+}
+
+bz_status bz_batch_step(bz_batch *B, int32_t nsteps, void *stream)
+{
+    if (!B) return fail(BZ_EINVAL, "batch is NULL");
+    if (nsteps < 0) return fail(BZ_EINVAL, "nsteps must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (nsteps > 0 && graphs_enabled()) {
+        if (!B->graph) {
+            BZ_CUDA(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
+            bz_status st = batch_launch(B, B->cap, true);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamEndCapture(B->cap, &graph);
+            if (st != BZ_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            if (e != cudaSuccess) return fail(BZ_ECUDA, "batch capture failed: %s", cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&B->graph, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return fail(BZ_ECUDA, "batch graph: %s", cudaGetErrorString(e));
+        }
+        for (int32_t k = 0; k < nsteps; ++k) BZ_CUDA(cudaGraphLaunch(B->graph, s));
+    } else {
+        for (int32_t k = 0; k < nsteps; ++k) BZ_TRY(batch_launch(B, s, true));
+    }
+    for (auto &v : B->step) v += nsteps;
+    return BZ_OK;
+}
+
+bz_status bz_batch_set_state(bz_batch *B, int32_t i, const void *src, int64_t step, void *stream)
+{
+    if (!B || i < 0 || i >= B->n || !src || step < 0) return fail(BZ_EINVAL, "invalid argument");
+    bz_handle *h = B->inst[i];
+    cudaStream_t s = (cudaStream_t)stream;
+    BZ_CUDA(cudaMemcpyAsync(h->h[step & 1], src, h->esz * (size_t)h->g.nr * h->g.nvt,
+                            cudaMemcpyDefault, s));
+    BZ_CUDA(cudaMemcpyAsync(h->d_step, &step, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    BZ_CUDA(cudaStreamSynchronize(s));
+    B->step[i] = step;
+    return BZ_OK;
+}
+
+bz_status bz_batch_get_state(bz_batch *B, int32_t i, void *dst, int64_t *step, void *stream)
+{
+    if (!B || i < 0 || i >= B->n || !dst) return fail(BZ_EINVAL, "invalid argument");
+    bz_handle *h = B->inst[i];
+    BZ_CUDA(cudaMemcpyAsync(dst, h->h[B->step[i] & 1], h->esz * (size_t)h->g.nr * h->g.nvt,
+                            cudaMemcpyDefault, (cudaStream_t)stream));
+    if (step) *step = B->step[i];
+    return BZ_OK;
+}
+
+bz_status bz_batch_moments(bz_batch *B, int32_t i, double *out, void *stream)
+{
+    if (!B || i < 0 || i >= B->n || !out) return fail(BZ_EINVAL, "invalid argument");
+    bz_handle *h = B->inst[i];
+    cudaStream_t s = (cudaStream_t)stream;
+    const Geo &g = h->g;
+    bzk::k_moments<float><<<std::min(g.nr, h->nsm * 8), 256, 0, s>>>(
+        g, (const float *)h->h[B->step[i] & 1], h->mom);
+    BZ_CUDA(cudaGetLastError());
+    BZ_CUDA(cudaMemcpyAsync(out, h->mom, sizeof(double) * 11 * (size_t)g.nr, cudaMemcpyDefault, s));
+    BZ_CUDA(cudaStreamSynchronize(s));
+    return BZ_OK;
+}
+
+bz_status bz_batch_tune(bz_batch *B, int32_t trial_steps, void *stream, int32_t *choice,
+                        double *ms, int32_t *ncand)
+{
+    if (!B || trial_steps < 1) return fail(BZ_EINVAL, "invalid argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    struct Cand { int maxt, cps, strip; };
+    std::vector<Cand> cands;
+    for (int maxt : {512, 1024})
+        for (int cps : {1, 2})
+            for (int strip : {4, 8, 16}) {
+                if (maxt == 1024 && cps == 2) continue;   // 64 registers x 2048 threads do not fit
+                cands.push_back({maxt, cps, strip});
+            }
+    cudaEvent_t e0, e1;
+    BZ_CUDA(cudaEventCreate(&e0));
+    BZ_CUDA(cudaEventCreate(&e1));
+    int best = -1;
+    double best_ms = 1e300;
+    for (size_t c = 0; c < cands.size(); ++c) {
+        double t = -1.0;
+        if (batch_apply(B, cands[c].maxt, cands[c].cps, cands[c].strip) == BZ_OK &&
+            batch_launch(B, s, false) == BZ_OK) {
+            cudaEventRecord(e0, s);
+            bool ok = true;
+            for (int k = 0; k < trial_steps && ok; ++k) ok = batch_launch(B, s, false) == BZ_OK;
+            cudaEventRecord(e1, s);
+            float f = 0.f;
+            if (ok && cudaEventSynchronize(e1) == cudaSuccess &&
+                cudaEventElapsedTime(&f, e0, e1) == cudaSuccess)
+                t = f / trial_steps;
+        }
+        if (ms && c < 12) ms[c] = t;
+        if (t > 0.0 && t < best_ms) {
+            best_ms = t;
+            best = (int)c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ncand) *ncand = (int32_t)cands.size();
+    if (best < 0) return fail(BZ_ECUDA, "no schedule could be timed");
+    BZ_TRY(batch_apply(B, cands[best].maxt, cands[best].cps, cands[best].strip));
+    if (choice) *choice = best;
+    return BZ_OK;
+}
+
+bz_status bz_batch_schedule(const bz_batch *B, int32_t out[3])
+{
+    if (!B || !out) return fail(BZ_EINVAL, "invalid argument");
+    out[0] = B->maxt;
+    out[1] = B->grid;
+    out[2] = B->strip;
     return BZ_OK;
 }
 

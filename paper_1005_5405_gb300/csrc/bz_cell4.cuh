@@ -299,25 +299,10 @@ __device__ __noinline__ void finalize_moments_f(const float *m, float e, double 
     for (int k = 0; k < 6; ++k) o[5 + k] = 2.f * m[4 + k] - 2.f * e * n * u[pa[k]] * u[pb[k]];
 }
 
-template <bool FUSED, int MAXT>
-__global__ void __launch_bounds__(MAXT, 1)
-k_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ ghost,
-        const PlanA<float, uint16_t> *__restrict__ pa, const uint32_t *__restrict__ ent,
-        const int *__restrict__ meta, float *__restrict__ hout, double *__restrict__ mom,
-        unsigned long long *__restrict__ stats, long long *__restrict__ clk)
+// Per-instance shared tables of the FP32 cell kernel (N entries each).
+__device__ __forceinline__ void cell4_setup(const Geo &g, const Cell4Smem &S)
 {
-    extern __shared__ __align__(16) char smem_raw[];
-    const int N = g.nv, N2 = N * N, nvt = g.nvt, T = blockDim.x, t = threadIdx.x;
-    Cell4Smem S = carve4(smem_raw, N, nvt);
-    (void)N2;
-    // Phase trace: SM clock at the barriers of the first kClkCells cells of CTA 0.
-    int ncell = 0;
-    auto stamp = [&](int ph) {
-        if (clk && blockIdx.x == 0 && t == 0 && ncell < kClkCells)
-            clk[ncell * kClkPhases + ph] = clock64();
-    };
-    const float eps = (float)g.eps;
-
+    const int N = g.nv, T = blockDim.x, t = threadIdx.x;
     for (int i = t; i < N; i += T) {
         const double v = g.axv[i], A = g.axA[i];
         S.conv[i] = make_float4((float)A, (float)v, (float)(v * v), 0.f);
@@ -337,8 +322,28 @@ k_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ 
         S.IAzq[i] = make_float4(S.IA[4 * i], S.IA[4 * i + 1], S.IA[4 * i + 2], S.IA[4 * i + 3]);
     }
     __syncthreads();
-    float *totf = reinterpret_cast<float *>(S.tot);
+}
 
+// One cell c of instance g: streaming into the slab (FUSED) or a copy of
+// h~, the Monte Carlo gather and scatter, the correction and the write-back.
+// Called by every thread of the CTA with the tables of g in place.
+template <bool FUSED>
+__device__ __forceinline__ void cell4_cell(const Geo &g, const Map4 &m, int c,
+                                           const float *__restrict__ hin,
+                                           const float *__restrict__ ghost,
+                                           const PlanA<float, uint16_t> *__restrict__ pa,
+                                           const uint32_t *__restrict__ ent,
+                                           const int *__restrict__ meta, float *__restrict__ hout,
+                                           double *__restrict__ mom, const Cell4Smem &S,
+                                           int &fallback, long long *__restrict__ clk, int ncell)
+{
+    const int N = g.nv, nvt = g.nvt, T = blockDim.x, t = threadIdx.x;
+    auto stamp = [&](int ph) {
+        if (clk && blockIdx.x == 0 && t == 0 && ncell < kClkCells)
+            clk[ncell * kClkPhases + ph] = clock64();
+    };
+    const float eps = (float)g.eps;
+    float *totf = reinterpret_cast<float *>(S.tot);
     // Quad of this thread.
     const int Q = m.Q, nq = N / 4;
     const int q = t % Q, kchunk = t / Q;
@@ -373,293 +378,305 @@ k_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ 
         r -= r >= nq ? nq : 0;
         return jx * Q4 + rowq + r;
     };
-    int fallback = 0;
+    const int ix = c % g.nx, iy = c / g.nx;
+    const float4 *own4 = reinterpret_cast<const float4 *>(hin + (int64_t)c * nvt);
+    stamp(0);
 
-    for (int kc = blockIdx.x; kc < g.nr; kc += gridDim.x, ++ncell) {
-        const int c = cell_of(g, kc);
-        const int ix = c % g.nx, iy = c / g.nx;
-        const float4 *own4 = reinterpret_cast<const float4 *>(hin + (int64_t)c * nvt);
-        stamp(0);
-
-        // ---- slab <- h~ ------------------------------------------------------
-        if (active) {
-            if (FUSED) {
-                const float cuy = S.cu[jy] * ry, ay = fabsf(cuy);
-                const int64_t plane = (int64_t)nvt / 4;
-                if (ix > 0 && ix < g.nx - 1 && iy > 0 && iy < g.ny - 1) {
-                    // Interior cell: all upwind sources are neighbour slabs.
-                    const float4 *ys = cuy > 0.f ? own4 - (int64_t)g.nx * plane
-                                                 : own4 + (int64_t)g.nx * plane;
-                    const float4 *xr = own4 + plane, *xl = own4 - plane;
-                    const int e = min(jx1, half), b = max(jx0, half);
+    // ---- slab <- h~ ------------------------------------------------------
+    if (active) {
+        if (FUSED) {
+            const float cuy = S.cu[jy] * ry, ay = fabsf(cuy);
+            const int64_t plane = (int64_t)nvt / 4;
+            if (ix > 0 && ix < g.nx - 1 && iy > 0 && iy < g.ny - 1) {
+                // Interior cell: all upwind sources are neighbour slabs.
+                const float4 *ys = cuy > 0.f ? own4 - (int64_t)g.nx * plane
+                                             : own4 + (int64_t)g.nx * plane;
+                const float4 *xr = own4 + plane, *xl = own4 - plane;
+                const int e = min(jx1, half), b = max(jx0, half);
 #pragma unroll 4
-                    for (int jx = jx0; jx < e; ++jx) {
-                        const int o = jx * Q4 + q;
-                        const float4 h0 = own4[o], hx = xr[o], hy = ys[o];
-                        S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]), ay);
-                    }
+                for (int jx = jx0; jx < e; ++jx) {
+                    const int o = jx * Q4 + q;
+                    const float4 h0 = own4[o], hx = xr[o], hy = ys[o];
+                    S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]), ay);
+                }
 #pragma unroll 4
-                    for (int jx = b; jx < jx1; ++jx) {
-                        const int o = jx * Q4 + q;
-                        const float4 h0 = own4[o], hx = xl[o], hy = ys[o];
-                        S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]), ay);
-                    }
-                } else {
-                    const float4 *ys = nullptr;
-                    const float *yg = nullptr;
-                    if (cuy > 0.f) {
-                        if (iy > 0) ys = own4 - (int64_t)g.nx * plane;
-                        else yg = ghost + (2 * g.ny + ix) * N;
-                    } else {
-                        if (iy < g.ny - 1) ys = own4 + (int64_t)g.nx * plane;
-                        else yg = ghost + (2 * g.ny + g.nx + ix) * N;
-                    }
-                    for (int jx = jx0; jx < jx1; ++jx) {
-                        const int o = jx * Q4 + q;
-                        const float4 h0 = own4[o];
-                        float4 hx;
-                        if (jx < half)   // v_x < 0: right neighbour or right-wall ghost
-                            hx = ix < g.nx - 1 ? own4[plane + o] : f4(ghost[(g.ny + iy) * N + jy]);
-                        else             // v_x > 0: left neighbour or left-wall ghost
-                            hx = ix > 0 ? own4[o - plane] : f4(ghost[iy * N + jy]);
-                        const float4 hy = ys ? ys[o] : f4(yg[jx]);
-                        S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]), ay);
-                    }
+                for (int jx = b; jx < jx1; ++jx) {
+                    const int o = jx * Q4 + q;
+                    const float4 h0 = own4[o], hx = xl[o], hy = ys[o];
+                    S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]), ay);
                 }
             } else {
-#pragma unroll 4
-                for (int jx = jx0; jx < jx1; ++jx) S.slab4[phys(jx)] = own4[jx * Q4 + q];
-            }
-        }
-        __syncthreads();
-
-        stamp(1);
-        // ---- phase A: g_l W_l on h~ (Jacobi) into shared memory ---------------
-        {
-            const float *slab = reinterpret_cast<const float *>(S.slab4);
-            int l = t;
-            for (; l + 15 * T < g.nt; l += 16 * T) {
-                PlanA<float, uint16_t> rec[16];
-#pragma unroll
-                for (int u = 0; u < 16; ++u) rec[u] = pa[l + u * T];
-#pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int a = rec[u].a(), b = rec[u].b();
-                    const float ha = a >= 0 ? slab[a] : 0.f;
-                    const float hb = b >= 0 ? slab[b] : 0.f;
-                    S.gw[l + u * T] = (ha + hb + eps * ha * hb) * rec[u].W;
+                const float4 *ys = nullptr;
+                const float *yg = nullptr;
+                if (cuy > 0.f) {
+                    if (iy > 0) ys = own4 - (int64_t)g.nx * plane;
+                    else yg = ghost + (2 * g.ny + ix) * N;
+                } else {
+                    if (iy < g.ny - 1) ys = own4 + (int64_t)g.nx * plane;
+                    else yg = ghost + (2 * g.ny + g.nx + ix) * N;
                 }
-            }
-            for (; l < g.nt; l += T) {
-                const PlanA<float, uint16_t> r = pa[l];
-                const int a = r.a(), b = r.b();
-                const float ha = a >= 0 ? slab[a] : 0.f;
-                const float hb = b >= 0 ? slab[b] : 0.f;
-                S.gw[l] = (ha + hb + eps * ha * hb) * r.W;
-            }
-        }
-        __syncthreads();
-
-        stamp(2);
-        // ---- N = w h~ in place, with the invariants of h~ ----------------------
-        float p0 = 0.f, p1 = 0.f, p3 = 0.f, p4 = 0.f;
-        if (active) {
-            QUAD_CONSTS;
-#pragma unroll 4
-            for (int jx = jx0; jx < jx1; ++jx) {
-                const int o = phys(jx);
-                float4 h = S.slab4[o];
-                const float4 cv = S.conv[jx];        // {A, v, v^2, -}
-                float n0 = h.x * (cv.x * Ayz[0]), n1 = h.y * (cv.x * Ayz[1]);
-                float n2 = h.z * (cv.x * Ayz[2]), n3 = h.w * (cv.x * Ayz[3]);
-                S.slab4[o] = make_float4(n0, n1, n2, n3);
-                const float sn = (n0 + n1) + (n2 + n3);
-                p0 += sn;
-                p1 += sn * cv.y;
-                p3 += n0 * vz[0] + n1 * vz[1] + n2 * vz[2] + n3 * vz[3];
-                p4 += n0 * (cv.z + qq[0]) + n1 * (cv.z + qq[1]) + n2 * (cv.z + qq[2]) +
-                      n3 * (cv.z + qq[3]);
-            }
-        }
-        __syncthreads();
-
-        stamp(3);
-        // ---- phase B: gains and losses (Eq. monteCarloInt) --------------------
-        // Each thread walks its run of the destination-sorted list, sums the
-        // terms of one node in a register and adds the sum with one atomic.
-        {
-            float *slabw = reinterpret_cast<float *>(S.slab4);
-            const int E = meta[0], C = meta[1];
-            const int base = t * C, n = max(0, min(C, E - base));
-            // Only the first and the last node of a run can be shared with the
-            // neighbouring runs; they are added atomically, the others plainly.
-            int cur = -1;
-            bool first = true;
-            float acc = 0.f;
-            auto flush = [&](bool shared) {
-                if (cur >= 0 && acc != 0.f) {
-                    if (shared) atomicAdd(slabw + cur, acc);
-                    else slabw[cur] += acc;
-                }
-            };
-            auto term = [&](uint32_t w, float r) {
-                const int dest = (int)(w >> 16);
-                if (dest != cur) {
-                    flush(first);
-                    first = cur < 0;
-                    cur = dest;
-                    acc = 0.f;
-                }
-                acc += (w & 0x8000u) ? -r : r;
-            };
-            int i = 0;
-            for (; i + 7 < n; i += 8) {
-                uint32_t w[8];
-                float r[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) w[u] = ent[(int64_t)(i + u) * T + t];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) r[u] = S.gw[w[u] & 0x7FFFu];   // before any flush
-#pragma unroll
-                for (int u = 0; u < 8; ++u) term(w[u], r[u]);
-            }
-            for (; i < n; ++i) {
-                const uint32_t w = ent[(int64_t)i * T + t];
-                term(w, S.gw[w & 0x7FFFu]);
-            }
-            flush(true);
-        }
-        __syncthreads();
-
-        stamp(4);
-        // ---- moments of N_c for the correction (post pass) --------------------
-        float acc[19];
-        {
-            QUAD_CONSTS;
-            float s[4][5];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int k = 0; k < 5; ++k) s[i][k] = 0.f;
-            if (active) {
-#pragma unroll 2
-                for (int jx = jx0; jx < jx1; ++jx) {
-                    float4 n = S.slab4[phys(jx)];
-                    const float4 gv = S.gram[jx];   // v, v^2, v^3, v^4
-                    const float nn[4] = {n.x, n.y, n.z, n.w};
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        s[i][0] += nn[i];
-                        s[i][1] += nn[i] * gv.x;
-                        s[i][2] += nn[i] * gv.y;
-                        s[i][3] += nn[i] * gv.z;
-                        s[i][4] += nn[i] * gv.w;
-                    }
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < 19; ++k) acc[k] = 0.f;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float z = vz[i], qi = qq[i];
-                const float s0 = s[i][0], s1 = s[i][1], s2 = s[i][2], s3 = s[i][3], s4 = s[i][4];
-                acc[0] += s0;
-                acc[1] += s1;
-                acc[2] += vy * s0;
-                acc[3] += z * s0;
-                acc[4] += s2;
-                acc[5] += vy * vy * s0;
-                acc[6] += z * z * s0;
-                acc[7] += vy * s1;
-                acc[8] += z * s1;
-                acc[9] += vy * z * s0;
-                acc[10] += s3 + qi * s1;
-                acc[11] += vy * (s2 + qi * s0);
-                acc[12] += z * (s2 + qi * s0);
-                acc[13] += s4 + 2.f * qi * s2 + qi * qi * s0;
-            }
-            acc[14] = p0;
-            acc[15] = p1;
-            acc[16] = vy * p0;
-            acc[17] = p3;
-            acc[18] = p4;
-        }
-        block_reduce4<19>(acc, S.red, totf);
-        stamp(5);
-
-        // ---- correction solve (thread 0) and per-cell tables --------------------
-        float *muf = reinterpret_cast<float *>(S.mu);
-        if (t == 0) {
-            if (!correction_spd(g, totf, muf)) {
-                double m8[5], Pd[19];
-                for (int a = 0; a < 19; ++a) Pd[a] = (double)totf[a];
-                correction_solve<float>(g, Pd, m8, &fallback);
-                for (int a = 0; a < 5; ++a) muf[a] = (float)m8[a];
-            }
-        }
-        __syncthreads();
-        const float mu0 = muf[0], mux = muf[1], muy = muf[2], muz = muf[3], mu4 = muf[4];
-        for (int i = t; i < N; i += T) S.fin[i].y = mux * S.v[i] + mu4 * S.v[i] * S.v[i];
-        __syncthreads();
-        stamp(6);
-
-        // ---- corrected write-back and output moments ---------------------------
-        float mo[10];
-        {
-            QUAD_CONSTS;
-            float tt[4][3];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) tt[i][0] = tt[i][1] = tt[i][2] = 0.f;
-            float ct[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) ct[i] = mu0 + muy * vy + muz * vz[i] + mu4 * qq[i];
-            if (active) {
-                float4 *dst4 = reinterpret_cast<float4 *>(hout + (int64_t)c * nvt);
-#pragma unroll 2
                 for (int jx = jx0; jx < jx1; ++jx) {
                     const int o = jx * Q4 + q;
-                    float4 n = S.slab4[phys(jx)];
-                    const float4 fv = S.fin[jx];        // 1/A, cx, A, A v
-                    const float av2 = S.Av2[jx];
-                    const float nn[4] = {n.x, n.y, n.z, n.w};
-                    float hn[4];
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float hc = nn[i] * (fv.x * IAyz[i]);
-                        const float corr = ct[i] + fv.y;
-                        hn[i] = hc + (1.f + eps * hc) * corr;
-                        tt[i][0] += hn[i] * fv.z;
-                        tt[i][1] += hn[i] * fv.w;
-                        tt[i][2] += hn[i] * av2;
-                    }
-                    dst4[o] = make_float4(hn[0], hn[1], hn[2], hn[3]);
+                    const float4 h0 = own4[o];
+                    float4 hx;
+                    if (jx < half)   // v_x < 0: right neighbour or right-wall ghost
+                        hx = ix < g.nx - 1 ? own4[plane + o] : f4(ghost[(g.ny + iy) * N + jy]);
+                    else             // v_x > 0: left neighbour or left-wall ghost
+                        hx = ix > 0 ? own4[o - plane] : f4(ghost[iy * N + jy]);
+                    const float4 hy = ys ? ys[o] : f4(yg[jx]);
+                    S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]), ay);
                 }
             }
+        } else {
+#pragma unroll 4
+            for (int jx = jx0; jx < jx1; ++jx) S.slab4[phys(jx)] = own4[jx * Q4 + q];
+        }
+    }
+    __syncthreads();
+
+    stamp(1);
+    // ---- phase A: g_l W_l on h~ (Jacobi) into shared memory ---------------
+    {
+        const float *slab = reinterpret_cast<const float *>(S.slab4);
+        int l = t;
+        for (; l + 15 * T < g.nt; l += 16 * T) {
+            PlanA<float, uint16_t> rec[16];
 #pragma unroll
-            for (int k = 0; k < 10; ++k) mo[k] = 0.f;
+            for (int u = 0; u < 16; ++u) rec[u] = pa[l + u * T];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float a = Ayz[i], z = vz[i];
-                const float t0 = a * tt[i][0], t1 = a * tt[i][1], t2 = a * tt[i][2];
-                mo[0] += t0;
-                mo[1] += t1;
-                mo[2] += vy * t0;
-                mo[3] += z * t0;
-                mo[4] += t2;
-                mo[5] += vy * vy * t0;
-                mo[6] += z * z * t0;
-                mo[7] += vy * t1;
-                mo[8] += z * t1;
-                mo[9] += vy * z * t0;
+            for (int u = 0; u < 16; ++u) {
+                const int a = rec[u].a(), b = rec[u].b();
+                const float ha = a >= 0 ? slab[a] : 0.f;
+                const float hb = b >= 0 ? slab[b] : 0.f;
+                S.gw[l + u * T] = (ha + hb + eps * ha * hb) * rec[u].W;
             }
         }
-        stamp(7);
-        block_reduce4<10>(mo, S.red, totf);
-        if (t == 0 && mom) finalize_moments_f(totf, eps, mom + (int64_t)c * 11);
-        __syncthreads();
-        stamp(8);
+        for (; l < g.nt; l += T) {
+            const PlanA<float, uint16_t> r = pa[l];
+            const int a = r.a(), b = r.b();
+            const float ha = a >= 0 ? slab[a] : 0.f;
+            const float hb = b >= 0 ? slab[b] : 0.f;
+            S.gw[l] = (ha + hb + eps * ha * hb) * r.W;
+        }
     }
+    __syncthreads();
+
+    stamp(2);
+    // ---- N = w h~ in place, with the invariants of h~ ----------------------
+    float p0 = 0.f, p1 = 0.f, p3 = 0.f, p4 = 0.f;
+    if (active) {
+        QUAD_CONSTS;
+#pragma unroll 4
+        for (int jx = jx0; jx < jx1; ++jx) {
+            const int o = phys(jx);
+            float4 h = S.slab4[o];
+            const float4 cv = S.conv[jx];        // {A, v, v^2, -}
+            float n0 = h.x * (cv.x * Ayz[0]), n1 = h.y * (cv.x * Ayz[1]);
+            float n2 = h.z * (cv.x * Ayz[2]), n3 = h.w * (cv.x * Ayz[3]);
+            S.slab4[o] = make_float4(n0, n1, n2, n3);
+            const float sn = (n0 + n1) + (n2 + n3);
+            p0 += sn;
+            p1 += sn * cv.y;
+            p3 += n0 * vz[0] + n1 * vz[1] + n2 * vz[2] + n3 * vz[3];
+            p4 += n0 * (cv.z + qq[0]) + n1 * (cv.z + qq[1]) + n2 * (cv.z + qq[2]) +
+                  n3 * (cv.z + qq[3]);
+        }
+    }
+    __syncthreads();
+
+    stamp(3);
+    // ---- phase B: gains and losses (Eq. monteCarloInt) --------------------
+    // Each thread walks its run of the destination-sorted list, sums the
+    // terms of one node in a register and adds the sum with one atomic.
+    {
+        float *slabw = reinterpret_cast<float *>(S.slab4);
+        const int E = meta[0], C = meta[1];
+        const int base = t * C, n = max(0, min(C, E - base));
+        // Only the first and the last node of a run can be shared with the
+        // neighbouring runs; they are added atomically, the others plainly.
+        int cur = -1;
+        bool first = true;
+        float acc = 0.f;
+        auto flush = [&](bool shared) {
+            if (cur >= 0 && acc != 0.f) {
+                if (shared) atomicAdd(slabw + cur, acc);
+                else slabw[cur] += acc;
+            }
+        };
+        auto term = [&](uint32_t w, float r) {
+            const int dest = (int)(w >> 16);
+            if (dest != cur) {
+                flush(first);
+                first = cur < 0;
+                cur = dest;
+                acc = 0.f;
+            }
+            acc += (w & 0x8000u) ? -r : r;
+        };
+        int i = 0;
+        for (; i + 7 < n; i += 8) {
+            uint32_t w[8];
+            float r[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) w[u] = ent[(int64_t)(i + u) * T + t];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) r[u] = S.gw[w[u] & 0x7FFFu];   // before any flush
+#pragma unroll
+            for (int u = 0; u < 8; ++u) term(w[u], r[u]);
+        }
+        for (; i < n; ++i) {
+            const uint32_t w = ent[(int64_t)i * T + t];
+            term(w, S.gw[w & 0x7FFFu]);
+        }
+        flush(true);
+    }
+    __syncthreads();
+
+    stamp(4);
+    // ---- moments of N_c for the correction (post pass) --------------------
+    float acc[19];
+    {
+        QUAD_CONSTS;
+        float s[4][5];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) s[i][k] = 0.f;
+        if (active) {
+#pragma unroll 2
+            for (int jx = jx0; jx < jx1; ++jx) {
+                float4 n = S.slab4[phys(jx)];
+                const float4 gv = S.gram[jx];   // v, v^2, v^3, v^4
+                const float nn[4] = {n.x, n.y, n.z, n.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    s[i][0] += nn[i];
+                    s[i][1] += nn[i] * gv.x;
+                    s[i][2] += nn[i] * gv.y;
+                    s[i][3] += nn[i] * gv.z;
+                    s[i][4] += nn[i] * gv.w;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 19; ++k) acc[k] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float z = vz[i], qi = qq[i];
+            const float s0 = s[i][0], s1 = s[i][1], s2 = s[i][2], s3 = s[i][3], s4 = s[i][4];
+            acc[0] += s0;
+            acc[1] += s1;
+            acc[2] += vy * s0;
+            acc[3] += z * s0;
+            acc[4] += s2;
+            acc[5] += vy * vy * s0;
+            acc[6] += z * z * s0;
+            acc[7] += vy * s1;
+            acc[8] += z * s1;
+            acc[9] += vy * z * s0;
+            acc[10] += s3 + qi * s1;
+            acc[11] += vy * (s2 + qi * s0);
+            acc[12] += z * (s2 + qi * s0);
+            acc[13] += s4 + 2.f * qi * s2 + qi * qi * s0;
+        }
+        acc[14] = p0;
+        acc[15] = p1;
+        acc[16] = vy * p0;
+        acc[17] = p3;
+        acc[18] = p4;
+    }
+    block_reduce4<19>(acc, S.red, totf);
+    stamp(5);
+
+    // ---- correction solve (thread 0) and per-cell tables --------------------
+    float *muf = reinterpret_cast<float *>(S.mu);
+    if (t == 0) {
+        if (!correction_spd(g, totf, muf)) {
+            double m8[5], Pd[19];
+            for (int a = 0; a < 19; ++a) Pd[a] = (double)totf[a];
+            correction_solve<float>(g, Pd, m8, &fallback);
+            for (int a = 0; a < 5; ++a) muf[a] = (float)m8[a];
+        }
+    }
+    __syncthreads();
+    const float mu0 = muf[0], mux = muf[1], muy = muf[2], muz = muf[3], mu4 = muf[4];
+    for (int i = t; i < N; i += T) S.fin[i].y = mux * S.v[i] + mu4 * S.v[i] * S.v[i];
+    __syncthreads();
+    stamp(6);
+
+    // ---- corrected write-back and output moments ---------------------------
+    float mo[10];
+    {
+        QUAD_CONSTS;
+        float tt[4][3];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) tt[i][0] = tt[i][1] = tt[i][2] = 0.f;
+        float ct[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) ct[i] = mu0 + muy * vy + muz * vz[i] + mu4 * qq[i];
+        if (active) {
+            float4 *dst4 = reinterpret_cast<float4 *>(hout + (int64_t)c * nvt);
+#pragma unroll 2
+            for (int jx = jx0; jx < jx1; ++jx) {
+                const int o = jx * Q4 + q;
+                float4 n = S.slab4[phys(jx)];
+                const float4 fv = S.fin[jx];        // 1/A, cx, A, A v
+                const float av2 = S.Av2[jx];
+                const float nn[4] = {n.x, n.y, n.z, n.w};
+                float hn[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float hc = nn[i] * (fv.x * IAyz[i]);
+                    const float corr = ct[i] + fv.y;
+                    hn[i] = hc + (1.f + eps * hc) * corr;
+                    tt[i][0] += hn[i] * fv.z;
+                    tt[i][1] += hn[i] * fv.w;
+                    tt[i][2] += hn[i] * av2;
+                }
+                dst4[o] = make_float4(hn[0], hn[1], hn[2], hn[3]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 10; ++k) mo[k] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float a = Ayz[i], z = vz[i];
+            const float t0 = a * tt[i][0], t1 = a * tt[i][1], t2 = a * tt[i][2];
+            mo[0] += t0;
+            mo[1] += t1;
+            mo[2] += vy * t0;
+            mo[3] += z * t0;
+            mo[4] += t2;
+            mo[5] += vy * vy * t0;
+            mo[6] += z * z * t0;
+            mo[7] += vy * t1;
+            mo[8] += z * t1;
+            mo[9] += vy * z * t0;
+        }
+    }
+    stamp(7);
+    block_reduce4<10>(mo, S.red, totf);
+    if (t == 0 && mom) finalize_moments_f(totf, eps, mom + (int64_t)c * 11);
+    __syncthreads();
+    stamp(8);
+}
+
+template <bool FUSED, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
+k_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ ghost,
+        const PlanA<float, uint16_t> *__restrict__ pa, const uint32_t *__restrict__ ent,
+        const int *__restrict__ meta, float *__restrict__ hout, double *__restrict__ mom,
+        unsigned long long *__restrict__ stats, long long *__restrict__ clk)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    const Cell4Smem S = carve4(smem_raw, g.nv, g.nvt);
+    cell4_setup(g, S);
+    int fallback = 0, ncell = 0;
+    for (int kc = blockIdx.x; kc < g.nr; kc += gridDim.x, ++ncell)
+        cell4_cell<FUSED>(g, m, cell_of(g, kc), hin, ghost, pa, ent, meta, hout, mom, S,
+                          fallback, clk, ncell);
     if (fallback && stats) atomicAdd(stats + 3, 1ull);
 }
+
 
 }  // namespace bzk

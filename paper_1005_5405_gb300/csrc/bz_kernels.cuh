@@ -346,19 +346,17 @@ __device__ __forceinline__ Face face_of(const Geo &g, int f, int64_t step)
 // ghost[f*nv + jt]: emitted h for inflow nodes of face f, indexed by the
 // tangential velocity index (jy for side walls, jx for bottom and lid).
 // shear[ix]: x-momentum flux through lid face ix (lid faces only).
+// One boundary face f: outgoing flux, wall density and ghost values, and on
+// the lid the shear.  Called by every thread of a CTA; sA, sv (kMaxN each),
+// red, tot (>= 2) and snw are shared scratch.
 template <typename R>
-__global__ void k_walls(Geo g, const int64_t *__restrict__ stepp, const R *__restrict__ h,
-                        R *__restrict__ ghost, double *__restrict__ nw_out,
-                        double *__restrict__ shear)
+__device__ __forceinline__ void walls_face(const Geo &g, int64_t step, const R *__restrict__ h,
+                                           R *__restrict__ ghost, double *__restrict__ nw_out,
+                                           double *__restrict__ shear, int f, R *sA, R *sv,
+                                           double *red, double *tot, double *snw)
 {
-    const int64_t step = *stepp;
-    __shared__ double red[kMaxWarps * kRedSlots];
-    __shared__ double tot[4];
-    __shared__ double s_nw;
-    const int f = blockIdx.x;
     const Face F = face_of(g, f, step);
     const int N = g.nv, N2 = N * N;
-    __shared__ R sA[kMaxN], sv[kMaxN];
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         sA[i] = (R)g.axA[i];
         sv[i] = (R)g.axv[i];
@@ -392,11 +390,11 @@ __global__ void k_walls(Geo g, const int64_t *__restrict__ stepp, const R *__res
         }
         double din = g.hn * tsum * g.zsum;
         double nw = (g.cout + g.eps * tot[0]) / din;
-        s_nw = nw;
+        *snw = nw;
         if (nw_out) nw_out[f] = nw;
     }
     __syncthreads();
-    const double nw = s_nw, lnw = log(nw), U = F.U;
+    const double nw = *snw, lnw = log(nw), U = F.U;
     for (int jt = threadIdx.x; jt < N; jt += blockDim.x) {
         double vt = g.axv[jt];
         // n_w Phi_w / Phi0 - 1 = expm1(ln n_w + 2 v_t U - U^2)
@@ -407,15 +405,29 @@ __global__ void k_walls(Geo g, const int64_t *__restrict__ stepp, const R *__res
         // Emitted part: sum over v_y < 0 of w v_x v_y h_w(jx), separable.
         double sx = 0.0, sy = 0.0;
         for (int jx = 0; jx < N; ++jx) {
-            double d = g.axv[jx] - U;
             double gh = expm1(lnw + 2.0 * g.axv[jx] * U - U * U) / g.eps;
             sx += g.axA[jx] * g.axv[jx] * gh;
-            (void)d;
         }
         for (int jy = 0; jy < N; ++jy)
             if (g.axv[jy] < 0.0) sy += g.axA[jy] * g.axv[jy];
         shear[f - 2 * g.ny - g.nx] = 2.0 * (tot[1] + sx * sy * g.zsum);
     }
+    __syncthreads();
+}
+
+// ghost[f*nv + jt]: emitted h for inflow nodes of face f, indexed by the
+// tangential velocity index (jy for side walls, jx for bottom and lid).
+// shear[ix]: x-momentum flux through lid face ix (lid faces only).
+template <typename R>
+__global__ void k_walls(Geo g, const int64_t *__restrict__ stepp, const R *__restrict__ h,
+                        R *__restrict__ ghost, double *__restrict__ nw_out,
+                        double *__restrict__ shear)
+{
+    __shared__ double red[kMaxWarps * kRedSlots];
+    __shared__ double tot[4];
+    __shared__ double s_nw;
+    __shared__ R sA[kMaxN], sv[kMaxN];
+    walls_face<R>(g, *stepp, h, ghost, nw_out, shear, blockIdx.x, sA, sv, red, tot, &s_nw);
 }
 
 // Advances the device step counter by one (the last launch of a step).

@@ -94,6 +94,24 @@ def adjoint128_v20(seed: int = 4) -> Problem:
                    steps=500)
 
 
+def batch64(n: int = 64, seed0: int = 100, nt: int = 5000) -> list:
+    """Batched workload: n independent cavities, instance k drawn with
+    numpy.random.default_rng(seed0 + k): square grid side from
+    {32, 48, 64, 96, 128}, velocity grid from {16^3, 20^3, 24^3} (box 4.0 for
+    16^3, 4.5 otherwise), Kn log-uniform in [0.05, 5], lid speed uniform in
+    [0.01, 0.2]; FP32, nt samples per step, Philox seed seed0 + k, instance k."""
+    out = []
+    for k in range(n):
+        rng = np.random.default_rng(seed0 + k)
+        side = int(rng.choice([32, 48, 64, 96, 128]))
+        nv = int(rng.choice([16, 20, 24]))
+        kn = float(np.exp(rng.uniform(np.log(0.05), np.log(5.0))))
+        u = float(rng.uniform(0.01, 0.2))
+        out.append(Problem(f"batch{seed0 + k}", side, side, kn, nv, 4.0 if nv == 16 else 4.5, nt,
+                           seed0 + k, lid_u0=u, instance=k, steps=500))
+    return out
+
+
 def small(name="small", nx=8, ny=8, nv=12, vmax=4.0, nt=1000, seed=1, **kw) -> Problem:
     """A problem small enough for the oracle to finish in well under a second."""
     return Problem(name, nx, ny, kw.pop("kn", 1.0), nv, vmax, nt, seed, **kw)

@@ -176,6 +176,7 @@ def test_graph_replay_matches_plain_launches(monkeypatch):
     b.set_state(h0.astype(np.float32), step=0)
     b.step(4)
     c, _, _ = make(p)
+    c.set_lid(0.05)
     monkeypatch.setenv("BZ_GRAPH", "0")
     c.step(4)
     assert f_metric(o, state(b), state(c)) < 1e-6
