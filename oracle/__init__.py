@@ -118,6 +118,7 @@ def lib():
                 "bzo_lid_shear": (None, [_P, C.c_int64, _D, _D]),
                 "bzo_mc_dNdt": (None, [_P, C.c_int64, _D, _D, _D]),
                 "bzo_num_threads": (C.c_int32, []),
+                "bzo_adjoint_step": (None, [_P, C.c_int64, _D, _D, _D, _D, C.c_double]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -265,6 +266,18 @@ class Oracle:
         for n in range(step0, step0 + nsteps):
             h, mom = self.step(h, n)
         return h, mom
+
+    def adjoint_step(self, h, lam, step=0, wD=0.0, grad_lid=None):
+        """dJ/dh^n from lam = dJ/dh^{n+1}; dJ/dU (nx) is added to grad_lid."""
+        h = self._state(h)
+        lam = self._state(lam)
+        out = np.empty_like(h)
+        if grad_lid is None:
+            grad_lid = np.zeros(self.nx)
+        assert grad_lid.dtype == np.float64 and grad_lid.shape == (self.nx,)
+        self.L.bzo_adjoint_step(C.byref(self.p), step, _dptr(h), _dptr(lam), _dptr(out),
+                                _dptr(grad_lid), wD)
+        return out, grad_lid
 
     def moments(self, h):
         h = self._state(h)

@@ -637,3 +637,224 @@ int32_t bzo_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------ */
+/* Adjoint of one time step (fixed sample stream)                      */
+/* ------------------------------------------------------------------ */
+/* With the samples of a step fixed, the step h^n -> h^{n+1} is a smooth map
+ * of h^n and of the lid speeds: streaming is linear in h^n apart from the
+ * wall ghosts, which are affine in the outgoing flux and nonlinear in U;
+ * the Monte Carlo update is bilinear in h~ (Eq. monteCarloInt); the
+ * correction (Eqs. rinorm_a, correzione) is differentiated through its 5x5
+ * solve.  Objective of interest: J = sum_n wD_n D_n, D_n the lid shear of
+ * h^n (Sec. 5.2).  Given lam = dJ/dh^{n+1}, bzo_adjoint_step returns
+ * dJ/dh^n (including wD dD_n/dh^n) and adds dJ/dU_i to grad_lid[i]. */
+
+/* Phi_w / Phi0 at node velocity v for wall velocity vw: exp(|v|^2 - |v - vw|^2). */
+static double ratio_w0(const double v[3], const double vw[3])
+{
+    double a = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    double d0 = v[0] - vw[0], d1 = v[1] - vw[1], d2 = v[2] - vw[2];
+    return exp(a - (d0 * d0 + d1 * d1 + d2 * d2));
+}
+
+/* For face f: D_in = sum_{vn>0} vn dV Phi_w and its derivative in the
+ * tangential wall speed (x component). */
+static void face_influx(const bzo_problem *p, int64_t step, int32_t f, double *din, double *ddin)
+{
+    int32_t cell, nvt = p->nv * p->nv * p->nv;
+    double nrm[3], vw[3], v[3], dv = bzo_dv(p), dV = dv * dv * dv;
+    face_info(p, step, f, &cell, nrm, vw);
+    double s = 0.0, ds = 0.0;
+    for (int32_t j = 0; j < nvt; ++j) {
+        node_velocity(p, j, v);
+        double vn = v[0] * nrm[0] + v[1] * nrm[1] + v[2] * nrm[2];
+        if (vn > 0.0) {
+            double m = vn * dV * wall_maxwellian(v, vw);
+            s += m;
+            ds += m * 2.0 * (v[0] - vw[0]);
+        }
+    }
+    *din = s;
+    *ddin = ds;
+}
+
+void bzo_adjoint_step(const bzo_problem *p, int64_t step, const double *h, const double *lam_in,
+                      double *lam_out, double *grad_lid, double wD)
+{
+    int32_t nx = p->nx, ny = p->ny, nr = nx * ny, n = p->nv, nf = bzo_num_faces(p);
+    int64_t nvt = (int64_t)n * n * n;
+    double eps = p->eps, dt = bzo_dt(p), dx = bzo_dx(p), dy = bzo_dy(p);
+    double *w, *vel;
+    tables(p, &w, &vel);
+
+    /* ---- forward recompute: walls, streaming, samples ---- */
+    double *nw = (double *)malloc(sizeof(double) * nf);
+    bzo_wall_density(p, step, h, nw);
+    double *ht = (double *)malloc(sizeof(double) * nr * nvt);
+    bzo_stream(p, step, h, ht);
+    bzo_sample_t *smp = (bzo_sample_t *)malloc(sizeof(bzo_sample_t) * p->nt);
+    bzo_sample_all(p, step, 0xFFFFFFFFu, smp);
+
+    /* ---- collision adjoint, cell by cell: lam^{n+1} -> lam~ ---- */
+    double *lt = (double *)calloc((size_t)nr * nvt, sizeof(double));
+#pragma omp parallel
+    {
+        double *dN = (double *)malloc(sizeof(double) * nvt);
+        double *hc = (double *)malloc(sizeof(double) * nvt);
+        double *lc = (double *)malloc(sizeof(double) * nvt);
+#pragma omp for schedule(static)
+        for (int32_t c = 0; c < nr; ++c) {
+            const double *hh = ht + (int64_t)c * nvt;
+            const double *lam = lam_in + (int64_t)c * nvt;
+            double *out = lt + (int64_t)c * nvt;
+            double phi[5];
+            /* forward: h_c, G, mu exactly as bzo_collide */
+            double pre[5] = {0, 0, 0, 0, 0};
+            for (int64_t j = 0; j < nvt; ++j) {
+                invariants(vel + 3 * j, phi);
+                for (int a = 0; a < 5; ++a) pre[a] += w[j] * hh[j] * phi[a];
+            }
+            memset(dN, 0, sizeof(double) * nvt);
+            for (int64_t l = 0; l < p->nt; ++l) {
+                const bzo_sample_t *q = smp + l;
+                double ha = q->idx[0] >= 0 ? hh[q->idx[0]] : 0.0;
+                double hb = q->idx[1] >= 0 ? hh[q->idx[1]] : 0.0;
+                double r = q->W * (ha + hb + eps * ha * hb);
+                if (q->idx[2] >= 0) dN[q->idx[2]] += r;
+                if (q->idx[3] >= 0) dN[q->idx[3]] += r;
+                if (q->idx[0] >= 0) dN[q->idx[0]] -= r;
+                if (q->idx[1] >= 0) dN[q->idx[1]] -= r;
+            }
+            for (int64_t j = 0; j < nvt; ++j) hc[j] = hh[j] + dN[j] / w[j];
+            double G[5][5] = {{0}}, R[5] = {0, 0, 0, 0, 0}, mu[5], Gs[5][5];
+            for (int64_t j = 0; j < nvt; ++j) {
+                invariants(vel + 3 * j, phi);
+                double f = w[j] * (1.0 + eps * hc[j]);
+                for (int a = 0; a < 5; ++a) {
+                    R[a] += w[j] * hc[j] * phi[a];
+                    for (int b = 0; b < 5; ++b) G[a][b] += f * phi[a] * phi[b];
+                }
+            }
+            memcpy(Gs, G, sizeof(G));
+            double rhs[5];
+            for (int a = 0; a < 5; ++a) rhs[a] = -(R[a] - pre[a]);
+            if (solve5(G, rhs, mu) != 0) mu[0] = mu[1] = mu[2] = mu[3] = mu[4] = 0.0;
+            /* nu = d J / d mu = sum_j lam_j (1 + eps h_c,j) psi_j ; xi = G^{-1} nu */
+            double nu[5] = {0, 0, 0, 0, 0}, xi[5];
+            for (int64_t j = 0; j < nvt; ++j) {
+                invariants(vel + 3 * j, phi);
+                for (int a = 0; a < 5; ++a) nu[a] += lam[j] * (1.0 + eps * hc[j]) * phi[a];
+            }
+            if (solve5(Gs, nu, xi) != 0) xi[0] = xi[1] = xi[2] = xi[3] = xi[4] = 0.0;
+            /* dJ/dh_c and the direct dJ/dh~ of the moments of h~ */
+            for (int64_t j = 0; j < nvt; ++j) {
+                invariants(vel + 3 * j, phi);
+                double px = 0.0, pm = 0.0;
+                for (int a = 0; a < 5; ++a) {
+                    px += phi[a] * xi[a];
+                    pm += phi[a] * mu[a];
+                }
+                lc[j] = (lam[j] - w[j] * px) * (1.0 + eps * pm);
+                out[j] = lc[j] + w[j] * px;
+            }
+            /* transposed Monte Carlo update: h_c = h~ + S(h~)/w, S bilinear */
+            for (int64_t l = 0; l < p->nt; ++l) {
+                const bzo_sample_t *q = smp + l;
+                double gam = 0.0;
+                if (q->idx[2] >= 0) gam += lc[q->idx[2]] / w[q->idx[2]];
+                if (q->idx[3] >= 0) gam += lc[q->idx[3]] / w[q->idx[3]];
+                if (q->idx[0] >= 0) gam -= lc[q->idx[0]] / w[q->idx[0]];
+                if (q->idx[1] >= 0) gam -= lc[q->idx[1]] / w[q->idx[1]];
+                gam *= q->W;
+                double ha = q->idx[0] >= 0 ? hh[q->idx[0]] : 0.0;
+                double hb = q->idx[1] >= 0 ? hh[q->idx[1]] : 0.0;
+                if (q->idx[0] >= 0) out[q->idx[0]] += gam * (1.0 + eps * hb);
+                if (q->idx[1] >= 0) out[q->idx[1]] += gam * (1.0 + eps * ha);
+            }
+        }
+        free(dN);
+        free(hc);
+        free(lc);
+    }
+
+    /* ---- streaming adjoint: lam~ -> lam^n, ghosts collected per face ---- */
+    double *lg = (double *)calloc((size_t)nf * nvt, sizeof(double)); /* dJ/d ghost_f(j) */
+    memset(lam_out, 0, sizeof(double) * nr * nvt);
+    for (int32_t c = 0; c < nr; ++c) {
+        int32_t ix = c % nx, iy = c / nx;
+        for (int64_t j = 0; j < nvt; ++j) {
+            double v[3];
+            node_velocity(p, (int32_t)j, v);
+            double ax = fabs(v[0] * dt / dx), ay = fabs(v[1] * dt / dy);
+            double L = lt[(int64_t)c * nvt + j];
+            lam_out[(int64_t)c * nvt + j] += (1.0 - ax - ay) * L;
+            if (v[0] > 0.0) {
+                if (ix > 0) lam_out[(int64_t)(c - 1) * nvt + j] += ax * L;
+                else lg[(int64_t)iy * nvt + j] += ax * L;
+            } else if (v[0] < 0.0) {
+                if (ix < nx - 1) lam_out[(int64_t)(c + 1) * nvt + j] += ax * L;
+                else lg[(int64_t)(ny + iy) * nvt + j] += ax * L;
+            } else {
+                lam_out[(int64_t)c * nvt + j] += ax * L;
+            }
+            if (v[1] > 0.0) {
+                if (iy > 0) lam_out[(int64_t)(c - nx) * nvt + j] += ay * L;
+                else lg[(int64_t)(2 * ny + ix) * nvt + j] += ay * L;
+            } else if (v[1] < 0.0) {
+                if (iy < ny - 1) lam_out[(int64_t)(c + nx) * nvt + j] += ay * L;
+                else lg[(int64_t)(2 * ny + nx + ix) * nvt + j] += ay * L;
+            } else {
+                lam_out[(int64_t)c * nvt + j] += ay * L;
+            }
+        }
+    }
+
+    /* ---- lid shear D_n: its own ghost sensitivities ---- */
+    if (wD != 0.0) {
+        for (int32_t ix = 0; ix < nx; ++ix) {
+            int32_t f = 2 * ny + nx + ix;
+            int64_t c = (int64_t)(ny - 1) * nx + ix;
+            for (int64_t j = 0; j < nvt; ++j) {
+                double v[3];
+                node_velocity(p, (int32_t)j, v);
+                double coef = wD * 2.0 * w[j] * v[0] * v[1] / nx;
+                if (v[1] > 0.0) lam_out[c * nvt + j] += coef;
+                else if (v[1] < 0.0) lg[(int64_t)f * nvt + j] += coef;
+            }
+        }
+    }
+
+    /* ---- ghosts -> outgoing flux of each face, and the lid speeds ---- */
+    for (int32_t f = 0; f < nf; ++f) {
+        int32_t cell;
+        double nrm[3], vw[3], v[3];
+        face_info(p, step, f, &cell, nrm, vw);
+        double din, ddin;
+        face_influx(p, step, f, &din, &ddin);
+        double lF = 0.0, lU = 0.0;
+        for (int64_t j = 0; j < nvt; ++j) {
+            double L = lg[(int64_t)f * nvt + j];
+            if (L == 0.0) continue;
+            node_velocity(p, (int32_t)j, v);
+            double r = ratio_w0(v, vw);
+            /* ghost = (n_w r - 1)/eps, n_w = out/in: d/dF = r/in (F: outgoing h-flux) */
+            lF += L * r / din;
+            /* d/dU = (n_w r / eps) [2 (v_x - U) - din'/din] */
+            lU += L * (nw[f] * r / eps) * (2.0 * (v[0] - vw[0]) - ddin / din);
+        }
+        for (int64_t j = 0; j < nvt; ++j) {
+            node_velocity(p, (int32_t)j, v);
+            double vn = v[0] * nrm[0] + v[1] * nrm[1] + v[2] * nrm[2];
+            if (vn < 0.0) lam_out[(int64_t)cell * nvt + j] += lF * (-vn) * w[j];
+        }
+        if (f >= 2 * ny + nx && grad_lid) grad_lid[f - 2 * ny - nx] += lU;
+    }
+    free(lg);
+    free(lt);
+    free(ht);
+    free(nw);
+    free(smp);
+    free(w);
+    free(vel);
+}

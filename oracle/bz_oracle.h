@@ -116,6 +116,13 @@ void bzo_lid_shear(const bzo_problem *p, int64_t step, const double *h, double *
 void bzo_mc_dNdt(const bzo_problem *p, int64_t step, const double *h, double *gain,
                  double *loss);
 
+/* Adjoint of step `step` with its sample set fixed: given h (= h^n) and
+ * lam_in = dJ/dh^{n+1}, writes lam_out = dJ/dh^n and adds dJ/dU_i (lid face
+ * speeds at t_n) to grad_lid[i] (nullable), for J containing wD * D_n, D_n
+ * the mean lid shear of h^n (bzo_lid_shear). */
+void bzo_adjoint_step(const bzo_problem *p, int64_t step, const double *h, const double *lam_in,
+                      double *lam_out, double *grad_lid, double wD);
+
 /* Number of OpenMP threads the oracle uses. */
 int32_t bzo_num_threads(void);
 
