@@ -429,12 +429,81 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args):
+    """The adjoint step (bz_adjoint_step) against the forward step on the
+    128x128 cavity with a 20^3 velocity grid (per-face lid speeds), and the
+    whole checkpointed backward pass of an M-step rollout per step."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1005_5405_gb300 import autodiff, binding
+    torch.cuda.set_device(0)
+    p = problem("adjoint128_v20")
+    cav = binding.Cavity(p)
+    h0 = workloads_state(p, torch)
+    cav.set_state(h0, step=0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn, k):
+        torch.cuda.synchronize()
+        ev[0].record()
+        for i in range(k):
+            fn(i)
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / 1e3 / k
+
+    for _ in range(args.warmup):
+        cav.step(1)
+    t_fwd = timed(lambda i: cav.step(1), args.steps)
+    h = cav.get_state()[0].clone()
+    lam = torch.randn_like(h) * 1e-3
+    g = torch.zeros(p.nx, dtype=torch.float64, device="cuda")
+    for i in range(args.warmup):
+        cav.adjoint_step(i, h, lam, lam, g, 0.1)
+    t_adj = timed(lambda i: cav.adjoint_step(100 + i, h, lam, lam, g, 0.1), args.steps)
+    M, every = args.steps, max(1, args.steps // 2)
+    prof = torch.tensor(p.lid_profile, dtype=torch.float64, requires_grad=True)
+    x0 = h0.clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, d = autodiff.rollout(cav, prof, x0, M, every=every)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    d.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    line = {
+        "metric": "adjoint step time / forward step time (128^2 x 20^3 FP32 cavity)",
+        "value": t_adj / t_fwd, "unit": "ratio", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_adj * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "adjoint128_v20", "nx": p.nx, "ny": p.ny, "nv": p.nv,
+                   "samples_per_step": p.nt, "l2": "state 524 MB > L2, no flush"},
+        "forward_ms_per_step": t_fwd * 1e3,
+        "adjoint_ms_per_step": t_adj * 1e3,
+        "rollout": {"steps": M, "checkpoint_every": every,
+                    "forward_ms_per_step": (t1 - t0) / M * 1e3,
+                    "backward_ms_per_step": (t2 - t1) / M * 1e3,
+                    "backward_over_forward": (t2 - t1) / (t1 - t0),
+                    "grad_lid_norm": float(prof.grad.norm())},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workloads_state(p, torch):
+    from paper_1005_5405_gb300 import workloads
+    return workloads.warm_state_device(p, seed=7, torch=torch)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.config == "batch64":
         run_batch(args)
+    elif args.config == "adjoint128_v20":
+        run_adjoint(args)
     else:
         run_ours(args)
 

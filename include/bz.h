@@ -184,6 +184,30 @@ bz_status bz_stats(bz_handle *h, int64_t out[8]);
  * For parity checks; the step path keeps its own copy in device scratch. */
 bz_status bz_sample_plan(bz_handle *h, int64_t step, int32_t *idx, double *W, void *stream);
 
+/* Adjoint of one time step with its Monte Carlo sample set fixed.  With the
+ * samples of step n fixed, the step h^n -> h^{n+1} (upwind streaming with
+ * diffuse walls, Eqs. streaming2D and bcMax; the Jacobi Monte Carlo update,
+ * Eqs. monteCarloInt and collision_step; the correction, Eqs. rinorm_a and
+ * correzione) is a smooth function of h^n and of the lid face speeds U_i at
+ * t_n.  The paper has no adjoint: this call transposes those equations so
+ * that gradients of a wall-shear objective (D of Sec. 5.2) with respect to
+ * the lid profile and the initial state can be taken through many steps.
+ *
+ * h_n: device, the state at step `step` (nx*ny*nv^3 elements of the handle's
+ * dtype, layout above).  lam_in: device, the same shape, dJ/dh^{n+1}.
+ * lam_out: device, the same shape, receives dJ/dh^n; it may be lam_in itself
+ * but must not overlap h_n.  grad_lid: device, nx doubles, or NULL; dJ/dU_i
+ * is ADDED to grad_lid[i].  wD: weight of the lid shear D_n of h^n in J
+ * (D_n as bz_lid_shear's out[nx]); its terms are added to lam_out and
+ * grad_lid.  The lid motion is the handle's (bz_set_lid).  The handle's
+ * state, step counter and moments are not touched; the adjoint scratch (the
+ * sample set, the ghost values and one state-sized buffer) is allocated on
+ * the first call (BZ_ENOMEM on failure).  BZ_EUNSUPPORTED when three
+ * velocity slabs and the per-sample products do not fit one block's shared
+ * memory.  Asynchronous on `stream`. */
+bz_status bz_adjoint_step(bz_handle *h, int64_t step, const void *h_n, const void *lam_in,
+                          void *lam_out, double *grad_lid, double wD, void *stream);
+
 /* Device Philox4x32-10 (Salmon et al., SC'11) words for n counters
  * (ctr: 4*n uint32, host or device) under key (k0, k1); out: 4*n uint32,
  * host or device.  Synchronous.  For cross-checks of the generator. */

@@ -80,6 +80,7 @@ _SIGNATURES = {
     "bz_stats": [_H, C.POINTER(C.c_int64)],
     "bz_sample_plan": [_H, C.c_int64, _V, _V, _V],
     "bz_philox": [C.c_uint32, C.c_uint32, _V, C.c_int64, _V],
+    "bz_adjoint_step": [_H, C.c_int64, _V, _V, _V, _V, C.c_double, _V],
     "bz_profile": [_H, C.c_int32],
     "bz_profile_read": [_H, C.POINTER(C.c_double), C.POINTER(C.c_int64)],
     "bz_phase_clocks": [_H, C.POINTER(C.c_int64), C.c_int32],
@@ -264,6 +265,25 @@ class Cavity:
         check(load().bz_sample_plan(self.h, step, idx.ctypes.data, W.ctypes.data,
                                     _stream_ptr(None)), "bz_sample_plan")
         return idx, W
+
+
+    def adjoint_step(self, step: int, h_n, lam_in, lam_out=None, grad_lid=None, wD: float = 0.0,
+                     stream=None):
+        """bz_adjoint_step: dJ/dh^n from lam_in = dJ/dh^{n+1} (CUDA tensors of
+        shape (nr, nv^3) in the handle's dtype; lam_out may be lam_in).  dJ/dU
+        of the lid faces is added to grad_lid ((nx,) float64 CUDA tensor) when
+        given; wD weights the lid shear D_n of h_n in J.  Returns lam_out."""
+        import torch
+        if lam_out is None:
+            lam_out = torch.empty_like(lam_in)
+        for t in (h_n, lam_in, lam_out):
+            assert t.dtype == self.torch_dtype and t.numel() == self.p.nr * self.p.nvt
+        if grad_lid is not None:
+            assert grad_lid.dtype == torch.float64 and grad_lid.numel() == self.p.nx
+        check(load().bz_adjoint_step(self.h, step, _ptr(h_n), _ptr(lam_in), _ptr(lam_out),
+                                     _ptr(grad_lid) if grad_lid is not None else None,
+                                     float(wD), _stream_ptr(stream)), "bz_adjoint_step")
+        return lam_out
 
 
 NOALLOC_MAX_PAIRS = 65536

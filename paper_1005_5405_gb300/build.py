@@ -52,7 +52,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
               f"-I{os.path.join(ROOT, 'include')}", f"-I{SRC}"]
     if verbose:
         common.append("-Xptxas=-v")
-    units = ["bz_api.cu", "bz_noalloc.cu"]
+    units = ["bz_api.cu", "bz_noalloc.cu", "bz_adjoint.cu"]
     objs = [os.path.join(OUT_DIR, u.replace(".cu", f".{os.getpid()}.o")) for u in units]
     # The translation units compile in parallel, then link into one library.
     procs = [subprocess.Popen(common + ["-c", "-o", o, os.path.join(SRC, u)],

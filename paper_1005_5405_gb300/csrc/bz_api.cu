@@ -104,6 +104,7 @@ struct bz_handle {
     size_t smem4 = 0;
     int *sc_count = nullptr, *sc_cursor = nullptr, *sc_meta = nullptr;  // scatter-list sort
     uint32_t *sc_ent = nullptr;
+    bz_adj_scratch adj{};               // bz_adjoint_step scratch, allocated on first use
 };
 
 namespace {
@@ -420,6 +421,7 @@ void release(bz_handle *H)
                     H->mom, H->gw_global, H->stats, H->flag, H->axv, H->axA, H->profile};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    bz_adj_release(&H->adj);
 }
 
 }  // namespace
@@ -889,6 +891,22 @@ bz_status bz_profile_read(bz_handle *H, double ms[4], int64_t launches[4])
     }
     clear_events(H);
     return BZ_OK;
+}
+
+bz_status bz_adjoint_step(bz_handle *H, int64_t step, const void *h_n, const void *lam_in,
+                          void *lam_out, double *grad_lid, double wD, void *stream)
+{
+    if (!H || !h_n || !lam_in || !lam_out) return fail(BZ_EINVAL, "NULL argument");
+    if (step < 0) return fail(BZ_EINVAL, "step must be >= 0");
+    if (!std::isfinite(wD)) return fail(BZ_EINVAL, "wD must be finite");
+    const size_t bytes = H->esz * (size_t)H->g.nr * H->g.nvt;
+    const char *a = (const char *)h_n, *b = (const char *)lam_out;
+    if (a < b + bytes && b < a + bytes) return fail(BZ_EINVAL, "lam_out overlaps h_n");
+    g_last_error.clear();
+    bz_status st = bz_adj_prepare(&H->adj, H->g, H->dtype, H->nsm, H->smem_optin);
+    if (st != BZ_OK) return st;
+    return bz_adj_launch(&H->adj, H->g, H->dtype, step, h_n, lam_in, lam_out, grad_lid, wD,
+                         H->stats, (cudaStream_t)stream, &H->launches);
 }
 
 bz_status bz_philox(uint32_t k0, uint32_t k1, const uint32_t *ctr, int64_t n, uint32_t *out)

@@ -1,5 +1,35 @@
 // bz_internal.h -- helpers shared by the library's translation units.
 #pragma once
 
+#include "bz.h"
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace bzk {
+struct Geo;
+}
+
 // Stores the text returned by bz_last_error() on this thread.
 void bz_record_error(const char *msg);
+
+// Scratch of bz_adjoint_step (bz_adjoint.cu), owned by a handle.
+struct bz_adj_scratch {
+    int4 *pidx;          // sample node indices, logical order
+    void *pa;            // gather records (a, b, W)
+    void *ghost;         // ghost values of the forward walls of step n
+    void *lt;            // dJ/dh~, one state
+    double *nw, *lF;     // wall densities, dJ/d(outgoing flux) per face
+    int64_t *step;       // device step counter of the recomputed step
+    int threads, grid;
+    size_t smem;
+};
+
+// Allocates the scratch and sets up the kernels on the first call.
+bz_status bz_adj_prepare(bz_adj_scratch *a, const bzk::Geo &g, int dtype, int nsm, int smem_optin);
+// The launches of one adjoint step (see bz_adjoint_step in bz.h).
+bz_status bz_adj_launch(bz_adj_scratch *a, const bzk::Geo &g, int dtype, int64_t step,
+                        const void *hn, const void *lam_in, void *lam_out, double *grad_lid,
+                        double wD, unsigned long long *stats, cudaStream_t s, long long *launches);
+void bz_adj_release(bz_adj_scratch *a);
