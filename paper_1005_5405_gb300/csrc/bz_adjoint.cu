@@ -7,6 +7,7 @@
 #include "bz.h"
 #include "bz_internal.h"
 #include "bz_adjoint.cuh"
+#include "bz_cell4.cuh"
 
 #include <cuda_runtime.h>
 
@@ -16,6 +17,12 @@
 #include <string>
 
 namespace {
+
+bool alloc_fault()
+{
+    const char *f = getenv("BZ_FAULT");
+    return f && std::string(f) == "alloc";
+}
 
 bz_status err(bz_status st, const char *msg)
 {
@@ -31,8 +38,30 @@ bz_status cuda_err(cudaError_t e, const char *what)
     return e == cudaErrorMemoryAllocation ? BZ_ENOMEM : BZ_ECUDA;
 }
 
+// Buffers used by both kernels of the cell phase.
 template <typename R>
-bz_status prepare(bz_adj_scratch *a, const bzk::Geo &g, int nsm, int optin)
+bz_status alloc_common(bz_adj_scratch *t, const bzk::Geo &g)
+{
+    const size_t bytes[7] = {sizeof(int4) * (size_t)g.nt,
+                             sizeof(bzk::PlanA<R, int>) * (size_t)g.nt,
+                             sizeof(R) * (size_t)g.nfaces * g.nv,
+                             sizeof(double) * g.nfaces,
+                             sizeof(double) * g.nfaces,
+                             sizeof(int64_t),
+                             sizeof(R) * (size_t)g.nr * g.nvt};
+    void **dst[7] = {(void **)&t->pidx, &t->pa, &t->ghost, (void **)&t->nw, (void **)&t->lF,
+                     (void **)&t->step, &t->lt};
+    for (int k = 0; k < 7; ++k) {
+        cudaError_t e = alloc_fault() ? cudaErrorMemoryAllocation : cudaMalloc(dst[k], bytes[k]);
+        if (e != cudaSuccess) return cuda_err(e, "adjoint scratch allocation");
+    }
+    return BZ_OK;
+}
+
+// Launch shape of the generic cell kernel (three slabs and the per-sample
+// products in shared memory).
+template <typename R>
+bz_status setup_generic(bz_adj_scratch *a, const bzk::Geo &g, int nsm, int optin)
 {
     const int n2 = g.nv * g.nv;
     const int threads = std::min(bzk::kMaxThreads, (n2 + 31) / 32 * 32);
@@ -51,29 +80,53 @@ bz_status prepare(bz_adj_scratch *a, const bzk::Geo &g, int nsm, int optin)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bzk::k_adj_cell<R>, threads, smem);
     if (e != cudaSuccess) return cuda_err(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (occ < 1) return err(BZ_EUNSUPPORTED, "adjoint cell kernel cannot be resident");
-    bz_adj_scratch t{};
-    t.threads = threads;
-    t.smem = smem;
-    t.grid = std::min(g.nr, nsm * occ);
-    const size_t bytes[7] = {sizeof(int4) * (size_t)g.nt,
-                             sizeof(bzk::PlanA<R, int>) * (size_t)g.nt,
-                             sizeof(R) * (size_t)g.nfaces * g.nv,
-                             sizeof(double) * g.nfaces,
-                             sizeof(double) * g.nfaces,
-                             sizeof(int64_t),
-                             sizeof(R) * (size_t)g.nr * g.nvt};
-    void **dst[7] = {(void **)&t.pidx, &t.pa, &t.ghost, (void **)&t.nw, (void **)&t.lF,
-                     (void **)&t.step, &t.lt};
-    for (int k = 0; k < 7; ++k) {
-        e = getenv("BZ_FAULT") && std::string(getenv("BZ_FAULT")) == "alloc"
-                ? cudaErrorMemoryAllocation
-                : cudaMalloc(dst[k], bytes[k]);
-        if (e != cudaSuccess) {
-            for (int m = 0; m < k; ++m) cudaFree(*dst[m]);
-            return cuda_err(e, "adjoint scratch allocation");
-        }
+    a->threads = threads;
+    a->smem = smem;
+    a->grid = std::min(g.nr, nsm * occ);
+    return BZ_OK;
+}
+
+// The FP32 quad kernel applies when the forward fast path's conditions hold
+// (velocity axis a multiple of 4, 16-bit node indices, 15-bit sample
+// indices) and the two extra slabs fit in shared memory.
+bz_status prepare_fast(bz_adj_scratch *a, const bzk::Geo &g, int nsm, int optin)
+{
+    const int N = g.nv, Q = N * N / 4;
+    const char *force = getenv("BZ_KERNEL");
+    if (force && std::string(force) == "generic") return BZ_OK;
+    if (N % 4 != 0 || N < 12 || g.nvt >= 65535 || g.nt > 32768 || Q > 1024) return BZ_OK;
+    const size_t smem = bzk::adj4_smem_bytes(N, g.nvt, g.nt);
+    if (smem > (size_t)optin) return BZ_OK;
+    int K = 1;
+    for (int k = 1; k <= N; ++k)
+        if (N % k == 0 && Q * k <= 1024) K = k;
+    const int T = (Q * K + 31) / 32 * 32;
+    cudaError_t e = cudaFuncSetAttribute(bzk::k_adj_cell4<1024>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_err(e, "cudaFuncSetAttribute");
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bzk::k_adj_cell4<1024>, T, smem);
+    if (e != cudaSuccess) return cuda_err(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (occ < 1) return BZ_OK;
+    const size_t bytes[6] = {sizeof(ushort4) * (size_t)g.nt,
+                             sizeof(bzk::PlanA<float, uint16_t>) * (size_t)g.nt,
+                             sizeof(int) * (size_t)g.nvt,
+                             sizeof(int) * (size_t)g.nvt,
+                             sizeof(int) * 2,
+                             sizeof(uint32_t) * ((size_t)4 * g.nt + bzk::kMaxThreads)};
+    void **dst[6] = {&a->pidx16, &a->pa16, (void **)&a->sc_count, (void **)&a->sc_cursor,
+                     (void **)&a->sc_meta, (void **)&a->sc_ent};
+    for (int k = 0; k < 6; ++k) {
+        e = alloc_fault() ? cudaErrorMemoryAllocation : cudaMalloc(dst[k], bytes[k]);
+        if (e != cudaSuccess) return cuda_err(e, "adjoint scratch allocation");
     }
-    *a = t;
+    a->fast = true;
+    a->threads = T;
+    a->smem = smem;
+    a->grid = std::min(g.nr, nsm * occ);
+    a->map[0] = Q;
+    a->map[1] = K;
+    a->map[2] = N / K;
     return BZ_OK;
 }
 
@@ -96,17 +149,56 @@ bz_status launch(bz_adj_scratch *a, const bzk::Geo &g0, int64_t step, const R *h
         bzk::k_walls<R><<<g.nfaces, 256, 0, s>>>(g, a->step, hn, (R *)a->ghost, a->nw, nullptr);
         e = check();
     }
-    if (e == cudaSuccess) {
-        const int pb = 256, pg = (g.nt + pb - 1) / pb;
-        bzk::k_plan<R, int><<<pg, pb, 0, s>>>(g, a->step, a->pidx, (bzk::PlanA<R, int> *)a->pa,
-                                              nullptr, nullptr);
-        e = check();
-    }
-    if (e == cudaSuccess) {
-        bzk::k_adj_cell<R><<<a->grid, a->threads, a->smem, s>>>(
-            g, hn, (const R *)a->ghost, a->pidx, (const bzk::PlanA<R, int> *)a->pa, lam_in,
-            (R *)a->lt, stats);
-        e = check();
+    const int pb = 256, pg = (g.nt + pb - 1) / pb;
+    bool fast = false;
+    if constexpr (sizeof(R) == 4) fast = a->fast;
+    if (fast) {
+        // FP32 quad kernel: plan in the shared-memory order and the
+        // destination-sorted scatter list, as the forward step builds them.
+        bzk::Geo gs = g;
+        gs.swz = 1;
+        const ushort4 *pi = (const ushort4 *)a->pidx16;
+        if (e == cudaSuccess) {
+            bzk::k_plan<float, uint16_t><<<pg, pb, 0, s>>>(
+                gs, a->step, (ushort4 *)a->pidx16, (bzk::PlanA<float, uint16_t> *)a->pa16,
+                nullptr, nullptr);
+            e = check();
+        }
+        if (e == cudaSuccess) e = cudaMemsetAsync(a->sc_count, 0, sizeof(int) * g.nvt, s);
+        if (e == cudaSuccess) {
+            bzk::k_scatter_count<<<pg, pb, 0, s>>>(g.nt, pi, a->sc_count);
+            e = check();
+        }
+        if (e == cudaSuccess) {
+            bzk::k_scatter_scan<<<1, 1024, 0, s>>>(g.nvt, a->threads, a->sc_count, a->sc_cursor,
+                                                   a->sc_meta);
+            e = check();
+        }
+        if (e == cudaSuccess) {
+            bzk::k_scatter_fill<<<pg, pb, 0, s>>>(g.nt, a->threads, pi, a->sc_cursor, a->sc_meta,
+                                                  a->sc_ent);
+            e = check();
+        }
+        if (e == cudaSuccess) {
+            const bzk::Map4 m{a->map[0], a->map[1], a->map[2]};
+            bzk::k_adj_cell4<1024><<<a->grid, a->threads, a->smem, s>>>(
+                gs, m, (const float *)hn, (const float *)a->ghost, pi,
+                (const bzk::PlanA<float, uint16_t> *)a->pa16, a->sc_ent, a->sc_meta,
+                (const float *)lam_in, (float *)a->lt, stats);
+            e = check();
+        }
+    } else {
+        if (e == cudaSuccess) {
+            bzk::k_plan<R, int><<<pg, pb, 0, s>>>(g, a->step, a->pidx,
+                                                  (bzk::PlanA<R, int> *)a->pa, nullptr, nullptr);
+            e = check();
+        }
+        if (e == cudaSuccess) {
+            bzk::k_adj_cell<R><<<a->grid, a->threads, a->smem, s>>>(
+                g, hn, (const R *)a->ghost, a->pidx, (const bzk::PlanA<R, int> *)a->pa, lam_in,
+                (R *)a->lt, stats);
+            e = check();
+        }
     }
     if (e == cudaSuccess) {
         bzk::k_adj_walls<R><<<g.nfaces, 256, 0, s>>>(g, a->step, (const R *)a->lt, a->nw, a->lF,
@@ -131,7 +223,18 @@ bz_status launch(bz_adj_scratch *a, const bzk::Geo &g0, int64_t step, const R *h
 bz_status bz_adj_prepare(bz_adj_scratch *a, const bzk::Geo &g, int dtype, int nsm, int optin)
 {
     if (a->lt) return BZ_OK;
-    return dtype == BZ_F64 ? prepare<double>(a, g, nsm, optin) : prepare<float>(a, g, nsm, optin);
+    bz_adj_scratch t{};
+    bz_status st = dtype == BZ_F64 ? alloc_common<double>(&t, g) : alloc_common<float>(&t, g);
+    if (st == BZ_OK && dtype == BZ_F32) st = prepare_fast(&t, g, nsm, optin);
+    if (st == BZ_OK && !t.fast)
+        st = dtype == BZ_F64 ? setup_generic<double>(&t, g, nsm, optin)
+                             : setup_generic<float>(&t, g, nsm, optin);
+    if (st != BZ_OK) {
+        bz_adj_release(&t);
+        return st;
+    }
+    *a = t;
+    return BZ_OK;
 }
 
 bz_status bz_adj_launch(bz_adj_scratch *a, const bzk::Geo &g, int dtype, int64_t step,
@@ -147,7 +250,8 @@ bz_status bz_adj_launch(bz_adj_scratch *a, const bzk::Geo &g, int dtype, int64_t
 
 void bz_adj_release(bz_adj_scratch *a)
 {
-    void *ptrs[] = {a->pidx, a->pa, a->ghost, a->lt, a->nw, a->lF, a->step};
+    void *ptrs[] = {a->pidx, a->pa, a->ghost, a->lt, a->nw, a->lF, a->step,
+                    a->pidx16, a->pa16, a->sc_count, a->sc_cursor, a->sc_meta, a->sc_ent};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     *a = bz_adj_scratch{};

@@ -88,7 +88,7 @@ __device__ __forceinline__ Cell4Smem carve4(char *base, int N, int nvt)
 // node << 16 | loss << 15 | l, sorted by node by a counting sort, and stored
 // so that thread t of the cell kernel reads its contiguous run of C words at
 // stride T (coalesced).  meta[0] = number of words E, meta[1] = C.
-__global__ void k_scatter_count(int nt, const ushort4 *__restrict__ pidx, int *__restrict__ count)
+static __global__ void k_scatter_count(int nt, const ushort4 *__restrict__ pidx, int *__restrict__ count)
 {
     int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= nt) return;
@@ -100,7 +100,7 @@ __global__ void k_scatter_count(int nt, const ushort4 *__restrict__ pidx, int *_
 }
 
 // Exclusive scan of the per-node counts (one CTA of 1024 threads).
-__global__ void __launch_bounds__(1024) k_scatter_scan(int nvt, int T, const int *__restrict__ count,
+static __global__ void __launch_bounds__(1024) k_scatter_scan(int nvt, int T, const int *__restrict__ count,
                                                       int *__restrict__ cursor, int *__restrict__ meta)
 {
     __shared__ int part[1024];
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(1024) k_scatter_scan(int nvt, int T, const int
     }
 }
 
-__global__ void k_scatter_fill(int nt, int T, const ushort4 *__restrict__ pidx,
+static __global__ void k_scatter_fill(int nt, int T, const ushort4 *__restrict__ pidx,
                                int *__restrict__ cursor, const int *__restrict__ meta,
                                uint32_t *__restrict__ ent)
 {
@@ -238,7 +238,7 @@ __device__ __forceinline__ float4 upwind4(float4 h0, float4 hx, float4 hy, float
 // Free streaming alone (Eq. streaming2D) for FP32 states with a multiple-of-4
 // velocity axis: each thread moves 16-byte quads of four jz nodes, one CTA
 // per cell at a time in the strip order, interior cells without branches.
-__global__ void __launch_bounds__(1024) k_stream4(Geo g, const float *__restrict__ hin,
+static __global__ void __launch_bounds__(1024) k_stream4(Geo g, const float *__restrict__ hin,
                                                   const float *__restrict__ ghost,
                                                   float *__restrict__ hout)
 {
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(1024) k_stream4(Geo g, const float *__restrict
 }
 
 // Eqs. densita..sforzi from float sums (see finalize_moments).
-__device__ __noinline__ void finalize_moments_f(const float *m, float e, double *o)
+static __device__ __noinline__ void finalize_moments_f(const float *m, float e, double *o)
 {
     const float rho = m[0], n = 1.f + e * rho;
     const float u[3] = {m[1] / n, m[2] / n, m[3] / n};
@@ -327,7 +327,195 @@ __device__ __forceinline__ void cell4_setup(const Geo &g, const Cell4Smem &S)
 // One cell c of instance g: streaming into the slab (FUSED) or a copy of
 // h~, the Monte Carlo gather and scatter, the correction and the write-back.
 // Called by every thread of the CTA with the tables of g in place.
-template <bool FUSED>
+// What the adjoint mode of cell4_cell adds: two more slabs (N_c, then
+// lam_c / w; dJ/dh~), 20 saved correction sums, a per-jx table, lam of the
+// cell in and dJ/dh~ out (global, logical order), the sample set.
+struct Adj4 {
+    float4 *B, *C;
+    float *P, *cxi;
+    const float *lam;
+    float *lt;
+    const ushort4 *pidx;
+};
+
+// x = G^{-1} rhs for the Gram matrix G = G0 + eps sum_j N_c,j psi_j psi_j^T
+// of the correction (P[0..13] its moment sums, as in correction_spd), by
+// elimination without pivoting; pivoted elimination if a pivot is not
+// positive (fallback set).
+static __device__ __noinline__ void gram_solve(const Geo &g, const float *P, const float *rhs, float *x,
+                                        int *fallback)
+{
+    const float e = (float)g.eps;
+    const float p4 = P[4] + P[5] + P[6];
+    const float m[5][5] = {
+        {P[0], P[1], P[2], P[3], p4},
+        {P[1], P[4], P[7], P[8], P[10]},
+        {P[2], P[7], P[5], P[9], P[11]},
+        {P[3], P[8], P[9], P[6], P[12]},
+        {p4, P[10], P[11], P[12], P[13]}};
+    float G[5][5], b[5];
+    for (int a = 0; a < 5; ++a) {
+        for (int c = 0; c < 5; ++c) G[a][c] = g.G0f[a * 5 + c] + e * m[a][c];
+        b[a] = rhs[a];
+    }
+    chol_or_ge<float>(G, b, x, fallback);
+}
+
+// Adjoint part of one cell (after the forward recompute of cell4_cell in
+// adjoint mode: S.slab4 holds h~, X.B holds N_c, muf[0..4] mu, X.P the sums
+// of G).  With lam = dJ/dh^{n+1} of the cell:
+//   nu = sum_j lam_j (1 + eps h_c,j) psi_j,  xi = G^{-1} nu,
+//   lam_c,j = (lam_j - w_j psi_j.xi)(1 + eps psi_j.mu)      (dJ/dN_c times w)
+//   dJ/dh~_j = lam_c,j + w_j psi_j.xi                        (N = w h~ and pre)
+//   gamma_l = W_l (q_a* + q_b* - q_a - q_b),  q = lam_c / w  (dJ/d(g_l W_l))
+//   dJ/dh~_a += gamma_l (1 + eps h~_b),  dJ/dh~_b += gamma_l (1 + eps h~_a).
+__device__ __forceinline__ void adj4_tail(const Geo &g, const Map4 &m, int c, const Cell4Smem &S,
+                                          const Adj4 &X, const PlanA<float, uint16_t> *__restrict__ pa,
+                                          float *muf, int &fallback)
+{
+    const int N = g.nv, nvt = g.nvt, T = blockDim.x, t = threadIdx.x;
+    const float eps = (float)g.eps;
+    float *totf = reinterpret_cast<float *>(S.tot);
+    const int Q = m.Q, nq = N / 4, q = t % Q, kchunk = t / Q;
+    const bool active = kchunk < m.K;
+    const int jy = q / nq, qz = q % nq, rowq = jy * nq;
+    const int jx0 = active ? kchunk * m.J : 0, jx1 = active ? jx0 + m.J : 0;
+    auto phys = [&](int jx) {
+        int r = qz + S.rot[jx];
+        r -= r >= nq ? nq : 0;
+        return jx * Q + rowq + r;
+    };
+    const float vy = S.v[jy];
+
+    // ---- nu, with lam of the cell staged into C ----------------------------
+    float nu[5];
+    {
+        float a0 = 0.f, a1 = 0.f, a3 = 0.f, a4 = 0.f;
+        if (active) {
+            const float4 *lam4 = reinterpret_cast<const float4 *>(X.lam + (int64_t)c * nvt);
+            const float4 z4 = S.vzq[qz], i4 = S.IAzq[qz];
+            const float iay = S.IA[jy];
+            const float vz[4] = {z4.x, z4.y, z4.z, z4.w};
+            const float IAyz[4] = {iay * i4.x, iay * i4.y, iay * i4.z, iay * i4.w};
+            float qq[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) qq[i] = vy * vy + vz[i] * vz[i];
+#pragma unroll 2
+            for (int jx = jx0; jx < jx1; ++jx) {
+                const int o = phys(jx);
+                const float4 n = X.B[o], l = lam4[jx * Q + q];
+                X.C[o] = l;
+                const float4 gv = S.gram[jx];      // v, v^2, v^3, v^4
+                const float ia = S.IA[jx];
+                const float nn[4] = {n.x, n.y, n.z, n.w}, ll[4] = {l.x, l.y, l.z, l.w};
+                float ts = 0.f, tz = 0.f, tq = 0.f;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float hc = nn[i] * (ia * IAyz[i]);
+                    const float tv = ll[i] * (1.f + eps * hc);
+                    ts += tv;
+                    tz += tv * vz[i];
+                    tq += tv * qq[i];
+                }
+                a0 += ts;
+                a1 += ts * gv.x;
+                a3 += tz;
+                a4 += ts * gv.y + tq;
+            }
+        }
+        nu[0] = a0;
+        nu[1] = a1;
+        nu[2] = vy * a0;
+        nu[3] = a3;
+        nu[4] = a4;
+    }
+    block_reduce4<5>(nu, S.red, totf);
+    float *xif = muf + 8;
+    if (t == 0) gram_solve(g, X.P, totf, xif, &fallback);
+    __syncthreads();
+    for (int i = t; i < N; i += T) X.cxi[i] = xif[1] * S.v[i] + xif[4] * S.v[i] * S.v[i];
+    __syncthreads();
+
+    // ---- lam_c / w into B, lam_c + w psi.xi into C ---------------------------
+    if (active) {
+        const float4 z4 = S.vzq[qz], a4v = S.Azq[qz], i4 = S.IAzq[qz];
+        const float ay = S.A[jy], iay = S.IA[jy];
+        const float vz[4] = {z4.x, z4.y, z4.z, z4.w};
+        const float Ayz[4] = {ay * a4v.x, ay * a4v.y, ay * a4v.z, ay * a4v.w};
+        const float IAyz[4] = {iay * i4.x, iay * i4.y, iay * i4.z, iay * i4.w};
+        float ctm[4], cti[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float qi = vy * vy + vz[i] * vz[i];
+            ctm[i] = muf[0] + muf[2] * vy + muf[3] * vz[i] + muf[4] * qi;
+            cti[i] = xif[0] + xif[2] * vy + xif[3] * vz[i] + xif[4] * qi;
+        }
+#pragma unroll 2
+        for (int jx = jx0; jx < jx1; ++jx) {
+            const int o = phys(jx);
+            const float4 l = X.C[o];
+            const float4 fv = S.fin[jx];          // 1/A, cx, A, A v
+            const float cxi = X.cxi[jx];
+            const float ll[4] = {l.x, l.y, l.z, l.w};
+            float bq[4], cq[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float w = fv.z * Ayz[i], px = cti[i] + cxi, pm = ctm[i] + fv.y;
+                const float lc = (ll[i] - w * px) * (1.f + eps * pm);
+                bq[i] = lc * (fv.x * IAyz[i]);
+                cq[i] = lc + w * px;
+            }
+            X.B[o] = make_float4(bq[0], bq[1], bq[2], bq[3]);
+            X.C[o] = make_float4(cq[0], cq[1], cq[2], cq[3]);
+        }
+    }
+    __syncthreads();
+
+    // ---- transposed Monte Carlo update --------------------------------------
+    {
+        const float *Bf = reinterpret_cast<const float *>(X.B);
+        const float *Af = reinterpret_cast<const float *>(S.slab4);
+        float *Cf = reinterpret_cast<float *>(X.C);
+        auto one = [&](ushort4 d, float W) {
+            float gam = 0.f;
+            if (d.z != 0xFFFF) gam += Bf[d.z];
+            if (d.w != 0xFFFF) gam += Bf[d.w];
+            if (d.x != 0xFFFF) gam -= Bf[d.x];
+            if (d.y != 0xFFFF) gam -= Bf[d.y];
+            gam *= W;
+            if (gam != 0.f) {
+                const float ha = d.x != 0xFFFF ? Af[d.x] : 0.f;
+                const float hb = d.y != 0xFFFF ? Af[d.y] : 0.f;
+                if (d.x != 0xFFFF) atomicAdd(Cf + d.x, gam * (1.f + eps * hb));
+                if (d.y != 0xFFFF) atomicAdd(Cf + d.y, gam * (1.f + eps * ha));
+            }
+        };
+        int l = t;
+        for (; l + 7 * T < g.nt; l += 8 * T) {
+            ushort4 d[8];
+            float W[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                d[u] = X.pidx[l + u * T];
+                W[u] = pa[l + u * T].W;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) one(d[u], W[u]);
+        }
+        for (; l < g.nt; l += T) one(X.pidx[l], pa[l].W);
+    }
+    __syncthreads();
+
+    // ---- dJ/dh~ of the cell out (logical order) ------------------------------
+    if (active) {
+        float4 *dst = reinterpret_cast<float4 *>(X.lt + (int64_t)c * nvt);
+#pragma unroll 2
+        for (int jx = jx0; jx < jx1; ++jx) dst[jx * Q + q] = X.C[phys(jx)];
+    }
+    __syncthreads();
+}
+
+template <bool FUSED, bool ADJ = false>
 __device__ __forceinline__ void cell4_cell(const Geo &g, const Map4 &m, int c,
                                            const float *__restrict__ hin,
                                            const float *__restrict__ ghost,
@@ -335,8 +523,12 @@ __device__ __forceinline__ void cell4_cell(const Geo &g, const Map4 &m, int c,
                                            const uint32_t *__restrict__ ent,
                                            const int *__restrict__ meta, float *__restrict__ hout,
                                            double *__restrict__ mom, const Cell4Smem &S,
-                                           int &fallback, long long *__restrict__ clk, int ncell)
+                                           int &fallback, long long *__restrict__ clk, int ncell,
+                                           const Adj4 *X = nullptr)
 {
+    // The forward step works in place on one slab; the adjoint keeps h~ in
+    // the slab and builds N, N_c in a second one.
+    float4 *nsl = ADJ ? X->B : S.slab4;
     const int N = g.nv, nvt = g.nvt, T = blockDim.x, t = threadIdx.x;
     auto stamp = [&](int ph) {
         if (clk && blockIdx.x == 0 && t == 0 && ncell < kClkCells)
@@ -473,7 +665,7 @@ __device__ __forceinline__ void cell4_cell(const Geo &g, const Map4 &m, int c,
             const float4 cv = S.conv[jx];        // {A, v, v^2, -}
             float n0 = h.x * (cv.x * Ayz[0]), n1 = h.y * (cv.x * Ayz[1]);
             float n2 = h.z * (cv.x * Ayz[2]), n3 = h.w * (cv.x * Ayz[3]);
-            S.slab4[o] = make_float4(n0, n1, n2, n3);
+            nsl[o] = make_float4(n0, n1, n2, n3);
             const float sn = (n0 + n1) + (n2 + n3);
             p0 += sn;
             p1 += sn * cv.y;
@@ -489,7 +681,7 @@ __device__ __forceinline__ void cell4_cell(const Geo &g, const Map4 &m, int c,
     // Each thread walks its run of the destination-sorted list, sums the
     // terms of one node in a register and adds the sum with one atomic.
     {
-        float *slabw = reinterpret_cast<float *>(S.slab4);
+        float *slabw = reinterpret_cast<float *>(nsl);
         const int E = meta[0], C = meta[1];
         const int base = t * C, n = max(0, min(C, E - base));
         // Only the first and the last node of a run can be shared with the
@@ -545,7 +737,7 @@ __device__ __forceinline__ void cell4_cell(const Geo &g, const Map4 &m, int c,
         if (active) {
 #pragma unroll 2
             for (int jx = jx0; jx < jx1; ++jx) {
-                float4 n = S.slab4[phys(jx)];
+                float4 n = nsl[phys(jx)];
                 const float4 gv = S.gram[jx];   // v, v^2, v^3, v^4
                 const float nn[4] = {n.x, n.y, n.z, n.w};
 #pragma unroll
@@ -597,12 +789,19 @@ __device__ __forceinline__ void cell4_cell(const Geo &g, const Map4 &m, int c,
             correction_solve<float>(g, Pd, m8, &fallback);
             for (int a = 0; a < 5; ++a) muf[a] = (float)m8[a];
         }
+        if constexpr (ADJ)
+            for (int a = 0; a < 14; ++a) X->P[a] = totf[a];
     }
     __syncthreads();
     const float mu0 = muf[0], mux = muf[1], muy = muf[2], muz = muf[3], mu4 = muf[4];
     for (int i = t; i < N; i += T) S.fin[i].y = mux * S.v[i] + mu4 * S.v[i] * S.v[i];
     __syncthreads();
     stamp(6);
+
+    if constexpr (ADJ) {
+        adj4_tail(g, m, c, S, *X, pa, muf, fallback);
+        return;
+    }
 
     // ---- corrected write-back and output moments ---------------------------
     float mo[10];
@@ -678,5 +877,44 @@ k_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ 
     if (fallback && stats) atomicAdd(stats + 3, 1ull);
 }
 
+
+// Shared-memory bytes of k_adj_cell4: those of k_cell4 plus two slabs, the
+// saved correction sums and one per-jx table.
+__host__ __device__ inline size_t adj4_smem_bytes(int nv, int nvt, int nt)
+{
+    size_t off = (cell4_smem_bytes(nv, nvt, nt) + 15) & ~(size_t)15;
+    return off + 2 * sizeof(float) * nvt + sizeof(float) * (16 + nv);
+}
+
+// Forward recompute and adjoint of the per-cell relaxation of one step for
+// every cell (FP32 fast path): lt = dJ/dh~ from lam = dJ/dh^{n+1}.
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
+k_adj_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ ghost,
+            const ushort4 *__restrict__ pidx, const PlanA<float, uint16_t> *__restrict__ pa,
+            const uint32_t *__restrict__ ent, const int *__restrict__ meta,
+            const float *__restrict__ lam, float *__restrict__ lt,
+            unsigned long long *__restrict__ stats)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    const Cell4Smem S = carve4(smem_raw, g.nv, g.nvt);
+    Adj4 X;
+    {
+        size_t off = (cell4_smem_bytes(g.nv, g.nvt, g.nt) + 15) & ~(size_t)15;
+        X.B = reinterpret_cast<float4 *>(smem_raw + off);
+        X.C = X.B + g.nvt / 4;
+        X.P = reinterpret_cast<float *>(X.C + g.nvt / 4);
+        X.cxi = X.P + 16;
+        X.lam = lam;
+        X.lt = lt;
+        X.pidx = pidx;
+    }
+    cell4_setup(g, S);
+    int fallback = 0;
+    for (int kc = blockIdx.x; kc < g.nr; kc += gridDim.x)
+        cell4_cell<true, true>(g, m, cell_of(g, kc), hin, ghost, pa, ent, meta, nullptr, nullptr,
+                               S, fallback, nullptr, 0, &X);
+    if (fallback && stats) atomicAdd(stats + 3, 1ull);
+}
 
 }  // namespace bzk

@@ -24,6 +24,13 @@ struct bz_adj_scratch {
     int64_t *step;       // device step counter of the recomputed step
     int threads, grid;
     size_t smem;
+    // FP32 fast path (quad kernel): 16-bit plan in the shared-memory order,
+    // the destination-sorted scatter list of the step, the quad mapping.
+    bool fast;
+    void *pidx16, *pa16;
+    int *sc_count, *sc_cursor, *sc_meta;
+    uint32_t *sc_ent;
+    int map[3];          // Q, K, J
 };
 
 // Allocates the scratch and sets up the kernels on the first call.
