@@ -99,12 +99,22 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(nr):
+# The per-cell kernel a handle runs (bz_info.kernel_variant) and the ncu
+# summary of its 64x64-cell profiling case.
+CELL_KERNELS = {0: ("k_cell<fused>", None),
+                1: ("k_cell4<fused>", "k_cell_fused_cavity64_v32.md"),
+                2: ("k_lz", "k_lz_cavity64_v32.md")}
+
+
+def profiled_traffic(nr, variant):
     """DRAM bytes per launch of the per-cell kernel, from the committed ncu
     summary of the 64x64-cell case scaled to `nr` cells (its traffic is
     proportional to the cells processed: 8 B per node).  None when the summary
     is absent or the kernel source has changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", "k_cell_fused_cavity64_v32.md")
+    name = CELL_KERNELS.get(variant, (None, None))[1]
+    if name is None:
+        return None
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     vals = {}
@@ -319,6 +329,7 @@ def run_ours(args):
         return
 
     nodes = p.nodes
+    variant = cav.get_info().kernel_variant
     value = job_throughput(nodes, args.steps, world, ms_max / 1e3)
     pairs = job_throughput(p.nr * p.nt, args.steps, world, ms_max / 1e3)
     cell_ms = kms[2] / max(1, kn[2])
@@ -344,14 +355,14 @@ def run_ours(args):
         "kernels_ms_per_step": {"walls": kms[0] / max(1, kn[0]), "sampling": kms[1] / max(1, kn[1]),
                                 "cell": cell_ms},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(p.nr),
-                     "kernel": "k_cell4<fused>" if cav.get_info().kernel_variant == 1 else "k_cell<fused>",
+                     "frac": achieved / peak, "traffic": profiled_traffic(p.nr, variant),
+                     "kernel": CELL_KERNELS.get(variant, ("?", None))[0],
                      "algorithmic_bytes": alg_bytes, "peak_source": peak_src,
                      "step_frac": (step_bytes / (ms_max / args.steps / 1e3) / 1e9) / peak},
         "streaming": {
             "node_updates_per_s": world * nodes / (stream_step_ms / 1e3),
             "ms_per_step": stream_step_ms, "kernel_ms": stream_kernel_ms,
-            "kernel": "k_stream4" if cav.get_info().kernel_variant == 1 else "k_stream",
+            "kernel": "k_stream4" if variant >= 1 else "k_stream",
             "achieved_gbs": 2 * esz * nodes / (stream_kernel_ms / 1e3) / 1e9,
             "frac": 2 * esz * nodes / (stream_kernel_ms / 1e3) / 1e9 / peak,
             "note": "8 B/node (read h once, write h~ once); walls kernel excluded"},

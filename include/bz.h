@@ -116,7 +116,8 @@ typedef struct {
     int32_t nr, nvt;        /* cells, velocity nodes */
     int32_t dtype;
     int32_t threads_per_cell, smem_bytes;  /* per-cell kernel launch shape */
-    int32_t kernel_variant;  /* 0: generic per-cell kernel; 1: FP32 4-node-vector kernel */
+    int32_t kernel_variant;  /* 0: generic per-cell kernel; 1: FP32 4-node-vector kernel;
+                                2: FP32 active-node kernel with deferred correction */
 } bz_info;
 
 /* Create a solver for the driven cavity.  Validates every argument
@@ -174,7 +175,10 @@ bz_status bz_get_info(const bz_handle *h, bz_info *out);
 /* Counters since creation: [0] steps, [1] samples with a node outside the
  * velocity box, [2] samples within 1e-9 dv of a cell face, [3] correction
  * solves that fell back from Cholesky to pivoted elimination, [4] kernel
- * launches issued, [5..7] reserved (0).  Synchronises the device. */
+ * launches issued; on the active-node path (bz_info.kernel_variant 2) [5]
+ * steps whose active velocity nodes exceeded the kernel's compact arrays (they
+ * ran the fallback kernel), [6] active nodes of the latest step, [7] the
+ * compact arrays' capacity; otherwise [5..7] are 0.  Synchronises the device. */
 bz_status bz_stats(bz_handle *h, int64_t out[8]);
 
 /* The Monte Carlo sample set of step `step` (Sec. 4.2, Algorithm 2) as the

@@ -9,6 +9,7 @@
 #include "bz_kernels.cuh"
 #include "bz_cell4.cuh"
 #include "bz_batch.cuh"
+#include "bz_lazy.cuh"
 
 #include <cuda_runtime.h>
 
@@ -105,6 +106,23 @@ struct bz_handle {
     int *sc_count = nullptr, *sc_cursor = nullptr, *sc_meta = nullptr;  // scatter-list sort
     uint32_t *sc_ent = nullptr;
     bz_adj_scratch adj{};               // bz_adjoint_step scratch, allocated on first use
+    // Active-node path with deferred correction (bz_lazy.cuh).  A buffer with
+    // lazy_buf set holds h_c and its cells' pending corrections in mu[buf];
+    // mu[buf] is all zero whenever lazy_buf is clear.
+    bool lazy = false;
+    float *mu[2] = {nullptr, nullptr};
+    bool lazy_buf[2] = {false, false};
+    int4 *lz_idx = nullptr;
+    bzk::PlanA<float, int> *lz_pa = nullptr;
+    bzk::PlanA<float, uint16_t> *lz_pc = nullptr;
+    ushort4 *lz_qc = nullptr;
+    int *lz_flag = nullptr, *lz_cidx = nullptr, *lz_act = nullptr, *lz_wpre = nullptr;
+    int *lz_meta = nullptr, *lz_count = nullptr, *lz_cursor = nullptr;
+    uint32_t *lz_mask = nullptr, *lz_ent = nullptr;
+    int lz_mcap = 0, lz_G = 0, lz_L = 0, lz_nchunk = 0, lz_T = 0, lz_grid = 0, lz_mprobe = 0;
+    size_t lz_smem = 0;
+    bzk::Map4 lz_map{};
+    float lz_e0[bzk::kLzX] = {};
 };
 
 namespace {
@@ -273,11 +291,330 @@ bz_status configure_cell4(bz_handle *H)
     return BZ_OK;
 }
 
+// ---------------------------------------------------------------------
+// Active-node path with deferred correction (bz_lazy.cuh)
+// ---------------------------------------------------------------------
+
+// A buffer's pending corrections are applied in place (paths that read
+// corrected states call this first).
+bz_status materialize_if_lazy(bz_handle *H, int x, cudaStream_t s)
+{
+    if (!H->lazy_buf[x]) return BZ_OK;
+    const Geo &g = H->g;
+    bzk::k_lz_materialize<<<std::min(g.nr, H->nsm * 8), 256, 0, s>>>(
+        g, nullptr, (const float *)H->h[x], H->mu[x], (float *)H->h[x], nullptr);
+    BZ_LAUNCHED(H);
+    BZ_CUDA(cudaMemsetAsync(H->mu[x], 0, sizeof(float) * 8 * (size_t)g.nr, s));
+    H->lazy_buf[x] = false;
+    return BZ_OK;
+}
+
+// Buffer x is about to be overwritten by a path that writes corrected states.
+bz_status drop_lazy(bz_handle *H, int x, cudaStream_t s)
+{
+    if (!H->lazy_buf[x]) return BZ_OK;
+    BZ_CUDA(cudaMemsetAsync(H->mu[x], 0, sizeof(float) * 8 * (size_t)H->g.nr, s));
+    H->lazy_buf[x] = false;
+    return BZ_OK;
+}
+
+// Value of monomial k of the 30-entry sum vector of bz_lazy.cuh at (x, y, z).
+double lz_monomial(int k, double x, double y, double z)
+{
+    const double v2 = x * x + y * y + z * z;
+    switch (k) {
+    case 0: return 1.0;
+    case 1: return x;
+    case 2: return y;
+    case 3: return z;
+    case 4: return x * x;
+    case 5: return y * y;
+    case 6: return z * z;
+    case 7: return x * y;
+    case 8: return x * z;
+    case 9: return y * z;
+    case 10: return x * x * x;
+    case 11: return y * y * y;
+    case 12: return z * z * z;
+    case 13: return x * x * y;
+    case 14: return x * x * z;
+    case 15: return x * y * y;
+    case 16: return y * y * z;
+    case 17: return x * z * z;
+    case 18: return y * z * z;
+    case 19: return x * y * z;
+    case 20: return x * x * v2;
+    case 21: return y * y * v2;
+    case 22: return z * z * v2;
+    case 23: return x * y * v2;
+    case 24: return x * z * v2;
+    case 25: return y * z * v2;
+    case 26: return v2;
+    case 27: return x * v2;
+    case 28: return y * v2;
+    default: return z * v2;
+    }
+}
+
+// Velocity axes with a kernel specialised on their length (the others run
+// the kernel that reads it at run time).
+int lz_nv_key(int nv) { return nv == 32 || nv == 20 ? nv : 0; }
+
+template <int G, int NV>
+bz_status setup_lz_one(bz_handle *H, size_t smem, int *occ)
+{
+    BZ_CUDA(cudaFuncSetAttribute(bzk::k_lz<G, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, bzk::k_lz<G, NV>, H->lz_T, smem));
+    return BZ_OK;
+}
+
+template <int G>
+bz_status setup_lz_kernel(bz_handle *H, size_t smem, int *occ)
+{
+    switch (lz_nv_key(H->g.nv)) {
+    case 32: return setup_lz_one<G, 32>(H, smem, occ);
+    case 20: return setup_lz_one<G, 20>(H, smem, occ);
+    default: return setup_lz_one<G, 0>(H, smem, occ);
+    }
+}
+
+template <int G>
+void launch_lz_kernel(bz_handle *H, const bzk::LzArgs &a, cudaStream_t s)
+{
+    switch (lz_nv_key(H->g.nv)) {
+    case 32: bzk::k_lz<G, 32><<<H->lz_grid, H->lz_T, H->lz_smem, s>>>(H->g, a); break;
+    case 20: bzk::k_lz<G, 20><<<H->lz_grid, H->lz_T, H->lz_smem, s>>>(H->g, a); break;
+    default: bzk::k_lz<G, 0><<<H->lz_grid, H->lz_T, H->lz_smem, s>>>(H->g, a); break;
+    }
+}
+
+// Decide whether the active-node path applies (FP32 fast path, 16-bit node
+// indices) and size it: the number of active nodes is measured on the sample
+// sets of the first steps (it depends on the grid and the sample count only,
+// not on the state), the compact arrays get a margin above it, and the
+// per-sample chunk fills the rest of half an SM's shared memory.  Needs the
+// per-axis tables on the device.
+bz_status configure_lazy(bz_handle *H)
+{
+    H->lazy = false;
+    const Geo &g = H->g;
+    const char *force = getenv("BZ_KERNEL");
+    if (force && (strcmp(force, "generic") == 0 || strcmp(force, "cell4") == 0)) return BZ_OK;
+    if (!H->fast || g.nvt >= 65536 || g.nvt % 32 != 0) return BZ_OK;
+    const int N = g.nv, nvt = g.nvt, nt = g.nt;
+    const size_t mub = sizeof(float) * 8 * (size_t)g.nr;
+    BZ_TRY(dalloc(&H->mu[0], mub));
+    BZ_TRY(dalloc(&H->mu[1], mub));
+    BZ_CUDA(cudaMemset(H->mu[0], 0, mub));
+    BZ_CUDA(cudaMemset(H->mu[1], 0, mub));
+    BZ_TRY(dalloc(&H->lz_idx, sizeof(int4) * (size_t)nt));
+    BZ_TRY(dalloc(&H->lz_pa, sizeof(bzk::PlanA<float, int>) * (size_t)nt));
+    BZ_TRY(dalloc(&H->lz_pc, sizeof(bzk::PlanA<float, uint16_t>) * (size_t)nt));
+    BZ_TRY(dalloc(&H->lz_qc, sizeof(ushort4) * (size_t)nt));
+    BZ_TRY(dalloc(&H->lz_flag, sizeof(int) * nvt));
+    BZ_TRY(dalloc(&H->lz_cidx, sizeof(int) * nvt));
+    BZ_TRY(dalloc(&H->lz_act, sizeof(int) * nvt));
+    BZ_TRY(dalloc(&H->lz_mask, sizeof(uint32_t) * (nvt / 32)));
+    BZ_TRY(dalloc(&H->lz_wpre, sizeof(int) * (nvt / 32)));
+    BZ_TRY(dalloc(&H->lz_meta, sizeof(int) * bzk::lz_meta_size(bzk::kLzMaxChunks)));
+    BZ_CUDA(cudaMemset(H->lz_flag, 0, sizeof(int) * nvt));
+    BZ_CUDA(cudaMemset(H->lz_meta, 0, sizeof(int) * bzk::lz_meta_size(bzk::kLzMaxChunks)));
+
+    // Active nodes of the sample sets of steps 0..3.
+    int64_t *dstep = nullptr;
+    BZ_TRY(dalloc(&dstep, sizeof(int64_t)));
+    Geo gl = g;
+    gl.swz = 0;
+    const int pb = 256, pg = (nt + pb - 1) / pb;
+    int mmax = 0;
+    cudaError_t e = cudaSuccess;
+    for (int64_t st = 0; st < 4 && e == cudaSuccess; ++st) {
+        e = cudaMemcpy(dstep, &st, sizeof(int64_t), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) break;
+        bzk::k_plan<float, int><<<pg, pb>>>(gl, dstep, H->lz_idx, H->lz_pa, nullptr, nullptr);
+        bzk::k_lz_mark<<<pg, pb>>>(nt, H->lz_idx, H->lz_flag);
+        bzk::k_lz_scan<<<1, 1024>>>(nvt, nvt, H->lz_flag, H->lz_cidx, H->lz_act, H->lz_mask,
+                                    H->lz_wpre, H->lz_meta);
+        int m = 0;
+        e = cudaMemcpy(&m, H->lz_meta, sizeof(int), cudaMemcpyDeviceToHost);
+        mmax = std::max(mmax, m);
+    }
+    cudaFree(dstep);
+    if (e != cudaSuccess) return fail(BZ_ECUDA, "active-node probe failed: %s", cudaGetErrorString(e));
+    H->lz_mprobe = mmax;
+    // The count varies little from step to step (it is a sum of many nearly
+    // independent node hits); a step above the capacity runs the fallback.
+    int mcap = std::min(nvt, (mmax + mmax / 10 + 64 + 31) / 32 * 32);
+    if (const char *mc = getenv("BZ_LAZY_MCAP")) mcap = std::max(1, std::min(nvt, atoi(mc)));
+
+    // Threads: node pairs along jz, 512 threads at most; a streaming stage
+    // holds K jx-planes.
+    const int Q = N * N / 2;
+    if (Q > 512) return BZ_OK;
+    const int K = bzk::lz_planes(N);
+    H->lz_map = bzk::Map4{Q, K, N / K};
+    H->lz_T = (Q * K + 31) / 32 * 32;
+    int smem_sm = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, H->dev);
+    const size_t budget = std::min((size_t)H->smem_optin, (size_t)smem_sm / 2 - 1024);
+    const size_t ring = bzk::lz_region_bytes(H->lz_T, 1, 0);
+    bool ok = false;
+    for (int G : {2, 1}) {
+        const size_t fixed = bzk::lz_fixed_bytes(N, nvt, mcap, G);
+        if (fixed + ring > budget) continue;
+        const size_t avail = budget - fixed;
+        const int Lmax = (int)std::min<size_t>(avail / (sizeof(float) * G), 32768);
+        const int nchunk = (nt + Lmax - 1) / Lmax;
+        if (nchunk > bzk::kLzMaxChunks) continue;
+        const int L = (nt + nchunk - 1) / nchunk;
+        const size_t smem = fixed + bzk::lz_region_bytes(H->lz_T, G, L);
+        int occ = 0;
+        if (G == 2) BZ_TRY(setup_lz_kernel<2>(H, smem, &occ));
+        else BZ_TRY(setup_lz_kernel<1>(H, smem, &occ));
+        if (occ < 1) continue;
+        H->lz_G = G;
+        H->lz_L = L;
+        H->lz_nchunk = nchunk;
+        H->lz_smem = smem;
+        int per_sm = occ;
+        if (const char *c = getenv("BZ_LAZY_CTAS")) per_sm = std::max(1, std::min(occ, atoi(c)));
+        H->lz_grid = std::min((g.nr + G - 1) / G, H->nsm * per_sm);
+        ok = true;
+        break;
+    }
+    if (!ok) return BZ_OK;
+    H->lz_mcap = mcap;
+    BZ_TRY(dalloc(&H->lz_count, sizeof(int) * (size_t)H->lz_nchunk * nvt));
+    BZ_TRY(dalloc(&H->lz_cursor, sizeof(int) * (size_t)H->lz_nchunk * nvt));
+    BZ_TRY(dalloc(&H->lz_ent, sizeof(uint32_t) * ((size_t)4 * nt + (size_t)H->lz_nchunk * H->lz_T)));
+    BZ_CUDA(cudaMemset(H->lz_count, 0, sizeof(int) * (size_t)H->lz_nchunk * nvt));
+    // Equilibrium sums of the 30 monomials (the moments of h^{n+1} need them).
+    std::vector<double> axv(N), axA(N);
+    BZ_CUDA(cudaMemcpy(axv.data(), g.axv, sizeof(double) * N, cudaMemcpyDeviceToHost));
+    BZ_CUDA(cudaMemcpy(axA.data(), g.axA, sizeof(double) * N, cudaMemcpyDeviceToHost));
+    for (int k = 0; k < bzk::kLzX; ++k) {
+        double acc = 0.0;
+        for (int jx = 0; jx < N; ++jx)
+            for (int jy = 0; jy < N; ++jy)
+                for (int jz = 0; jz < N; ++jz)
+                    acc += axA[jx] * axA[jy] * axA[jz] * lz_monomial(k, axv[jx], axv[jy], axv[jz]);
+        H->lz_e0[k] = (float)acc;
+    }
+    H->lazy = true;
+    return BZ_OK;
+}
+
+// One fused step on the active-node path: walls (applying the input's
+// pending corrections), the sample set, its compact form and scatter list,
+// the per-cell kernel, and the k_cell4 fallback that runs only when the step
+// has more active nodes than the compact arrays hold.
+bz_status launch_lazy(bz_handle *H, cudaStream_t s)
+{
+    const Geo &g = H->g;
+    Geo gl = g;
+    gl.swz = 0;
+    const int in = H->cur, out = in ^ 1;
+    float *hin = (float *)H->h[in];
+    float *hout = (float *)H->h[out];
+    {
+        ProfScope ps(H, 0, s);
+        bzk::k_walls<float><<<g.nfaces, 256, 0, s>>>(g, H->d_step, hin, (float *)H->ghost, H->nw,
+                                                     nullptr, H->mu[in]);
+        BZ_LAUNCHED(H);
+    }
+    const int pb = 256, pg = (g.nt + pb - 1) / pb;
+    {
+        ProfScope ps(H, 1, s);
+        bzk::k_plan<float, int><<<pg, pb, 0, s>>>(gl, H->d_step, H->lz_idx, H->lz_pa, nullptr,
+                                                  H->stats);
+        BZ_LAUNCHED(H);
+        bzk::k_lz_mark<<<pg, pb, 0, s>>>(g.nt, H->lz_idx, H->lz_flag);
+        BZ_LAUNCHED(H);
+        bzk::k_lz_scan<<<1, 1024, 0, s>>>(g.nvt, H->lz_mcap, H->lz_flag, H->lz_cidx, H->lz_act,
+                                          H->lz_mask, H->lz_wpre, H->lz_meta, H->stats);
+        BZ_LAUNCHED(H);
+        bzk::k_lz_remap<<<pg, pb, 0, s>>>(g.nt, H->lz_L, H->lz_idx, H->lz_pa, H->lz_cidx,
+                                          H->lz_meta, H->lz_pc, H->lz_qc, H->lz_count);
+        BZ_LAUNCHED(H);
+        bzk::k_lz_lscan<<<1, 1024, 0, s>>>(H->lz_nchunk, H->lz_T, H->lz_count, H->lz_cursor,
+                                           H->lz_meta);
+        BZ_LAUNCHED(H);
+        bzk::k_lz_lfill<<<pg, pb, 0, s>>>(g.nt, H->lz_L, H->lz_nchunk, H->lz_T, H->lz_qc,
+                                          H->lz_cursor, H->lz_meta, H->lz_ent);
+        BZ_LAUNCHED(H);
+    }
+    {
+        ProfScope ps(H, 2, s);
+        bzk::LzArgs a{};
+        a.m = H->lz_map;
+        a.hin = hin;
+        a.mu_in = H->mu[in];
+        a.ghost = (const float *)H->ghost;
+        a.hout = hout;
+        a.mu_out = H->mu[out];
+        a.mom = H->mom;
+        a.pc = H->lz_pc;
+        a.ent = H->lz_ent;
+        a.meta = H->lz_meta;
+        a.mask = H->lz_mask;
+        a.wpre = H->lz_wpre;
+        a.act = H->lz_act;
+        a.mcap = H->lz_mcap;
+        a.L = H->lz_L;
+        a.nchunk = H->lz_nchunk;
+        for (int k = 0; k < bzk::kLzX; ++k) a.e0[k] = H->lz_e0[k];
+        a.clk = H->prof_clk;
+        if (H->lz_G == 2) launch_lz_kernel<2>(H, a, s);
+        else launch_lz_kernel<1>(H, a, s);
+        BZ_LAUNCHED(H);
+    }
+    {
+        // Fallback (each launch returns at once unless the step overflowed);
+        // timed with the per-step plan.
+        ProfScope ps(H, 1, s);
+        const ushort4 *pi = (const ushort4 *)H->pidx;
+        auto *pa16 = (bzk::PlanA<float, uint16_t> *)H->pa;
+        BZ_CUDA(cudaMemsetAsync(H->sc_count, 0, sizeof(int) * g.nvt, s));
+        bzk::k_lz_fb_plan<<<pg, pb, 0, s>>>(g.nt, g.nv, H->lz_meta, H->lz_idx, H->lz_pa,
+                                            (ushort4 *)H->pidx, pa16, H->sc_count);
+        BZ_LAUNCHED(H);
+        bzk::k_scatter_scan<<<1, 1024, 0, s>>>(g.nvt, H->threads4, H->sc_count, H->sc_cursor,
+                                               H->sc_meta, H->lz_meta);
+        BZ_LAUNCHED(H);
+        bzk::k_scatter_fill<<<pg, pb, 0, s>>>(g.nt, H->threads4, pi, H->sc_cursor, H->sc_meta,
+                                              H->sc_ent, H->lz_meta);
+        BZ_LAUNCHED(H);
+        bzk::k_lz_materialize<<<std::min(g.nr, H->nsm * 8), 256, 0, s>>>(
+            g, H->lz_meta, hin, H->mu[in], hin, H->mu[out]);
+        BZ_LAUNCHED(H);
+        const int grid = H->grid4f;
+        if (H->maxt4 == 512)
+            bzk::k_cell4<true, 512><<<grid, H->threads4, H->smem4, s>>>(
+                g, H->map, hin, (const float *)H->ghost, pa16, H->sc_ent, H->sc_meta, hout, H->mom,
+                H->stats, nullptr, H->lz_meta);
+        else
+            bzk::k_cell4<true, 1024><<<grid, H->threads4, H->smem4, s>>>(
+                g, H->map, hin, (const float *)H->ghost, pa16, H->sc_ent, H->sc_meta, hout, H->mom,
+                H->stats, nullptr, H->lz_meta);
+        BZ_LAUNCHED(H);
+    }
+    H->cur = out;
+    H->mom_valid = true;
+    H->lazy_buf[out] = true;
+    return advance(H, s);
+}
+
 template <typename R, typename I>
 bz_status launch_step(bz_handle *H, cudaStream_t s, bool fused, bool do_stream, bool do_collide)
 {
     using V4 = typename bzk::Idx4<I>::type;
     using PA = bzk::PlanA<R, I>;
+    if constexpr (sizeof(R) == 4)
+        if (fused && H->lazy) return launch_lazy(H, s);
+    // Every other path reads and writes corrected states.
+    BZ_TRY(materialize_if_lazy(H, H->cur, s));
+    BZ_TRY(drop_lazy(H, H->cur ^ 1, s));
     Geo &g = H->g;
     R *hin = (R *)H->h[H->cur];
     R *hout = (R *)H->h[H->cur ^ 1];
@@ -420,6 +757,11 @@ void release(bz_handle *H)
     void *ptrs[] = {H->d_step, H->sc_count, H->sc_cursor, H->sc_meta, H->sc_ent, H->prof_clk, H->h[0], H->h[1], H->ht, H->pidx, H->pa, H->ghost, H->nw, H->shear,
                     H->mom, H->gw_global, H->stats, H->flag, H->axv, H->axA, H->profile};
     for (void *p : ptrs)
+        if (p) cudaFree(p);
+    void *lz[] = {H->mu[0], H->mu[1], H->lz_idx, H->lz_pa, H->lz_pc, H->lz_qc, H->lz_flag,
+                  H->lz_cidx, H->lz_act, H->lz_wpre, H->lz_meta, H->lz_count, H->lz_cursor,
+                  H->lz_mask, H->lz_ent};
+    for (void *p : lz)
         if (p) cudaFree(p);
     bz_adj_release(&H->adj);
 }
@@ -584,6 +926,8 @@ bz_status bz_create(const bz_space *space, const bz_vel *vel, const bz_walls *wa
     g.axv = H->axv;
     g.axA = H->axA;
     g.lid_profile = walls->lid_profile ? H->profile : nullptr;
+    st = configure_lazy(H);
+    if (st != BZ_OK) return bail(st);
     *out = H;
     return BZ_OK;
 }
@@ -623,6 +967,7 @@ bz_status capture_pair(bz_handle *H)
     const int64_t step0 = H->step;
     const long long l0 = H->launches;
     const bool mv0 = H->mom_valid;
+    const bool lz0[2] = {H->lazy_buf[0], H->lazy_buf[1]};
     BZ_CUDA(cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal));
     bz_status st = one_step(H, H->cap_stream, true, false, false);
     if (st == BZ_OK) st = one_step(H, H->cap_stream, true, false, false);
@@ -633,6 +978,8 @@ bz_status capture_pair(bz_handle *H)
     H->step = step0;
     H->launches = l0;
     H->mom_valid = mv0;
+    H->lazy_buf[0] = lz0[0];
+    H->lazy_buf[1] = lz0[1];
     if (st != BZ_OK) {
         if (graph) cudaGraphDestroy(graph);
         return st;
@@ -662,12 +1009,19 @@ bz_status bz_step_ex(bz_handle *H, int32_t nsteps, uint32_t flags, void *stream)
     if (ds && dc && !H->ht) BZ_TRY(dalloc(&H->ht, H->esz * (size_t)H->g.nr * H->g.nvt));
     int32_t n = 0;
     if (fused && nsteps >= 2 && !H->prof && graphs_enabled()) {
+        // The captured steps read the buffers as they are now: bring the
+        // pair into the state the steps leave it in before capturing.
+        if (!H->lazy) {
+            BZ_TRY(materialize_if_lazy(H, H->cur, s));
+            BZ_TRY(drop_lazy(H, H->cur ^ 1, s));
+        }
         if (!H->graph[H->cur]) BZ_TRY(capture_pair(H));
         for (; n + 1 < nsteps; n += 2) {
             BZ_CUDA(cudaGraphLaunch(H->graph[H->cur], s));
             H->step += 2;
             H->launches += H->graph_launches;
             H->mom_valid = true;
+            if (H->lazy) H->lazy_buf[0] = H->lazy_buf[1] = true;
         }
     }
     for (; n < nsteps; ++n) BZ_TRY(one_step(H, s, fused, ds, dc));
@@ -685,6 +1039,7 @@ bz_status bz_moments(bz_handle *H, double *out, void *stream)
     cudaStream_t s = (cudaStream_t)stream;
     const Geo &g = H->g;
     if (!H->mom_valid) {
+        BZ_TRY(materialize_if_lazy(H, H->cur, s));
         int grid = std::min(g.nr, H->nsm * 8);
         if (H->dtype == BZ_F64)
             bzk::k_moments<double><<<grid, 256, 0, s>>>(g, (const double *)H->h[H->cur], H->mom);
@@ -716,7 +1071,8 @@ bz_status bz_lid_shear(bz_handle *H, double *out, void *stream)
                                                       (double *)H->ghost, H->nw, H->shear);
     else
         bzk::k_walls<float><<<g.nfaces, 256, 0, s>>>(g, H->d_step, (const float *)H->h[H->cur],
-                                                     (float *)H->ghost, H->nw, H->shear);
+                                                     (float *)H->ghost, H->nw, H->shear,
+                                                     H->lazy ? H->mu[H->cur] : nullptr);
     BZ_LAUNCHED(H);
     double *tmp = H->mom;  // reuse: nr*11 >= nx+1 always (ny >= 1)
     if ((size_t)g.nr * 11 < (size_t)g.nx + 1) return fail(BZ_EINVAL, "internal size");
@@ -730,6 +1086,7 @@ bz_status bz_lid_shear(bz_handle *H, double *out, void *stream)
 bz_status bz_get_state(bz_handle *H, void *dst, int64_t *step, void *stream)
 {
     if (!H || !dst) return fail(BZ_EINVAL, "NULL argument");
+    BZ_TRY(materialize_if_lazy(H, H->cur, (cudaStream_t)stream));
     BZ_CUDA(cudaMemcpyAsync(dst, H->h[H->cur], H->esz * (size_t)H->g.nr * H->g.nvt,
                             cudaMemcpyDefault, (cudaStream_t)stream));
     if (step) *step = H->step;
@@ -740,6 +1097,7 @@ bz_status bz_set_state(bz_handle *H, const void *src, int64_t step, void *stream
 {
     if (!H || !src) return fail(BZ_EINVAL, "NULL argument");
     if (step < 0) return fail(BZ_EINVAL, "step must be >= 0");
+    BZ_TRY(drop_lazy(H, H->cur, (cudaStream_t)stream));
     BZ_CUDA(cudaMemcpyAsync(H->h[H->cur], src, H->esz * (size_t)H->g.nr * H->g.nvt,
                             cudaMemcpyDefault, (cudaStream_t)stream));
     BZ_CUDA(cudaMemcpyAsync(H->d_step, &step, sizeof(int64_t), cudaMemcpyHostToDevice,
@@ -790,9 +1148,9 @@ bz_status bz_get_info(const bz_handle *H, bz_info *o)
     o->nr = g.nr;
     o->nvt = g.nvt;
     o->dtype = H->dtype;
-    o->threads_per_cell = H->fast ? H->threads4 : H->threads;
-    o->smem_bytes = (int32_t)(H->fast ? H->smem4 : H->smem_cell);
-    o->kernel_variant = H->fast ? 1 : 0;
+    o->threads_per_cell = H->lazy ? H->lz_T : H->fast ? H->threads4 : H->threads;
+    o->smem_bytes = (int32_t)(H->lazy ? H->lz_smem : H->fast ? H->smem4 : H->smem_cell);
+    o->kernel_variant = H->lazy ? 2 : H->fast ? 1 : 0;
     return BZ_OK;
 }
 
@@ -805,6 +1163,7 @@ bz_status bz_stats(bz_handle *H, int64_t out[8])
     for (int i = 0; i < 8; ++i) out[i] = (int64_t)d[i];
     out[0] = H->step;
     out[4] = H->launches;
+    out[7] = H->lz_mcap;
     return BZ_OK;
 }
 

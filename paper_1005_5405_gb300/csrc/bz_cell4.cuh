@@ -100,9 +100,12 @@ static __global__ void k_scatter_count(int nt, const ushort4 *__restrict__ pidx,
 }
 
 // Exclusive scan of the per-node counts (one CTA of 1024 threads).
+// gate (nullable): when it is given and gate[1] is 0, the kernel does nothing.
 static __global__ void __launch_bounds__(1024) k_scatter_scan(int nvt, int T, const int *__restrict__ count,
-                                                      int *__restrict__ cursor, int *__restrict__ meta)
+                                                      int *__restrict__ cursor, int *__restrict__ meta,
+                                                      const int *__restrict__ gate = nullptr)
 {
+    if (gate && !gate[1]) return;
     __shared__ int part[1024];
     const int t = threadIdx.x, per = (nvt + 1023) / 1024;
     const int b = t * per, e = min(nvt, b + per);
@@ -129,8 +132,9 @@ static __global__ void __launch_bounds__(1024) k_scatter_scan(int nvt, int T, co
 
 static __global__ void k_scatter_fill(int nt, int T, const ushort4 *__restrict__ pidx,
                                int *__restrict__ cursor, const int *__restrict__ meta,
-                               uint32_t *__restrict__ ent)
+                               uint32_t *__restrict__ ent, const int *__restrict__ gate = nullptr)
 {
+    if (gate && !gate[1]) return;
     int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= nt) return;
     const int C = meta[1];
@@ -865,8 +869,10 @@ __global__ void __launch_bounds__(MAXT, 1)
 k_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ ghost,
         const PlanA<float, uint16_t> *__restrict__ pa, const uint32_t *__restrict__ ent,
         const int *__restrict__ meta, float *__restrict__ hout, double *__restrict__ mom,
-        unsigned long long *__restrict__ stats, long long *__restrict__ clk)
+        unsigned long long *__restrict__ stats, long long *__restrict__ clk,
+        const int *__restrict__ gate = nullptr)
 {
+    if (gate && !gate[1]) return;
     extern __shared__ __align__(16) char smem_raw[];
     const Cell4Smem S = carve4(smem_raw, g.nv, g.nvt);
     cell4_setup(g, S);

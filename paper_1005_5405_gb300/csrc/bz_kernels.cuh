@@ -349,11 +349,14 @@ __device__ __forceinline__ Face face_of(const Geo &g, int f, int64_t step)
 // One boundary face f: outgoing flux, wall density and ghost values, and on
 // the lid the shear.  Called by every thread of a CTA; sA, sv (kMaxN each),
 // red, tot (>= 2) and snw are shared scratch.
+// mu (nullable): per-cell deferred corrections (8 floats per cell) of a state
+// stored as h_c, whose value is h_c + (1 + eps h_c)(mu_c . psi_j).
 template <typename R>
 __device__ __forceinline__ void walls_face(const Geo &g, int64_t step, const R *__restrict__ h,
                                            R *__restrict__ ghost, double *__restrict__ nw_out,
                                            double *__restrict__ shear, int f, R *sA, R *sv,
-                                           double *red, double *tot, double *snw)
+                                           double *red, double *tot, double *snw,
+                                           const float *__restrict__ mu = nullptr)
 {
     const Face F = face_of(g, f, step);
     const int N = g.nv, N2 = N * N;
@@ -361,6 +364,9 @@ __device__ __forceinline__ void walls_face(const Geo &g, int64_t step, const R *
         sA[i] = (R)g.axA[i];
         sv[i] = (R)g.axv[i];
     }
+    R m5[5] = {R(0), R(0), R(0), R(0), R(0)};
+    if (mu)
+        for (int k = 0; k < 5; ++k) m5[k] = (R)mu[(int64_t)F.cell * 8 + k];
     __syncthreads();
     const R *hc = h + (int64_t)F.cell * g.nvt;
     const bool lid = f >= 2 * g.ny + g.nx;
@@ -376,6 +382,12 @@ __device__ __forceinline__ void walls_face(const Geo &g, int64_t step, const R *
         if (vn < R(0)) {
             R w = sA[jx] * sA[jy] * sA[jz];
             R hv = hc[j];
+            if (mu) {
+                const R vz = sv[jz];
+                const R kap = m5[0] + m5[1] * vx + m5[2] * vy + m5[3] * vz +
+                              m5[4] * (vx * vx + vy * vy + vz * vz);
+                hv = hv + (R(1) + (R)g.eps * hv) * kap;
+            }
             acc[0] -= vn * w * hv;
             if (lid) acc[1] += w * vx * vy * hv;
         }
@@ -421,13 +433,13 @@ __device__ __forceinline__ void walls_face(const Geo &g, int64_t step, const R *
 template <typename R>
 __global__ void k_walls(Geo g, const int64_t *__restrict__ stepp, const R *__restrict__ h,
                         R *__restrict__ ghost, double *__restrict__ nw_out,
-                        double *__restrict__ shear)
+                        double *__restrict__ shear, const float *__restrict__ mu = nullptr)
 {
     __shared__ double red[kMaxWarps * kRedSlots];
     __shared__ double tot[4];
     __shared__ double s_nw;
     __shared__ R sA[kMaxN], sv[kMaxN];
-    walls_face<R>(g, *stepp, h, ghost, nw_out, shear, blockIdx.x, sA, sv, red, tot, &s_nw);
+    walls_face<R>(g, *stepp, h, ghost, nw_out, shear, blockIdx.x, sA, sv, red, tot, &s_nw, mu);
 }
 
 // Advances the device step counter by one (the last launch of a step).

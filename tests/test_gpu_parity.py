@@ -117,17 +117,25 @@ def test_collide_matches_oracle(p, kernel):
     assert np.allclose(mom_g, mom_o, rtol=1e-4, atol=1e-6 * (1 + np.abs(mom_o).max()))
 
 
-@pytest.fixture(params=["auto", "t512", "generic"])
+@pytest.fixture(params=["auto", "overflow", "cell4", "t512", "generic"])
 def kernel(request, monkeypatch):
     """Run a test with the library's own choice of per-cell kernel (the FP32
-    4-node-vector kernel where it applies), with that kernel in its 512-thread
-    shape, and with the generic kernel."""
-    monkeypatch.delenv("BZ_KERNEL", raising=False)
-    monkeypatch.delenv("BZ_CELL_THREADS", raising=False)
+    active-node kernel with deferred correction where it applies), with that
+    kernel's compact arrays capped below the step's active-node count (every
+    step then takes the k_cell4 fallback on the device), with the FP32
+    4-node-vector kernel (BZ_KERNEL=cell4) in its 1024- and 512-thread shapes,
+    and with the generic kernel."""
+    for k in ("BZ_KERNEL", "BZ_CELL_THREADS", "BZ_LAZY_MCAP"):
+        monkeypatch.delenv(k, raising=False)
     if request.param == "generic":
         monkeypatch.setenv("BZ_KERNEL", "generic")
+    elif request.param == "cell4":
+        monkeypatch.setenv("BZ_KERNEL", "cell4")
     elif request.param == "t512":
+        monkeypatch.setenv("BZ_KERNEL", "cell4")
         monkeypatch.setenv("BZ_CELL_THREADS", "512")
+    elif request.param == "overflow":
+        monkeypatch.setenv("BZ_LAZY_MCAP", "8")
     return request.param
 
 
@@ -136,6 +144,8 @@ def test_fused_step_matches_oracle(p, kernel):
     cav, o, h0 = make(p)
     if kernel == "generic":
         assert cav.get_info().kernel_variant == 0
+    if kernel in ("cell4", "t512"):
+        assert cav.get_info().kernel_variant in (0, 1)
     h_o = h0
     for n in range(3):
         cav.step(1)
@@ -292,11 +302,47 @@ def test_checkpoint_resume():
     assert f_metric(o, state(a), state(c)) < 1e-6
 
 
-def test_fast_kernel_is_selected_for_fp32_quads():
-    for nv, expect in ((32, 1), (24, 1), (16, 1), (12, 1), (10, 0), (8, 0)):
+def test_fast_kernel_is_selected_for_fp32_quads(monkeypatch):
+    for nv, expect in ((32, 2), (24, 2), (16, 2), (12, 2), (10, 0), (8, 0)):
         p = workloads.small(nx=2, ny=2, nv=nv, vmax=4.0, nt=2000)
         assert binding.Cavity(p).get_info().kernel_variant == expect, nv
     assert binding.Cavity(workloads.small(nv=12, dtype="f64")).get_info().kernel_variant == 0
+    monkeypatch.setenv("BZ_KERNEL", "cell4")
+    assert binding.Cavity(workloads.small(nv=16, nt=2000)).get_info().kernel_variant == 1
+
+
+def test_deferred_correction_is_applied_by_every_reader():
+    """After steps on the active-node path the stored state carries pending
+    corrections: the lid shear, the moments, a state copy, a split step and
+    a restart from a copied state must all see the corrected state."""
+    p = workloads.small(nx=6, ny=5, nv=16, vmax=4.0, nt=3000, seed=11, dtype="f32", eps=0.1,
+                        lid_u0=0.1)
+    cav, o, h0 = make(p)
+    assert cav.get_info().kernel_variant == 2
+    h_o = h0
+    for n in range(3):
+        h_o, mom_o = o.step(h_o, n)
+    cav.step(3)
+    d = cav.lid_shear().cpu().numpy()
+    ref = o.lid_shear(h_o, 3)
+    assert np.allclose(d, ref, rtol=1e-4, atol=1e-5 * np.abs(ref).max())
+    mom = cav.moments().cpu().numpy()
+    assert np.allclose(mom, mom_o, rtol=1e-4, atol=1e-5 * (1 + np.abs(mom_o).max()))
+    assert f_metric(o, state(cav), h_o) < 3e-5
+    # a split step after lazy steps, then fused steps again
+    cav.step_ex(1, binding.BZ_SPLIT)
+    h_o, _ = o.step(h_o, 3)
+    assert f_metric(o, state(cav), h_o) < 4e-5
+    cav.step(2)
+    for n in (4, 5):
+        h_o, mom_o = o.step(h_o, n)
+    snap, st = cav.get_state()
+    assert st == 6 and f_metric(o, snap.double().cpu().numpy(), h_o) < 6e-5
+    c2 = binding.Cavity(p)
+    c2.set_state(snap.clone(), step=st)
+    c2.step(1)
+    cav.step(1)
+    assert f_metric(o, state(c2), state(cav)) < 1e-6
 
 
 def test_stats_and_info():
@@ -325,3 +371,4 @@ def test_errors_are_reported():
     finally:
         del os.environ["BZ_FAULT"]
     cav.step(1)
+
