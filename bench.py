@@ -502,6 +502,49 @@ def run_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
+def run_percell(args):
+    """Per-cell sample sets (every cell draws its own 10^4 samples, FP64
+    kinematics and node selection inside the per-cell kernel) against the
+    shared set on the same 64x64 cavity with a 24^3 velocity grid."""
+    import dataclasses
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1005_5405_gb300 import binding
+    torch.cuda.set_device(0)
+    p = problem("percell64_v24")
+    res = {}
+    for mode in ("per_cell", "shared"):
+        q = dataclasses.replace(p, per_cell=(mode == "per_cell"))
+        cav = binding.Cavity(q)
+        cav.set_state(workloads_state(q, torch), step=0)
+        cav.step(args.warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        cav.step(args.steps)
+        e1.record()
+        torch.cuda.synchronize()
+        res[mode] = e0.elapsed_time(e1) / args.steps
+        res[mode + "_variant"] = cav.get_info().kernel_variant
+        del cav
+        torch.cuda.empty_cache()
+    t = res["per_cell"] / 1e3
+    line = {
+        "metric": "phase-space node updates/s with per-cell sample sets (64^2 x 24^3 FP32)",
+        "value": p.nodes / t, "unit": "node-updates/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["per_cell"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": p.dtype, "data": "synthetic",
+        "config": {"workload": p.name, "nx": p.nx, "ny": p.ny, "nv": p.nv,
+                   "samples_per_cell": p.nt, "l2": "state 226 MB > L2, no flush"},
+        "samples_drawn_per_s": p.nr * p.nt / t,
+        "shared_set_ms_per_step": res["shared"],
+        "per_cell_over_shared": res["per_cell"] / res["shared"],
+        "kernel_variants": {"per_cell": res["per_cell_variant"], "shared": res["shared_variant"]},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def workloads_state(p, torch):
     from paper_1005_5405_gb300 import workloads
     return workloads.warm_state_device(p, seed=7, torch=torch)
@@ -515,6 +558,8 @@ def main():
         run_batch(args)
     elif args.config == "adjoint128_v20":
         run_adjoint(args)
+    elif args.config == "percell64_v24":
+        run_percell(args)
     else:
         run_ours(args)
 

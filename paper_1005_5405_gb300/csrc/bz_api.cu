@@ -109,6 +109,7 @@ struct bz_handle {
     // Active-node path with deferred correction (bz_lazy.cuh).  A buffer with
     // lazy_buf set holds h_c and its cells' pending corrections in mu[buf];
     // mu[buf] is all zero whenever lazy_buf is clear.
+    bool per_cell = false;              // every cell draws its own sample set
     bool lazy = false;
     float *mu[2] = {nullptr, nullptr};
     bool lazy_buf[2] = {false, false};
@@ -254,6 +255,7 @@ bz_status configure_cell4(bz_handle *H)
     const char *force = getenv("BZ_KERNEL");
     H->fast = false;
     if (force && strcmp(force, "generic") == 0) return BZ_OK;
+    if (H->per_cell) return BZ_OK;         // the shared-set kernels only
     if (H->dtype != BZ_F32 || !H->idx16 || N % 4 != 0 || N < 12) return BZ_OK;
     if (g.nt > 32768) return BZ_OK;                 // 15-bit sample index in the scatter list
     if (bzk::cell4_smem_bytes(N, g.nvt, g.nt) > (size_t)H->smem_optin) return BZ_OK;
@@ -623,7 +625,7 @@ bz_status launch_step(bz_handle *H, cudaStream_t s, bool fused, bool do_stream, 
         bzk::k_walls<R><<<g.nfaces, 256, 0, s>>>(g, H->d_step, hin, (R *)H->ghost, H->nw, nullptr);
         BZ_LAUNCHED(H);
     }
-    if (do_collide || fused) {
+    if ((do_collide || fused) && !H->per_cell) {
         ProfScope ps(H, 1, s);
         int pb = 256, pg = (g.nt + pb - 1) / pb;
         bzk::k_plan<R, I><<<pg, pb, 0, s>>>(g, H->d_step, (V4 *)H->pidx, (PA *)H->pa, nullptr, H->stats);
@@ -637,9 +639,14 @@ bz_status launch_step(bz_handle *H, cudaStream_t s, bool fused, bool do_stream, 
     }
     if (fused) {
         ProfScope ps(H, 2, s);
-        bzk::k_cell<R, true, I><<<H->grid_cell_fused, H->threads, H->smem_cell, s>>>(
-            g, hin, (const R *)H->ghost, (const V4 *)H->pidx, (const PA *)H->pa,
-            (R *)H->gw_global, hout, H->mom, H->stats, H->gw_in_smem);
+        if (H->per_cell)
+            bzk::k_cell<R, true, I, true><<<H->grid_cell_fused, H->threads, H->smem_cell, s>>>(
+                g, hin, (const R *)H->ghost, (const V4 *)H->pidx, (const PA *)H->pa,
+                (R *)H->gw_global, hout, H->mom, H->stats, H->gw_in_smem, H->d_step);
+        else
+            bzk::k_cell<R, true, I><<<H->grid_cell_fused, H->threads, H->smem_cell, s>>>(
+                g, hin, (const R *)H->ghost, (const V4 *)H->pidx, (const PA *)H->pa,
+                (R *)H->gw_global, hout, H->mom, H->stats, H->gw_in_smem);
         BZ_LAUNCHED(H);
         H->cur ^= 1;
         H->mom_valid = true;
@@ -680,9 +687,14 @@ bz_status launch_step(bz_handle *H, cudaStream_t s, bool fused, bool do_stream, 
     }
     if (do_collide) {
         ProfScope ps(H, 2, s);
-        bzk::k_cell<R, false, I><<<H->grid_cell, H->threads, H->smem_cell, s>>>(
-            g, hin, (const R *)H->ghost, (const V4 *)H->pidx, (const PA *)H->pa,
-            (R *)H->gw_global, hout, H->mom, H->stats, H->gw_in_smem);
+        if (H->per_cell)
+            bzk::k_cell<R, false, I, true><<<H->grid_cell, H->threads, H->smem_cell, s>>>(
+                g, hin, (const R *)H->ghost, (const V4 *)H->pidx, (const PA *)H->pa,
+                (R *)H->gw_global, hout, H->mom, H->stats, H->gw_in_smem, H->d_step);
+        else
+            bzk::k_cell<R, false, I><<<H->grid_cell, H->threads, H->smem_cell, s>>>(
+                g, hin, (const R *)H->ghost, (const V4 *)H->pidx, (const PA *)H->pa,
+                (R *)H->gw_global, hout, H->mom, H->stats, H->gw_in_smem);
         BZ_LAUNCHED(H);
         H->cur ^= 1;
         H->mom_valid = true;
@@ -691,18 +703,25 @@ bz_status launch_step(bz_handle *H, cudaStream_t s, bool fused, bool do_stream, 
     return BZ_OK;
 }
 
+template <typename R, typename I, bool PC>
+bz_status configure_kernels_pc(bz_handle *H, int *occ_f, int *occ_c)
+{
+    BZ_CUDA(cudaFuncSetAttribute(bzk::k_cell<R, true, I, PC>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)H->smem_cell));
+    BZ_CUDA(cudaFuncSetAttribute(bzk::k_cell<R, false, I, PC>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)H->smem_cell));
+    BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_f, bzk::k_cell<R, true, I, PC>,
+                                                          H->threads, H->smem_cell));
+    BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_c, bzk::k_cell<R, false, I, PC>,
+                                                          H->threads, H->smem_cell));
+    return BZ_OK;
+}
+
 template <typename R, typename I>
 bz_status configure_kernels(bz_handle *H, int *occ_f, int *occ_c)
 {
-    BZ_CUDA(cudaFuncSetAttribute(bzk::k_cell<R, true, I>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)H->smem_cell));
-    BZ_CUDA(cudaFuncSetAttribute(bzk::k_cell<R, false, I>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)H->smem_cell));
-    BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_f, bzk::k_cell<R, true, I>,
-                                                          H->threads, H->smem_cell));
-    BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_c, bzk::k_cell<R, false, I>,
-                                                          H->threads, H->smem_cell));
-    return BZ_OK;
+    return H->per_cell ? configure_kernels_pc<R, I, true>(H, occ_f, occ_c)
+                       : configure_kernels_pc<R, I, false>(H, occ_f, occ_c);
 }
 
 template <typename R>
@@ -711,12 +730,16 @@ bz_status configure_cell_kernel(bz_handle *H)
     Geo &g = H->g;
     int n2 = g.nv * g.nv;
     H->threads = std::min(bzk::kMaxThreads, (n2 + 31) / 32 * 32);
-    size_t with_gw = bzk::cell_smem_bytes<R>(g.nv, g.nvt, g.nt, true);
-    size_t without = bzk::cell_smem_bytes<R>(g.nv, g.nvt, g.nt, false);
+    // Per-cell sample sets keep each sample's four node indices in shared memory.
+    const size_t idxb = !H->per_cell ? 0 : H->idx16 ? sizeof(ushort4) : sizeof(int4);
+    size_t with_gw = bzk::cell_smem_bytes<R>(g.nv, g.nvt, g.nt, true, idxb);
+    size_t without = bzk::cell_smem_bytes<R>(g.nv, g.nvt, g.nt, false, idxb);
     if (without > (size_t)H->smem_optin)
         return fail(BZ_EUNSUPPORTED,
-                    "velocity slab of %d nodes needs %zu bytes of shared memory; the device "
-                    "offers %d per block", g.nvt, without, H->smem_optin);
+                    "velocity slab of %d nodes%s needs %zu bytes of shared memory; the device "
+                    "offers %d per block", g.nvt,
+                    H->per_cell ? " and the node indices of every per-cell sample" : "", without,
+                    H->smem_optin);
     H->gw_in_smem = with_gw <= (size_t)H->smem_optin;
     H->smem_cell = H->gw_in_smem ? with_gw : without;
     int occ_f = 0, occ_c = 0;
@@ -793,8 +816,6 @@ bz_status bz_create(const bz_space *space, const bz_vel *vel, const bz_walls *wa
         return fail(BZ_EINVAL, "dtype must be BZ_F32 or BZ_F64");
     if (params->sample_mode != BZ_SHARED && params->sample_mode != BZ_PER_CELL)
         return fail(BZ_EINVAL, "unknown sample_mode");
-    if (params->sample_mode == BZ_PER_CELL)
-        return fail(BZ_EUNSUPPORTED, "per-cell sample sets are not implemented");
     if (!(params->cfl >= 0.0 && params->cfl <= 1.0)) return fail(BZ_EINVAL, "cfl must be in [0, 1]");
     if (!(params->eps >= 0.0) || !std::isfinite(params->eps)) return fail(BZ_EINVAL, "eps must be >= 0");
     if (!(params->kcoll >= 0.0) || !std::isfinite(params->kcoll))
@@ -843,6 +864,7 @@ bz_status bz_create(const bz_space *space, const bz_vel *vel, const bz_walls *wa
     g.strip = g.nx >= 16 ? 8 : g.nx;
     H->dtype = params->dtype;
     H->esz = params->dtype == BZ_F64 ? 8 : 4;
+    H->per_cell = params->sample_mode == BZ_PER_CELL;
 
     // Per-axis tables (host, FP64) and the constants of the wall fluxes.
     std::vector<double> axv(N), axA(N);
@@ -1257,6 +1279,8 @@ bz_status bz_adjoint_step(bz_handle *H, int64_t step, const void *h_n, const voi
 {
     if (!H || !h_n || !lam_in || !lam_out) return fail(BZ_EINVAL, "NULL argument");
     if (step < 0) return fail(BZ_EINVAL, "step must be >= 0");
+    if (H->per_cell)
+        return fail(BZ_EUNSUPPORTED, "the adjoint is implemented for the shared sample set only");
     if (!std::isfinite(wD)) return fail(BZ_EINVAL, "wD must be finite");
     const size_t bytes = H->esz * (size_t)H->g.nr * H->g.nvt;
     const char *a = (const char *)h_n, *b = (const char *)lam_out;
@@ -1396,6 +1420,8 @@ bz_status bz_batch_create(int32_t n, const bz_space *spaces, const bz_vel *vels,
     if (!spaces || !vels || !walls || !params) return fail(BZ_EINVAL, "NULL argument");
     for (int i = 0; i < n; ++i) {
         if (params[i].dtype != BZ_F32) return fail(BZ_EUNSUPPORTED, "instance %d: batches are FP32", i);
+        if (params[i].sample_mode != BZ_SHARED)
+            return fail(BZ_EUNSUPPORTED, "instance %d: batches use the shared sample set", i);
         if (vels[i].nv % 4 != 0 || vels[i].nv < 12)
             return fail(BZ_EUNSUPPORTED, "instance %d: nv must be a multiple of 4, >= 12", i);
         if (params[i].n_pairs > 32768)

@@ -630,6 +630,7 @@ template <typename R>
 struct CellSmem {
     R *slab;           // nvt
     R *gw;             // nt (or nullptr when the products live in global scratch)
+    void *sidx;        // nt node-index records of the cell's own samples (per-cell sets)
     AxisTab<R> tab;    // 10 * N
     double *red;       // kMaxWarps * kRedSlots
     double *tot;       // kRedSlots
@@ -654,32 +655,45 @@ __device__ __forceinline__ CellSmem<R> carve(char *base, const Geo &g, bool gw_i
     s.slab = (R *)(base + off); off += sizeof(R) * g.nvt;
     off = (off + 15) & ~(size_t)15;
     s.gw = gw_in_smem ? (R *)(base + off) : nullptr;
+    if (gw_in_smem) off += sizeof(R) * g.nt;
+    off = (off + 15) & ~(size_t)15;
+    s.sidx = base + off;
     return s;
 }
 
+// idx_bytes: bytes per sample of the per-cell sample records (0 for the
+// shared set, whose records stay in global memory).
 template <typename R>
-__host__ __device__ inline size_t cell_smem_bytes(int nv, int nvt, int nt, bool gw_in_smem)
+__host__ __device__ inline size_t cell_smem_bytes(int nv, int nvt, int nt, bool gw_in_smem,
+                                                  size_t idx_bytes = 0)
 {
     size_t off = sizeof(double) * (kMaxWarps * kRedSlots + kRedSlots + 8) + sizeof(R) * 10 * nv;
     off = (off + 15) & ~(size_t)15;
     off += sizeof(R) * nvt;
     off = (off + 15) & ~(size_t)15;
     if (gw_in_smem) off += sizeof(R) * nt;
+    off = (off + 15) & ~(size_t)15;
+    off += idx_bytes * nt;
     return off;
 }
 
 // FUSED: the slab is filled by streaming h^n (Eq. streaming2D) instead of
-// loading h~ from global memory.
-template <typename R, bool FUSED, typename I>
+// loading h~ from global memory.  PC: every cell draws its own sample set
+// (Philox counter word 2 = the cell index, step from *stepp) in the gather
+// phase and keeps its node indices in shared memory; pidx and pa are unused.
+template <typename R, bool FUSED, typename I, bool PC = false>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 k_cell(Geo g, const R *__restrict__ hin, const R *__restrict__ ghost,
        const typename Idx4<I>::type *__restrict__ pidx, const PlanA<R, I> *__restrict__ pa,
        R *__restrict__ gw_global,
        R *__restrict__ hout, double *__restrict__ mom, unsigned long long *__restrict__ stats,
-       int gw_in_smem)
+       int gw_in_smem, const int64_t *__restrict__ stepp = nullptr)
 {
     extern __shared__ __align__(16) char smem_raw[];
     CellSmem<R> S = carve<R>(smem_raw, g, gw_in_smem != 0);
+    using V4 = typename Idx4<I>::type;
+    V4 *sidx = reinterpret_cast<V4 *>(S.sidx);
+    const int64_t step = PC ? *stepp : 0;
     const int N = g.nv, N2 = N * N, nvt = g.nvt, T = blockDim.x, t = threadIdx.x;
     const R eps = (R)g.eps;
     R *gw = S.gw ? S.gw : gw_global + (int64_t)blockIdx.x * g.nt;
@@ -758,7 +772,30 @@ k_cell(Geo g, const R *__restrict__ hin, const R *__restrict__ ghost,
 
         // ---- phase A: g_l W_l from the pre-collision values (Jacobi) -------
         // Plan entries are loaded four at a time to keep L2 requests in flight.
-        {
+        if constexpr (PC) {
+            // The cell's own samples (Sec. 4.2 / Algorithm 2 with the cell in
+            // the Philox counter): kinematics and node selection in FP64.
+            for (int l0 = 0; l0 < g.nt; l0 += T) {
+                const int l = l0 + t;
+                const bool act = l < g.nt;
+                SampleOut o = {};
+                if (act) {
+                    o = draw_sample(g, step, (uint32_t)c, (uint32_t)l);
+                    sidx[l] = Idx4<I>::make(o.idx);
+                    const R ha = o.idx[0] >= 0 ? S.slab[o.idx[0]] : R(0);
+                    const R hb = o.idx[1] >= 0 ? S.slab[o.idx[1]] : R(0);
+                    gw[l] = (ha + hb + eps * ha * hb) * (R)o.W;
+                }
+                if (stats) {
+                    const unsigned mo = __ballot_sync(0xFFFFFFFFu, act && o.outside);
+                    const unsigned mn = __ballot_sync(0xFFFFFFFFu, act && o.near);
+                    if ((t & 31) == 0) {
+                        if (mo) atomicAdd(stats + 1, (unsigned long long)__popc(mo));
+                        if (mn) atomicAdd(stats + 2, (unsigned long long)__popc(mn));
+                    }
+                }
+            }
+        } else {
             int l = t;
             for (; l + 3 * T < g.nt; l += 4 * T) {
                 PlanA<R, I> q[4];
@@ -781,6 +818,7 @@ k_cell(Geo g, const R *__restrict__ hin, const R *__restrict__ ghost,
             }
         }
         __syncthreads();
+        const V4 *pix = PC ? sidx : pidx;
 
         // ---- N = w h~ in place, and the conserved moments of h~ ------------
         R pre[5] = {R(0), R(0), R(0), R(0), R(0)};
@@ -807,7 +845,6 @@ k_cell(Geo g, const R *__restrict__ hin, const R *__restrict__ ghost,
 
         // ---- phase B: scatter the gains and losses (Eq. monteCarloInt) -----
         {
-            using V4 = typename Idx4<I>::type;
             auto scatter = [&](const V4 &q, R r) {
                 if (r != R(0)) {
                     const int a = idx_of(q.x), b = idx_of(q.y), as = idx_of(q.z), bs = idx_of(q.w);
@@ -823,13 +860,13 @@ k_cell(Geo g, const R *__restrict__ hin, const R *__restrict__ ghost,
                 R r[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    q[u] = pidx[l + u * T];
+                    q[u] = pix[l + u * T];
                     r[u] = gw[l + u * T];
                 }
 #pragma unroll
                 for (int u = 0; u < 4; ++u) scatter(q[u], r[u]);
             }
-            for (; l < g.nt; l += T) scatter(pidx[l], gw[l]);
+            for (; l < g.nt; l += T) scatter(pix[l], gw[l]);
         }
         __syncthreads();
 

@@ -17,6 +17,7 @@ y = L, diffuse walls at T0, initial uniform Maxwellian n0 = 1, h0 = 0):
                  0.05 sin(2 pi t / 50), 2x10^4 samples/step, seed 3, FP32
   adjoint128_v20 128x128 cells, 20^3 on [-4.5,4.5]^3, Kn 0.2, per-face lid
                  0.1 + N(0, 0.01^2), 5000 samples/step, seed 4, FP32
+  percell64_v24  cavity64_v24 with its own 10^4 samples in every cell
 """
 from __future__ import annotations
 
@@ -92,6 +93,11 @@ def adjoint128_v20(seed: int = 4) -> Problem:
     prof = 0.1 + 0.01 * rng.standard_normal(128)
     return Problem("adjoint128_v20", 128, 128, 0.2, 20, 4.5, 5000, seed, lid_profile=prof,
                    steps=500)
+
+
+def percell64_v24() -> Problem:
+    """cavity64_v24 with an independent sample set in every cell."""
+    return Problem("percell64_v24", 64, 64, 0.1, 24, 4.5, 10_000, 2, per_cell=True, steps=2000)
 
 
 def batch64(n: int = 64, seed0: int = 100, nt: int = 5000) -> list:

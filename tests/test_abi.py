@@ -50,8 +50,10 @@ def test_argument_validation_without_gpu(lib):
     assert create(kn=-1.0)[0] == binding.BZ_EINVAL
     assert create(cfl=1.5)[0] == binding.BZ_EINVAL
     assert create(lid_period=-1.0)[0] == binding.BZ_EINVAL
-    st, msg = create(per_cell=True)
-    assert st == binding.BZ_EUNSUPPORTED and "per-cell" in msg
+    # Batches run the shared sample set only (checked before any device work).
+    with pytest.raises(binding.BzError) as e:
+        binding.Batch([workloads.small(per_cell=True)])
+    assert e.value.status == binding.BZ_EUNSUPPORTED and "shared sample set" in str(e.value)
 
 
 def test_allocation_fault_injection(lib):
