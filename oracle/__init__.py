@@ -68,6 +68,7 @@ class Problem(C.Structure):
         ("seed", C.c_uint32), ("instance", C.c_uint32), ("per_cell", C.c_int32),
         ("lid_u0", C.c_double), ("lid_amp", C.c_double), ("lid_period", C.c_double),
         ("lid_profile", C.POINTER(C.c_double)),
+        ("rv", C.c_double), ("rx", C.c_double), ("ry", C.c_double),
     ]
 
 
@@ -119,6 +120,10 @@ def lib():
                 "bzo_mc_dNdt": (None, [_P, C.c_int64, _D, _D, _D]),
                 "bzo_num_threads": (C.c_int32, []),
                 "bzo_adjoint_step": (None, [_P, C.c_int64, _D, _D, _D, _D, C.c_double]),
+                "bzo_axis_edge": (C.c_double, [_P, C.c_int32]),
+                "bzo_axis_width": (C.c_double, [_P, C.c_int32]),
+                "bzo_cell_dx": (C.c_double, [_P, C.c_int32]),
+                "bzo_cell_dy": (C.c_double, [_P, C.c_int32]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -144,7 +149,7 @@ class Oracle:
 
     def __init__(self, nx, ny, kn, nv, vmax, nt, seed, eps=None, cfl=0.5,
                  kcoll=K_HARD_SPHERE, instance=0, per_cell=False, lid_u0=0.1,
-                 lid_amp=0.0, lid_period=0.0, lid_profile=None):
+                 lid_amp=0.0, lid_period=0.0, lid_profile=None, rv=0.0, rx=0.0, ry=0.0):
         if eps is None or eps == 0.0:
             if lid_profile is not None:
                 eps = float(np.max(np.abs(lid_profile))) + abs(lid_amp)
@@ -158,7 +163,8 @@ class Oracle:
             assert self._profile.shape == (nx,)
         self.p = Problem(nx, ny, kn, nv, vmax, eps, cfl, kcoll, nt, seed, instance,
                          1 if per_cell else 0, lid_u0, lid_amp, lid_period,
-                         _dptr(self._profile) if self._profile is not None else None)
+                         _dptr(self._profile) if self._profile is not None else None,
+                         rv, rx, ry)
         self.L = lib()
         self.nx, self.ny, self.nv = nx, ny, nv
         self.nr = nx * ny
@@ -177,6 +183,18 @@ class Oracle:
     @property
     def dx(self):
         return self.L.bzo_dx(C.byref(self.p))
+
+    def axis_edges(self):
+        """Per-axis velocity cell edges (nv + 1,)."""
+        return np.array([self.L.bzo_axis_edge(C.byref(self.p), k) for k in range(self.nv + 1)])
+
+    def axis_widths(self):
+        return np.array([self.L.bzo_axis_width(C.byref(self.p), j) for j in range(self.nv)])
+
+    def cell_widths(self):
+        """(dx per column (nx,), dy per row (ny,))."""
+        return (np.array([self.L.bzo_cell_dx(C.byref(self.p), i) for i in range(self.nx)]),
+                np.array([self.L.bzo_cell_dy(C.byref(self.p), i) for i in range(self.ny)]))
 
     def node_v(self):
         """Per-axis node velocities (nv,)."""

@@ -38,17 +38,73 @@ double bzo_dv(const bzo_problem *p) { return (2.0 * p->vmax) / (double)p->nv; }
 double bzo_dx(const bzo_problem *p) { return (1.0 / p->kn) / (double)p->nx; }
 double bzo_dy(const bzo_problem *p) { return (1.0 / p->kn) / (double)p->ny; }
 
-/* Node velocity of axis index j: cell centre of [-vmax + j dv, -vmax + (j+1) dv]. */
-double bzo_node_v(const bzo_problem *p, int32_t j)
+static int stretched(double r) { return r > 0.0 && r != 1.0; }
+
+/* Velocity cell edges (Sec. 5.1).  Uniform: -vmax + k dv.  Stretched with
+ * ratio rv: the nv/2 cells of each half axis have widths d0, d0/rv, d0/rv^2,
+ * ... outward from the origin (the smallest cells at the origin), summing to
+ * vmax; the edges are symmetric about 0. */
+double bzo_axis_edge(const bzo_problem *p, int32_t k)
 {
-    return -p->vmax + ((double)j + 0.5) * bzo_dv(p);
+    if (!stretched(p->rv)) return -p->vmax + (double)k * bzo_dv(p);
+    int32_t m = p->nv / 2;
+    double q = 1.0 / p->rv;
+    double d0 = p->vmax * (q - 1.0) / (pow(q, (double)m) - 1.0);
+    int32_t i = k >= m ? k - m : m - k;           /* edge index from the origin */
+    double e = d0 * (pow(q, (double)i) - 1.0) / (q - 1.0);
+    return k >= m ? e : -e;
 }
 
-/* Time step from the maximum Courant number per direction (Sec. 5.1). */
+double bzo_axis_width(const bzo_problem *p, int32_t j)
+{
+    if (!stretched(p->rv)) return bzo_dv(p);
+    return bzo_axis_edge(p, j + 1) - bzo_axis_edge(p, j);
+}
+
+/* Node velocity of axis index j: the centre of its cell. */
+double bzo_node_v(const bzo_problem *p, int32_t j)
+{
+    if (!stretched(p->rv)) return -p->vmax + ((double)j + 0.5) * bzo_dv(p);
+    return 0.5 * (bzo_axis_edge(p, j) + bzo_axis_edge(p, j + 1));
+}
+
+/* Spatial cell widths (Sec. 5.1, stretched physical grid): widths shrink by
+ * rx per cell toward each side wall and by ry per cell toward the lid (the
+ * smallest cells at the upper corners), normalised to the side L. */
+static double stretched_width(int32_t n, int32_t d, int32_t i, double r, double L)
+{
+    /* cell i has distance d(i) (in cells) from the refined end(s); width ~ r^-d */
+    double sum = 0.0;
+    for (int32_t k = 0; k < n; ++k) {
+        int32_t dk = d < 0 ? (k < n - 1 - k ? k : n - 1 - k) : n - 1 - k;
+        sum += pow(1.0 / r, (double)dk);
+    }
+    int32_t di = d < 0 ? (i < n - 1 - i ? i : n - 1 - i) : n - 1 - i;
+    return L * pow(1.0 / r, (double)di) / sum;
+}
+
+double bzo_cell_dx(const bzo_problem *p, int32_t ix)
+{
+    if (!stretched(p->rx)) return bzo_dx(p);
+    return stretched_width(p->nx, -1, ix, p->rx, 1.0 / p->kn);
+}
+
+double bzo_cell_dy(const bzo_problem *p, int32_t iy)
+{
+    if (!stretched(p->ry)) return bzo_dy(p);
+    return stretched_width(p->ny, 1, iy, p->ry, 1.0 / p->kn);
+}
+
+/* Time step from the maximum Courant number per direction (Sec. 5.1), with
+ * the fastest node and the narrowest cell. */
 double bzo_dt(const bzo_problem *p)
 {
     double vtop = bzo_node_v(p, p->nv - 1);
-    double h = bzo_dx(p) < bzo_dy(p) ? bzo_dx(p) : bzo_dy(p);
+    double h = bzo_cell_dx(p, 0);
+    for (int32_t i = 1; i < p->nx; ++i)
+        if (bzo_cell_dx(p, i) < h) h = bzo_cell_dx(p, i);
+    for (int32_t i = 0; i < p->ny; ++i)
+        if (bzo_cell_dy(p, i) < h) h = bzo_cell_dy(p, i);
     return p->cfl * h / vtop;
 }
 
@@ -61,6 +117,14 @@ static void node_velocity(const bzo_problem *p, int32_t j, double v[3])
     v[2] = bzo_node_v(p, jz);
 }
 
+/* dV_j of node j: the product of its three axis widths. */
+static double node_volume(const bzo_problem *p, int32_t j)
+{
+    int32_t n = p->nv;
+    int32_t jz = j % n, jy = (j / n) % n, jx = j / (n * n);
+    return bzo_axis_width(p, jx) * bzo_axis_width(p, jy) * bzo_axis_width(p, jz);
+}
+
 /* Equilibrium Maxwellian Phi0 in V0 units with n0 = 1 (Eq. MaxwellDist). */
 static double phi0(const double v[3])
 {
@@ -70,9 +134,9 @@ static double phi0(const double v[3])
 /* N_j ~ dV_j Phi0_j h_j (Sec. 3): the node weight dV_j Phi0_j. */
 double bzo_weight(const bzo_problem *p, int32_t j)
 {
-    double v[3], dv = bzo_dv(p);
+    double v[3];
     node_velocity(p, j, v);
-    return dv * dv * dv * phi0(v);
+    return node_volume(p, j) * phi0(v);
 }
 
 /* Lid speed of lid face ix at the start of step `step`. */
@@ -126,6 +190,25 @@ int32_t bzo_node_of(const bzo_problem *p, const double v[3], int32_t *near_face)
 {
     double dv = bzo_dv(p);
     int32_t id[3], inside = 1, near = 0;
+    if (stretched(p->rv)) {
+        /* the cell whose edges hold v (a value on an edge goes to the upper cell) */
+        for (int c = 0; c < 3; ++c) {
+            if (!(v[c] >= bzo_axis_edge(p, 0)) || v[c] >= bzo_axis_edge(p, p->nv)) {
+                inside = 0;
+                id[c] = -1;
+                continue;
+            }
+            int32_t k = 0;
+            while (v[c] >= bzo_axis_edge(p, k + 1)) ++k;
+            double w = bzo_axis_width(p, k);
+            if (v[c] - bzo_axis_edge(p, k) < 1e-9 * w || bzo_axis_edge(p, k + 1) - v[c] < 1e-9 * w)
+                near = 1;
+            id[c] = k;
+        }
+        if (near_face) *near_face = near;
+        if (!inside) return -1;
+        return (id[0] * p->nv + id[1]) * p->nv + id[2];
+    }
     for (int c = 0; c < 3; ++c) {
         double t = (v[c] + p->vmax) / dv;
         double fl = floor(t);
@@ -245,7 +328,6 @@ static double wall_maxwellian(const double v[3], const double vw[3])
 static double face_density(const bzo_problem *p, int64_t step, int32_t f, const double *hcell)
 {
     int32_t nvt = p->nv * p->nv * p->nv;
-    double dv = bzo_dv(p), dV = dv * dv * dv;
     int32_t cell;
     double nrm[3], vw[3], v[3];
     face_info(p, step, f, &cell, nrm, vw);
@@ -256,7 +338,7 @@ static double face_density(const bzo_problem *p, int64_t step, int32_t f, const 
         if (vn < 0.0)
             out += -vn * bzo_weight(p, j) * (1.0 + p->eps * hcell[j]);
         else if (vn > 0.0)
-            in += vn * dV * wall_maxwellian(v, vw);
+            in += vn * node_volume(p, j) * wall_maxwellian(v, vw);
     }
     return out / in;
 }
@@ -295,7 +377,9 @@ static void stream_cell(const bzo_problem *p, int64_t step, int32_t c, const dou
     int32_t nx = p->nx, ny = p->ny, n = p->nv;
     int32_t ix = c % nx, iy = c / nx;
     int64_t nvt = (int64_t)n * n * n;
-    double dt = bzo_dt(p), dx = bzo_dx(p), dy = bzo_dy(p);
+    /* Each cell uses its own widths: the upwind finite-volume update of a
+     * cell of width dx_i (uniform widths give Eq. streaming2D as printed). */
+    double dt = bzo_dt(p), dx = bzo_cell_dx(p, ix), dy = bzo_cell_dy(p, iy);
     for (int64_t j = 0; j < nvt; ++j) {
         double v[3];
         node_velocity(p, (int32_t)j, v);
@@ -598,9 +682,9 @@ void bzo_lid_shear(const bzo_problem *p, int64_t step, const double *h, double *
             s += bzo_weight(p, (int32_t)j) * v[0] * v[1] * hf;
         }
         out[ix] = 2.0 * s;
-        mean += out[ix];
+        mean += out[ix] * bzo_cell_dx(p, ix);
     }
-    out[nx] = mean / nx;
+    out[nx] = mean * p->kn;                     /* (1/L) sum_ix dx_ix shear_ix */
     free(nw);
 }
 
@@ -663,14 +747,14 @@ static double ratio_w0(const double v[3], const double vw[3])
 static void face_influx(const bzo_problem *p, int64_t step, int32_t f, double *din, double *ddin)
 {
     int32_t cell, nvt = p->nv * p->nv * p->nv;
-    double nrm[3], vw[3], v[3], dv = bzo_dv(p), dV = dv * dv * dv;
+    double nrm[3], vw[3], v[3];
     face_info(p, step, f, &cell, nrm, vw);
     double s = 0.0, ds = 0.0;
     for (int32_t j = 0; j < nvt; ++j) {
         node_velocity(p, j, v);
         double vn = v[0] * nrm[0] + v[1] * nrm[1] + v[2] * nrm[2];
         if (vn > 0.0) {
-            double m = vn * dV * wall_maxwellian(v, vw);
+            double m = vn * node_volume(p, j) * wall_maxwellian(v, vw);
             s += m;
             ds += m * 2.0 * (v[0] - vw[0]);
         }
@@ -684,7 +768,7 @@ void bzo_adjoint_step(const bzo_problem *p, int64_t step, const double *h, const
 {
     int32_t nx = p->nx, ny = p->ny, nr = nx * ny, n = p->nv, nf = bzo_num_faces(p);
     int64_t nvt = (int64_t)n * n * n;
-    double eps = p->eps, dt = bzo_dt(p), dx = bzo_dx(p), dy = bzo_dy(p);
+    double eps = p->eps, dt = bzo_dt(p);
     double *w, *vel;
     tables(p, &w, &vel);
 
@@ -783,10 +867,11 @@ void bzo_adjoint_step(const bzo_problem *p, int64_t step, const double *h, const
     memset(lam_out, 0, sizeof(double) * nr * nvt);
     for (int32_t c = 0; c < nr; ++c) {
         int32_t ix = c % nx, iy = c / nx;
+        double dxc = bzo_cell_dx(p, ix), dyc = bzo_cell_dy(p, iy);
         for (int64_t j = 0; j < nvt; ++j) {
             double v[3];
             node_velocity(p, (int32_t)j, v);
-            double ax = fabs(v[0] * dt / dx), ay = fabs(v[1] * dt / dy);
+            double ax = fabs(v[0] * dt / dxc), ay = fabs(v[1] * dt / dyc);
             double L = lt[(int64_t)c * nvt + j];
             lam_out[(int64_t)c * nvt + j] += (1.0 - ax - ay) * L;
             if (v[0] > 0.0) {
@@ -818,7 +903,7 @@ void bzo_adjoint_step(const bzo_problem *p, int64_t step, const double *h, const
             for (int64_t j = 0; j < nvt; ++j) {
                 double v[3];
                 node_velocity(p, (int32_t)j, v);
-                double coef = wD * 2.0 * w[j] * v[0] * v[1] / nx;
+                double coef = wD * 2.0 * w[j] * v[0] * v[1] * bzo_cell_dx(p, ix) * p->kn;
                 if (v[1] > 0.0) lam_out[c * nvt + j] += coef;
                 else if (v[1] < 0.0) lg[(int64_t)f * nvt + j] += coef;
             }

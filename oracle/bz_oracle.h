@@ -40,6 +40,10 @@ typedef struct {
     int32_t per_cell;          /* 0: one sample set shared by all cells; 1: per cell */
     double lid_u0, lid_amp, lid_period; /* U(t) = base + amp sin(2 pi t / period) */
     const double *lid_profile; /* nx per-face base lid speeds, or NULL => lid_u0 */
+    /* Stretched grids (Sec. 5.1; 0 or 1 = uniform).  rv: velocity cells grow
+     * outward from the origin by 1/rv per cell (nv even).  rx: spatial cells
+     * shrink by rx per cell toward each side wall; ry: toward the lid. */
+    double rv, rx, ry;
 } bzo_problem;
 
 /* One Monte Carlo collision sample (Eq. monteCarloInt, Sec. 4.2 sampling). */
@@ -52,12 +56,20 @@ typedef struct {
     int32_t near_face;         /* 1 if a component lies within 1e-9 dv of a face */
 } bzo_sample_t;
 
-/* Derived quantities. */
+/* Derived quantities.  bzo_dv/dx/dy are the uniform spacings (2 vmax / nv,
+ * L / nx, L / ny); on stretched grids the per-node and per-cell widths are
+ * bzo_axis_width, bzo_cell_dx and bzo_cell_dy. */
 double bzo_dv(const bzo_problem *p);
 double bzo_dx(const bzo_problem *p);
 double bzo_dy(const bzo_problem *p);
 double bzo_dt(const bzo_problem *p);
 double bzo_node_v(const bzo_problem *p, int32_t jaxis);
+/* Velocity cell edge k (0..nv) of one axis and the width of cell j. */
+double bzo_axis_edge(const bzo_problem *p, int32_t k);
+double bzo_axis_width(const bzo_problem *p, int32_t jaxis);
+/* Width of spatial column ix and of row iy. */
+double bzo_cell_dx(const bzo_problem *p, int32_t ix);
+double bzo_cell_dy(const bzo_problem *p, int32_t iy);
 double bzo_weight(const bzo_problem *p, int32_t j);        /* dV Phi0(v_j) */
 double bzo_lid_speed(const bzo_problem *p, int32_t ix, int64_t step);
 
@@ -107,7 +119,8 @@ void bzo_step_cell(const bzo_problem *p, int64_t step, int32_t c, const double *
  * [rho, ux, uy, uz, theta, Pxx, Pyy, Pzz, Pxy, Pxz, Pyz]. */
 void bzo_moments(const bzo_problem *p, const double *h, double *mom);
 
-/* x-momentum flux through each lid face (wall shear), nx values + mean. */
+/* x-momentum flux through each lid face (wall shear), nx values, and D: their
+ * mean over the lid, weighted by the face widths (out[nx]). */
 void bzo_lid_shear(const bzo_problem *p, int64_t step, const double *h, double *out);
 
 /* Monte Carlo estimate of Eq. coll8Dim (Eq. monteCarloInt) for one cell with

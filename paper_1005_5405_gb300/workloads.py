@@ -47,6 +47,9 @@ class Problem:
     instance: int = 0
     per_cell: bool = False
     steps: int = 1
+    rv: float = 0.0             # stretched velocity cells (0 or 1: uniform)
+    rx: float = 0.0             # stretched spatial cells toward the side walls
+    ry: float = 0.0             # ... and toward the lid
 
     @property
     def nr(self) -> int:
