@@ -545,6 +545,48 @@ def run_percell(args):
     print(json.dumps(line), flush=True)
 
 
+def run_paper(args):
+    """The paper's own cavity setups (Sec. 5.1: stretched velocity and
+    spatial grids, lid speed 0.01) for delta = 0.1, 1 and 10: time per step
+    from rest, and the lid shear D after the timed steps (context; the
+    paper's Table 1 values are long-term means of much longer runs)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1005_5405_gb300 import binding, workloads
+    torch.cuda.set_device(0)
+    rows = []
+    for delta in (0.1, 1.0, 10.0):
+        p = workloads.paper_cavity(delta)
+        cav = binding.Cavity(p)
+        cav.step(args.warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        cav.step(args.steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        d = cav.lid_shear().cpu().numpy()[-1]
+        info = cav.get_info()
+        rows.append({"delta": delta, "nx": p.nx, "nv": p.nv, "samples": p.nt, "ms_per_step": ms,
+                     "node_updates_per_s": p.nodes / (ms / 1e3), "dt": info.dt,
+                     "steps_from_rest": args.warmup + args.steps, "D": float(d),
+                     "kernel_variant": info.kernel_variant})
+        del cav
+        torch.cuda.empty_cache()
+    mid = rows[1]
+    line = {
+        "metric": "phase-space node updates/s, paper cavity delta = 1 (160^2 x 20^3 stretched, FP32)",
+        "value": mid["node_updates_per_s"], "unit": "node-updates/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mid["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": {"workload": "paper_cavity", "l2": "state > L2, no flush"},
+        "setups": rows,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def workloads_state(p, torch):
     from paper_1005_5405_gb300 import workloads
     return workloads.warm_state_device(p, seed=7, torch=torch)
@@ -560,6 +602,8 @@ def main():
         run_adjoint(args)
     elif args.config == "percell64_v24":
         run_percell(args)
+    elif args.config == "paper_cavity":
+        run_paper(args)
     else:
         run_ours(args)
 

@@ -66,16 +66,26 @@ enum {
 };
 
 /* Spatial grid (Sec. 3, Sec. 5.1): nx x ny cells on the square cavity of
- * side L = 1/kn (Knudsen number kn = 1/delta). */
+ * side L = 1/kn (Knudsen number kn = 1/delta).  rx, ry: stretched cells
+ * (Sec. 5.1; 0 or 1 = uniform): column widths shrink by the factor rx per
+ * cell toward each side wall, row heights by ry per cell toward the lid, the
+ * smallest cells at the lid corners; widths sum to L.  The time step then
+ * follows from the narrowest cell. */
 typedef struct {
     int32_t nx, ny;
     double kn;
+    double rx, ry;
 } bz_space;
 
-/* Velocity grid (Sec. 3): nv^3 nodes on the cube [-vmax, vmax]^3 (V0 units). */
+/* Velocity grid (Sec. 3): nv^3 nodes on the cube [-vmax, vmax]^3 (V0 units).
+ * rv: stretched cells (Sec. 5.1; 0 or 1 = uniform; nv even): along each axis
+ * the cell widths grow by 1/rv per cell outward from the origin (the
+ * smallest cells at the origin), edges symmetric about 0; a node sits at the
+ * centre of its cell and its weight is its cell volume times Phi0. */
 typedef struct {
     int32_t nv;
     double vmax;
+    double rv;
 } bz_vel;
 
 /* Walls (Sec. 2 Eq. bcMax, Sec. 5.1): the lid speed of lid face ix at time

@@ -36,11 +36,12 @@ class BzError(RuntimeError):
 
 
 class bz_space(C.Structure):
-    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("kn", C.c_double)]
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("kn", C.c_double),
+                ("rx", C.c_double), ("ry", C.c_double)]
 
 
 class bz_vel(C.Structure):
-    _fields_ = [("nv", C.c_int32), ("vmax", C.c_double)]
+    _fields_ = [("nv", C.c_int32), ("vmax", C.c_double), ("rv", C.c_double)]
 
 
 class bz_walls(C.Structure):
@@ -159,8 +160,8 @@ class Cavity:
         if p.lid_profile is not None:
             self._prof = np.ascontiguousarray(p.lid_profile, dtype=np.float64)
             prof_ptr = self._prof.ctypes.data_as(C.POINTER(C.c_double))
-        sp = bz_space(p.nx, p.ny, p.kn)
-        ve = bz_vel(p.nv, p.vmax)
+        sp = bz_space(p.nx, p.ny, p.kn, p.rx, p.ry)
+        ve = bz_vel(p.nv, p.vmax, p.rv)
         wa = bz_walls(p.lid_u0, p.lid_amp, p.lid_period, prof_ptr)
         pa = bz_params(p.nt, p.seed, p.instance, p.eps, p.cfl, kcoll,
                        BZ_F64 if p.dtype == "f64" else BZ_F32,
@@ -294,8 +295,8 @@ def collide_noalloc(p: Problem, step: int, h_in, h_out, mom=None, stream=None):
     any device allocation by the library (see include/bz.h).  h_in/h_out are
     CUDA tensors of shape (nr, nv^3) in the problem's dtype; mom is an
     optional (nr, 11) float64 CUDA tensor; p.eps must be > 0."""
-    sp = bz_space(p.nx, p.ny, p.kn)
-    ve = bz_vel(p.nv, p.vmax)
+    sp = bz_space(p.nx, p.ny, p.kn, p.rx, p.ry)
+    ve = bz_vel(p.nv, p.vmax, p.rv)
     pa = bz_params(p.nt, p.seed, p.instance, p.eps, p.cfl, 0.0,
                    BZ_F64 if p.dtype == "f64" else BZ_F32,
                    BZ_PER_CELL if p.per_cell else BZ_SHARED)
@@ -313,7 +314,7 @@ def _structs(p: Problem, kcoll: float = 0.0):
     pa = bz_params(p.nt, p.seed, p.instance, p.eps, p.cfl, kcoll,
                    BZ_F64 if p.dtype == "f64" else BZ_F32,
                    BZ_PER_CELL if p.per_cell else BZ_SHARED)
-    return bz_space(p.nx, p.ny, p.kn), bz_vel(p.nv, p.vmax), wa, pa, prof
+    return bz_space(p.nx, p.ny, p.kn, p.rx, p.ry), bz_vel(p.nv, p.vmax, p.rv), wa, pa, prof
 
 
 class Batch:

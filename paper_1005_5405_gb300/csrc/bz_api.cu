@@ -110,6 +110,9 @@ struct bz_handle {
     // lazy_buf set holds h_c and its cells' pending corrections in mu[buf];
     // mu[buf] is all zero whenever lazy_buf is clear.
     bool per_cell = false;              // every cell draws its own sample set
+    bool stretched = false;             // non-uniform velocity or spatial cells
+    double *axe = nullptr, *axd = nullptr, *wlid = nullptr;
+    double *sx = nullptr, *sy = nullptr;
     bool lazy = false;
     float *mu[2] = {nullptr, nullptr};
     bool lazy_buf[2] = {false, false};
@@ -256,6 +259,7 @@ bz_status configure_cell4(bz_handle *H)
     H->fast = false;
     if (force && strcmp(force, "generic") == 0) return BZ_OK;
     if (H->per_cell) return BZ_OK;         // the shared-set kernels only
+    if (H->stretched) return BZ_OK;        // uniform grids only
     if (H->dtype != BZ_F32 || !H->idx16 || N % 4 != 0 || N < 12) return BZ_OK;
     if (g.nt > 32768) return BZ_OK;                 // 15-bit sample index in the scatter list
     if (bzk::cell4_smem_bytes(N, g.nvt, g.nt) > (size_t)H->smem_optin) return BZ_OK;
@@ -781,6 +785,9 @@ void release(bz_handle *H)
                     H->mom, H->gw_global, H->stats, H->flag, H->axv, H->axA, H->profile};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    void *st[] = {H->axe, H->axd, H->wlid, H->sx, H->sy};
+    for (void *p : st)
+        if (p) cudaFree(p);
     void *lz[] = {H->mu[0], H->mu[1], H->lz_idx, H->lz_pa, H->lz_pc, H->lz_qc, H->lz_flag,
                   H->lz_cidx, H->lz_act, H->lz_wpre, H->lz_meta, H->lz_count, H->lz_cursor,
                   H->lz_mask, H->lz_ent};
@@ -810,6 +817,10 @@ bz_status bz_create(const bz_space *space, const bz_vel *vel, const bz_walls *wa
     if (vel->nv < 2 || vel->nv > bzk::kMaxN)
         return fail(BZ_EINVAL, "nv must be in [2, %d]", bzk::kMaxN);
     if (!(vel->vmax > 0.0) || !std::isfinite(vel->vmax)) return fail(BZ_EINVAL, "vmax must be > 0");
+    for (double r : {vel->rv, space->rx, space->ry})
+        if (!(r >= 0.0) || !(r <= 1.0)) return fail(BZ_EINVAL, "stretching ratios must be in [0, 1]");
+    if (vel->rv > 0.0 && vel->rv < 1.0 && vel->nv % 2 != 0)
+        return fail(BZ_EINVAL, "a stretched velocity grid needs an even nv");
     if (params->n_pairs < 1 || params->n_pairs > 0x7FFFFFFF)
         return fail(BZ_EINVAL, "n_pairs must be in [1, 2^31-1]");
     if (params->dtype != BZ_F32 && params->dtype != BZ_F64)
@@ -849,8 +860,49 @@ bz_status bz_create(const bz_space *space, const bz_vel *vel, const bz_walls *wa
     g.dx = (1.0 / space->kn) / (double)g.nx;
     g.dy = (1.0 / space->kn) / (double)g.ny;
     const double cfl = params->cfl > 0.0 ? params->cfl : 0.5;
-    const double vtop = -g.vmax + ((double)(N - 1) + 0.5) * g.dv;
-    g.dt = cfl * std::min(g.dx, g.dy) / vtop;
+    // Grids (Sec. 3, Sec. 5.1), uniform or stretched.
+    const bool sv = vel->rv > 0.0 && vel->rv < 1.0;
+    const bool sxg = space->rx > 0.0 && space->rx < 1.0, syg = space->ry > 0.0 && space->ry < 1.0;
+    H->stretched = sv || sxg || syg;
+    std::vector<double> edges(N + 1), axv(N), axw(N);
+    if (sv) {
+        // Half-axis widths d0, d0 q, d0 q^2, ... (q = 1/rv) from the origin
+        // outward summing to vmax; edges mirrored about 0.
+        const int m = N / 2;
+        const double q = 1.0 / vel->rv;
+        const double d0 = g.vmax * (q - 1.0) / (std::pow(q, (double)m) - 1.0);
+        for (int k = 0; k <= N; ++k) {
+            const int i = k >= m ? k - m : m - k;
+            const double e = d0 * (std::pow(q, (double)i) - 1.0) / (q - 1.0);
+            edges[k] = k >= m ? e : -e;
+        }
+        for (int j = 0; j < N; ++j) {
+            axv[j] = 0.5 * (edges[j] + edges[j + 1]);
+            axw[j] = edges[j + 1] - edges[j];
+        }
+    } else {
+        for (int j = 0; j < N; ++j) {
+            axv[j] = -g.vmax + ((double)j + 0.5) * g.dv;
+            axw[j] = g.dv;
+        }
+    }
+    // Spatial widths: shrinking by r per cell toward the refined end(s).
+    auto widths = [](int n, bool both_ends, double r, double L) {
+        std::vector<double> w(n, L / n);
+        if (!(r > 0.0 && r < 1.0)) return w;
+        auto dist = [&](int k) { return both_ends ? std::min(k, n - 1 - k) : n - 1 - k; };
+        double sum = 0.0;
+        for (int k = 0; k < n; ++k) sum += std::pow(1.0 / r, (double)dist(k));
+        for (int k = 0; k < n; ++k) w[k] = L * std::pow(1.0 / r, (double)dist(k)) / sum;
+        return w;
+    };
+    const std::vector<double> cdx = widths(g.nx, true, space->rx, 1.0 / space->kn);
+    const std::vector<double> cdy = widths(g.ny, false, space->ry, 1.0 / space->kn);
+    double hmin = cdx[0];
+    for (double w : cdx) hmin = std::min(hmin, w);
+    for (double w : cdy) hmin = std::min(hmin, w);
+    const double vtop = axv[N - 1];
+    g.dt = cfl * hmin / vtop;
     const double kcoll =
         params->kcoll > 0.0 ? params->kcoll : 5.0 * 1.016034 / 16.0 * std::sqrt(2.0 / M_PI);
     g.cw = M_PI * kcoll * g.dt / (double)g.nt;
@@ -866,12 +918,10 @@ bz_status bz_create(const bz_space *space, const bz_vel *vel, const bz_walls *wa
     H->esz = params->dtype == BZ_F64 ? 8 : 4;
     H->per_cell = params->sample_mode == BZ_PER_CELL;
 
-    // Per-axis tables (host, FP64) and the constants of the wall fluxes.
-    std::vector<double> axv(N), axA(N);
-    for (int j = 0; j < N; ++j) {
-        axv[j] = -g.vmax + ((double)j + 0.5) * g.dv;
-        axA[j] = g.dv * (1.0 / std::sqrt(M_PI)) * std::exp(-axv[j] * axv[j]);
-    }
+    // Per-axis weight factors (w_j = A_x A_y A_z) and the wall flux constants.
+    std::vector<double> axA(N);
+    for (int j = 0; j < N; ++j)
+        axA[j] = axw[j] * (1.0 / std::sqrt(M_PI)) * std::exp(-axv[j] * axv[j]);
     double hn = 0.0, zsum = 0.0;
     for (int j = 0; j < N; ++j) {
         zsum += axA[j];
@@ -929,6 +979,37 @@ bz_status bz_create(const bz_space *space, const bz_vel *vel, const bz_walls *wa
         BZ_STEP(configure_cell_kernel<float>(H));
     BZ_STEP(configure_cell4(H));
 #undef BZ_STEP
+    if (H->stretched) {
+        std::vector<double> fx(g.nx), fy(g.ny);
+        std::vector<double> wl(g.nx);
+        for (int i = 0; i < g.nx; ++i) {
+            fx[i] = g.dx / cdx[i];
+            wl[i] = cdx[i] * space->kn;
+        }
+        for (int i = 0; i < g.ny; ++i) fy[i] = g.dx / cdy[i];
+        st = dalloc(&H->axe, sizeof(double) * (N + 1));
+        if (st == BZ_OK) st = dalloc(&H->axd, sizeof(double) * N);
+        if (st == BZ_OK) st = dalloc(&H->sx, sizeof(double) * g.nx);
+        if (st == BZ_OK) st = dalloc(&H->sy, sizeof(double) * g.ny);
+        if (st == BZ_OK) st = dalloc(&H->wlid, sizeof(double) * g.nx);
+        if (st != BZ_OK) return bail(st);
+        e = cudaMemcpy(H->axe, edges.data(), sizeof(double) * (N + 1), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(H->axd, axw.data(), sizeof(double) * N, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(H->sx, fx.data(), sizeof(double) * g.nx, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(H->sy, fy.data(), sizeof(double) * g.ny, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(H->wlid, wl.data(), sizeof(double) * g.nx, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            fail(BZ_ECUDA, "grid table upload failed: %s", cudaGetErrorString(e));
+            return bail(BZ_ECUDA);
+        }
+        if (sv) {
+            g.axe = H->axe;
+            g.axd = H->axd;
+        }
+        g.sx = H->sx;
+        g.sy = H->sy;
+        g.wlid = H->wlid;
+    }
     e = cudaMemcpy(H->axv, axv.data(), sizeof(double) * N, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(H->axA, axA.data(), sizeof(double) * N, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && walls->lid_profile) {
@@ -1098,7 +1179,7 @@ bz_status bz_lid_shear(bz_handle *H, double *out, void *stream)
     BZ_LAUNCHED(H);
     double *tmp = H->mom;  // reuse: nr*11 >= nx+1 always (ny >= 1)
     if ((size_t)g.nr * 11 < (size_t)g.nx + 1) return fail(BZ_EINVAL, "internal size");
-    bzk::k_shear_mean<<<1, 256, 0, s>>>(H->shear, g.nx, tmp);
+    bzk::k_shear_mean<<<1, 256, 0, s>>>(H->shear, g.nx, g.wlid, tmp);
     BZ_LAUNCHED(H);
     H->mom_valid = false;
     BZ_CUDA(cudaMemcpyAsync(out, tmp, sizeof(double) * (g.nx + 1), cudaMemcpyDefault, s));
@@ -1281,6 +1362,7 @@ bz_status bz_adjoint_step(bz_handle *H, int64_t step, const void *h_n, const voi
     if (step < 0) return fail(BZ_EINVAL, "step must be >= 0");
     if (H->per_cell)
         return fail(BZ_EUNSUPPORTED, "the adjoint is implemented for the shared sample set only");
+    if (H->stretched) return fail(BZ_EUNSUPPORTED, "the adjoint is implemented for uniform grids only");
     if (!std::isfinite(wD)) return fail(BZ_EINVAL, "wD must be finite");
     const size_t bytes = H->esz * (size_t)H->g.nr * H->g.nvt;
     const char *a = (const char *)h_n, *b = (const char *)lam_out;
@@ -1422,6 +1504,9 @@ bz_status bz_batch_create(int32_t n, const bz_space *spaces, const bz_vel *vels,
         if (params[i].dtype != BZ_F32) return fail(BZ_EUNSUPPORTED, "instance %d: batches are FP32", i);
         if (params[i].sample_mode != BZ_SHARED)
             return fail(BZ_EUNSUPPORTED, "instance %d: batches use the shared sample set", i);
+        if ((vels[i].rv > 0.0 && vels[i].rv < 1.0) || (spaces[i].rx > 0.0 && spaces[i].rx < 1.0) ||
+            (spaces[i].ry > 0.0 && spaces[i].ry < 1.0))
+            return fail(BZ_EUNSUPPORTED, "instance %d: batches use uniform grids", i);
         if (vels[i].nv % 4 != 0 || vels[i].nv < 12)
             return fail(BZ_EUNSUPPORTED, "instance %d: nv must be a multiple of 4, >= 12", i);
         if (params[i].n_pairs > 32768)

@@ -45,6 +45,13 @@ struct Geo {
     float G0f[25];              // the same, rounded to float
     int swz;                    // plan node indices in the quad-rotated shared-memory order
     int strip;                  // cells are visited in column strips of this width
+    // Stretched grids (nullptr when uniform).  axe: nv + 1 velocity cell
+    // edges; axd: nv widths; sx, sy: per column / row, dx / dx_i and
+    // dx / dy_j (the Courant numbers are cu(v) times these); wlid: per lid
+    // face, dx_i / L (the weights of the lid-shear mean).
+    const double *axe, *axd;
+    const double *sx, *sy;
+    const double *wlid;
 };
 
 // Visiting order of the cells by the persistent per-cell kernels: column
@@ -117,6 +124,34 @@ __device__ __forceinline__ int node_of(const double v[3], double vmax, double dv
     return (a * n + b) * n + c;
 }
 
+// Stretched velocity cells: the cell k with e[k] <= v < e[k+1] (a value on
+// an edge belongs to the upper cell), by bisection over the n + 1 edges.
+__device__ __forceinline__ int node_axis_edges(double v, const double *__restrict__ e, int n,
+                                               int *near)
+{
+    if (!(v >= e[0]) || v >= e[n]) return -1;
+    int lo = 0, hi = n - 1;                  // e[lo] <= v < e[hi + 1]
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (v >= e[mid]) lo = mid;
+        else hi = mid - 1;
+    }
+    const double w = __dsub_rn(e[lo + 1], e[lo]);
+    if (__dsub_rn(v, e[lo]) < 1e-9 * w || __dsub_rn(e[lo + 1], v) < 1e-9 * w) *near = 1;
+    return lo;
+}
+
+__device__ __forceinline__ int node_of(const double v[3], const Geo &g, int *near)
+{
+    if (!g.axe) return node_of(v, g.vmax, g.dv, g.nv, near);
+    const int n = g.nv;
+    int a = node_axis_edges(v[0], g.axe, n, near);
+    int b = node_axis_edges(v[1], g.axe, n, near);
+    int c = node_axis_edges(v[2], g.axe, n, near);
+    if (a < 0 || b < 0 || c < 0) return -1;
+    return (a * n + b) * n + c;
+}
+
 struct SampleOut {
     int idx[4];
     double W;
@@ -162,10 +197,10 @@ __device__ __forceinline__ SampleOut draw_sample(const Geo &g, int64_t step, uin
     }
     SampleOut o;
     int near = 0;
-    o.idx[0] = node_of(v, g.vmax, g.dv, g.nv, &near);
-    o.idx[1] = node_of(v1, g.vmax, g.dv, g.nv, &near);
-    o.idx[2] = node_of(vs, g.vmax, g.dv, g.nv, &near);
-    o.idx[3] = node_of(v1s, g.vmax, g.dv, g.nv, &near);
+    o.idx[0] = node_of(v, g, &near);
+    o.idx[1] = node_of(v1, g, &near);
+    o.idx[2] = node_of(vs, g, &near);
+    o.idx[3] = node_of(v1s, g, &near);
     o.near = near;
     o.outside = (o.idx[0] < 0) | (o.idx[1] < 0) | (o.idx[2] < 0) | (o.idx[3] < 0);
     o.W = __dmul_rn(g.cw, fabs(s));
@@ -398,7 +433,7 @@ __device__ __forceinline__ void walls_face(const Geo &g, int64_t step, const R *
         double tsum = 0.0;
         for (int jt = 0; jt < N; ++jt) {
             double d = g.axv[jt] - F.U;
-            tsum += g.dv * 0.5641895835477563 * exp(-d * d);
+            tsum += (g.axd ? g.axd[jt] : g.dv) * 0.5641895835477563 * exp(-d * d);
         }
         double din = g.hn * tsum * g.zsum;
         double nw = (g.cout + g.eps * tot[0]) / din;
@@ -445,13 +480,16 @@ __global__ void k_walls(Geo g, const int64_t *__restrict__ stepp, const R *__res
 // Advances the device step counter by one (the last launch of a step).
 static __global__ void k_advance(int64_t *__restrict__ stepp) { *stepp += 1; }
 
-static __global__ void k_shear_mean(const double *__restrict__ shear, int nx, double *__restrict__ out)
+// out[0..nx) = the face shears, out[nx] = D, their mean over the lid
+// weighted by the face widths (wlid[i] = dx_i / L; nullptr: uniform faces).
+static __global__ void k_shear_mean(const double *__restrict__ shear, int nx,
+                                    const double *__restrict__ wlid, double *__restrict__ out)
 {
     __shared__ double red[kMaxWarps * kRedSlots];
     __shared__ double tot[1];
     double a[1] = {0.0};
     for (int i = threadIdx.x; i < nx; i += blockDim.x) {
-        a[0] += shear[i];
+        a[0] += wlid ? shear[i] * wlid[i] * nx : shear[i];
         out[i] = shear[i];
     }
     block_reduce<1, double>(a, red, tot);
@@ -496,10 +534,12 @@ __global__ void k_stream(Geo g, const R *__restrict__ h, const R *__restrict__ g
     const R ry = (R)(g.dx / g.dy);
     for (int c = blockIdx.x; c < g.nr; c += gridDim.x) {
         const int ix = c % g.nx, iy = c / g.nx;
+        // Courant numbers of this cell: its own widths on stretched grids.
+        const R fx = g.sx ? (R)g.sx[ix] : R(1), fy = g.sy ? (R)g.sy[iy] : ry;
         for (int j = threadIdx.x; j < g.nvt; j += blockDim.x) {
             int jx = j / N2, jy = (j / N) % N;
             ht[(int64_t)c * g.nvt + j] =
-                upwind_node<R>(g, h, ghost, c, ix, iy, j, jx, jy, cu[jx], cu[jy] * ry);
+                upwind_node<R>(g, h, ghost, c, ix, iy, j, jx, jy, cu[jx] * fx, cu[jy] * fy);
         }
     }
 }
@@ -725,10 +765,12 @@ k_cell(Geo g, const R *__restrict__ hin, const R *__restrict__ ghost,
             // per thread; at a wall the source is the face's ghost value.
             const int64_t nvt64 = nvt;
             const R *own = hin + (int64_t)c * nvt64;
+            // Courant factors of this cell (its own widths on stretched grids).
+            const R fx = g.sx ? (R)g.sx[ix] : R(1), fy = g.sy ? (R)g.sy[iy] : ry;
             const int nneg = N / 2, npos = (N + 1) / 2;
             for (int p = t; p < N2; p += T) {
                 const int jy = p / N;
-                const R cuy = S.tab.cu[jy] * ry, ay = fabs(cuy);
+                const R cuy = S.tab.cu[jy] * fy, ay = fabs(cuy);
                 const R *ys = own;
                 int ystr = N2, yoff = p;
                 if (cuy > R(0)) {
@@ -745,7 +787,7 @@ k_cell(Geo g, const R *__restrict__ hin, const R *__restrict__ ghost,
                 for (int jx = 0; jx < nneg; ++jx) {
                     const int j = jx * N2 + p;
                     R h0 = own[j], hx = xs[jx * xstr], hy = ys[jx * ystr + yoff];
-                    R ax = fabs(S.tab.cu[jx]);
+                    R ax = fabs(S.tab.cu[jx]) * fx;
                     S.slab[j] = h0 - ax * (h0 - hx) - ay * (h0 - hy);
                 }
                 for (int jx = nneg; jx < npos; ++jx) {       // v_x = 0 (odd N)
@@ -760,7 +802,7 @@ k_cell(Geo g, const R *__restrict__ hin, const R *__restrict__ ghost,
                 for (int jx = npos; jx < N; ++jx) {
                     const int j = jx * N2 + p;
                     R h0 = own[j], hx = xs[jx * xstr], hy = ys[jx * ystr + yoff];
-                    R ax = fabs(S.tab.cu[jx]);
+                    R ax = fabs(S.tab.cu[jx]) * fx;
                     S.slab[j] = h0 - ax * (h0 - hx) - ay * (h0 - hy);
                 }
             }

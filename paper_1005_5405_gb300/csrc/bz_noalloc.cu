@@ -137,6 +137,9 @@ extern "C" bz_status bz_collide_noalloc(const bz_space *space, const bz_vel *vel
     if (params->dtype != BZ_F32 && params->dtype != BZ_F64) return err(BZ_EINVAL, "dtype");
     if (params->sample_mode != BZ_SHARED)
         return err(BZ_EUNSUPPORTED, "only the shared sample set is implemented");
+    if ((vel->rv > 0.0 && vel->rv < 1.0) || (space->rx > 0.0 && space->rx < 1.0) ||
+        (space->ry > 0.0 && space->ry < 1.0))
+        return err(BZ_EUNSUPPORTED, "uniform grids only");
     if (step < 0) return err(BZ_EINVAL, "step must be >= 0");
     if (h_in == h_out) return err(BZ_EINVAL, "h_in and h_out must not overlap");
 

@@ -18,6 +18,8 @@ y = L, diffuse walls at T0, initial uniform Maxwellian n0 = 1, h0 = 0):
   adjoint128_v20 128x128 cells, 20^3 on [-4.5,4.5]^3, Kn 0.2, per-face lid
                  0.1 + N(0, 0.01^2), 5000 samples/step, seed 4, FP32
   percell64_v24  cavity64_v24 with its own 10^4 samples in every cell
+  paper_cavity   the paper's own setups (stretched grids, lid 0.01), delta
+                 0.1, 1, 10
 """
 from __future__ import annotations
 
@@ -101,6 +103,21 @@ def adjoint128_v20(seed: int = 4) -> Problem:
 def percell64_v24() -> Problem:
     """cavity64_v24 with an independent sample set in every cell."""
     return Problem("percell64_v24", 64, 64, 0.1, 24, 4.5, 10_000, 2, per_cell=True, steps=2000)
+
+
+def paper_cavity(delta: float) -> Problem:
+    """The paper's driven-cavity setups (Sec. 5.1): lid speed 0.01, velocity
+    box [-3, 3]^3 with stretched cells, stretched spatial cells refined toward
+    the lid corners.  delta = 0.1 and 1: 160x160 cells, 20^3 nodes (rv
+    0.945), rx 0.996, ry 0.998, 1024 (delta 0.1) or 6144 (delta 1) samples
+    per step; delta = 10: 192x192 cells, 18^3 nodes (rv 0.970), rx 0.990,
+    ry 0.995, 8192 samples.  FP32."""
+    if delta >= 10:
+        return Problem("paper_delta10", 192, 192, 1.0 / delta, 18, 3.0, 8192, 6, lid_u0=0.01,
+                       rv=0.970, rx=0.990, ry=0.995, steps=1000)
+    nt = 1024 if delta <= 0.1 else 6144
+    return Problem(f"paper_delta{delta:g}", 160, 160, 1.0 / delta, 20, 3.0, nt, 5, lid_u0=0.01,
+                   rv=0.945, rx=0.996, ry=0.998, steps=1000)
 
 
 def batch64(n: int = 64, seed0: int = 100, nt: int = 5000) -> list:
