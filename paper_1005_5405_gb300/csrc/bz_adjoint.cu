@@ -209,8 +209,16 @@ bz_status launch(bz_adj_scratch *a, const bzk::Geo &g0, int64_t step, const R *h
         int dev = 0, nsm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        const int grid = std::min(g.nr, nsm * 8);
-        bzk::k_adj_stream<R><<<grid, 256, 0, s>>>(g, (const R *)a->lt, a->lF, lam_out, wD);
+        if (fast) {
+            const int Q = g.nv * g.nv / 4;
+            const int blk = Q * std::max(1, 512 / Q);
+            const int grid = std::min(g.nr, nsm * std::max(1, 2048 / blk));
+            bzk::k_adj_stream4<<<grid, blk, 0, s>>>(g, (const float *)a->lt, a->lF,
+                                                     (float *)lam_out, wD);
+        } else {
+            const int grid = std::min(g.nr, nsm * 8);
+            bzk::k_adj_stream<R><<<grid, 256, 0, s>>>(g, (const R *)a->lt, a->lF, lam_out, wD);
+        }
         e = check();
     }
     if (launches) *launches += n;

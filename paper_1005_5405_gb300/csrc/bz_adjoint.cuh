@@ -290,7 +290,8 @@ k_adj_cell(Geo g, const R *__restrict__ hin, const R *__restrict__ ghost,
 // Per face: the sensitivities of its ghost values, gathered from dJ/dh~ of
 // the boundary cell (inflow nodes, weight |Cu_n|) and, on the lid, from the
 // shear D_n; turned into dJ/dF (F = outgoing flux sum |v_n| w h) in lF[f] and,
-// on the lid, into dJ/dU added to grad_lid.
+// on the lid, into dJ/dU added to grad_lid.  The factor r = Phi_w / (n_w
+// Phi0) depends on v_x only (walls at rest: 1) and is tabulated per face.
 template <typename R>
 __global__ void k_adj_walls(Geo g, const int64_t *__restrict__ stepp, const R *__restrict__ lt,
                             const double *__restrict__ nw, double *__restrict__ lF,
@@ -298,25 +299,32 @@ __global__ void k_adj_walls(Geo g, const int64_t *__restrict__ stepp, const R *_
 {
     __shared__ double red[kMaxWarps * kRedSlots];
     __shared__ double tot[4];
+    __shared__ double rt[kMaxN], sA[kMaxN], sv[kMaxN];
     const int64_t step = *stepp;
     const int f = blockIdx.x;
     const Face F = face_of(g, f, step);
     const int N = g.nv, N2 = N * N;
     const bool lid = f >= 2 * g.ny + g.nx;
     const double cdx = g.dt / (F.nax == 0 ? g.dx : g.dy), U = F.U;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        sv[i] = g.axv[i];
+        sA[i] = g.axA[i];
+        rt[i] = lid ? exp(2.0 * g.axv[i] * U - U * U) : 1.0;
+    }
+    __syncthreads();
     const R *L = lt + (int64_t)F.cell * g.nvt;
+    const double dcoef = lid && wD != 0.0 ? wD * 2.0 / g.nx : 0.0;
     double acc[2] = {0.0, 0.0};     // sum lg r, sum lg r v_x
     for (int j = threadIdx.x; j < g.nvt; j += blockDim.x) {
-        const int jx = j / N2, jy = (j / N) % N, jz = j % N;
-        const double vx = g.axv[jx], vy = g.axv[jy];
+        const int jx = j / N2, jy = (j / N) % N, jz = j - (j / N) * N;
+        const double vx = sv[jx], vy = sv[jy];
         const double vn = (F.nax == 0 ? vx : vy) * F.nsign;
         if (vn > 0.0) {
             double lg = vn * cdx * (double)L[j];
-            if (lid && wD != 0.0)
-                lg += wD * 2.0 * g.axA[jx] * g.axA[jy] * g.axA[jz] * vx * vy / g.nx;
-            const double r = lid ? exp(2.0 * vx * U - U * U) : 1.0;
-            acc[0] += lg * r;
-            acc[1] += lg * r * vx;
+            if (dcoef != 0.0) lg += dcoef * sA[jx] * sA[jy] * sA[jz] * vx * vy;
+            const double lr = lg * rt[jx];
+            acc[0] += lr;
+            acc[1] += lr * vx;
         }
     }
     block_reduce<2, double>(acc, red, tot);

@@ -884,6 +884,72 @@ k_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ 
 }
 
 
+// dJ/dh^n from dJ/dh~ (FP32, velocity axis a multiple of 4): the transposed
+// upwind stencil (h^n_c feeds h~ of its downwind neighbours: right for v_x >
+// 0, above for v_y > 0) in 16-byte quads of four jz nodes, plus on boundary
+// cells the outgoing-flux terms lF[f] |v_n| w of their faces and on the lid
+// row the lid-shear term wD 2 w v_x v_y / nx.  blockDim a multiple of Q.
+static __global__ void __launch_bounds__(1024) k_adj_stream4(Geo g, const float *__restrict__ lt,
+                                                             const double *__restrict__ lF,
+                                                             float *__restrict__ lam_out, double wD)
+{
+    __shared__ float sv[kMaxN], sax[kMaxN], say[kMaxN], sA[kMaxN];
+    const int N = g.nv, nq = N / 4, Q = N * N / 4, half = N / 2;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const double v = g.axv[i];
+        sv[i] = (float)v;
+        sax[i] = (float)(fabs(v) * g.dt / g.dx);
+        say[i] = (float)(fabs(v) * g.dt / g.dy);
+        sA[i] = (float)g.axA[i];
+    }
+    __syncthreads();
+    const int64_t plane = g.nvt / 4;
+    const int q = threadIdx.x % Q, jxs = threadIdx.x / Q, jstep = blockDim.x / Q;
+    const int jy = q / nq, jz0 = 4 * (q % nq);
+    const float vy = sv[jy], ay = say[jy];
+    const float dcoef = (float)(wD * 2.0 / g.nx);
+    for (int c = blockIdx.x; c < g.nr; c += gridDim.x) {
+        const int ix = c % g.nx, iy = c / g.nx;
+        const float4 *own = reinterpret_cast<const float4 *>(lt) + (int64_t)c * plane;
+        float4 *dst = reinterpret_cast<float4 *>(lam_out) + (int64_t)c * plane;
+        // Downwind y neighbour of this thread's row (v_y > 0: above).
+        const bool yd = jy >= half ? iy < g.ny - 1 : iy > 0;
+        const float4 *ys = own + (jy >= half ? (int64_t)g.nx : -(int64_t)g.nx) * plane;
+        const bool edge = ix == 0 || ix == g.nx - 1 || iy == 0 || iy == g.ny - 1;
+        for (int jx = jxs; jx < N; jx += jstep) {
+            const int o = jx * Q + q;
+            const float ax = sax[jx];
+            const bool xd = jx >= half ? ix < g.nx - 1 : ix > 0;   // v_x > 0: right
+            const float4 l0 = own[o];
+            const float4 lx = xd ? own[o + (jx >= half ? plane : -plane)] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 ly = yd ? ys[o] : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 r;
+            const float c0 = 1.f - ax - ay;
+            r.x = c0 * l0.x + ax * lx.x + ay * ly.x;
+            r.y = c0 * l0.y + ax * lx.y + ay * ly.y;
+            r.z = c0 * l0.z + ax * lx.z + ay * ly.z;
+            r.w = c0 * l0.w + ax * lx.w + ay * ly.w;
+            if (edge) {
+                const float vx = sv[jx];
+                float ex = 0.f;
+                if (ix == 0 && vx < 0.f) ex -= (float)lF[iy] * vx;
+                if (ix == g.nx - 1 && vx > 0.f) ex += (float)lF[g.ny + iy] * vx;
+                if (iy == 0 && vy < 0.f) ex -= (float)lF[2 * g.ny + ix] * vy;
+                float dl = 0.f;
+                if (iy == g.ny - 1 && vy > 0.f) {
+                    ex += (float)lF[2 * g.ny + g.nx + ix] * vy;
+                    dl = dcoef * vx * vy;
+                }
+                const float wxy = sA[jx] * sA[jy];
+                float *rr = &r.x;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) rr[i] += (ex + dl) * wxy * sA[jz0 + i];
+            }
+            dst[o] = r;
+        }
+    }
+}
+
 // Shared-memory bytes of k_adj_cell4: those of k_cell4 plus two slabs, the
 // saved correction sums and one per-jx table.
 __host__ __device__ inline size_t adj4_smem_bytes(int nv, int nvt, int nt)

@@ -666,6 +666,23 @@ __global__ void __launch_bounds__(512, 2) k_lz(Geo g, LzArgs a)
             __syncthreads();
             const bool yin = yup ? iy > 0 : iy < g.ny - 1;
             const float *yg = a.ghost + (yup ? 2 * g.ny + ix : 2 * g.ny + g.nx + ix) * N;
+            // The (v_y, v_z) part of each source cell's pending correction at
+            // this thread's two nodes: mu_y v_y + mu_z v_z + mu_4 (v_y^2 + v_z^2)
+            // for the own cell (o), the y source (y), the right (r) and left (l) cells.
+            float bdo[2], bdy[2], bdr[2], bdl[2];
+            {
+                const float vy = S.v[jy];
+                const float2 z2 = S.vz2[qz];
+                const float vz[2] = {z2.x, z2.y};
+#pragma unroll
+                for (int i = 0; i < 2; ++i) {
+                    const float qi = vy * vy + vz[i] * vz[i];
+                    bdo[i] = S.mus[2] * vy + S.mus[3] * vz[i] + S.mus[4] * qi;
+                    bdy[i] = S.mus[ys * 8 + 2] * vy + S.mus[ys * 8 + 3] * vz[i] + S.mus[ys * 8 + 4] * qi;
+                    bdr[i] = S.mus[8 + 2] * vy + S.mus[8 + 3] * vz[i] + S.mus[8 + 4] * qi;
+                    bdl[i] = S.mus[16 + 2] * vy + S.mus[16 + 3] * vz[i] + S.mus[16 + 4] * qi;
+                }
+            }
             // Per-thread power sums over jx of N = w h~ / (A_y A_z) for the pair.
             float s[2][5];
 #pragma unroll
@@ -690,25 +707,16 @@ __global__ void __launch_bounds__(512, 2) k_lz(Geo g, LzArgs a)
                     const float ax = S.cax[jx], ay = S.cuy[jy];
                     const float4 gv = S.gram[jx];
                     const float Ax = S.A[jx];
-                    // Pending correction of each source: ca(jx) + mu_y v_y + mu_z v_z
-                    // + mu_4 (v_y^2 + v_z^2) with that source cell's mu.
-                    const float vy = S.v[jy];
-                    const float2 z2 = S.vz2[qz];
-                    const float vz[2] = {z2.x, z2.y};
+                    // Pending correction of each source: ca(jx) + its (v_y, v_z) part.
                     const float cao = S.ca[jx], cax = S.ca[xs * N + jx], cay = S.ca[ys * N + jx];
                     const float h0a[2] = {h0.x, h0.y}, hxa[2] = {hx.x, hx.y}, hya[2] = {hy.x, hy.y};
                     float ht[2];
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
-                        const float qi = vy * vy + vz[i] * vz[i];
-                        const float bdo = S.mus[2] * vy + S.mus[3] * vz[i] + S.mus[4] * qi;
-                        const float bdx = S.mus[xs * 8 + 2] * vy + S.mus[xs * 8 + 3] * vz[i] +
-                                          S.mus[xs * 8 + 4] * qi;
-                        const float bdy = S.mus[ys * 8 + 2] * vy + S.mus[ys * 8 + 3] * vz[i] +
-                                          S.mus[ys * 8 + 4] * qi;
-                        const float u0 = lz_corr(h0a[i], cao + bdo, eps);
+                        const float bdx = xr ? bdr[i] : bdl[i];
+                        const float u0 = lz_corr(h0a[i], cao + bdo[i], eps);
                         const float ux = xin ? lz_corr(hxa[i], cax + bdx, eps) : hxa[i];
-                        const float uy = yin ? lz_corr(hya[i], cay + bdy, eps) : hya[i];
+                        const float uy = yin ? lz_corr(hya[i], cay + bdy[i], eps) : hya[i];
                         ht[i] = u0 - ax * (u0 - ux) - ay * (u0 - uy);
                         const float n = ht[i] * Ax;       // times A_y A_z after the loop
                         s[i][0] += n;
