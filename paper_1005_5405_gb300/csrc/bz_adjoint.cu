@@ -73,8 +73,9 @@ bz_status setup_generic(bz_adj_scratch *a, const bzk::Geo &g, int nsm, int optin
                  "memory: %zu bytes, the device offers %d", g.nt, smem, optin);
         return err(BZ_EUNSUPPORTED, buf);
     }
-    cudaError_t e = cudaFuncSetAttribute(bzk::k_adj_cell<R>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // The limit is a property of the kernel, shared by every handle: set it to
+    // the device maximum so that no handle lowers it below another's need.
+    cudaError_t e = bz_allow_max_smem(bzk::k_adj_cell<R>, optin);
     if (e != cudaSuccess) return cuda_err(e, "cudaFuncSetAttribute");
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bzk::k_adj_cell<R>, threads, smem);
@@ -101,8 +102,7 @@ bz_status prepare_fast(bz_adj_scratch *a, const bzk::Geo &g, int nsm, int optin)
     for (int k = 1; k <= N; ++k)
         if (N % k == 0 && Q * k <= 1024) K = k;
     const int T = (Q * K + 31) / 32 * 32;
-    cudaError_t e = cudaFuncSetAttribute(bzk::k_adj_cell4<1024>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = bz_allow_max_smem(bzk::k_adj_cell4<1024>, optin);
     if (e != cudaSuccess) return cuda_err(e, "cudaFuncSetAttribute");
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bzk::k_adj_cell4<1024>, T, smem);

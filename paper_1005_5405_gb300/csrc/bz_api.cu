@@ -243,8 +243,9 @@ bool launch_cell4(bz_handle *H, cudaStream_t s, bool fused, const R *hin, R *hou
 template <bool F, int M>
 bz_status setup_cell4_kernel(bz_handle *H, int *occ)
 {
-    BZ_CUDA(cudaFuncSetAttribute(bzk::k_cell4<F, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)H->smem4));
+    // Kernel attributes are shared by every handle in the process: the limit
+    // is set to the device maximum so that no handle lowers it for another.
+    BZ_CUDA(bz_allow_max_smem(bzk::k_cell4<F, M>, H->smem_optin));
     BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, bzk::k_cell4<F, M>, H->threads4,
                                                           H->smem4));
     return BZ_OK;
@@ -369,8 +370,7 @@ int lz_nv_key(int nv) { return nv == 32 || nv == 20 ? nv : 0; }
 template <int G, int NV>
 bz_status setup_lz_one(bz_handle *H, size_t smem, int *occ)
 {
-    BZ_CUDA(cudaFuncSetAttribute(bzk::k_lz<G, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
+    BZ_CUDA(bz_allow_max_smem(bzk::k_lz<G, NV>, H->smem_optin));
     BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, bzk::k_lz<G, NV>, H->lz_T, smem));
     return BZ_OK;
 }
@@ -710,10 +710,8 @@ bz_status launch_step(bz_handle *H, cudaStream_t s, bool fused, bool do_stream, 
 template <typename R, typename I, bool PC>
 bz_status configure_kernels_pc(bz_handle *H, int *occ_f, int *occ_c)
 {
-    BZ_CUDA(cudaFuncSetAttribute(bzk::k_cell<R, true, I, PC>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)H->smem_cell));
-    BZ_CUDA(cudaFuncSetAttribute(bzk::k_cell<R, false, I, PC>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)H->smem_cell));
+    BZ_CUDA(bz_allow_max_smem(bzk::k_cell<R, true, I, PC>, H->smem_optin));
+    BZ_CUDA(bz_allow_max_smem(bzk::k_cell<R, false, I, PC>, H->smem_optin));
     BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_f, bzk::k_cell<R, true, I, PC>,
                                                           H->threads, H->smem_cell));
     BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ_c, bzk::k_cell<R, false, I, PC>,
@@ -1441,8 +1439,10 @@ void batch_free(bz_batch *B)
 template <int M>
 bz_status batch_occupancy(bz_batch *B, int *occ)
 {
-    BZ_CUDA(cudaFuncSetAttribute(bzk::kb_cell4<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)B->smem));
+    int dev = 0, optin = 0;
+    BZ_CUDA(cudaGetDevice(&dev));
+    BZ_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    BZ_CUDA(bz_allow_max_smem(bzk::kb_cell4<M>, optin));
     BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, bzk::kb_cell4<M>, M, B->smem));
     return BZ_OK;
 }

@@ -14,6 +14,20 @@ struct Geo;
 // Stores the text returned by bz_last_error() on this thread.
 void bz_record_error(const char *msg);
 
+// A kernel's dynamic shared-memory limit is one setting for the whole
+// process, shared by every handle that launches it: it is raised to the most
+// the device allows next to the kernel's static shared memory, so that no
+// handle can lower it below another handle's need.
+template <typename Kernel>
+cudaError_t bz_allow_max_smem(Kernel kernel, int optin)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                optin - (int)fa.sharedSizeBytes);
+}
+
 // Scratch of bz_adjoint_step (bz_adjoint.cu), owned by a handle.
 struct bz_adj_scratch {
     int4 *pidx;          // sample node indices, logical order

@@ -92,8 +92,7 @@ bz_status run(const bzk::Geo &g0, unsigned char *scr, int64_t step, const void *
                    "the velocity slab and the %d per-sample products need %zu bytes of shared "
                    "memory; the device offers %d", g.nt, smem, optin);
     const int threads = std::min(bzk::kMaxThreads, (g.nv * g.nv + 31) / 32 * 32);
-    cudaError_t e = cudaFuncSetAttribute(bzk::k_cell<R, false, int>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = bz_allow_max_smem(bzk::k_cell<R, false, int>, optin);
     int occ = 0;
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bzk::k_cell<R, false, int>,

@@ -372,3 +372,19 @@ def test_errors_are_reported():
         del os.environ["BZ_FAULT"]
     cav.step(1)
 
+
+
+@pytest.mark.parametrize("kernel_env", [None, "cell4", "generic"])
+def test_handles_of_different_sizes_coexist(monkeypatch, kernel_env):
+    """Kernel attributes (the dynamic shared-memory limit) are shared by all
+    handles of the process: creating a handle that needs less shared memory
+    must not break the launches of one created before it."""
+    if kernel_env:
+        monkeypatch.setenv("BZ_KERNEL", kernel_env)
+    probs = [workloads.small(nx=3, ny=3, nv=nv, vmax=4.0, nt=1500, seed=40 + nv, dtype="f32",
+                             eps=0.1) for nv in (24, 16, 12)]
+    made = [make(p) for p in probs]             # all created before any step
+    for (cav, o, h0), p in zip(made, probs):
+        cav.step(1)
+        h_o, _ = o.step(h0, 0)
+        assert f_metric(o, state(cav), h_o) < 1e-5, p.nv
