@@ -229,13 +229,17 @@ bz_status bz_philox(uint32_t k0, uint32_t k1, const uint32_t *ctr, int64_t n, ui
 
 /* ---------------------------------------------------------------------
  * Batches: many independent cavity instances (each with its own grids, Kn,
- * lid, sample count and Philox key) advanced together, one persistent launch
- * per kernel class and step, the step captured once in a CUDA graph.  Every
- * instance must be FP32 with nv a multiple of 4 and >= 12, and at most 32768
- * samples per step (BZ_EUNSUPPORTED otherwise).  The batch owns its instances;
- * instance i is addressed by its index.  The state of an instance at step n
- * lives in one of its two buffers chosen by the parity of n, so the per-
- * instance calls below are the way to read and write it. */
+ * lid, sample count and Philox key) advanced together, every step one CUDA
+ * graph launch.  Two schedules: persistent kernels (one launch per kernel
+ * class and step over the cells of all instances, the FP32 4-node-vector
+ * per-cell kernel) or fan-out (every instance's own active-node step, the
+ * instances spread over up to 8 concurrent graph branches); bz_batch_tune
+ * chooses.  Every instance must be FP32 with nv a multiple of 4 and >= 12,
+ * at most 32768 samples per step, the shared sample set and uniform grids
+ * (BZ_EUNSUPPORTED otherwise).  The batch owns its instances; instance i is
+ * addressed by its index.  The state of an instance at step n lives in one of
+ * its two buffers chosen by the parity of n, so the per-instance calls below
+ * are the way to read and write it. */
 typedef struct bz_batch bz_batch;
 
 bz_status bz_batch_create(int32_t n, const bz_space *spaces, const bz_vel *vels,
@@ -248,14 +252,17 @@ bz_status bz_batch_get_state(bz_batch *b, int32_t i, void *dst, int64_t *step, v
 /* Moments of instance i's current state (as bz_moments). */
 bz_status bz_batch_moments(bz_batch *b, int32_t i, double *out, void *stream);
 /* Autotuner: times `trial_steps` recomputations of the current step (the
- * state is not advanced) for every launch schedule (threads per CTA 512 or
- * 1024, CTAs per SM, cell-strip width 4, 8 or 16), keeps the fastest and
- * returns its index in *choice (nullable) and the milliseconds per step of
- * every schedule in ms[0..ncand) (nullable, up to 12 entries). */
+ * state is not advanced) for every schedule (persistent kernels: threads per
+ * CTA 512 or 1024, CTAs per SM, cell-strip width 4, 8 or 16; fan-out: 1, 2, 4
+ * or 8 branches, as a graph), keeps the fastest and returns its index in
+ * *choice (nullable) and the milliseconds per step of every schedule in
+ * ms[0..ncand) (nullable, up to 16 entries). */
 bz_status bz_batch_tune(bz_batch *b, int32_t trial_steps, void *stream, int32_t *choice,
                         double *ms, int32_t *ncand);
-/* Launch schedule in use: threads per CTA, persistent CTAs, strip width. */
-bz_status bz_batch_schedule(const bz_batch *b, int32_t out[3]);
+/* Schedule in use: out[0..2] the persistent kernels' threads per CTA,
+ * persistent CTAs and strip width; out[3] the fan-out branches (0 when the
+ * persistent kernels run). */
+bz_status bz_batch_schedule(const bz_batch *b, int32_t out[4]);
 
 /* Per-kernel timing with CUDA events recorded on the launching stream around
  * every kernel the handle launches while enabled (enable != 0); disabling

@@ -374,16 +374,16 @@ class Batch:
 
     def tune(self, trial_steps=2, stream=None):
         choice = C.c_int32()
-        ms = (C.c_double * 12)()
+        ms = (C.c_double * 16)()
         nc = C.c_int32()
         check(load().bz_batch_tune(self.h, trial_steps, _stream_ptr(stream), C.byref(choice), ms,
                                    C.byref(nc)), "bz_batch_tune")
         return choice.value, list(ms)[: nc.value]
 
     def schedule(self):
-        out = (C.c_int32 * 3)()
+        out = (C.c_int32 * 4)()
         check(load().bz_batch_schedule(self.h, out), "bz_batch_schedule")
-        return {"threads": out[0], "ctas": out[1], "strip": out[2]}
+        return {"threads": out[0], "ctas": out[1], "strip": out[2], "fanout_branches": out[3]}
 
 
 def philox(key, ctr):

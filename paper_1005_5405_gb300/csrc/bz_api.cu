@@ -515,7 +515,7 @@ bz_status configure_lazy(bz_handle *H)
 // pending corrections), the sample set, its compact form and scatter list,
 // the per-cell kernel, and the k_cell4 fallback that runs only when the step
 // has more active nodes than the compact arrays hold.
-bz_status launch_lazy(bz_handle *H, cudaStream_t s)
+bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true)
 {
     const Geo &g = H->g;
     Geo gl = g;
@@ -594,6 +594,9 @@ bz_status launch_lazy(bz_handle *H, cudaStream_t s)
         bzk::k_lz_materialize<<<std::min(g.nr, H->nsm * 8), 256, 0, s>>>(
             g, H->lz_meta, hin, H->mu[in], hin, H->mu[out]);
         BZ_LAUNCHED(H);
+        // The input now holds corrected values: its pending corrections go.
+        bzk::k_lz_clear<<<H->nsm, 256, 0, s>>>(H->lz_meta, H->mu[in], (int64_t)g.nr * 8);
+        BZ_LAUNCHED(H);
         const int grid = H->grid4f;
         if (H->maxt4 == 512)
             bzk::k_cell4<true, 512><<<grid, H->threads4, H->smem4, s>>>(
@@ -605,6 +608,7 @@ bz_status launch_lazy(bz_handle *H, cudaStream_t s)
                 H->stats, nullptr, H->lz_meta);
         BZ_LAUNCHED(H);
     }
+    if (!advance_step) return BZ_OK;           // a repeatable trial of the step
     H->cur = out;
     H->mom_valid = true;
     H->lazy_buf[out] = true;
@@ -1413,6 +1417,17 @@ struct bz_batch {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t graph = nullptr;
     std::vector<int64_t> step;
+    // Fan-out mode: every instance's own step (the active-node kernels) on
+    // `branches` forked streams, the whole step captured as one multi-branch
+    // graph; one graph per parity pattern of the instances' steps.
+    int mode = 0;                           // 0 persistent kernels, 1 fan-out
+    int branches = 1;
+    bool fan_ok = false;                    // every instance runs the active-node path
+    std::vector<cudaStream_t> br;
+    std::vector<cudaEvent_t> ev;            // fork + one join event per branch
+    std::vector<int> owner;                 // branch of each instance
+    cudaGraphExec_t fgraph[2] = {nullptr, nullptr};
+    std::vector<int> fkey[2];
 };
 
 namespace {
@@ -1429,6 +1444,10 @@ bzk::Map4 map_for(int N, int maxt)
 void batch_free(bz_batch *B)
 {
     if (B->graph) cudaGraphExecDestroy(B->graph);
+    for (auto &g : B->fgraph)
+        if (g) cudaGraphExecDestroy(g);
+    for (cudaStream_t st : B->br) cudaStreamDestroy(st);
+    for (cudaEvent_t e : B->ev) cudaEventDestroy(e);
     if (B->cap) cudaStreamDestroy(B->cap);
     void *ptrs[] = {B->d_inst, B->d_cell_pre, B->d_face_pre, B->d_samp_pre};
     for (void *p : ptrs)
@@ -1470,6 +1489,135 @@ bz_status batch_apply(bz_batch *B, int maxt, int ctas_per_sm, int strip)
 }
 
 // One step of every instance; advance = false recomputes the current step.
+constexpr int kMaxBranches = 8;
+
+void drop_fan_graphs(bz_batch *B)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (B->fgraph[k]) cudaGraphExecDestroy(B->fgraph[k]);
+        B->fgraph[k] = nullptr;
+        B->fkey[k].clear();
+    }
+}
+
+// Instances go to the branch with the least work so far (largest first).
+void assign_branches(bz_batch *B, int nb)
+{
+    std::vector<int> order(B->n);
+    for (int i = 0; i < B->n; ++i) order[i] = i;
+    auto work = [&](int i) { return (double)B->inst[i]->g.nr * B->inst[i]->g.nvt; };
+    std::sort(order.begin(), order.end(), [&](int a, int b) { return work(a) > work(b); });
+    std::vector<double> load(nb, 0.0);
+    B->owner.assign(B->n, 0);
+    for (int i : order) {
+        int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        B->owner[i] = k;
+        load[k] += work(i);
+    }
+    B->branches = nb;
+}
+
+// The instances' states for the persistent kernels: corrected, no pending
+// corrections (leaving fan-out mode), or fresh zero corrections (entering it).
+bz_status batch_set_mode(bz_batch *B, int mode, cudaStream_t s)
+{
+    if (mode == B->mode) return BZ_OK;
+    for (int i = 0; i < B->n; ++i) {
+        bz_handle *h = B->inst[i];
+        const size_t mb = sizeof(float) * 8 * (size_t)h->g.nr;
+        if (mode == 0) {
+            const int b = (int)(B->step[i] & 1);
+            bzk::k_lz_materialize<<<std::min(h->g.nr, h->nsm * 8), 256, 0, s>>>(
+                h->g, nullptr, (const float *)h->h[b], h->mu[b], (float *)h->h[b], nullptr);
+            BZ_CUDA(cudaGetLastError());
+        }
+        BZ_CUDA(cudaMemsetAsync(h->mu[0], 0, mb, s));
+        BZ_CUDA(cudaMemsetAsync(h->mu[1], 0, mb, s));
+        h->lazy_buf[0] = h->lazy_buf[1] = false;
+    }
+    B->mode = mode;
+    return BZ_OK;
+}
+
+// Fan-out mode keeps states with pending corrections: apply them in place
+// (the value is unchanged) before instance i's state is read.
+bz_status batch_correct_in_place(bz_batch *B, int i, cudaStream_t s)
+{
+    if (B->mode != 1) return BZ_OK;
+    bz_handle *h = B->inst[i];
+    const int b = (int)(B->step[i] & 1);
+    bzk::k_lz_materialize<<<std::min(h->g.nr, h->nsm * 8), 256, 0, s>>>(
+        h->g, nullptr, (const float *)h->h[b], h->mu[b], (float *)h->h[b], nullptr);
+    BZ_CUDA(cudaGetLastError());
+    BZ_CUDA(cudaMemsetAsync(h->mu[b], 0, sizeof(float) * 8 * (size_t)h->g.nr, s));
+    return BZ_OK;
+}
+
+// One fan-out step: fork to the branches, each instance's active-node step
+// on its branch (advance: the step counter moves on; else a repeatable trial),
+// join back to s.
+bz_status fan_launch(bz_batch *B, cudaStream_t s, bool advance_step)
+{
+    const int nb = B->branches;
+    BZ_CUDA(cudaEventRecord(B->ev[0], s));
+    for (int k = 0; k < nb; ++k) BZ_CUDA(cudaStreamWaitEvent(B->br[k], B->ev[0], 0));
+    for (int i = 0; i < B->n; ++i) {
+        bz_handle *h = B->inst[i];
+        h->cur = (int)(B->step[i] & 1);
+        h->step = B->step[i];
+        BZ_TRY(launch_lazy(h, B->br[B->owner[i]], advance_step));
+    }
+    for (int k = 0; k < nb; ++k) {
+        BZ_CUDA(cudaEventRecord(B->ev[1 + k], B->br[k]));
+        BZ_CUDA(cudaStreamWaitEvent(s, B->ev[1 + k], 0));
+    }
+    return BZ_OK;
+}
+
+// Graph of one fan-out step for the instances' current step parities.
+bz_status fan_graph(bz_batch *B, cudaGraphExec_t *out)
+{
+    std::vector<int> key(B->n);
+    for (int i = 0; i < B->n; ++i) key[i] = (int)(B->step[i] & 1);
+    for (int k = 0; k < 2; ++k)
+        if (B->fgraph[k] && B->fkey[k] == key) {
+            *out = B->fgraph[k];
+            return BZ_OK;
+        }
+    std::vector<int> cur0(B->n);
+    std::vector<int64_t> st0(B->n);
+    std::vector<long long> l0(B->n);
+    for (int i = 0; i < B->n; ++i) {
+        cur0[i] = B->inst[i]->cur;
+        st0[i] = B->inst[i]->step;
+        l0[i] = B->inst[i]->launches;
+    }
+    BZ_CUDA(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
+    bz_status st = fan_launch(B, B->cap, true);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(B->cap, &graph);
+    for (int i = 0; i < B->n; ++i) {           // capturing ran no step
+        B->inst[i]->cur = cur0[i];
+        B->inst[i]->step = st0[i];
+        B->inst[i]->launches = l0[i];
+    }
+    if (st != BZ_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(BZ_ECUDA, "batch capture failed: %s", cudaGetErrorString(e));
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(BZ_ECUDA, "batch graph: %s", cudaGetErrorString(e));
+    const int slot = B->fgraph[0] ? (B->fgraph[1] ? 0 : 1) : 0;
+    if (B->fgraph[slot]) cudaGraphExecDestroy(B->fgraph[slot]);
+    B->fgraph[slot] = ex;
+    B->fkey[slot] = key;
+    *out = ex;
+    return BZ_OK;
+}
+
 bz_status batch_launch(bz_batch *B, cudaStream_t s, bool advance)
 {
     const int pb = 256;
@@ -1582,6 +1730,26 @@ bz_status bz_batch_create(int32_t n, const bz_space *spaces, const bz_vel *vels,
     st = batch_occupancy<512>(B, &occ512);
     if (st == BZ_OK) st = occ512 >= 2 ? batch_apply(B, 512, 2, 8) : batch_apply(B, 1024, 1, 8);
     if (st != BZ_OK) return bail(st);
+    // Fan-out mode: branch streams and their fork / join events.
+    B->fan_ok = true;
+    for (bz_handle *h : B->inst) B->fan_ok = B->fan_ok && h->lazy;
+    B->br.assign(kMaxBranches, nullptr);
+    B->ev.assign(kMaxBranches + 1, nullptr);
+    for (auto &st2 : B->br)
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking);
+    for (auto &ev : B->ev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        fail(BZ_ECUDA, "batch set-up failed: %s", cudaGetErrorString(e));
+        return bail(BZ_ECUDA);
+    }
+    assign_branches(B, 4);
+    if (const char *m = getenv("BZ_BATCH_MODE"))
+        if (strcmp(m, "fanout") == 0 && B->fan_ok) {
+            st = batch_set_mode(B, 1, nullptr);
+            if (st == BZ_OK) st = cudaDeviceSynchronize() == cudaSuccess ? BZ_OK : BZ_ECUDA;
+            if (st != BZ_OK) return bail(st);
+        }
     *out = B;
     return BZ_OK;
 }
@@ -1600,6 +1768,27 @@ bz_status bz_batch_step(bz_batch *B, int32_t nsteps, void *stream)
     if (!B) return fail(BZ_EINVAL, "batch is NULL");
     if (nsteps < 0) return fail(BZ_EINVAL, "nsteps must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;
+    if (B->mode == 1) {
+        for (int32_t k = 0; k < nsteps; ++k) {
+            if (graphs_enabled()) {
+                cudaGraphExec_t ex = nullptr;
+                BZ_TRY(fan_graph(B, &ex));
+                BZ_CUDA(cudaGraphLaunch(ex, s));
+                for (int i = 0; i < B->n; ++i) {
+                    bz_handle *h = B->inst[i];
+                    h->launches += 14;
+                    h->step = B->step[i] + 1;
+                    h->cur = (int)(h->step & 1);
+                    h->lazy_buf[h->cur] = true;
+                    h->mom_valid = true;
+                }
+            } else {
+                BZ_TRY(fan_launch(B, s, true));
+            }
+            for (auto &v : B->step) v += 1;
+        }
+        return BZ_OK;
+    }
     if (nsteps > 0 && graphs_enabled()) {
         if (!B->graph) {
             BZ_CUDA(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
@@ -1630,6 +1819,8 @@ bz_status bz_batch_set_state(bz_batch *B, int32_t i, const void *src, int64_t st
     cudaStream_t s = (cudaStream_t)stream;
     BZ_CUDA(cudaMemcpyAsync(h->h[step & 1], src, h->esz * (size_t)h->g.nr * h->g.nvt,
                             cudaMemcpyDefault, s));
+    if (h->mu[step & 1])                       // a new state has no pending corrections
+        BZ_CUDA(cudaMemsetAsync(h->mu[step & 1], 0, sizeof(float) * 8 * (size_t)h->g.nr, s));
     BZ_CUDA(cudaMemcpyAsync(h->d_step, &step, sizeof(int64_t), cudaMemcpyHostToDevice, s));
     BZ_CUDA(cudaStreamSynchronize(s));
     B->step[i] = step;
@@ -1640,6 +1831,7 @@ bz_status bz_batch_get_state(bz_batch *B, int32_t i, void *dst, int64_t *step, v
 {
     if (!B || i < 0 || i >= B->n || !dst) return fail(BZ_EINVAL, "invalid argument");
     bz_handle *h = B->inst[i];
+    BZ_TRY(batch_correct_in_place(B, i, (cudaStream_t)stream));
     BZ_CUDA(cudaMemcpyAsync(dst, h->h[B->step[i] & 1], h->esz * (size_t)h->g.nr * h->g.nvt,
                             cudaMemcpyDefault, (cudaStream_t)stream));
     if (step) *step = B->step[i];
@@ -1652,6 +1844,7 @@ bz_status bz_batch_moments(bz_batch *B, int32_t i, double *out, void *stream)
     bz_handle *h = B->inst[i];
     cudaStream_t s = (cudaStream_t)stream;
     const Geo &g = h->g;
+    BZ_TRY(batch_correct_in_place(B, i, s));
     bzk::k_moments<float><<<std::min(g.nr, h->nsm * 8), 256, 0, s>>>(
         g, (const float *)h->h[B->step[i] & 1], h->mom);
     BZ_CUDA(cudaGetLastError());
@@ -1665,33 +1858,63 @@ bz_status bz_batch_tune(bz_batch *B, int32_t trial_steps, void *stream, int32_t 
 {
     if (!B || trial_steps < 1) return fail(BZ_EINVAL, "invalid argument");
     cudaStream_t s = (cudaStream_t)stream;
-    struct Cand { int maxt, cps, strip; };
+    // Candidates: the persistent kernels (threads per CTA, CTAs per SM, strip
+    // width), then fan-out graphs of the instances' own steps (branches).
+    struct Cand { int mode, maxt, cps, strip, branches; };
     std::vector<Cand> cands;
     for (int maxt : {512, 1024})
         for (int cps : {1, 2})
             for (int strip : {4, 8, 16}) {
                 if (maxt == 1024 && cps == 2) continue;   // 64 registers x 2048 threads do not fit
-                cands.push_back({maxt, cps, strip});
+                cands.push_back({0, maxt, cps, strip, 0});
             }
+    if (B->fan_ok)
+        for (int nb : {1, 2, 4, 8}) cands.push_back({1, 0, 0, 0, nb});
     cudaEvent_t e0, e1;
     BZ_CUDA(cudaEventCreate(&e0));
     BZ_CUDA(cudaEventCreate(&e1));
     int best = -1;
     double best_ms = 1e300;
     for (size_t c = 0; c < cands.size(); ++c) {
+        const Cand &k = cands[c];
         double t = -1.0;
-        if (batch_apply(B, cands[c].maxt, cands[c].cps, cands[c].strip) == BZ_OK &&
-            batch_launch(B, s, false) == BZ_OK) {
-            cudaEventRecord(e0, s);
-            bool ok = true;
-            for (int k = 0; k < trial_steps && ok; ++k) ok = batch_launch(B, s, false) == BZ_OK;
-            cudaEventRecord(e1, s);
-            float f = 0.f;
-            if (ok && cudaEventSynchronize(e1) == cudaSuccess &&
-                cudaEventElapsedTime(&f, e0, e1) == cudaSuccess)
-                t = f / trial_steps;
+        if (k.mode == 0) {
+            if (batch_set_mode(B, 0, s) == BZ_OK &&
+                batch_apply(B, k.maxt, k.cps, k.strip) == BZ_OK && batch_launch(B, s, false) == BZ_OK) {
+                cudaEventRecord(e0, s);
+                bool ok = true;
+                for (int r = 0; r < trial_steps && ok; ++r) ok = batch_launch(B, s, false) == BZ_OK;
+                cudaEventRecord(e1, s);
+                float f = 0.f;
+                if (ok && cudaEventSynchronize(e1) == cudaSuccess &&
+                    cudaEventElapsedTime(&f, e0, e1) == cudaSuccess)
+                    t = f / trial_steps;
+            }
+        } else if (batch_set_mode(B, 1, s) == BZ_OK) {
+            // A graph of one repeatable (non-advancing) fan-out step.
+            assign_branches(B, k.branches);
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t ex = nullptr;
+            std::vector<long long> l0(B->n);
+            for (int i = 0; i < B->n; ++i) l0[i] = B->inst[i]->launches;
+            bool ok = cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            bz_status st = ok ? fan_launch(B, B->cap, false) : BZ_ECUDA;
+            ok = cudaStreamEndCapture(B->cap, &graph) == cudaSuccess && ok && st == BZ_OK;
+            for (int i = 0; i < B->n; ++i) B->inst[i]->launches = l0[i];
+            ok = ok && cudaGraphInstantiate(&ex, graph, 0) == cudaSuccess;
+            if (graph) cudaGraphDestroy(graph);
+            if (ok && cudaGraphLaunch(ex, s) == cudaSuccess) {
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < trial_steps && ok; ++r) ok = cudaGraphLaunch(ex, s) == cudaSuccess;
+                cudaEventRecord(e1, s);
+                float f = 0.f;
+                if (ok && cudaEventSynchronize(e1) == cudaSuccess &&
+                    cudaEventElapsedTime(&f, e0, e1) == cudaSuccess)
+                    t = f / trial_steps;
+            }
+            if (ex) cudaGraphExecDestroy(ex);
         }
-        if (ms && c < 12) ms[c] = t;
+        if (ms && c < 16) ms[c] = t;
         if (t > 0.0 && t < best_ms) {
             best_ms = t;
             best = (int)c;
@@ -1701,17 +1924,25 @@ bz_status bz_batch_tune(bz_batch *B, int32_t trial_steps, void *stream, int32_t 
     cudaEventDestroy(e1);
     if (ncand) *ncand = (int32_t)cands.size();
     if (best < 0) return fail(BZ_ECUDA, "no schedule could be timed");
-    BZ_TRY(batch_apply(B, cands[best].maxt, cands[best].cps, cands[best].strip));
+    const Cand &k = cands[best];
+    BZ_TRY(batch_set_mode(B, k.mode, s));
+    if (k.mode == 0) {
+        BZ_TRY(batch_apply(B, k.maxt, k.cps, k.strip));
+    } else {
+        assign_branches(B, k.branches);
+        drop_fan_graphs(B);
+    }
     if (choice) *choice = best;
     return BZ_OK;
 }
 
-bz_status bz_batch_schedule(const bz_batch *B, int32_t out[3])
+bz_status bz_batch_schedule(const bz_batch *B, int32_t out[4])
 {
     if (!B || !out) return fail(BZ_EINVAL, "invalid argument");
     out[0] = B->maxt;
     out[1] = B->grid;
     out[2] = B->strip;
+    out[3] = B->mode == 1 ? B->branches : 0;
     return BZ_OK;
 }
 

@@ -234,6 +234,16 @@ __global__ void k_lz_fb_plan(int nt, int N, const int *__restrict__ meta,
     if (u.w != 0xFFFF) atomicAdd(count + u.w, 1);
 }
 
+// Clears n floats when gate[1] is set (the pending corrections of a state
+// that the fallback corrected in place).
+__global__ void k_lz_clear(const int *__restrict__ gate, float *__restrict__ x, int64_t n)
+{
+    if (!gate[1]) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = 0.f;
+}
+
 // The correction of a stored node value: h = h_c + (1 + eps h_c) kappa.
 __device__ __forceinline__ float lz_corr(float hc, float kappa, float eps)
 {

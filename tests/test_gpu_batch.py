@@ -34,9 +34,15 @@ def _warm(p, seed):
     return workloads.warm_state(p, seed=seed).astype(np.float32)
 
 
-def test_batch_matches_single_instances_and_oracle():
+@pytest.mark.parametrize("mode", ["persistent", "fanout"])
+def test_batch_matches_single_instances_and_oracle(monkeypatch, mode):
+    """Both schedules: the persistent per-cell kernels over all instances,
+    and the fan-out graph of the instances' own active-node steps."""
+    if mode == "fanout":
+        monkeypatch.setenv("BZ_BATCH_MODE", "fanout")
     ps = _problems()
     b = binding.Batch(ps)
+    assert (b.schedule()["fanout_branches"] > 0) == (mode == "fanout")
     singles = []
     for i, p in enumerate(ps):
         h0 = _warm(p, 40 + i)
@@ -72,6 +78,8 @@ def test_tuner_keeps_state_and_graph_replay_is_exact(monkeypatch):
         assert st == 0 and bool((h == before[i]).all())
     sched = b.schedule()
     assert sched["threads"] in (512, 1024) and sched["strip"] in (4, 8, 16)
+    assert sched["fanout_branches"] in (0, 1, 2, 4, 8)
+    assert len(ms) == 13                 # 9 persistent schedules + 4 fan-out widths
     b.step(4)
     monkeypatch.setenv("BZ_GRAPH", "0")
     c = binding.Batch(ps)
