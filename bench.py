@@ -90,20 +90,23 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(files):
+    """Hash of the device-code headers a kernel is compiled from."""
     h = hashlib.sha256()
     src = os.path.join(ROOT, "paper_1005_5405_gb300", "csrc")
-    for f in sorted(os.listdir(src)):
+    for f in files:
         with open(os.path.join(src, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-# The per-cell kernel a handle runs (bz_info.kernel_variant) and the ncu
-# summary of its 64x64-cell profiling case.
-CELL_KERNELS = {0: ("k_cell<fused>", None),
-                1: ("k_cell4<fused>", "k_cell_fused_cavity64_v32.md"),
-                2: ("k_lz", "k_lz_cavity64_v32.md")}
+# The per-cell kernel a handle runs (bz_info.kernel_variant), the ncu summary
+# of its 64x64-cell profiling case, and the headers its device code lives in.
+CELL_KERNELS = {0: ("k_cell<fused>", None, ()),
+                1: ("k_cell4<fused>", "k_cell_fused_cavity64_v32.md",
+                    ("bz_kernels.cuh", "bz_cell4.cuh")),
+                2: ("k_lz", "k_lz_cavity64_v32.md",
+                    ("bz_kernels.cuh", "bz_cell4.cuh", "bz_lazy.cuh"))}
 
 
 def profiled_traffic(nr, variant):
@@ -111,7 +114,7 @@ def profiled_traffic(nr, variant):
     summary of the 64x64-cell case scaled to `nr` cells (its traffic is
     proportional to the cells processed: 8 B per node).  None when the summary
     is absent or the kernel source has changed since it was taken."""
-    name = CELL_KERNELS.get(variant, (None, None))[1]
+    _, name, files = CELL_KERNELS.get(variant, (None, None, ()))
     if name is None:
         return None
     path = os.path.join(ROOT, "profiles", name)
@@ -122,7 +125,7 @@ def profiled_traffic(nr, variant):
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip().split()[0] if v.strip() else ""
-    if vals.get("source_hash") != kernel_source_hash():
+    if vals.get("source_hash") != kernel_source_hash(files):
         return None
     try:
         return float(vals["dram_bytes_per_cell"]) * nr
@@ -356,7 +359,7 @@ def run_ours(args):
                                 "cell": cell_ms},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(p.nr, variant),
-                     "kernel": CELL_KERNELS.get(variant, ("?", None))[0],
+                     "kernel": CELL_KERNELS.get(variant, ("?", None, ()))[0],
                      "algorithmic_bytes": alg_bytes, "peak_source": peak_src,
                      "step_frac": (step_bytes / (ms_max / args.steps / 1e3) / 1e9) / peak},
         "streaming": {
