@@ -118,14 +118,14 @@ struct bz_handle {
     bool lazy_buf[2] = {false, false};
     int4 *lz_idx = nullptr;
     bzk::PlanA<float, int> *lz_pa = nullptr;
-    bzk::PlanA<float, uint16_t> *lz_pc = nullptr;
     ushort4 *lz_qc = nullptr;
     int *lz_flag = nullptr, *lz_cidx = nullptr, *lz_act = nullptr, *lz_wpre = nullptr;
-    int *lz_meta = nullptr, *lz_count = nullptr, *lz_cursor = nullptr;
-    uint32_t *lz_mask = nullptr, *lz_ent = nullptr;
-    int lz_mcap = 0, lz_G = 0, lz_L = 0, lz_nchunk = 0, lz_T = 0, lz_grid = 0, lz_mprobe = 0;
+    int *lz_meta = nullptr, *lz_count = nullptr, *lz_cursor = nullptr, *lz_rowend = nullptr;
+    int *lz_dest0 = nullptr;
+    uint32_t *lz_mask = nullptr;
+    uint2 *lz_rec = nullptr;
+    int lz_mcap = 0, lz_G = 0, lz_T = 0, lz_grid = 0, lz_mprobe = 0;
     size_t lz_smem = 0;
-    bzk::Map4 lz_map{};
     float lz_e0[bzk::kLzX] = {};
 };
 
@@ -395,20 +395,22 @@ void launch_lz_kernel(bz_handle *H, const bzk::LzArgs &a, cudaStream_t s)
     }
 }
 
-// Decide whether the active-node path applies (FP32 fast path, 16-bit node
-// indices) and size it: the number of active nodes is measured on the sample
-// sets of the first steps (it depends on the grid and the sample count only,
-// not on the state), the compact arrays get a margin above it, and the
-// per-sample chunk fills the rest of half an SM's shared memory.  Needs the
-// per-axis tables on the device.
+// Decide whether the active-node path applies (FP32 fast path, at most 32
+// nodes per axis) and size it: the number of active nodes is measured on the
+// sample sets of the first steps (it depends on the grid and the sample count
+// only, not on the state) and the compact arrays get a margin above it.  The
+// largest group of cells per CTA (4, else 2) whose shared memory fits is
+// taken.  Needs the per-axis tables on the device.
 bz_status configure_lazy(bz_handle *H)
 {
     H->lazy = false;
     const Geo &g = H->g;
     const char *force = getenv("BZ_KERNEL");
     if (force && (strcmp(force, "generic") == 0 || strcmp(force, "cell4") == 0)) return BZ_OK;
-    if (!H->fast || g.nvt >= 65536 || g.nvt % 32 != 0) return BZ_OK;
+    if (!H->fast || g.nv > bzk::kLzMaxN || g.nv % 4 != 0 || g.nvt % 32 != 0) return BZ_OK;
     const int N = g.nv, nvt = g.nvt, nt = g.nt;
+    const int P4 = bzk::lz_planes4(N);
+    if (P4 == 0) return BZ_OK;
     const size_t mub = sizeof(float) * 8 * (size_t)g.nr;
     BZ_TRY(dalloc(&H->mu[0], mub));
     BZ_TRY(dalloc(&H->mu[1], mub));
@@ -416,16 +418,15 @@ bz_status configure_lazy(bz_handle *H)
     BZ_CUDA(cudaMemset(H->mu[1], 0, mub));
     BZ_TRY(dalloc(&H->lz_idx, sizeof(int4) * (size_t)nt));
     BZ_TRY(dalloc(&H->lz_pa, sizeof(bzk::PlanA<float, int>) * (size_t)nt));
-    BZ_TRY(dalloc(&H->lz_pc, sizeof(bzk::PlanA<float, uint16_t>) * (size_t)nt));
     BZ_TRY(dalloc(&H->lz_qc, sizeof(ushort4) * (size_t)nt));
     BZ_TRY(dalloc(&H->lz_flag, sizeof(int) * nvt));
     BZ_TRY(dalloc(&H->lz_cidx, sizeof(int) * nvt));
     BZ_TRY(dalloc(&H->lz_act, sizeof(int) * nvt));
     BZ_TRY(dalloc(&H->lz_mask, sizeof(uint32_t) * (nvt / 32)));
     BZ_TRY(dalloc(&H->lz_wpre, sizeof(int) * (nvt / 32)));
-    BZ_TRY(dalloc(&H->lz_meta, sizeof(int) * bzk::lz_meta_size(bzk::kLzMaxChunks)));
+    BZ_TRY(dalloc(&H->lz_meta, sizeof(int) * bzk::kLzMetaSize));
     BZ_CUDA(cudaMemset(H->lz_flag, 0, sizeof(int) * nvt));
-    BZ_CUDA(cudaMemset(H->lz_meta, 0, sizeof(int) * bzk::lz_meta_size(bzk::kLzMaxChunks)));
+    BZ_CUDA(cudaMemset(H->lz_meta, 0, sizeof(int) * bzk::kLzMetaSize));
 
     // Active nodes of the sample sets of steps 0..3.
     int64_t *dstep = nullptr;
@@ -451,50 +452,37 @@ bz_status configure_lazy(bz_handle *H)
     H->lz_mprobe = mmax;
     // The count varies little from step to step (it is a sum of many nearly
     // independent node hits); a step above the capacity runs the fallback.
-    int mcap = std::min(nvt, (mmax + mmax / 10 + 64 + 31) / 32 * 32);
+    int mcap = std::min(nvt, (mmax + mmax / 20 + 64 + 31) / 32 * 32);
     if (const char *mc = getenv("BZ_LAZY_MCAP")) mcap = std::max(1, std::min(nvt, atoi(mc)));
 
-    // Threads: node pairs along jz, 512 threads at most; a streaming stage
-    // holds K jx-planes.
-    const int Q = N * N / 2;
-    if (Q > 512) return BZ_OK;
-    const int K = bzk::lz_planes(N);
-    H->lz_map = bzk::Map4{Q, K, N / K};
-    H->lz_T = (Q * K + 31) / 32 * 32;
-    int smem_sm = 0;
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, H->dev);
-    const size_t budget = std::min((size_t)H->smem_optin, (size_t)smem_sm / 2 - 1024);
-    const size_t ring = bzk::lz_region_bytes(H->lz_T, 1, 0);
+    // One CTA of two 256-thread roles per SM; the largest group of cells
+    // whose shared memory fits.
+    H->lz_T = bzk::kLzThreads;
     bool ok = false;
-    for (int G : {2, 1}) {
-        const size_t fixed = bzk::lz_fixed_bytes(N, nvt, mcap, G);
-        if (fixed + ring > budget) continue;
-        const size_t avail = budget - fixed;
-        const int Lmax = (int)std::min<size_t>(avail / (sizeof(float) * G), 32768);
-        const int nchunk = (nt + Lmax - 1) / Lmax;
-        if (nchunk > bzk::kLzMaxChunks) continue;
-        const int L = (nt + nchunk - 1) / nchunk;
-        const size_t smem = fixed + bzk::lz_region_bytes(H->lz_T, G, L);
+    for (int G : {4, 2}) {
+        // Term records address a compact array with 16-bit byte offsets.
+        if ((size_t)mcap * 4 * G > 65535) continue;
+        const size_t smem = bzk::lz_offsets(nvt, mcap, G).end;
+        if (smem > (size_t)H->smem_optin) continue;
         int occ = 0;
-        if (G == 2) BZ_TRY(setup_lz_kernel<2>(H, smem, &occ));
-        else BZ_TRY(setup_lz_kernel<1>(H, smem, &occ));
+        if (G == 4) BZ_TRY(setup_lz_kernel<4>(H, smem, &occ));
+        else BZ_TRY(setup_lz_kernel<2>(H, smem, &occ));
         if (occ < 1) continue;
         H->lz_G = G;
-        H->lz_L = L;
-        H->lz_nchunk = nchunk;
         H->lz_smem = smem;
-        int per_sm = occ;
-        if (const char *c = getenv("BZ_LAZY_CTAS")) per_sm = std::max(1, std::min(occ, atoi(c)));
-        H->lz_grid = std::min((g.nr + G - 1) / G, H->nsm * per_sm);
+        H->lz_grid = std::min((g.nr + G - 1) / G, H->nsm);
+        if (const char *c = getenv("BZ_LAZY_CTAS")) H->lz_grid = std::max(1, std::min(H->lz_grid, atoi(c)));
         ok = true;
         break;
     }
     if (!ok) return BZ_OK;
     H->lz_mcap = mcap;
-    BZ_TRY(dalloc(&H->lz_count, sizeof(int) * (size_t)H->lz_nchunk * nvt));
-    BZ_TRY(dalloc(&H->lz_cursor, sizeof(int) * (size_t)H->lz_nchunk * nvt));
-    BZ_TRY(dalloc(&H->lz_ent, sizeof(uint32_t) * ((size_t)4 * nt + (size_t)H->lz_nchunk * H->lz_T)));
-    BZ_CUDA(cudaMemset(H->lz_count, 0, sizeof(int) * (size_t)H->lz_nchunk * nvt));
+    BZ_TRY(dalloc(&H->lz_count, sizeof(int) * (size_t)nvt));
+    BZ_TRY(dalloc(&H->lz_cursor, sizeof(int) * (size_t)nvt));
+    BZ_TRY(dalloc(&H->lz_rowend, sizeof(int) * (size_t)nvt));
+    BZ_TRY(dalloc(&H->lz_dest0, sizeof(int) * (size_t)bzk::kLzRoleT));
+    BZ_TRY(dalloc(&H->lz_rec, sizeof(uint2) * ((size_t)4 * nt + (size_t)8 * bzk::kLzRoleT)));
+    BZ_CUDA(cudaMemset(H->lz_count, 0, sizeof(int) * (size_t)nvt));
     // Equilibrium sums of the 30 monomials (the moments of h^{n+1} need them).
     std::vector<double> axv(N), axA(N);
     BZ_CUDA(cudaMemcpy(axv.data(), g.axv, sizeof(double) * N, cudaMemcpyDeviceToHost));
@@ -540,39 +528,36 @@ bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true)
         bzk::k_lz_scan<<<1, 1024, 0, s>>>(g.nvt, H->lz_mcap, H->lz_flag, H->lz_cidx, H->lz_act,
                                           H->lz_mask, H->lz_wpre, H->lz_meta, H->stats);
         BZ_LAUNCHED(H);
-        bzk::k_lz_remap<<<pg, pb, 0, s>>>(g.nt, H->lz_L, H->lz_idx, H->lz_pa, H->lz_cidx,
-                                          H->lz_meta, H->lz_pc, H->lz_qc, H->lz_count);
+        bzk::k_lz_remap<<<pg, pb, 0, s>>>(g.nt, H->lz_idx, H->lz_cidx, H->lz_qc, H->lz_count);
         BZ_LAUNCHED(H);
-        bzk::k_lz_lscan<<<1, 1024, 0, s>>>(H->lz_nchunk, H->lz_T, H->lz_count, H->lz_cursor,
-                                           H->lz_meta);
+        bzk::k_lz_lscan<<<1, 1024, 0, s>>>(bzk::kLzRoleT, H->lz_count, H->lz_cursor, H->lz_rowend,
+                                           H->lz_meta, H->lz_rec, H->lz_dest0);
         BZ_LAUNCHED(H);
-        bzk::k_lz_lfill<<<pg, pb, 0, s>>>(g.nt, H->lz_L, H->lz_nchunk, H->lz_T, H->lz_qc,
-                                          H->lz_cursor, H->lz_meta, H->lz_ent);
+        bzk::k_lz_lfill<<<pg, pb, 0, s>>>(g.nt, bzk::kLzRoleT, H->lz_G == 4 ? 4 : 3, H->lz_qc, H->lz_pa,
+                                          H->lz_cursor, H->lz_rowend, H->lz_meta, H->lz_rec,
+                                          H->lz_dest0);
         BZ_LAUNCHED(H);
     }
     {
         ProfScope ps(H, 2, s);
         bzk::LzArgs a{};
-        a.m = H->lz_map;
         a.hin = hin;
         a.mu_in = H->mu[in];
         a.ghost = (const float *)H->ghost;
         a.hout = hout;
         a.mu_out = H->mu[out];
         a.mom = H->mom;
-        a.pc = H->lz_pc;
-        a.ent = H->lz_ent;
+        a.rec = H->lz_rec;
+        a.dest0 = H->lz_dest0;
         a.meta = H->lz_meta;
         a.mask = H->lz_mask;
         a.wpre = H->lz_wpre;
         a.act = H->lz_act;
         a.mcap = H->lz_mcap;
-        a.L = H->lz_L;
-        a.nchunk = H->lz_nchunk;
         for (int k = 0; k < bzk::kLzX; ++k) a.e0[k] = H->lz_e0[k];
         a.clk = H->prof_clk;
-        if (H->lz_G == 2) launch_lz_kernel<2>(H, a, s);
-        else launch_lz_kernel<1>(H, a, s);
+        if (H->lz_G == 4) launch_lz_kernel<4>(H, a, s);
+        else launch_lz_kernel<2>(H, a, s);
         BZ_LAUNCHED(H);
     }
     {
@@ -790,9 +775,9 @@ void release(bz_handle *H)
     void *st[] = {H->axe, H->axd, H->wlid, H->sx, H->sy};
     for (void *p : st)
         if (p) cudaFree(p);
-    void *lz[] = {H->mu[0], H->mu[1], H->lz_idx, H->lz_pa, H->lz_pc, H->lz_qc, H->lz_flag,
-                  H->lz_cidx, H->lz_act, H->lz_wpre, H->lz_meta, H->lz_count, H->lz_cursor,
-                  H->lz_mask, H->lz_ent};
+    void *lz[] = {H->mu[0], H->mu[1], H->lz_idx, H->lz_pa, H->lz_qc, H->lz_flag, H->lz_cidx,
+                  H->lz_act, H->lz_wpre, H->lz_meta, H->lz_count, H->lz_cursor, H->lz_rowend,
+                  H->lz_dest0, H->lz_mask, H->lz_rec};
     for (void *p : lz)
         if (p) cudaFree(p);
     bz_adj_release(&H->adj);

@@ -8,8 +8,8 @@
 //   shared samples maps to (v, v1, v*, v1*): for Maxwellian draws a small
 //   fraction of the grid (about 7% of 32^3 at 2x10^4 samples).  Every other
 //   node keeps h_c = h~.  The per-step plan lists those "active" nodes once
-//   (compact index m), and the per-cell gather and scatter work on arrays of
-//   M entries instead of the whole velocity slab.
+//   (compact index m), and the collision terms of every cell work on arrays
+//   of M entries instead of the whole velocity slab.
 // * The correction h^{n+1} = h_c + (1 + eps h_c)(mu . psi) needs mu, which
 //   needs the moments of every node.  Instead of holding the whole slab until
 //   mu is known, the step stores h_c and the cell's mu; whoever reads the
@@ -17,10 +17,17 @@
 //   the correction on the fly.  The state is therefore the pair (h_c, mu);
 //   mu = 0 is an ordinary state.
 //
-// Without the slab a CTA needs two small compact arrays and a chunk of the
-// per-sample products, so two CTAs share an SM and each works on G cells at
-// once (the G values of a node are adjacent, so one vector access serves all
-// G cells and each sample is read from L2 once per G cells).
+// Without the slab a CTA needs two compact arrays, so two CTAs share an SM
+// and each works on G cells at once: the G values of a node are adjacent, so
+// one vector access serves all G cells and every collision term is decoded
+// once per G cells.
+//
+// The collision terms are applied as a pull: the plan sorts the terms
+// (destination, sample, sign) by destination and gives each thread a run of
+// them; a term carries the byte offsets of the sample's two pre-collision
+// nodes and its signed weight, so the thread recomputes the sample's product
+// from h~ and sums a destination's terms in registers.  Floating-point
+// arithmetic on node pairs uses the packed FP32x2 instructions.
 //
 // The conserved-moment sums of N_c and the output moments come from 26
 // monomial sums (degree <= 4) of N = w h~ over all nodes, taken while
@@ -33,17 +40,30 @@
 
 namespace bzk {
 
-constexpr int kLzMaxChunks = 16;
 constexpr int kLzMono = 26;        // monomial sums per cell
 constexpr int kLzX = 30;           // with v^2, v_x v^2, v_y v^2, v_z v^2
+constexpr int kLzRoleT = 256;      // threads of each role: streaming, collision
+constexpr int kLzThreads = 2 * kLzRoleT;
+constexpr int kLzRoleWarps = kLzRoleT / 32;
+constexpr int kLzMaxG = 4;         // cells per CTA group
+constexpr int kLzMaxN = 32;        // velocity nodes per axis (N^2 / 4 <= kLzRoleT)
+constexpr int kLzStages = 4;       // streaming stages staged per thread
 
-// meta layout: [0] M, [1] overflow, [2 + k] S_k (k <= nchunk, start of chunk k
-// in the sorted order), [3 + nchunk + k] C_k (words per thread), [4 +
-// 2 nchunk + k] base_k (first word of chunk k in the list).
-__host__ __device__ constexpr int lz_meta_s(int k) { return 2 + k; }
-__host__ __device__ constexpr int lz_meta_c(int nchunk, int k) { return 3 + nchunk + k; }
-__host__ __device__ constexpr int lz_meta_b(int nchunk, int k) { return 4 + 2 * nchunk + k; }
-__host__ __device__ constexpr int lz_meta_size(int nchunk) { return 5 + 3 * nchunk; }
+// meta layout: [0] M, [1] overflow (M > mcap), [2] E (terms of the step),
+// [3] C (terms per thread).
+constexpr int kLzMetaSize = 4;
+
+// Planes per streaming stage: the largest divisor K of N/2 with K N^2/4 <=
+// kLzRoleT (one node quad per streaming thread; stages never straddle jx =
+// N/2, so the upwind x source is the same cell for the whole stage).  0:
+// unsupported.
+__host__ __device__ constexpr int lz_planes4(int N)
+{
+    int K = 0;
+    for (int k = 1; k <= N / 2; ++k)
+        if ((N / 2) % k == 0 && k * (N * N / 4) <= kLzRoleT) K = k;
+    return K;
+}
 
 // ---------------------------------------------------------------------
 // Per-step plan (once per step; every cell shares it)
@@ -113,11 +133,9 @@ __global__ void __launch_bounds__(1024) k_lz_scan(int nvt, int mcap, int *__rest
     }
 }
 
-// Compact sample records (a, b, W) and (a, b, a*, b*), and the per-(chunk,
-// destination) term counts of the scatter list.
-__global__ void k_lz_remap(int nt, int L, const int4 *__restrict__ idx,
-                           const PlanA<float, int> *__restrict__ pa, const int *__restrict__ cidx,
-                           const int *__restrict__ meta, PlanA<float, uint16_t> *__restrict__ pc,
+// Compact node indices (a, b, a*, b*) of every sample, and the number of
+// terms per destination.
+__global__ void k_lz_remap(int nt, const int4 *__restrict__ idx, const int *__restrict__ cidx,
                            ushort4 *__restrict__ qc, int *__restrict__ count)
 {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
@@ -125,22 +143,24 @@ __global__ void k_lz_remap(int nt, int L, const int4 *__restrict__ idx,
     const int4 q = idx[l];
     const int d[4] = {q.x >= 0 ? cidx[q.x] : -1, q.y >= 0 ? cidx[q.y] : -1,
                       q.z >= 0 ? cidx[q.z] : -1, q.w >= 0 ? cidx[q.w] : -1};
-    pc[l] = make_plan_a<float, uint16_t>(d[0], d[1], (double)pa[l].W);
     qc[l] = Idx4<uint16_t>::make(d);
-    const int M = meta[0], k = l / L;
 #pragma unroll
     for (int r = 0; r < 4; ++r)
-        if (d[r] >= 0) atomicAdd(count + k * M + d[r], 1);
+        if (d[r] >= 0) atomicAdd(count + d[r], 1);
 }
 
-// Exclusive scan of the counts over (chunk, destination) and the per-chunk
-// layout of the list for T threads; clears the counts.
-__global__ void __launch_bounds__(1024) k_lz_lscan(int nchunk, int T, int *__restrict__ count,
-                                                  int *__restrict__ cursor, int *__restrict__ meta)
+// Exclusive scan of the term counts over the M destinations (cursor = first
+// position of each destination's terms in the sorted order, rowend = one past
+// its last), the number of terms E and the run length C of each of the
+// kernel's T threads; clears the counts.  One CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) k_lz_lscan(int T, int *__restrict__ count,
+                                                  int *__restrict__ cursor, int *__restrict__ rowend,
+                                                  int *__restrict__ meta, uint2 *__restrict__ rec,
+                                                  int *__restrict__ dest0)
 {
     __shared__ int part[1024];
-    const int t = threadIdx.x, n = nchunk * meta[0], per = (n + 1023) / 1024;
-    const int b = min(n, t * per), e = min(n, b + per);
+    const int t = threadIdx.x, M = meta[0], per = (M + 1023) / 1024;
+    const int b = min(M, t * per), e = min(M, b + per);
     int s = 0;
     for (int i = b; i < e; ++i) s += count[i];
     part[t] = s;
@@ -155,48 +175,56 @@ __global__ void __launch_bounds__(1024) k_lz_lscan(int nchunk, int T, int *__res
     for (int i = b; i < e; ++i) {
         cursor[i] = run;
         run += count[i];
+        rowend[i] = run;
         count[i] = 0;
     }
-    __syncthreads();
-    if (t == 0) {
-        const int M = meta[0];
-        int base = 0;
-        for (int k = 0; k <= nchunk; ++k) {
-            const int key = k * M;
-            const int S = k == nchunk ? part[1023] : (key < n ? cursor[key] : part[1023]);
-            meta[lz_meta_s(k)] = S;
-        }
-        for (int k = 0; k < nchunk; ++k) {
-            const int E = meta[lz_meta_s(k + 1)] - meta[lz_meta_s(k)];
-            const int C = (E + T - 1) / T;
-            meta[lz_meta_c(nchunk, k)] = C;
-            meta[lz_meta_b(nchunk, k)] = base;
-            base += C * T;
-        }
+    // Runs of C terms, C a multiple of 8; the positions past the last term
+    // hold zero records (weight 0, no destination change) and every run
+    // starts at the zero entry M until k_lz_lfill names its first term.
+    const int E = part[1023], C = ((E + T - 1) / T + 7) / 8 * 8;
+    if (t == 1023) {
+        meta[2] = E;
+        meta[3] = C;
     }
+    for (int p = E + t; p < C * T; p += 1024) {
+        const int tt = p / C, i = p - tt * C;
+        rec[(int64_t)i * T + tt] = make_uint2(0u, 0u);
+    }
+    for (int tt = t; tt < T; tt += 1024) dest0[tt] = M;
 }
 
-// Scatter list: every (destination, sample, sign) term of chunk k as
-// m << 16 | loss << 15 | l' (l' the sample's index within its chunk), sorted
-// by m; thread tt's run of C_k words of the sorted order is stored at stride
-// T from base_k, so that the threads' i-th words are adjacent.
-__global__ void k_lz_lfill(int nt, int L, int nchunk, int T, const ushort4 *__restrict__ qc,
-                           int *__restrict__ cursor, const int *__restrict__ meta,
-                           uint32_t *__restrict__ ent)
+// The term records, sorted by destination: position p of the sorted order
+// goes to thread p / C, slot i = p mod C, stored at rec[i T + p / C] so that
+// the threads' i-th records are adjacent.  A record is
+//   x = a_off | b_off << 16 | last,   y = +-W (bits of the float),
+// with a_off, b_off the byte offsets of the sample's pre-collision nodes in
+// the kernel's compact array (entries of 1 << osh bytes; a node outside the
+// grid points to the zero entry M), last set on the final term of a
+// destination, and the sign negative for the loss terms (the destination is
+// a or b).  dest0[tt] is the destination of thread tt's first term.
+// Nothing is written when the step overflowed (the kernel does not run then).
+__global__ void k_lz_lfill(int nt, int T, int osh, const ushort4 *__restrict__ qc,
+                           const PlanA<float, int> *__restrict__ pa, int *__restrict__ cursor,
+                           const int *__restrict__ rowend, const int *__restrict__ meta,
+                           uint2 *__restrict__ rec, int *__restrict__ dest0)
 {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= nt) return;
-    const int M = meta[0], k = l / L, lp = l - k * L;
-    const int S = meta[lz_meta_s(k)], C = meta[lz_meta_c(nchunk, k)];
-    const int base = meta[lz_meta_b(nchunk, k)];
+    if (l >= nt || meta[1]) return;
+    const int M = meta[0], C = meta[3];
     const ushort4 q = qc[l];
-    const unsigned short d[4] = {q.x, q.y, q.z, q.w};
+    const int d[4] = {idx_of(q.x), idx_of(q.y), idx_of(q.z), idx_of(q.w)};
+    const uint32_t ao = (uint32_t)(d[0] >= 0 ? d[0] : M) << osh;
+    const uint32_t bo = (uint32_t)(d[1] >= 0 ? d[1] : M) << osh;
+    const uint32_t x = ao | (bo << 16);
+    const float W = pa[l].W;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-        if (d[r] == 0xFFFF) continue;
-        const int pos = atomicAdd(cursor + k * M + d[r], 1) - S;
+        if (d[r] < 0) continue;
+        const int pos = atomicAdd(cursor + d[r], 1);
         const int tt = pos / C, i = pos - tt * C;
-        ent[base + (int64_t)i * T + tt] = ((uint32_t)d[r] << 16) | (r < 2 ? 0x8000u : 0u) | (uint32_t)lp;
+        const uint32_t last = pos == rowend[d[r]] - 1 ? 1u : 0u;
+        rec[(int64_t)i * T + tt] = make_uint2(x | last, __float_as_uint(r < 2 ? -W : W));
+        if (i == 0) dest0[tt] = d[r];
     }
 }
 
@@ -293,35 +321,34 @@ __global__ void k_lz_materialize(Geo g, const int *__restrict__ skip_unless,
 }
 
 // ---------------------------------------------------------------------
-// The per-cell kernel
+// Packed FP32x2 arithmetic (each component rounds like fmaf / __fadd_rn).
 // ---------------------------------------------------------------------
+__device__ __forceinline__ float2 lz_add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 lz_mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 lz_fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 lz_dup(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 lz_lo(float4 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ float2 lz_hi(float4 a) { return make_float2(a.z, a.w); }
 
+// Values of a node in the G cells of a group (adjacent in shared memory).
 template <int G> struct LzVec;
-template <> struct LzVec<1> { using T = float; };
 template <> struct LzVec<2> { using T = float2; };
+template <> struct LzVec<4> { using T = float4; };
 
-__device__ __forceinline__ float lz_get(float a, int) { return a; }
-__device__ __forceinline__ float lz_get(float2 a, int g) { return g ? a.y : a.x; }
-__device__ __forceinline__ float lz_axpy(float s, float a, float b) { return fmaf(s, a, b); }
-__device__ __forceinline__ float2 lz_axpy(float s, float2 a, float2 b)
+__device__ __forceinline__ float2 lz_zero2() { return make_float2(0.f, 0.f); }
+__device__ __forceinline__ void lz_set_zero(float2 &a) { a = lz_zero2(); }
+__device__ __forceinline__ void lz_set_zero(float4 &a) { a = make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ void lz_atomic_add(float2 *p, float2 v)
 {
-    return make_float2(fmaf(s, a.x, b.x), fmaf(s, a.y, b.y));
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
 }
-__device__ __forceinline__ float lz_gw(float W, float a, float b, float e)
+__device__ __forceinline__ void lz_atomic_add(float4 *p, float4 v)
 {
-    return W * (a + b + e * a * b);
-}
-__device__ __forceinline__ float2 lz_gw(float W, float2 a, float2 b, float e)
-{
-    return make_float2(W * (a.x + b.x + e * a.x * b.x), W * (a.y + b.y + e * a.y * b.y));
-}
-template <typename V> __device__ __forceinline__ V lz_zero();
-template <> __device__ __forceinline__ float lz_zero<float>() { return 0.f; }
-template <> __device__ __forceinline__ float2 lz_zero<float2>() { return make_float2(0.f, 0.f); }
-__device__ __forceinline__ float lz_shfl_up(float v, int o) { return __shfl_up_sync(0xFFFFFFFFu, v, o); }
-__device__ __forceinline__ float2 lz_shfl_up(float2 v, int o)
-{
-    return make_float2(__shfl_up_sync(0xFFFFFFFFu, v.x, o), __shfl_up_sync(0xFFFFFFFFu, v.y, o));
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+    atomicAdd(&p->z, v.z);
+    atomicAdd(&p->w, v.w);
 }
 
 // ---------------------------------------------------------------------
@@ -330,93 +357,75 @@ __device__ __forceinline__ float2 lz_shfl_up(float2 v, int o)
 // values of its own nodes several streaming stages ahead, with no register
 // cost and no synchronisation with other threads.
 // ---------------------------------------------------------------------
-constexpr int kLzStages = 3;       // stages in flight per thread
-
 __device__ __forceinline__ uint32_t lz_saddr(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ void lz_cp8(void *dst, const void *src)
+__device__ __forceinline__ void lz_cp16(void *dst, const void *src)
 {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(lz_saddr(dst)), "l"(src)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(lz_saddr(dst)), "l"(src)
                  : "memory");
 }
 __device__ __forceinline__ void lz_cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void lz_cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ void lz_cp_wait_stage()
 {
     asm volatile("cp.async.wait_group %0;" ::"n"(kLzStages - 1) : "memory");
 }
-__device__ __forceinline__ void lz_cp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // Everything the kernel needs besides the geometry (by value).
 struct LzArgs {
-    Map4 m;                 // node-pair mapping: Q pairs per jx-plane, K planes per
-                            // stage (thread t works on plane t / Q of each stage),
-                            // J = N / K stages per cell
     const float *hin, *mu_in, *ghost;
     float *hout, *mu_out;
     double *mom;
-    const PlanA<float, uint16_t> *pc;
-    const uint32_t *ent;
+    const uint2 *rec;       // term records (k_lz_lfill)
+    const int *dest0;       // first destination of each thread's run
     const int *meta;
     const uint32_t *mask;
     const int *wpre, *act;
-    int mcap, L, nchunk;
+    int mcap;
     float e0[kLzX];         // sum_j w_j X_k(v_j) of the 30 monomials
     long long *clk;         // nullable: phase trace of CTA 0 (kClkCells groups x kClkPhases)
 };
 
-constexpr int kLzMaxWarps = 16;    // the kernel runs at most 512 threads
-
-// Shared memory.  A fixed-layout head (compile-time offsets, so the kernel
-// keeps no pointers to it in registers): reduction scratch and per-cell sums,
-// per-axis tables, the correction tables of the five cells a cell's
-// streaming reads, the stage barriers.  Then, at run-time offsets: the
-// active-node bit mask and word prefixes, the compact arrays (h~ and the
-// collision increment, G values per node), and one region used first as the
-// per-thread staging slots of the streaming prefetch (kLzStages stages x
-// {own, x source, y source} x threads, 8 bytes each) and then as the chunk of
-// per-sample products.
+// Shared memory.  A fixed-layout head (compile-time offsets): warp partial
+// sums, per-axis tables, the groups' cells and the correction tables of the
+// cells the streaming reads.  Then two compact arrays of h~ (G values per
+// active node plus a zero entry; the streaming warps fill one while the
+// collision warps use the other), the compact array of collision
+// increments, the per-thread staging slots of the streaming prefetch
+// (kLzStages stages x {own, x source, y source} x streaming threads, 16 bytes
+// each), the active-node bit mask, its word prefixes and the node list.
 struct LzHead {
-    float red[kLzMaxWarps * 32];
-    float tot[64];
-    float F[4 * 32], D[4 * 32];       // fill sums and increment sums per cell
-    float v[kMaxN], A[kMaxN], IA[kMaxN], cax[kMaxN], cuy[kMaxN];
-    float4 gram[kMaxN];               // v, v^2, v^3, v^4
-    float2 vz2[kMaxN / 2], Az2[kMaxN / 2];   // v and A of the node pairs along jz
-    float ca[5 * kMaxN];              // mu0 + mu_x v + mu_4 v^2 of the five cells
-    float mus[5 * 8];                 // mu of the five cells
+    float fpart[2][kLzMaxG][kLzRoleWarps][32];   // warp partials of the F sums, per group buffer
+    float dpart[kLzMaxG][kLzRoleWarps][32];      // warp partials of the D sums
+    float4 ta[kLzMaxN];                          // -ax, -ax, A, A
+    float4 tv12[kLzMaxN];                        // v, v, v^2, v^2
+    float4 tv34[kLzMaxN];                        // v^3, v^3, v^4, v^4
+    float v[kLzMaxN], A[kLzMaxN], IA[kLzMaxN], cuy[kLzMaxN];
+    float4 tcx[kLzMaxG][kLzMaxN];                // ca of the own and the upwind x cell, duplicated
+    float2 tcy[kLzMaxG][2][kLzMaxN];             // ca of the cell below (0) and above (1), duplicated
+    float mus[kLzMaxG][5][8];                    // mu of own, right, left, below, above (0 outside)
+    int4 cell[2][kLzMaxG];                       // c, ix, iy of a group's cells (c < 0: none), per buffer
 };
+constexpr uint32_t kLzAOff = (sizeof(LzHead) + 15) & ~(size_t)15;
 
-__host__ __device__ inline size_t lz_region_bytes(int T, int G, int L)
-{
-    const size_t ring = (size_t)kLzStages * 3 * T * sizeof(float2),
-                 chunk = sizeof(float) * (size_t)G * L;
-    return ring > chunk ? ring : chunk;
-}
-
-// Bytes before the region, and the run-time offsets.
 struct LzOff {
-    uint32_t mask, wpre, act, A, B, region;
+    uint32_t abytes, a1, bc, ring, mask, wpre, act, end;
 };
 __host__ __device__ inline LzOff lz_offsets(int nvt, int mcap, int G)
 {
     LzOff o;
-    size_t off = (sizeof(LzHead) + 15) & ~(size_t)15;
+    o.abytes = (uint32_t)(((sizeof(float) * (size_t)G * (mcap + 1)) + 127) & ~(size_t)127);
+    size_t off = kLzAOff + o.abytes;
+    o.a1 = (uint32_t)off; off += o.abytes;
+    o.bc = (uint32_t)off; off += o.abytes;
+    o.ring = (uint32_t)off; off += (size_t)kLzStages * 3 * kLzRoleT * sizeof(float4);
     o.mask = (uint32_t)off; off += sizeof(uint32_t) * (nvt / 32);
     o.wpre = (uint32_t)off; off += sizeof(uint16_t) * (nvt / 32);
     o.act = (uint32_t)off; off += sizeof(uint16_t) * (size_t)mcap;
-    off = (off + 15) & ~(size_t)15;
-    o.A = (uint32_t)off; off += sizeof(float) * (size_t)G * mcap;
-    o.B = (uint32_t)off; off += sizeof(float) * (size_t)G * mcap;
-    off = (off + 127) & ~(size_t)127;
-    o.region = (uint32_t)off;
+    o.end = (uint32_t)((off + 15) & ~(size_t)15);
     return o;
-}
-__host__ __device__ inline size_t lz_fixed_bytes(int nv, int nvt, int mcap, int G)
-{
-    (void)nv;
-    return lz_offsets(nvt, mcap, G).region;
 }
 
 // Monomial index of psi_a * phi_b in the 30-entry sum vector X (psi = 1,
@@ -426,17 +435,21 @@ __host__ __device__ inline size_t lz_fixed_bytes(int nv, int nvt, int mcap, int 
 // 14 v_x^2 v_z; 15 v_x v_y^2; 16 v_y^2 v_z; 17 v_x v_z^2; 18 v_y v_z^2;
 // 19 v_x v_y v_z; 20-22 v_x^2 v^2, v_y^2 v^2, v_z^2 v^2; 23-25 v_x v_y v^2,
 // v_x v_z v^2, v_y v_z v^2; 26 v^2; 27-29 v_x v^2, v_y v^2, v_z v^2.
-__device__ __constant__ const unsigned char kLzPsiPhi[5][10] = {
-    {0, 1, 2, 3, 4, 5, 6, 7, 8, 9},
-    {1, 4, 7, 8, 10, 15, 17, 13, 14, 19},
-    {2, 7, 5, 9, 13, 11, 18, 15, 19, 16},
-    {3, 8, 9, 6, 14, 16, 12, 19, 17, 18},
-    {26, 27, 28, 29, 20, 21, 22, 23, 24, 25}};
+__host__ __device__ constexpr int lz_psiphi(int a, int b)
+{
+    constexpr unsigned char t[5][10] = {
+        {0, 1, 2, 3, 4, 5, 6, 7, 8, 9},
+        {1, 4, 7, 8, 10, 15, 17, 13, 14, 19},
+        {2, 7, 5, 9, 13, 11, 18, 15, 19, 16},
+        {3, 8, 9, 6, 14, 16, 12, 19, 17, 18},
+        {26, 27, 28, 29, 20, 21, 22, 23, 24, 25}};
+    return t[a][b];
+}
 
 // The 26 monomial sums of sum_nodes n(v) from per-thread power sums over jx
 // (s[p] = sum n v_x^p) at fixed v_y = y, v_z = z.
 __device__ __forceinline__ void lz_mono_from_powers(const float (&s)[5], float y, float z,
-                                                    float (&M)[kLzMono])
+                                                    float (&M)[32])
 {
     const float y2 = y * y, z2 = z * z, q = y2 + z2, yz = y * z;
     M[0] += s[0];
@@ -469,16 +482,35 @@ __device__ __forceinline__ void lz_mono_from_powers(const float (&s)[5], float y
 }
 
 // The same sums for one node value d at velocity (x, y, z).
-__device__ __forceinline__ void lz_mono_node(float d, float x, float y, float z,
-                                             float (&M)[kLzMono])
+__device__ __forceinline__ void lz_mono_node(float d, float x, float y, float z, float (&M)[32])
 {
-    const float s[5] = {d, d * x, d * x * x, d * x * x * x, d * x * x * x * x};
+    const float x2 = x * x;
+    const float s[5] = {d, d * x, d * x2, d * x2 * x, d * x2 * x2};
     lz_mono_from_powers(s, y, z, M);
+}
+
+// Sum of 32 values over a warp, left with lane l holding the total of value l
+// (recursive halving: 31 shuffles instead of 32 x 5).
+__device__ __forceinline__ float lz_warp_reduce_scatter(float (&v)[32])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = up ? v[i] : v[i + o];
+            const float keep = up ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, o);
+        }
+    }
+    return v[0];
 }
 
 // X (30) from the 26 sums.
 __device__ __forceinline__ void lz_extend(const float *T, float *X)
 {
+#pragma unroll
     for (int k = 0; k < kLzMono; ++k) X[k] = T[k];
     X[26] = T[4] + T[5] + T[6];
     X[27] = T[10] + T[15] + T[17];
@@ -488,10 +520,11 @@ __device__ __forceinline__ void lz_extend(const float *T, float *X)
 
 // Correction and output moments of one cell from the sums F (of N = w h~)
 // and D (of the collision increment): mu to mu_out, moments to mom.
-__device__ __noinline__ void lz_finish(const Geo &g, const LzArgs &a, int c, const float *F,
+__device__ __forceinline__ void lz_finish(const Geo &g, const LzArgs &a, int c, const float *F,
                                        const float *D, int *fallback)
 {
     float T[kLzMono], X[kLzX], XF[kLzX];
+#pragma unroll
     for (int k = 0; k < kLzMono; ++k) T[k] = F[k] + D[k];
     lz_extend(T, X);
     lz_extend(F, XF);
@@ -519,10 +552,12 @@ __device__ __noinline__ void lz_finish(const Geo &g, const LzArgs &a, int c, con
     // Moments of h^{n+1}: sum w h phi = sum N_c phi + sum_a mu_a (E0 + eps sum N_c psi_a phi).
     const float eps = (float)g.eps;
     float m10[10];
+#pragma unroll
     for (int b = 0; b < 10; ++b) {
         float s = X[b];
+#pragma unroll
         for (int k = 0; k < 5; ++k) {
-            const int x = kLzPsiPhi[k][b];
+            const int x = lz_psiphi(k, b);
             s += mu[k] * (a.e0[x] + eps * X[x]);
         }
         m10[b] = s;
@@ -530,389 +565,596 @@ __device__ __noinline__ void lz_finish(const Geo &g, const LzArgs &a, int c, con
     if (a.mom) finalize_moments_f(m10, eps, a.mom + (int64_t)c * 11);
 }
 
-// Planes per streaming stage for node pairs and 512 threads: the largest
-// divisor K of N with K * N^2 / 2 <= 512.
-__host__ __device__ constexpr int lz_planes(int N)
+// The (v_y, v_z) part of a cell's pending correction at a thread's four
+// nodes (jy, 4 qz .. 4 qz + 3): mu_y v_y + mu_z v_z + mu_4 (v_y^2 + v_z^2), as
+// two node pairs.
+__device__ __forceinline__ void lz_bd(const float *mu, const float *v, int jy, int qz, float2 (&bd)[2])
 {
-    int K = 1;
-    for (int k = 1; k <= N; ++k)
-        if (N % k == 0 && k * (N * N / 2) <= 512) K = k;
-    return K;
+    const float vy = v[jy];
+    float b[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float vz = v[4 * qz + i];
+        b[i] = mu[2] * vy + mu[3] * vz + mu[4] * (vy * vy + vz * vz);
+    }
+    bd[0] = make_float2(b[0], b[1]);
+    bd[1] = make_float2(b[2], b[3]);
 }
 
+// lz_mono_from_powers for two cells at once (s and M hold one value per
+// cell; y and z are the node's, shared by both).
+__device__ __forceinline__ void lz_mono_from_powers2(const float2 (&s)[5], float y, float z,
+                                                     float2 (&M)[32])
+{
+    const float y2 = y * y, z2 = z * z, q = y2 + z2, yz = y * z;
+    const float2 Y = lz_dup(y), Z = lz_dup(z), Y2 = lz_dup(y2), Z2 = lz_dup(z2), YZ = lz_dup(yz);
+    M[0] = lz_add2(M[0], s[0]);
+    M[1] = lz_add2(M[1], s[1]);
+    M[2] = lz_fma2(Y, s[0], M[2]);
+    M[3] = lz_fma2(Z, s[0], M[3]);
+    M[4] = lz_add2(M[4], s[2]);
+    M[5] = lz_fma2(Y2, s[0], M[5]);
+    M[6] = lz_fma2(Z2, s[0], M[6]);
+    M[7] = lz_fma2(Y, s[1], M[7]);
+    M[8] = lz_fma2(Z, s[1], M[8]);
+    M[9] = lz_fma2(YZ, s[0], M[9]);
+    M[10] = lz_add2(M[10], s[3]);
+    M[11] = lz_fma2(lz_dup(y2 * y), s[0], M[11]);
+    M[12] = lz_fma2(lz_dup(z2 * z), s[0], M[12]);
+    M[13] = lz_fma2(Y, s[2], M[13]);
+    M[14] = lz_fma2(Z, s[2], M[14]);
+    M[15] = lz_fma2(Y2, s[1], M[15]);
+    M[16] = lz_fma2(lz_dup(y2 * z), s[0], M[16]);
+    M[17] = lz_fma2(Z2, s[1], M[17]);
+    M[18] = lz_fma2(lz_dup(y * z2), s[0], M[18]);
+    M[19] = lz_fma2(YZ, s[1], M[19]);
+    const float2 Q = lz_dup(q);
+    const float2 t2 = lz_fma2(Q, s[0], s[2]), t3 = lz_fma2(Q, s[1], s[3]);
+    M[20] = lz_add2(M[20], lz_fma2(Q, s[2], s[4]));
+    M[21] = lz_fma2(Y2, t2, M[21]);
+    M[22] = lz_fma2(Z2, t2, M[22]);
+    M[23] = lz_fma2(Y, t3, M[23]);
+    M[24] = lz_fma2(Z, t3, M[24]);
+    M[25] = lz_fma2(YZ, t2, M[25]);
+}
+
+// lz_warp_reduce_scatter for two cells at once.
+__device__ __forceinline__ float2 lz_warp_reduce_scatter2(float2 (&v)[32])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float2 send = up ? v[i] : v[i + o];
+            const float2 keep = up ? v[i + o] : v[i];
+            v[i] = make_float2(keep.x + __shfl_xor_sync(0xFFFFFFFFu, send.x, o),
+                               keep.y + __shfl_xor_sync(0xFFFFFFFFu, send.y, o));
+        }
+    }
+    return v[0];
+}
+
+// Shared-memory accesses by 32-bit shared address.
+__device__ __forceinline__ void lz_cp16s(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void lz_sts4(uint32_t dst, float v)
+{
+    asm volatile("st.shared.v4.f32 [%0], {%1, %1, %1, %1};" ::"r"(dst), "f"(v) : "memory");
+}
+__device__ __forceinline__ float4 lz_lds4(uint32_t src)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(src)
+                 : "memory");
+    return v;
+}
+
+// A streaming thread's constant geometry.
+struct LzQuad {
+    int S, J, Jh, P4, pl, N, jy;
+    bool yup, streams;
+    int64_t pbytes;             // bytes per cell (N^3 floats)
+    int sbytes;                 // bytes per stage of a cell (S float4)
+    uint32_t ring0, ring_end;   // shared addresses: this thread's slots of ring slot 0; ring end
+};
+constexpr uint32_t kLzSrcStride = kLzRoleT * 16;          // between the three sources of a stage
+constexpr uint32_t kLzSlotStride = 3 * kLzSrcStride;      // between stage slots
+
+// Prefetch position of a thread: cell pk of the group, stage pst of that
+// cell, the shared address of the slots it fills next, and what the cell's
+// sources are (cells, or a wall's ghost values).
+struct LzPf {
+    int pk, pst;
+    uint32_t slot;
+    const char *own;         // this thread's quad of stage pst of cell pk
+    int64_t yoff;            // byte offset of the y source cell
+    float gxr, gxl;          // ghost values of the right and left walls (cells at a wall)
+    const float *gy;         // ghost values of the bottom or top wall, by jx (cells at a wall)
+    bool xin_r, xin_l, yin;  // the right, left and y sources are cells
+};
+
+__device__ __forceinline__ void lz_pf_cell(LzPf &p, const LzQuad &q, const Geo &g, const LzArgs &a,
+                                           const int4 *cells, const char *hin_t)
+{
+    const int4 ce = cells[p.pk];
+    p.own = hin_t + (int64_t)ce.x * q.pbytes;
+    p.xin_r = ce.y < g.nx - 1;
+    p.xin_l = ce.y > 0;
+    p.yin = q.yup ? ce.z > 0 : ce.z < g.ny - 1;
+    p.yoff = q.yup ? -(int64_t)g.nx * q.pbytes : (int64_t)g.nx * q.pbytes;
+    p.gxr = p.xin_r ? 0.f : __ldg(a.ghost + (g.ny + ce.z) * q.N + q.jy);
+    p.gxl = p.xin_l ? 0.f : __ldg(a.ghost + ce.z * q.N + q.jy);
+    p.gy = a.ghost + (q.yup ? 2 * g.ny + ce.y : 2 * g.ny + g.nx + ce.y) * q.N + q.pl;
+}
+
+// Stages this thread's own, x-source and y-source quads of the next stage
+// (a wall's ghost value where the source lies outside the cavity) and
+// commits one group of copies (an empty one past the group's last stage).
+__device__ __forceinline__ void lz_prefetch(LzPf &p, const LzQuad &q, const Geo &g, const LzArgs &a,
+                                            const int4 *cells, const char *hin_t, int ncell)
+{
+    if (q.streams && p.pk < ncell) {
+        if (p.pst == 0) lz_pf_cell(p, q, g, a, cells, hin_t);
+        lz_cp16s(p.slot, p.own);
+        // x source: the right cell while v_x < 0 (the first half of the
+        // stages), the left cell after.
+        if (p.pst < q.Jh) {
+            if (p.xin_r) lz_cp16s(p.slot + kLzSrcStride, p.own + q.pbytes);
+            else lz_sts4(p.slot + kLzSrcStride, p.gxr);
+        } else {
+            if (p.xin_l) lz_cp16s(p.slot + kLzSrcStride, p.own - q.pbytes);
+            else lz_sts4(p.slot + kLzSrcStride, p.gxl);
+        }
+        if (p.yin) lz_cp16s(p.slot + 2 * kLzSrcStride, p.own + p.yoff);
+        else lz_sts4(p.slot + 2 * kLzSrcStride, __ldg(p.gy + p.pst * q.P4));
+        p.own += q.sbytes;
+    }
+    lz_cp_commit();
+    p.slot += kLzSlotStride;
+    if (p.slot == q.ring_end) p.slot = q.ring0;
+    if (++p.pst == q.J) {
+        p.pst = 0;
+        ++p.pk;
+    }
+}
+
+// Per-cell state of a thread's streaming: the (v_y, v_z) parts of the
+// sources' pending corrections and the power sums over jx of N = w h~ /
+// (A_y A_z) for the quad's two node pairs.
+struct LzAcc {
+    float2 bdo[2], bdx[2], bdy[2];
+    float2 s0[2], s1[2], s2[2], s3[2], s4[2];
+};
+
+// One streaming stage of one cell (Eq. streaming2D with the deferred
+// correction applied to its sources): h~ to dst, the power sums, and the
+// active nodes of the quad to the compact array (component k of G).
+template <int G>
+__device__ __forceinline__ void lz_stream_stage(uint32_t sl, int jx, int j0, int k, const LzHead &H,
+                                                const float4 *tcx, const float2 *tcy, LzAcc &c,
+                                                float4 *dst, const uint32_t *smask, const uint16_t *swpre,
+                                                float *Af, float2 eps2, float2 one2, float2 nay2)
+{
+    const float4 h0 = lz_lds4(sl), hx = lz_lds4(sl + kLzSrcStride), hy = lz_lds4(sl + 2 * kLzSrcStride);
+    const float4 cx4 = tcx[jx];
+    const float2 cy2 = tcy[jx];
+    const float4 ta = H.ta[jx];
+    const float2 nax2 = lz_lo(ta), A2 = lz_hi(ta);
+    const float4 v12 = H.tv12[jx], v34 = H.tv34[jx];
+    const float2 h0p[2] = {lz_lo(h0), lz_hi(h0)}, hxp[2] = {lz_lo(hx), lz_hi(hx)},
+                 hyp[2] = {lz_lo(hy), lz_hi(hy)};
+    float2 ht[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        // u = h_c + (1 + eps h_c) kappa of each source, as h_c (1 + eps kappa) + kappa.
+        const float2 ko = lz_add2(lz_lo(cx4), c.bdo[p]);
+        const float2 u0 = lz_fma2(h0p[p], lz_fma2(eps2, ko, one2), ko);
+        const float2 kx = lz_add2(lz_hi(cx4), c.bdx[p]);
+        const float2 ux = lz_fma2(hxp[p], lz_fma2(eps2, kx, one2), kx);
+        const float2 ky = lz_add2(cy2, c.bdy[p]);
+        const float2 uy = lz_fma2(hyp[p], lz_fma2(eps2, ky, one2), ky);
+        // Eq. streaming2D: u0 - ax (u0 - ux) - ay (u0 - uy).
+        const float2 mux = make_float2(-ux.x, -ux.y), muy = make_float2(-uy.x, -uy.y);
+        float2 h = lz_fma2(nax2, lz_add2(u0, mux), u0);
+        h = lz_fma2(nay2, lz_add2(u0, muy), h);
+        ht[p] = h;
+        const float2 n = lz_mul2(h, A2);
+        c.s0[p] = lz_add2(c.s0[p], n);
+        c.s1[p] = lz_fma2(n, lz_lo(v12), c.s1[p]);
+        c.s2[p] = lz_fma2(n, lz_hi(v12), c.s2[p]);
+        c.s3[p] = lz_fma2(n, lz_lo(v34), c.s3[p]);
+        c.s4[p] = lz_fma2(n, lz_hi(v34), c.s4[p]);
+    }
+    *dst = make_float4(ht[0].x, ht[0].y, ht[1].x, ht[1].y);
+    // Active nodes of the quad (nodes j0 .. j0 + 3) go to the compact array.
+    const uint32_t mw = smask[j0 >> 5];
+    const int sh = j0 & 31;
+    const uint32_t bits = (mw >> sh) & 15u;
+    if (bits) {
+        int mi = swpre[j0 >> 5] + __popc(mw & ((1u << sh) - 1u));
+        const float hv[4] = {ht[0].x, ht[0].y, ht[1].x, ht[1].y};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (bits >> i & 1u) Af[(mi++) * G + k] = hv[i];
+    }
+}
+
+// g = ha + hb + eps ha hb per cell, acc += w g (Eq. monteCarloInt: the
+// sample's product, signed and weighted for its destination).
+__device__ __forceinline__ void lz_term(float2 ha, float2 hb, float2 eps2, float2 w2, float2 &acc)
+{
+    const float2 g = lz_fma2(lz_mul2(eps2, ha), hb, lz_add2(ha, hb));
+    acc = lz_fma2(w2, g, acc);
+}
+__device__ __forceinline__ void lz_term(float4 ha, float4 hb, float2 eps2, float2 w2, float4 &acc)
+{
+    float2 lo = lz_lo(acc), hi = lz_hi(acc);
+    lz_term(lz_lo(ha), lz_lo(hb), eps2, w2, lo);
+    lz_term(lz_hi(ha), lz_hi(hb), eps2, w2, hi);
+    acc = make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
+// The state of a thread's run: the sum of its current destination, which is
+// stored when the destination's last term has passed (atomically for the
+// thread's first destination and its unfinished last one, which neighbouring
+// runs may share).
+template <typename V> struct LzRun {
+    V acc;
+    int dest;
+    bool first;
+};
+
+template <typename V>
+__device__ __forceinline__ void lz_apply(V ha, V hb, uint2 r, float2 eps2, LzRun<V> &st, V *Bv)
+{
+    lz_term(ha, hb, eps2, lz_dup(__uint_as_float(r.y)), st.acc);
+    if (r.x & 1u) {
+        if (st.first) lz_atomic_add(Bv + st.dest, st.acc);
+        else Bv[st.dest] = st.acc;
+        st.first = false;
+        ++st.dest;
+        lz_set_zero(st.acc);
+    }
+}
+
+// Applies 8 records (the operands of two terms are read before either of
+// them can store a destination's sum).
+template <typename V, uint32_t AMASK>
+__device__ __forceinline__ void lz_apply8(const uint2 (&r)[8], const char *Ab, float2 eps2, LzRun<V> &st,
+                                          V *Bv)
+{
+#pragma unroll
+    for (int h = 0; h < 8; h += 2) {
+        const V ha0 = *reinterpret_cast<const V *>(Ab + (r[h].x & AMASK));
+        const V hb0 = *reinterpret_cast<const V *>(Ab + (r[h].x >> 16));
+        const V ha1 = *reinterpret_cast<const V *>(Ab + (r[h + 1].x & AMASK));
+        const V hb1 = *reinterpret_cast<const V *>(Ab + (r[h + 1].x >> 16));
+        lz_apply(ha0, hb0, r[h], eps2, st, Bv);
+        lz_apply(ha1, hb1, r[h + 1], eps2, st, Bv);
+    }
+}
+
+// Barrier among the 256 threads of one role (named barrier 1: streaming,
+// 2: collision; 0 is __syncthreads).
+__device__ __forceinline__ void lz_role_bar(int id)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(kLzRoleT) : "memory");
+}
+
+// One CTA of 512 threads per SM, two roles working on consecutive groups of
+// G cells: warps 0-7 stream group i (Eq. streaming2D, the power sums, the
+// active nodes to one compact array) while warps 8-15 apply the collision
+// terms, the correction and the write-back of group i - 1 from the other
+// compact array.  Streaming is bound by HBM and the collision terms by
+// shared memory, so the two overlap.
+//
 // NV: the velocity axis length as a compile-time constant (0: read g.nv at
-// run time).  Thread t owns node pair q = t mod Q of jx-plane (t div Q) of
-// every streaming stage.
+// run time).  Streaming thread t < S = K N^2/4 owns node quad q = t mod
+// (N^2/4) (four consecutive jz at one (jx, jy)) of jx-plane t div (N^2/4) of
+// every stage; a stage covers K planes and a cell J = N / K stages.
 template <int G, int NV>
-__global__ void __launch_bounds__(512, 2) k_lz(Geo g, LzArgs a)
+__global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
 {
     using V = typename LzVec<G>::T;
     extern __shared__ __align__(16) char smem_raw[];
     if (a.meta[1]) return;                        // too many active nodes: k_cell4 runs
     const int N = NV ? NV : g.nv;
-    const int N2 = N * N, nvt = N2 * N, T = blockDim.x, t = threadIdx.x;
-    const int Q = N2 / 2, nq = N / 2, P = NV ? lz_planes(NV) : a.m.K, J = N / P;
+    const int N2 = N * N, nvt = N2 * N, t = threadIdx.x;
+    const int Qd = N2 / 4, nq = N / 4, P4 = lz_planes4(N), J = N / P4, Jh = J / 2;
+    const int S = P4 * Qd;                        // float4 per stage (the threads that stream)
     const int half = N / 2;
-    const int64_t plane = nvt / 2;                // float2 per cell
-    LzHead &S = *reinterpret_cast<LzHead *>(smem_raw);
+    const int64_t plane4 = nvt / 4;               // float4 per cell
+    LzHead &H = *reinterpret_cast<LzHead *>(smem_raw);
+    const int M = a.meta[0];
     const LzOff so = lz_offsets(nvt, a.mcap, G);
+    float4 *ring = reinterpret_cast<float4 *>(smem_raw + so.ring);
+    V *Bv = reinterpret_cast<V *>(smem_raw + so.bc);
+    float *Bf = reinterpret_cast<float *>(smem_raw + so.bc);
     uint32_t *smask = reinterpret_cast<uint32_t *>(smem_raw + so.mask);
     uint16_t *swpre = reinterpret_cast<uint16_t *>(smem_raw + so.wpre);
     uint16_t *sact = reinterpret_cast<uint16_t *>(smem_raw + so.act);
-    float *region = reinterpret_cast<float *>(smem_raw + so.region);
-    V *Ac = reinterpret_cast<V *>(smem_raw + so.A);
-    V *Bc = reinterpret_cast<V *>(smem_raw + so.B);
-    V *gw = reinterpret_cast<V *>(region);
-    float2 *slots = reinterpret_cast<float2 *>(region);   // [stage][source][thread]
     const float eps = (float)g.eps;
-    const int M = a.meta[0];
+    const float2 eps2 = lz_dup(eps), one2 = lz_dup(1.f);
+    const int lane = t & 31, warp = t >> 5;
+    const bool streamer = t < kLzRoleT;
+
     // ---- tables (once per launch) ----------------------------------------
-    for (int i = t; i < N; i += T) {
+    for (int i = t; i < N; i += kLzThreads) {
         const double v = g.axv[i], A = g.axA[i];
-        S.v[i] = (float)v;
-        S.A[i] = (float)A;
-        S.IA[i] = (float)(1.0 / A);
-        S.cax[i] = (float)fabs(v * g.dt / g.dx);
-        S.cuy[i] = (float)fabs(v * g.dt / g.dy);
-        S.gram[i] = make_float4((float)v, (float)(v * v), (float)(v * v * v), (float)(v * v * v * v));
+        const float nax = -(float)fabs(v * g.dt / g.dx), fA = (float)A, fv = (float)v;
+        H.v[i] = fv;
+        H.A[i] = fA;
+        H.IA[i] = (float)(1.0 / A);
+        H.cuy[i] = (float)fabs(v * g.dt / g.dy);
+        H.ta[i] = make_float4(nax, nax, fA, fA);
+        const float v2 = (float)(v * v), v3 = (float)(v * v * v), v4 = (float)(v * v * v * v);
+        H.tv12[i] = make_float4(fv, fv, v2, v2);
+        H.tv34[i] = make_float4(v3, v3, v4, v4);
     }
-    for (int w = t; w < nvt / 32; w += T) {
+    for (int w = t; w < nvt / 32; w += kLzThreads) {
         smask[w] = a.mask[w];
         swpre[w] = (uint16_t)a.wpre[w];
     }
-    for (int m = t; m < M; m += T) sact[m] = (uint16_t)a.act[m];
-    __syncthreads();
-    for (int i = t; i < N / 2; i += T) {
-        S.vz2[i] = make_float2(S.v[2 * i], S.v[2 * i + 1]);
-        S.Az2[i] = make_float2(S.A[2 * i], S.A[2 * i + 1]);
-    }
+    for (int m = t; m < M; m += kLzThreads) sact[m] = (uint16_t)a.act[m];
     __syncthreads();
 
-    const int q = t % Q, pl = t / Q;
-    const bool active = pl < P;
-    const int jy = q / nq, qz = q % nq;
+    // A streaming thread's quad.
+    const bool streams = t < S;
+    const int pl = streams ? t / Qd : 0, q = streams ? t - pl * Qd : 0;
+    const int jy = q / nq, qz = q - jy * nq;
     const bool yup = jy >= half;                  // v_y > 0: the y source is below
-    const int ys = yup ? 3 : 4;
-    const float2 *hin2 = reinterpret_cast<const float2 *>(a.hin);
-    float2 *hout2 = reinterpret_cast<float2 *>(a.hout);
-    int fallback = 0;
+    const float2 nay2 = lz_dup(-H.cuy[jy]);
+    const float4 *hin4 = reinterpret_cast<const float4 *>(a.hin);
+    float4 *hout4 = reinterpret_cast<float4 *>(a.hout);
     const int ngroups = (g.nr + G - 1) / G;
-    int ngrp = 0;
-    auto stamp = [&](int ph) {
-        if (a.clk && blockIdx.x == 0 && t == 0 && ngrp < kClkCells)
-            a.clk[ngrp * kClkPhases + ph] = clock64();
-    };
+    const int nmine = blockIdx.x < ngroups ? (ngroups - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    int fallback = 0;
 
-    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x, ++ngrp) {
-        stamp(0);
-        int cg[G], cx[G], cy[G];
-        int ncell = 0;
+    // Iteration it: the streaming warps take this CTA's group it, the
+    // collision warps its group it - 1.
+    for (int it = 0; it <= nmine; ++it) {
+        const bool clk = a.clk && blockIdx.x == 0 && it < kClkCells;
+        if (clk && t == 0) a.clk[it * kClkPhases + 0] = clock64();
+        if (streamer) {
+            if (it < nmine) {
+                const int grp = blockIdx.x + it * gridDim.x, buf = it & 1;
+                float *Af = reinterpret_cast<float *>(smem_raw + kLzAOff + buf * so.abytes);
+                if (t < G) {
+                    const int kc = grp * G + t;
+                    const int c = kc < g.nr ? cell_of(g, kc) : -1;
+                    H.cell[buf][t] = make_int4(c, c >= 0 ? c % g.nx : 0, c >= 0 ? c / g.nx : 0, 0);
+                }
+                lz_role_bar(1);
+                int ncell = 0;
 #pragma unroll
-        for (int k = 0; k < G; ++k) {
-            const int kc = grp * G + k;
-            cg[k] = kc < g.nr ? cell_of(g, kc) : -1;
-            cx[k] = cg[k] >= 0 ? cg[k] % g.nx : 0;
-            cy[k] = cg[k] >= 0 ? cg[k] / g.nx : 0;
-            ncell += cg[k] >= 0 ? 1 : 0;
-        }
-        // Prefetch position: cell pk of the group, stage pst of that cell.
-        // Each call copies this thread's own, x-source and y-source pairs of
-        // that stage into its slots (sources beyond a wall are not copied)
-        // and commits one group of copies.
-        int pk = 0, pst = 0, pslot = 0;
-        auto prefetch = [&]() {
-            if (active && pk < ncell) {
-                const int c = G == 1 || pk == 0 ? cg[0] : cg[G - 1];
-                const int ix = G == 1 || pk == 0 ? cx[0] : cx[G - 1];
-                const int iy = G == 1 || pk == 0 ? cy[0] : cy[G - 1];
-                const int jx = pst * P + pl;
-                const float2 *own = hin2 + (int64_t)c * plane + jx * Q + q;
-                float2 *sl = slots + pslot * 3 * T + t;
-                lz_cp8(sl, own);
-                const bool xr = jx < half;
-                if (xr ? ix < g.nx - 1 : ix > 0) lz_cp8(sl + T, own + (xr ? plane : -plane));
-                if (yup ? iy > 0 : iy < g.ny - 1)
-                    lz_cp8(sl + 2 * T, own + (yup ? -(int64_t)g.nx : (int64_t)g.nx) * plane);
-            }
-            lz_cp_commit();
-            if (++pst == J) {
-                pst = 0;
-                ++pk;
-            }
-            if (++pslot == kLzStages) pslot = 0;
-        };
-        // The region was the previous group's per-sample chunk.
-        __syncthreads();
+                for (int k = 0; k < G; ++k) ncell += H.cell[buf][k].x >= 0 ? 1 : 0;
+                // mu of the five cells each cell's streaming reads (0 outside the cavity).
+                for (int i = t; i < G * 40; i += kLzRoleT) {
+                    const int k = i / 40, r = i - k * 40, s5 = r / 8, m = r - s5 * 8;
+                    const int4 ce = H.cell[buf][k];
+                    int cs = ce.x;
+                    bool ok = ce.x >= 0 && m < 5;
+                    if (s5 == 1) { ok = ok && ce.y < g.nx - 1; cs = ce.x + 1; }
+                    if (s5 == 2) { ok = ok && ce.y > 0; cs = ce.x - 1; }
+                    if (s5 == 3) { ok = ok && ce.z > 0; cs = ce.x - g.nx; }
+                    if (s5 == 4) { ok = ok && ce.z < g.ny - 1; cs = ce.x + g.nx; }
+                    H.mus[k][s5][m] = ok ? a.mu_in[(int64_t)cs * 8 + m] : 0.f;
+                }
+                // kLzStages - 1 stages in flight ahead of the one being used.
+                const uint32_t ring0 = lz_saddr(ring) + t * 16;
+                const LzQuad qd{S, J, Jh, P4, pl, N, jy, yup, streams, (int64_t)nvt * 4, S * 16, ring0,
+                                ring0 + kLzStages * kLzSlotStride};
+                const char *hin_t = reinterpret_cast<const char *>(hin4 + t);
+                LzPf pf{};
+                pf.slot = ring0;
+                const int4 *cells = H.cell[buf];
 #pragma unroll
-        for (int kk = 0; kk < kLzStages; ++kk) prefetch();
-        for (int i = t; i < M; i += T) Bc[i] = lz_zero<V>();
-        if (ncell < G)
-            for (int i = t; i < M; i += T) Ac[i] = lz_zero<V>();
+                for (int kk = 0; kk < kLzStages - 1; ++kk) lz_prefetch(pf, qd, g, a, cells, hin_t, ncell);
+                lz_role_bar(1);
+                // Correction tables of the group's cells: ca(jx) = mu_0 + mu_x
+                // v_x + mu_4 v_x^2 of the own cell, the upwind x cell (right for
+                // jx < N/2, left otherwise), and the cells below and above.
+                for (int i = t; i < G * N; i += kLzRoleT) {
+                    const int k = i / N, jx = i - k * N;
+                    const float vx = H.v[jx];
+                    float ca[5];
+#pragma unroll
+                    for (int s5 = 0; s5 < 5; ++s5) {
+                        const float *m = H.mus[k][s5];
+                        ca[s5] = m[0] + m[1] * vx + m[4] * vx * vx;
+                    }
+                    const float cx = jx < half ? ca[1] : ca[2];
+                    H.tcx[k][jx] = make_float4(ca[0], ca[0], cx, cx);
+                    H.tcy[k][0][jx] = lz_dup(ca[3]);
+                    H.tcy[k][1][jx] = lz_dup(ca[4]);
+                }
+                lz_role_bar(1);
 
-        // ---- streaming with the deferred correction applied to its sources
-        int cslot = 0;                            // slots of the stage being consumed
+                // ---- streaming with the deferred correction applied to its sources
+                uint32_t cslot = ring0;           // slots of the stage being used
 #pragma unroll 1
-        for (int k = 0; k < ncell; ++k) {
-            const int c = k == 0 ? cg[0] : cg[G - 1];
-            const int ix = k == 0 ? cx[0] : cx[G - 1], iy = k == 0 ? cy[0] : cy[G - 1];
-            // mu of the five cells the streaming reads: own, right, left, below, above.
-            __syncthreads();
-            if (t < 40) {
-                const int s5 = t / 8, r = t % 8;
-                int cs = c;
-                bool ok = true;
-                if (s5 == 1) { ok = ix < g.nx - 1; cs = c + 1; }
-                if (s5 == 2) { ok = ix > 0; cs = c - 1; }
-                if (s5 == 3) { ok = iy > 0; cs = c - g.nx; }
-                if (s5 == 4) { ok = iy < g.ny - 1; cs = c + g.nx; }
-                S.mus[t] = ok && r < 5 ? a.mu_in[(int64_t)cs * 8 + r] : 0.f;
-            }
-            __syncthreads();
-            for (int i = t; i < 5 * N; i += T) {
-                const int s5 = i / N, jx = i - s5 * N;
-                const float vx = S.v[jx];
-                S.ca[i] = S.mus[s5 * 8] + S.mus[s5 * 8 + 1] * vx + S.mus[s5 * 8 + 4] * vx * vx;
-            }
-            __syncthreads();
-            const bool yin = yup ? iy > 0 : iy < g.ny - 1;
-            const float *yg = a.ghost + (yup ? 2 * g.ny + ix : 2 * g.ny + g.nx + ix) * N;
-            // The (v_y, v_z) part of each source cell's pending correction at
-            // this thread's two nodes: mu_y v_y + mu_z v_z + mu_4 (v_y^2 + v_z^2)
-            // for the own cell (o), the y source (y), the right (r) and left (l) cells.
-            float bdo[2], bdy[2], bdr[2], bdl[2];
-            {
-                const float vy = S.v[jy];
-                const float2 z2 = S.vz2[qz];
-                const float vz[2] = {z2.x, z2.y};
+                for (int k = 0; k < ncell; ++k) {
+                    LzAcc ac;
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const float qi = vy * vy + vz[i] * vz[i];
-                    bdo[i] = S.mus[2] * vy + S.mus[3] * vz[i] + S.mus[4] * qi;
-                    bdy[i] = S.mus[ys * 8 + 2] * vy + S.mus[ys * 8 + 3] * vz[i] + S.mus[ys * 8 + 4] * qi;
-                    bdr[i] = S.mus[8 + 2] * vy + S.mus[8 + 3] * vz[i] + S.mus[8 + 4] * qi;
-                    bdl[i] = S.mus[16 + 2] * vy + S.mus[16 + 3] * vz[i] + S.mus[16 + 4] * qi;
-                }
-            }
-            // Per-thread power sums over jx of N = w h~ / (A_y A_z) for the pair.
-            float s[2][5];
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int pp = 0; pp < 5; ++pp) s[i][pp] = 0.f;
+                    for (int p = 0; p < 2; ++p)
+                        ac.s0[p] = ac.s1[p] = ac.s2[p] = ac.s3[p] = ac.s4[p] = lz_zero2();
+                    lz_bd(H.mus[k][0], H.v, jy, qz, ac.bdo);
+                    lz_bd(H.mus[k][1], H.v, jy, qz, ac.bdx);
+                    lz_bd(H.mus[k][yup ? 3 : 4], H.v, jy, qz, ac.bdy);
+                    const float4 *tcx = H.tcx[k];
+                    const float2 *tcy = H.tcy[k][yup ? 0 : 1];
+                    float4 *dst = hout4 + (int64_t)cells[k].x * plane4 + t;
+                    int jx = pl, j0 = 4 * t;
 #pragma unroll 1
-            for (int st = 0; st < J; ++st) {
-                // This thread's copies of the stage have landed.
-                lz_cp_wait_stage();
-                const float2 *sl = slots + cslot * 3 * T + t;
-                if (active) {
-                    const int jx = st * P + pl;
-                    const bool xr = jx < half;                 // v_x < 0: source right
-                    const bool xin = xr ? ix < g.nx - 1 : ix > 0;
-                    const int xs = xr ? 1 : 2;
-                    const float2 h0 = sl[0];
-                    const float xgv = xin ? 0.f : a.ghost[(xr ? g.ny + iy : iy) * N + jy];
-                    const float2 hx = xin ? sl[T] : make_float2(xgv, xgv);
-                    const float ygv = yin ? 0.f : yg[jx];
-                    const float2 hy = yin ? sl[2 * T] : make_float2(ygv, ygv);
-                    const float ax = S.cax[jx], ay = S.cuy[jy];
-                    const float4 gv = S.gram[jx];
-                    const float Ax = S.A[jx];
-                    // Pending correction of each source: ca(jx) + its (v_y, v_z) part.
-                    const float cao = S.ca[jx], cax = S.ca[xs * N + jx], cay = S.ca[ys * N + jx];
-                    const float h0a[2] = {h0.x, h0.y}, hxa[2] = {hx.x, hx.y}, hya[2] = {hy.x, hy.y};
-                    float ht[2];
-#pragma unroll
-                    for (int i = 0; i < 2; ++i) {
-                        const float bdx = xr ? bdr[i] : bdl[i];
-                        const float u0 = lz_corr(h0a[i], cao + bdo[i], eps);
-                        const float ux = xin ? lz_corr(hxa[i], cax + bdx, eps) : hxa[i];
-                        const float uy = yin ? lz_corr(hya[i], cay + bdy[i], eps) : hya[i];
-                        ht[i] = u0 - ax * (u0 - ux) - ay * (u0 - uy);
-                        const float n = ht[i] * Ax;       // times A_y A_z after the loop
-                        s[i][0] += n;
-                        s[i][1] = fmaf(n, gv.x, s[i][1]);
-                        s[i][2] = fmaf(n, gv.y, s[i][2]);
-                        s[i][3] = fmaf(n, gv.z, s[i][3]);
-                        s[i][4] = fmaf(n, gv.w, s[i][4]);
+                    for (int st = 0; st < J; ++st) {
+                        if (st == Jh) lz_bd(H.mus[k][2], H.v, jy, qz, ac.bdx);   // the left cell now
+                        // The slots read last stage take the stage kLzStages - 1
+                        // ahead; then this stage's copies have landed.
+                        lz_prefetch(pf, qd, g, a, cells, hin_t, ncell);
+                        lz_cp_wait_stage();
+                        if (streams)
+                            lz_stream_stage<G>(cslot, jx, j0, k, H, tcx, tcy, ac, dst, smask, swpre, Af, eps2,
+                                               one2, nay2);
+                        cslot += kLzSlotStride;
+                        if (cslot == qd.ring_end) cslot = ring0;
+                        jx += P4;
+                        j0 += 4 * S;
+                        dst += S;
                     }
-                    hout2[(int64_t)c * plane + jx * Q + q] = make_float2(ht[0], ht[1]);
-                    // Active nodes of the pair go to the compact array.
-                    const int j0 = jx * N2 + jy * N + 2 * qz;
-                    const uint32_t mw = smask[j0 >> 5];
-                    const int sh = j0 & 31;
-                    const uint32_t bits = (mw >> sh) & 3u;
-                    if (bits) {
-                        int mi = swpre[j0 >> 5] + __popc(mw & ((1u << sh) - 1u));
-                        float *Af = reinterpret_cast<float *>(Ac);
-                        if (bits & 1u) Af[(mi++) * G + k] = ht[0];
-                        if (bits & 2u) Af[mi * G + k] = ht[1];
+                    // The 26 monomial sums of the thread's nodes, summed over the warp.
+                    float Msum[32];
+#pragma unroll
+                    for (int r = 0; r < 32; ++r) Msum[r] = 0.f;
+                    if (streams) {
+                        const float Ay = H.A[jy];
+                        const float sv[4][5] = {
+                            {ac.s0[0].x, ac.s1[0].x, ac.s2[0].x, ac.s3[0].x, ac.s4[0].x},
+                            {ac.s0[0].y, ac.s1[0].y, ac.s2[0].y, ac.s3[0].y, ac.s4[0].y},
+                            {ac.s0[1].x, ac.s1[1].x, ac.s2[1].x, ac.s3[1].x, ac.s4[1].x},
+                            {ac.s0[1].y, ac.s1[1].y, ac.s2[1].y, ac.s3[1].y, ac.s4[1].y}};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float Ayz = Ay * H.A[4 * qz + i];
+                            float si[5];
+#pragma unroll
+                            for (int pp = 0; pp < 5; ++pp) si[pp] = sv[i][pp] * Ayz;
+                            lz_mono_from_powers(si, H.v[jy], H.v[4 * qz + i], Msum);
+                        }
                     }
+                    H.fpart[buf][k][warp][lane] = lz_warp_reduce_scatter(Msum);
                 }
-                // The slots just read take the stage kLzStages ahead.
-                prefetch();
-                if (++cslot == kLzStages) cslot = 0;
+                lz_cp_wait_all();
             }
-            float Msum[kLzMono];
+            if (clk && t == 0) a.clk[it * kClkPhases + 1] = clock64();
+        } else if (it >= 1) {
+            const int tc = t - kLzRoleT, wc = warp - kLzRoleWarps, buf = (it - 1) & 1;
+            char *Ab = smem_raw + kLzAOff + buf * so.abytes;
+            float *Af = reinterpret_cast<float *>(Ab);
+            int ncell = 0, cg[G];
 #pragma unroll
-            for (int r = 0; r < kLzMono; ++r) Msum[r] = 0.f;
-            if (active) {
-                const float2 a2 = S.Az2[qz], z2 = S.vz2[qz];
-                const float Ay = S.A[jy], vy = S.v[jy];
-                const float Ayz[2] = {Ay * a2.x, Ay * a2.y}, vz[2] = {z2.x, z2.y};
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-#pragma unroll
-                    for (int pp = 0; pp < 5; ++pp) s[i][pp] *= Ayz[i];
-                    lz_mono_from_powers(s[i], vy, vz[i], Msum);
-                }
+            for (int k = 0; k < G; ++k) {
+                cg[k] = H.cell[buf][k].x;
+                ncell += cg[k] >= 0 ? 1 : 0;
             }
-            block_reduce4<kLzMono>(Msum, S.red, S.tot);
-            if (t < kLzMono) S.F[k * 32 + t] = S.tot[t];
-            stamp(1 + k);
-        }
-        lz_cp_wait_all();
-        __syncthreads();
-
-        // ---- Monte Carlo terms (Eq. monteCarloInt), chunk by chunk ---------
-        for (int ck = 0; ck < a.nchunk; ++ck) {
-            const int lb = ck * a.L, le = min(g.nt, lb + a.L);
+            // ---- Monte Carlo terms (Eq. monteCarloInt) ----------------------
+            // The increments start from zero; the zero entry M of h~ stands for
+            // nodes outside the grid, and cells missing from a short group hold 0.
+            for (int i = tc; i < (M + 1) * G; i += kLzRoleT) Bf[i] = 0.f;
+            if (tc < G) Af[M * G + tc] = 0.f;
+            if (ncell < G)
+                for (int i = tc; i < M * G; i += kLzRoleT)
+                    if (i % G >= ncell) Af[i] = 0.f;
+            lz_role_bar(2);
             {
-                // Eight sample records in flight per thread.
-                int l = lb + t;
-                for (; l + 7 * T < le; l += 8 * T) {
-                    PlanA<float, uint16_t> r[8];
+                // Each thread applies its run of the destination-sorted terms:
+                // it sums one destination's terms in registers and stores the
+                // sum when the destination's last term has passed (atomically
+                // for its first destination and its unfinished last one, which
+                // neighbouring runs may share).
+                const int C = a.meta[3];
+                if (C > 0) {
+                    constexpr uint32_t amask = G == 4 ? 0xFFF0u : 0xFFF8u;
+                    LzRun<V> st;
+                    lz_set_zero(st.acc);
+                    st.dest = a.dest0[tc];
+                    st.first = true;
+                    // Batches of 8 records, two in flight while one is applied
+                    // (the records stream from L2); a run is C records, C a
+                    // multiple of 8, zero-padded by the plan.
+                    const uint2 *rp = a.rec + tc;
+                    constexpr int Ts = kLzRoleT;
+                    uint2 ra[8], rb[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) r[u] = a.pc[l + u * T];
+                    for (int u = 0; u < 8; ++u) ra[u] = rp[u * Ts];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int ia = r[u].a(), ib = r[u].b();
-                        const V va = ia >= 0 ? Ac[ia] : lz_zero<V>();
-                        const V vb = ib >= 0 ? Ac[ib] : lz_zero<V>();
-                        gw[l + u * T - lb] = lz_gw(r[u].W, va, vb, eps);
+                    for (int u = 0; u < 8; ++u) rb[u] = C > 8 ? rp[(8 + u) * Ts] : make_uint2(0u, 0u);
+                    rp += 16 * Ts;
+                    for (int i = 0; i < C; i += 16) {
+                        const bool more = i + 16 < C, more2 = i + 24 < C;
+                        uint2 ca[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) ca[u] = ra[u];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            if (more) ra[u] = rp[u * Ts];
+                        lz_apply8<V, amask>(ca, Ab, eps2, st, Bv);
+                        if (i + 8 < C) {
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) ca[u] = rb[u];
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if (more2) rb[u] = rp[(8 + u) * Ts];
+                            lz_apply8<V, amask>(ca, Ab, eps2, st, Bv);
+                        }
+                        rp += 16 * Ts;
                     }
-                }
-                for (; l < le; l += T) {
-                    const PlanA<float, uint16_t> r = a.pc[l];
-                    const int ia = r.a(), ib = r.b();
-                    const V va = ia >= 0 ? Ac[ia] : lz_zero<V>();
-                    const V vb = ib >= 0 ? Ac[ib] : lz_zero<V>();
-                    gw[l - lb] = lz_gw(r.W, va, vb, eps);
+                    lz_atomic_add(Bv + st.dest, st.acc);
                 }
             }
-            __syncthreads();
-            if (ck == 0) stamp(3);
-            {
-                // Each thread walks its run of the destination-sorted list,
-                // sums the terms of one destination in registers and adds the
-                // sum once: plainly for a destination inside its run, with
-                // atomics for the first and last ones (neighbouring runs may
-                // share them).  The G values of a node are adjacent, so one
-                // 8-byte access serves the group.
-                const int S0 = a.meta[lz_meta_s(ck)], E = a.meta[lz_meta_s(ck + 1)] - S0;
-                const int C = a.meta[lz_meta_c(a.nchunk, ck)];
-                const uint32_t *ent = a.ent + a.meta[lz_meta_b(a.nchunk, ck)];
-                const int n = max(0, min(C, E - t * C));
-                float *Bf = reinterpret_cast<float *>(Bc);
-                int cur = -1;
-                bool first = true;
-                V acc = lz_zero<V>();
-                auto flush = [&](bool shared) {
-                    if (cur < 0) return;
-                    if (shared) {
-#pragma unroll
-                        for (int k = 0; k < G; ++k) atomicAdd(Bf + cur * G + k, lz_get(acc, k));
-                    } else {
-                        Bc[cur] = lz_axpy(1.f, acc, Bc[cur]);
-                    }
-                };
-                auto term = [&](uint32_t w, V r) {
-                    const int dest = (int)(w >> 16);
-                    if (dest != cur) {
-                        flush(first);
-                        first = cur < 0;
-                        cur = dest;
-                        acc = lz_zero<V>();
-                    }
-                    acc = lz_axpy((w & 0x8000u) ? -1.f : 1.f, r, acc);
-                };
-                // Batches of 8 words; two batches ahead are in flight while
-                // one is applied (the list streams from L2).
-                int i = 0;
-                uint32_t wa[8], wb[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    wa[u] = u < n ? ent[u * T + t] : 0u;
-                    wb[u] = 8 + u < n ? ent[(8 + u) * T + t] : 0u;
-                }
-                for (; i + 7 < n; i += 8) {
-                    uint32_t w[8];
-                    V r[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        w[u] = wa[u];
-                        wa[u] = wb[u];
-                    }
-                    if (i + 23 < n) {
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) wb[u] = ent[(i + 16 + u) * T + t];
-                    } else {
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) wb[u] = i + 16 + u < n ? ent[(i + 16 + u) * T + t] : 0u;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) r[u] = gw[w[u] & 0x7FFFu];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) term(w[u], r[u]);
-                }
-                for (; i < n; ++i) {
-                    const uint32_t w = ent[i * T + t];
-                    term(w, gw[w & 0x7FFFu]);
-                }
-                flush(true);
-            }
-            __syncthreads();
-            if (ck == 0) stamp(4);
-        }
-        stamp(5);
+            lz_role_bar(2);
+            if (clk && tc == 0) a.clk[it * kClkPhases + 2] = clock64();
 
-        // ---- sums of the collision increment; correction and moments ------
-#pragma unroll 1
-        for (int k = 0; k < ncell; ++k) {
-            float Dsum[kLzMono];
+            // ---- sums of the collision increment, two cells at a time -------
 #pragma unroll
-            for (int r = 0; r < kLzMono; ++r) Dsum[r] = 0.f;
-            const float *Bf = reinterpret_cast<const float *>(Bc);
-            for (int mm = t; mm < M; mm += T) {
-                const int j = sact[mm];
-                const int jx = j / N2, jyy = (j / N) % N, jz = j % N;
-                lz_mono_node(Bf[mm * G + k], S.v[jx], S.v[jyy], S.v[jz], Dsum);
+            for (int k2 = 0; k2 < G; k2 += 2) {
+                float2 D2[32];
+#pragma unroll
+                for (int r = 0; r < 32; ++r) D2[r] = lz_zero2();
+                if (k2 < ncell) {
+                    for (int mm = tc; mm < M; mm += kLzRoleT) {
+                        const int j = sact[mm], jxy = j / N;
+                        const int jx = jxy / N, jyy = jxy - jx * N, jz = j - jxy * N;
+                        const float2 d = *reinterpret_cast<const float2 *>(Bf + mm * G + k2);
+                        const float x = H.v[jx], x2 = x * x;
+                        const float2 sp[5] = {d, lz_mul2(d, lz_dup(x)), lz_mul2(d, lz_dup(x2)),
+                                              lz_mul2(d, lz_dup(x2 * x)), lz_mul2(d, lz_dup(x2 * x2))};
+                        lz_mono_from_powers2(sp, H.v[jyy], H.v[jz], D2);
+                    }
+                }
+                const float2 r = lz_warp_reduce_scatter2(D2);
+                H.dpart[k2][wc][lane] = r.x;
+                H.dpart[k2 + 1][wc][lane] = r.y;
             }
-            block_reduce4<kLzMono>(Dsum, S.red, S.tot);
-            if (t < kLzMono) S.D[k * 32 + t] = S.tot[t];
+            lz_role_bar(2);
+            if (clk && tc == 0) a.clk[it * kClkPhases + 3] = clock64();
+            // One warp per cell of the group: totals over the warps, then the
+            // correction and the moments.
+            for (int k = wc; k < ncell; k += kLzRoleWarps) {
+                if (lane < kLzMono) {
+                    float f = 0.f, d = 0.f;
+#pragma unroll
+                    for (int w = 0; w < kLzRoleWarps; ++w) {
+                        f += H.fpart[buf][k][w][lane];
+                        d += H.dpart[k][w][lane];
+                    }
+                    H.fpart[buf][k][0][lane] = f;
+                    H.dpart[k][0][lane] = d;
+                }
+                __syncwarp();
+                if (lane == 0)
+                    lz_finish(g, a, cg[k], H.fpart[buf][k][0], H.dpart[k][0], &fallback);
+            }
+            if (clk && tc == 0) a.clk[it * kClkPhases + 4] = clock64();
+
+            // ---- h_c = h~ + dN / w on the active nodes ----------------------
+            for (int mm = tc; mm < M; mm += kLzRoleT) {
+                const int j = sact[mm], jxy = j / N;
+                const int jx = jxy / N, jyy = jxy - jx * N, jz = j - jxy * N;
+                const float iw = H.IA[jx] * H.IA[jyy] * H.IA[jz];
+#pragma unroll
+                for (int k = 0; k < G; ++k)
+                    if (k < ncell)
+                        a.hout[(int64_t)cg[k] * nvt + j] = fmaf(Bf[mm * G + k], iw, Af[mm * G + k]);
+            }
+            if (clk && tc == 0) a.clk[it * kClkPhases + 5] = clock64();
         }
         __syncthreads();
-        // One warp per cell of the group.
-        if ((t & 31) == 0 && (t >> 5) < ncell) {
-            const int k = t >> 5;
-            lz_finish(g, a, k == 0 ? cg[0] : cg[G - 1], S.F + k * 32, S.D + k * 32, &fallback);
-        }
-        stamp(6);
-
-        // ---- h_c = h~ + dN / w on the active nodes --------------------------
-        {
-            const float *Af = reinterpret_cast<const float *>(Ac);
-            const float *Bf = reinterpret_cast<const float *>(Bc);
-            for (int i = t; i < M * G; i += T) {
-                const int mm = i / G, k = i - mm * G;
-                if (k >= ncell) continue;
-                const int j = sact[mm];
-                const int jx = j / N2, jyy = (j / N) % N, jz = j % N;
-                const float iw = S.IA[jx] * S.IA[jyy] * S.IA[jz];
-                a.hout[(int64_t)(k == 0 ? cg[0] : cg[G - 1]) * nvt + j] = fmaf(Bf[i], iw, Af[i]);
-            }
-        }
-        __syncthreads();
-        stamp(7);
     }
     (void)fallback;
 }
