@@ -98,14 +98,23 @@ bz_status prepare_fast(bz_adj_scratch *a, const bzk::Geo &g, int nsm, int optin)
     if (N % 4 != 0 || N < 12 || g.nvt >= 65535 || g.nt > 32768 || Q > 1024) return BZ_OK;
     const size_t smem = bzk::adj4_smem_bytes(N, g.nvt, g.nt);
     if (smem > (size_t)optin) return BZ_OK;
+    // Two CTAs of up to 512 threads per SM when their shared memory fits, so
+    // that one CTA's serial sections (the 5x5 solves) overlap the other's work.
+    int smem_sm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const int maxt = (int)smem <= smem_sm / 2 - 1024 && Q <= 512 ? 512 : 1024;
     int K = 1;
     for (int k = 1; k <= N; ++k)
-        if (N % k == 0 && Q * k <= 1024) K = k;
+        if (N % k == 0 && Q * k <= maxt) K = k;
     const int T = (Q * K + 31) / 32 * 32;
-    cudaError_t e = bz_allow_max_smem(bzk::k_adj_cell4<1024>, optin);
+    cudaError_t e = maxt == 512 ? bz_allow_max_smem(bzk::k_adj_cell4<512>, optin)
+                                : bz_allow_max_smem(bzk::k_adj_cell4<1024>, optin);
     if (e != cudaSuccess) return cuda_err(e, "cudaFuncSetAttribute");
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bzk::k_adj_cell4<1024>, T, smem);
+    e = maxt == 512
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bzk::k_adj_cell4<512>, T, smem)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bzk::k_adj_cell4<1024>, T, smem);
     if (e != cudaSuccess) return cuda_err(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (occ < 1) return BZ_OK;
     const size_t bytes[6] = {sizeof(ushort4) * (size_t)g.nt,
@@ -181,10 +190,16 @@ bz_status launch(bz_adj_scratch *a, const bzk::Geo &g0, int64_t step, const R *h
         }
         if (e == cudaSuccess) {
             const bzk::Map4 m{a->map[0], a->map[1], a->map[2]};
-            bzk::k_adj_cell4<1024><<<a->grid, a->threads, a->smem, s>>>(
-                gs, m, (const float *)hn, (const float *)a->ghost, pi,
-                (const bzk::PlanA<float, uint16_t> *)a->pa16, a->sc_ent, a->sc_meta,
-                (const float *)lam_in, (float *)a->lt, stats);
+            if (a->threads <= 512)
+                bzk::k_adj_cell4<512><<<a->grid, a->threads, a->smem, s>>>(
+                    gs, m, (const float *)hn, (const float *)a->ghost, pi,
+                    (const bzk::PlanA<float, uint16_t> *)a->pa16, a->sc_ent, a->sc_meta,
+                    (const float *)lam_in, (float *)a->lt, stats);
+            else
+                bzk::k_adj_cell4<1024><<<a->grid, a->threads, a->smem, s>>>(
+                    gs, m, (const float *)hn, (const float *)a->ghost, pi,
+                    (const bzk::PlanA<float, uint16_t> *)a->pa16, a->sc_ent, a->sc_meta,
+                    (const float *)lam_in, (float *)a->lt, stats);
             e = check();
         }
     } else {

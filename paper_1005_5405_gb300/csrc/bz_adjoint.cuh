@@ -299,7 +299,7 @@ __global__ void k_adj_walls(Geo g, const int64_t *__restrict__ stepp, const R *_
 {
     __shared__ double red[kMaxWarps * kRedSlots];
     __shared__ double tot[4];
-    __shared__ double rt[kMaxN], sA[kMaxN], sv[kMaxN];
+    __shared__ R rt[kMaxN], sA[kMaxN], sv[kMaxN];
     const int64_t step = *stepp;
     const int f = blockIdx.x;
     const Face F = face_of(g, f, step);
@@ -307,26 +307,32 @@ __global__ void k_adj_walls(Geo g, const int64_t *__restrict__ stepp, const R *_
     const bool lid = f >= 2 * g.ny + g.nx;
     const double cdx = g.dt / (F.nax == 0 ? g.dx : g.dy), U = F.U;
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        sv[i] = g.axv[i];
-        sA[i] = g.axA[i];
-        rt[i] = lid ? exp(2.0 * g.axv[i] * U - U * U) : 1.0;
+        sv[i] = (R)g.axv[i];
+        sA[i] = (R)g.axA[i];
+        rt[i] = (R)(lid ? exp(2.0 * g.axv[i] * U - U * U) : 1.0);
     }
     __syncthreads();
     const R *L = lt + (int64_t)F.cell * g.nvt;
-    const double dcoef = lid && wD != 0.0 ? wD * 2.0 / g.nx : 0.0;
-    double acc[2] = {0.0, 0.0};     // sum lg r, sum lg r v_x
-    for (int j = threadIdx.x; j < g.nvt; j += blockDim.x) {
-        const int jx = j / N2, jy = (j / N) % N, jz = j - (j / N) * N;
-        const double vx = sv[jx], vy = sv[jy];
-        const double vn = (F.nax == 0 ? vx : vy) * F.nsign;
-        if (vn > 0.0) {
-            double lg = vn * cdx * (double)L[j];
-            if (dcoef != 0.0) lg += dcoef * sA[jx] * sA[jy] * sA[jz] * vx * vy;
-            const double lr = lg * rt[jx];
-            acc[0] += lr;
-            acc[1] += lr * vx;
+    const R dcoef = (R)(lid && wD != 0.0 ? wD * 2.0 / g.nx : 0.0), rcdx = (R)cdx;
+    // Thread t takes node jz = t mod N of every (t div N)-th (jx, jy) row;
+    // per-thread sums in the state's precision, the block sum in double.
+    R a0 = R(0), a1 = R(0);        // sum lg r, sum lg r v_x
+    const int per = blockDim.x / N, jz = threadIdx.x % N;
+    if ((int)threadIdx.x < per * N) {
+        for (int row = threadIdx.x / N; row < N2; row += per) {
+            const int jx = row / N, jy = row - jx * N;
+            const R vx = sv[jx], vy = sv[jy];
+            const R vn = (F.nax == 0 ? vx : vy) * (R)F.nsign;
+            if (vn > R(0)) {
+                R lg = vn * rcdx * L[row * N + jz];
+                if (dcoef != R(0)) lg += dcoef * sA[jx] * sA[jy] * sA[jz] * vx * vy;
+                const R lr = lg * rt[jx];
+                a0 += lr;
+                a1 += lr * vx;
+            }
         }
     }
+    double acc[2] = {(double)a0, (double)a1};
     block_reduce<2, double>(acc, red, tot);
     if (threadIdx.x == 0) {
         double ts = 0.0, dts = 0.0;

@@ -530,7 +530,8 @@ bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true)
         BZ_LAUNCHED(H);
         bzk::k_lz_remap<<<pg, pb, 0, s>>>(g.nt, H->lz_idx, H->lz_cidx, H->lz_qc, H->lz_count);
         BZ_LAUNCHED(H);
-        bzk::k_lz_lscan<<<1, 1024, 0, s>>>(bzk::kLzRoleT, H->lz_count, H->lz_cursor, H->lz_rowend,
+        bzk::k_lz_lscan<<<1, 1024, 0, s>>>(bzk::kLzRoleT, H->lz_G == 4 ? 4 : 3, H->lz_count,
+                                           H->lz_cursor, H->lz_rowend,
                                            H->lz_meta, H->lz_rec, H->lz_dest0);
         BZ_LAUNCHED(H);
         bzk::k_lz_lfill<<<pg, pb, 0, s>>>(g.nt, bzk::kLzRoleT, H->lz_G == 4 ? 4 : 3, H->lz_qc, H->lz_pa,

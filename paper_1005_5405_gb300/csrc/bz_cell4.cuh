@@ -916,6 +916,7 @@ static __global__ void __launch_bounds__(1024) k_adj_stream4(Geo g, const float 
         const bool yd = jy >= half ? iy < g.ny - 1 : iy > 0;
         const float4 *ys = own + (jy >= half ? (int64_t)g.nx : -(int64_t)g.nx) * plane;
         const bool edge = ix == 0 || ix == g.nx - 1 || iy == 0 || iy == g.ny - 1;
+#pragma unroll 4
         for (int jx = jxs; jx < N; jx += jstep) {
             const int o = jx * Q + q;
             const float ax = sax[jx];
@@ -950,18 +951,22 @@ static __global__ void __launch_bounds__(1024) k_adj_stream4(Geo g, const float 
     }
 }
 
+// The per-sample products of the forward gather live in the last adjoint
+// slab when they fit (that slab is first used after them).
+__host__ __device__ inline bool adj4_gw_in_slab(int nvt, int nt) { return nt <= nvt; }
+
 // Shared-memory bytes of k_adj_cell4: those of k_cell4 plus two slabs, the
 // saved correction sums and one per-jx table.
 __host__ __device__ inline size_t adj4_smem_bytes(int nv, int nvt, int nt)
 {
-    size_t off = (cell4_smem_bytes(nv, nvt, nt) + 15) & ~(size_t)15;
+    size_t off = (cell4_smem_bytes(nv, nvt, adj4_gw_in_slab(nvt, nt) ? 0 : nt) + 15) & ~(size_t)15;
     return off + 2 * sizeof(float) * nvt + sizeof(float) * (16 + nv);
 }
 
 // Forward recompute and adjoint of the per-cell relaxation of one step for
 // every cell (FP32 fast path): lt = dJ/dh~ from lam = dJ/dh^{n+1}.
 template <int MAXT>
-__global__ void __launch_bounds__(MAXT, 1)
+__global__ void __launch_bounds__(MAXT, 1024 / MAXT)
 k_adj_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ ghost,
             const ushort4 *__restrict__ pidx, const PlanA<float, uint16_t> *__restrict__ pa,
             const uint32_t *__restrict__ ent, const int *__restrict__ meta,
@@ -969,10 +974,11 @@ k_adj_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restric
             unsigned long long *__restrict__ stats)
 {
     extern __shared__ __align__(16) char smem_raw[];
-    const Cell4Smem S = carve4(smem_raw, g.nv, g.nvt);
+    Cell4Smem S = carve4(smem_raw, g.nv, g.nvt);
     Adj4 X;
     {
-        size_t off = (cell4_smem_bytes(g.nv, g.nvt, g.nt) + 15) & ~(size_t)15;
+        const bool gin = adj4_gw_in_slab(g.nvt, g.nt);
+        size_t off = (cell4_smem_bytes(g.nv, g.nvt, gin ? 0 : g.nt) + 15) & ~(size_t)15;
         X.B = reinterpret_cast<float4 *>(smem_raw + off);
         X.C = X.B + g.nvt / 4;
         X.P = reinterpret_cast<float *>(X.C + g.nvt / 4);
@@ -980,6 +986,7 @@ k_adj_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restric
         X.lam = lam;
         X.lt = lt;
         X.pidx = pidx;
+        if (gin) S.gw = reinterpret_cast<float *>(X.C);
     }
     cell4_setup(g, S);
     int fallback = 0;

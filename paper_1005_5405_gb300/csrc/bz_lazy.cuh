@@ -70,7 +70,7 @@ __host__ __device__ constexpr int lz_planes4(int N)
 // ---------------------------------------------------------------------
 
 // Marks every node a sample of the step maps to.
-__global__ void k_lz_mark(int nt, const int4 *__restrict__ idx, int *__restrict__ flag)
+static __global__ void k_lz_mark(int nt, const int4 *__restrict__ idx, int *__restrict__ flag)
 {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= nt) return;
@@ -85,7 +85,7 @@ __global__ void k_lz_mark(int nt, const int4 *__restrict__ idx, int *__restrict_
 // 1024 threads: cidx[j] = m, act[m] = j, the bit mask of marked nodes and, per
 // 32-node word, the compact index of its first marked node.  Clears the flags.
 // stats (nullable): [5] counts steps whose active set exceeded mcap.
-__global__ void __launch_bounds__(1024) k_lz_scan(int nvt, int mcap, int *__restrict__ flag,
+static __global__ void __launch_bounds__(1024) k_lz_scan(int nvt, int mcap, int *__restrict__ flag,
                                                  int *__restrict__ cidx, int *__restrict__ act,
                                                  uint32_t *__restrict__ mask, int *__restrict__ wpre,
                                                  int *__restrict__ meta,
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(1024) k_lz_scan(int nvt, int mcap, int *__rest
 
 // Compact node indices (a, b, a*, b*) of every sample, and the number of
 // terms per destination.
-__global__ void k_lz_remap(int nt, const int4 *__restrict__ idx, const int *__restrict__ cidx,
+static __global__ void k_lz_remap(int nt, const int4 *__restrict__ idx, const int *__restrict__ cidx,
                            ushort4 *__restrict__ qc, int *__restrict__ count)
 {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
@@ -152,17 +152,21 @@ __global__ void k_lz_remap(int nt, const int4 *__restrict__ idx, const int *__re
 // Exclusive scan of the term counts over the M destinations (cursor = first
 // position of each destination's terms in the sorted order, rowend = one past
 // its last), the number of terms E and the run length C of each of the
-// kernel's T threads; clears the counts.  One CTA of 1024 threads.
-__global__ void __launch_bounds__(1024) k_lz_lscan(int T, int *__restrict__ count,
-                                                  int *__restrict__ cursor, int *__restrict__ rowend,
-                                                  int *__restrict__ meta, uint2 *__restrict__ rec,
-                                                  int *__restrict__ dest0)
+// kernel's T threads; clears the counts.  A destination without terms gets
+// one term of weight 0 (at the zero entry M, entries of 1 << osh bytes), so
+// that every destination has a row and a run steps to the next destination
+// at each row end.  One CTA of 1024 threads.
+static __global__ void __launch_bounds__(1024) k_lz_lscan(int T, int osh, int *__restrict__ count,
+                                                         int *__restrict__ cursor,
+                                                         int *__restrict__ rowend,
+                                                         int *__restrict__ meta, uint2 *__restrict__ rec,
+                                                         int *__restrict__ dest0)
 {
     __shared__ int part[1024];
     const int t = threadIdx.x, M = meta[0], per = (M + 1023) / 1024;
     const int b = min(M, t * per), e = min(M, b + per);
     int s = 0;
-    for (int i = b; i < e; ++i) s += count[i];
+    for (int i = b; i < e; ++i) s += max(count[i], 1);
     part[t] = s;
     __syncthreads();
     for (int off = 1; off < 1024; off <<= 1) {
@@ -171,26 +175,34 @@ __global__ void __launch_bounds__(1024) k_lz_lscan(int T, int *__restrict__ coun
         part[t] += v;
         __syncthreads();
     }
-    int run = part[t] - s;
-    for (int i = b; i < e; ++i) {
-        cursor[i] = run;
-        run += count[i];
-        rowend[i] = run;
-        count[i] = 0;
-    }
     // Runs of C terms, C a multiple of 8; the positions past the last term
     // hold zero records (weight 0, no destination change) and every run
     // starts at the zero entry M until k_lz_lfill names its first term.
     const int E = part[1023], C = ((E + T - 1) / T + 7) / 8 * 8;
-    if (t == 1023) {
-        meta[2] = E;
-        meta[3] = C;
-    }
     for (int p = E + t; p < C * T; p += 1024) {
         const int tt = p / C, i = p - tt * C;
         rec[(int64_t)i * T + tt] = make_uint2(0u, 0u);
     }
     for (int tt = t; tt < T; tt += 1024) dest0[tt] = M;
+    __syncthreads();
+    const uint32_t zo = (uint32_t)M << osh;
+    int run = part[t] - s;
+    for (int i = b; i < e; ++i) {
+        cursor[i] = run;
+        if (count[i] == 0) {
+            const int tt = run / C, j = run - tt * C;
+            rec[(int64_t)j * T + tt] = make_uint2(zo | (zo << 16) | 1u, 0u);
+            if (j == 0) dest0[tt] = i;
+            ++run;
+        }
+        run += count[i];
+        rowend[i] = run;
+        count[i] = 0;
+    }
+    if (t == 1023) {
+        meta[2] = E;
+        meta[3] = C;
+    }
 }
 
 // The term records, sorted by destination: position p of the sorted order
@@ -203,8 +215,9 @@ __global__ void __launch_bounds__(1024) k_lz_lscan(int T, int *__restrict__ coun
 // destination, and the sign negative for the loss terms (the destination is
 // a or b).  dest0[tt] is the destination of thread tt's first term.
 // Nothing is written when the step overflowed (the kernel does not run then).
+template <typename PA>
 __global__ void k_lz_lfill(int nt, int T, int osh, const ushort4 *__restrict__ qc,
-                           const PlanA<float, int> *__restrict__ pa, int *__restrict__ cursor,
+                           const PA *__restrict__ pa, int *__restrict__ cursor,
                            const int *__restrict__ rowend, const int *__restrict__ meta,
                            uint2 *__restrict__ rec, int *__restrict__ dest0)
 {
@@ -233,7 +246,7 @@ __global__ void k_lz_lfill(int nt, int T, int osh, const ushort4 *__restrict__ q
 // derived from the logical one, the input is corrected in place and mu_out
 // is cleared (k_cell4 writes corrected states).  All return at once otherwise.
 // ---------------------------------------------------------------------
-__global__ void k_lz_fb_plan(int nt, int N, const int *__restrict__ meta,
+static __global__ void k_lz_fb_plan(int nt, int N, const int *__restrict__ meta,
                              const int4 *__restrict__ idx, const PlanA<float, int> *__restrict__ pa,
                              ushort4 *__restrict__ pidx16, PlanA<float, uint16_t> *__restrict__ pa16,
                              int *__restrict__ count)
@@ -264,7 +277,7 @@ __global__ void k_lz_fb_plan(int nt, int N, const int *__restrict__ meta,
 
 // Clears n floats when gate[1] is set (the pending corrections of a state
 // that the fallback corrected in place).
-__global__ void k_lz_clear(const int *__restrict__ gate, float *__restrict__ x, int64_t n)
+static __global__ void k_lz_clear(const int *__restrict__ gate, float *__restrict__ x, int64_t n)
 {
     if (!gate[1]) return;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -281,7 +294,7 @@ __device__ __forceinline__ float lz_corr(float hc, float kappa, float eps)
 // h <- h_c + (1 + eps h_c)(mu_c . psi_j) for every node (in place allowed);
 // mu_zero (nullable) is then cleared.  When skip_unless (nullable) points to
 // 0, does nothing.  One CTA per cell at a time; float4 over jz.
-__global__ void k_lz_materialize(Geo g, const int *__restrict__ skip_unless,
+static __global__ void k_lz_materialize(Geo g, const int *__restrict__ skip_unless,
                                  const float *__restrict__ hin, const float *__restrict__ mu,
                                  float *__restrict__ hout, float *__restrict__ mu_zero)
 {
@@ -1064,35 +1077,37 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
                     lz_set_zero(st.acc);
                     st.dest = a.dest0[tc];
                     st.first = true;
-                    // Batches of 8 records, two in flight while one is applied
-                    // (the records stream from L2); a run is C records, C a
-                    // multiple of 8, zero-padded by the plan.
+                    // Batches of 8 records in three register buffers: a buffer
+                    // is refilled as soon as it has been applied, two batches
+                    // ahead (the records stream from L2).  A run is C records,
+                    // C a multiple of 8, zero-padded by the plan.
                     const uint2 *rp = a.rec + tc;
-                    constexpr int Ts = kLzRoleT;
-                    uint2 ra[8], rb[8];
+                    constexpr int Ts = kLzRoleT, Bs = 8 * kLzRoleT;
+                    uint2 r0[8], r1[8], r2[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) ra[u] = rp[u * Ts];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) rb[u] = C > 8 ? rp[(8 + u) * Ts] : make_uint2(0u, 0u);
-                    rp += 16 * Ts;
-                    for (int i = 0; i < C; i += 16) {
-                        const bool more = i + 16 < C, more2 = i + 24 < C;
-                        uint2 ca[8];
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) ca[u] = ra[u];
+                    for (int u = 0; u < 8; ++u) {
+                        r0[u] = rp[u * Ts];
+                        r1[u] = C > 8 ? rp[Bs + u * Ts] : make_uint2(0u, 0u);
+                        r2[u] = C > 16 ? rp[2 * Bs + u * Ts] : make_uint2(0u, 0u);
+                    }
+                    for (int i = 0; i < C; i += 24) {
+                        rp += 3 * Bs;
+                        lz_apply8<V, amask>(r0, Ab, eps2, st, Bv);
 #pragma unroll
                         for (int u = 0; u < 8; ++u)
-                            if (more) ra[u] = rp[u * Ts];
-                        lz_apply8<V, amask>(ca, Ab, eps2, st, Bv);
+                            if (i + 24 < C) r0[u] = rp[u * Ts];
                         if (i + 8 < C) {
-#pragma unroll
-                            for (int u = 0; u < 8; ++u) ca[u] = rb[u];
+                            lz_apply8<V, amask>(r1, Ab, eps2, st, Bv);
 #pragma unroll
                             for (int u = 0; u < 8; ++u)
-                                if (more2) rb[u] = rp[(8 + u) * Ts];
-                            lz_apply8<V, amask>(ca, Ab, eps2, st, Bv);
+                                if (i + 32 < C) r1[u] = rp[Bs + u * Ts];
                         }
-                        rp += 16 * Ts;
+                        if (i + 16 < C) {
+                            lz_apply8<V, amask>(r2, Ab, eps2, st, Bv);
+#pragma unroll
+                            for (int u = 0; u < 8; ++u)
+                                if (i + 40 < C) r2[u] = rp[2 * Bs + u * Ts];
+                        }
                     }
                     lz_atomic_add(Bv + st.dest, st.acc);
                 }
@@ -1124,8 +1139,10 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
             lz_role_bar(2);
             if (clk && tc == 0) a.clk[it * kClkPhases + 3] = clock64();
             // One warp per cell of the group: totals over the warps, then the
-            // correction and the moments.
-            for (int k = wc; k < ncell; k += kLzRoleWarps) {
+            // correction and the moments; meanwhile the other collision warps
+            // write h_c = h~ + dN / w of the active nodes.
+            if (wc < ncell) {
+                const int k = wc;
                 if (lane < kLzMono) {
                     float f = 0.f, d = 0.f;
 #pragma unroll
@@ -1139,19 +1156,19 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
                 __syncwarp();
                 if (lane == 0)
                     lz_finish(g, a, cg[k], H.fpart[buf][k][0], H.dpart[k][0], &fallback);
+            } else {
+                const int nw = kLzRoleT - 32 * ncell;
+                for (int mm = tc - 32 * ncell; mm < M; mm += nw) {
+                    const int j = sact[mm], jxy = j / N;
+                    const int jx = jxy / N, jyy = jxy - jx * N, jz = j - jxy * N;
+                    const float iw = H.IA[jx] * H.IA[jyy] * H.IA[jz];
+#pragma unroll
+                    for (int k = 0; k < G; ++k)
+                        if (k < ncell)
+                            a.hout[(int64_t)cg[k] * nvt + j] = fmaf(Bf[mm * G + k], iw, Af[mm * G + k]);
+                }
             }
             if (clk && tc == 0) a.clk[it * kClkPhases + 4] = clock64();
-
-            // ---- h_c = h~ + dN / w on the active nodes ----------------------
-            for (int mm = tc; mm < M; mm += kLzRoleT) {
-                const int j = sact[mm], jxy = j / N;
-                const int jx = jxy / N, jyy = jxy - jx * N, jz = j - jxy * N;
-                const float iw = H.IA[jx] * H.IA[jyy] * H.IA[jz];
-#pragma unroll
-                for (int k = 0; k < G; ++k)
-                    if (k < ncell)
-                        a.hout[(int64_t)cg[k] * nvt + j] = fmaf(Bf[mm * G + k], iw, Af[mm * G + k]);
-            }
             if (clk && tc == 0) a.clk[it * kClkPhases + 5] = clock64();
         }
         __syncthreads();
