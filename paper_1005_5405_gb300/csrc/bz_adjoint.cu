@@ -117,15 +117,16 @@ bz_status prepare_fast(bz_adj_scratch *a, const bzk::Geo &g, int nsm, int optin)
             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bzk::k_adj_cell4<1024>, T, smem);
     if (e != cudaSuccess) return cuda_err(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (occ < 1) return BZ_OK;
-    const size_t bytes[6] = {sizeof(ushort4) * (size_t)g.nt,
+    const size_t bytes[7] = {sizeof(ushort4) * (size_t)g.nt,
                              sizeof(bzk::PlanA<float, uint16_t>) * (size_t)g.nt,
-                             sizeof(int) * (size_t)g.nvt,
-                             sizeof(int) * (size_t)g.nvt,
-                             sizeof(int) * 2,
-                             sizeof(uint32_t) * ((size_t)4 * g.nt + bzk::kMaxThreads)};
-    void **dst[6] = {&a->pidx16, &a->pa16, (void **)&a->sc_count, (void **)&a->sc_cursor,
-                     (void **)&a->sc_meta, (void **)&a->sc_ent};
-    for (int k = 0; k < 6; ++k) {
+                             sizeof(int) * 2 * (size_t)g.nvt,
+                             sizeof(int) * 2 * (size_t)g.nvt,
+                             sizeof(int) * 4,
+                             sizeof(uint32_t) * ((size_t)4 * g.nt + bzk::kMaxThreads),
+                             sizeof(uint4) * ((size_t)2 * g.nt + bzk::kMaxThreads)};
+    void **dst[7] = {&a->pidx16, &a->pa16, (void **)&a->sc_count, (void **)&a->sc_cursor,
+                     (void **)&a->sc_meta, (void **)&a->sc_ent, (void **)&a->lrec};
+    for (int k = 0; k < 7; ++k) {
         e = alloc_fault() ? cudaErrorMemoryAllocation : cudaMalloc(dst[k], bytes[k]);
         if (e != cudaSuccess) return cuda_err(e, "adjoint scratch allocation");
     }
@@ -173,19 +174,21 @@ bz_status launch(bz_adj_scratch *a, const bzk::Geo &g0, int64_t step, const R *h
                 nullptr, nullptr);
             e = check();
         }
-        if (e == cudaSuccess) e = cudaMemsetAsync(a->sc_count, 0, sizeof(int) * g.nvt, s);
+        // The forward list and the loss list of the transposed update.
+        if (e == cudaSuccess) e = cudaMemsetAsync(a->sc_count, 0, sizeof(int) * 2 * g.nvt, s);
         if (e == cudaSuccess) {
-            bzk::k_scatter_count<<<pg, pb, 0, s>>>(g.nt, pi, a->sc_count);
+            bzk::k_adj_count2<<<pg, pb, 0, s>>>(g.nt, g.nvt, pi, a->sc_count);
             e = check();
         }
         if (e == cudaSuccess) {
-            bzk::k_scatter_scan<<<1, 1024, 0, s>>>(g.nvt, a->threads, a->sc_count, a->sc_cursor,
-                                                   a->sc_meta);
+            bzk::k_adj_scan2<<<2, 1024, 0, s>>>(g.nvt, a->threads, a->sc_count, a->sc_cursor,
+                                                a->sc_meta);
             e = check();
         }
         if (e == cudaSuccess) {
-            bzk::k_scatter_fill<<<pg, pb, 0, s>>>(g.nt, a->threads, pi, a->sc_cursor, a->sc_meta,
-                                                  a->sc_ent);
+            bzk::k_adj_fill2<<<pg, pb, 0, s>>>(g.nt, g.nvt, a->threads, pi,
+                                               (const bzk::PlanA<float, uint16_t> *)a->pa16,
+                                               a->sc_cursor, a->sc_meta, a->sc_ent, a->lrec);
             e = check();
         }
         if (e == cudaSuccess) {
@@ -193,13 +196,13 @@ bz_status launch(bz_adj_scratch *a, const bzk::Geo &g0, int64_t step, const R *h
             if (a->threads <= 512)
                 bzk::k_adj_cell4<512><<<a->grid, a->threads, a->smem, s>>>(
                     gs, m, (const float *)hn, (const float *)a->ghost, pi,
-                    (const bzk::PlanA<float, uint16_t> *)a->pa16, a->sc_ent, a->sc_meta,
-                    (const float *)lam_in, (float *)a->lt, stats);
+                    (const bzk::PlanA<float, uint16_t> *)a->pa16, a->sc_ent, a->sc_meta, a->lrec,
+                    a->sc_meta + 2, (const float *)lam_in, (float *)a->lt, stats);
             else
                 bzk::k_adj_cell4<1024><<<a->grid, a->threads, a->smem, s>>>(
                     gs, m, (const float *)hn, (const float *)a->ghost, pi,
-                    (const bzk::PlanA<float, uint16_t> *)a->pa16, a->sc_ent, a->sc_meta,
-                    (const float *)lam_in, (float *)a->lt, stats);
+                    (const bzk::PlanA<float, uint16_t> *)a->pa16, a->sc_ent, a->sc_meta, a->lrec,
+                    a->sc_meta + 2, (const float *)lam_in, (float *)a->lt, stats);
             e = check();
         }
     } else {
@@ -274,7 +277,8 @@ bz_status bz_adj_launch(bz_adj_scratch *a, const bzk::Geo &g, int dtype, int64_t
 void bz_adj_release(bz_adj_scratch *a)
 {
     void *ptrs[] = {a->pidx, a->pa, a->ghost, a->lt, a->nw, a->lF, a->step,
-                    a->pidx16, a->pa16, a->sc_count, a->sc_cursor, a->sc_meta, a->sc_ent};
+                    a->pidx16, a->pa16, a->sc_count, a->sc_cursor, a->sc_meta, a->sc_ent,
+                    a->lrec};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     *a = bz_adj_scratch{};

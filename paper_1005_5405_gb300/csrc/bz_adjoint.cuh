@@ -299,17 +299,23 @@ __global__ void k_adj_walls(Geo g, const int64_t *__restrict__ stepp, const R *_
 {
     __shared__ double red[kMaxWarps * kRedSlots];
     __shared__ double tot[4];
-    __shared__ R rt[kMaxN], sA[kMaxN], sv[kMaxN];
+    __shared__ R rt[kMaxN], sA[kMaxN], sv[kMaxN], se[kMaxN], sde[kMaxN];
     const int64_t step = *stepp;
     const int f = blockIdx.x;
     const Face F = face_of(g, f, step);
     const int N = g.nv, N2 = N * N;
     const bool lid = f >= 2 * g.ny + g.nx;
     const double cdx = g.dt / (F.nax == 0 ? g.dx : g.dy), U = F.U;
+    // Per node of the axis: r = Phi_w / (n_w Phi0) (walls at rest: 1) and the
+    // terms of the inflow density D_in(U) and of its U-derivative.
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        sv[i] = (R)g.axv[i];
+        const R v = (R)g.axv[i], u = (R)U;
+        sv[i] = v;
         sA[i] = (R)g.axA[i];
-        rt[i] = (R)(lid ? exp(2.0 * g.axv[i] * U - U * U) : 1.0);
+        rt[i] = lid ? exp(R(2) * v * u - u * u) : R(1);
+        const R d = v - u, e = (R)(g.dv * 0.5641895835477563) * exp(-d * d);
+        se[i] = e;
+        sde[i] = e * R(2) * d;
     }
     __syncthreads();
     const R *L = lt + (int64_t)F.cell * g.nvt;
@@ -337,10 +343,8 @@ __global__ void k_adj_walls(Geo g, const int64_t *__restrict__ stepp, const R *_
     if (threadIdx.x == 0) {
         double ts = 0.0, dts = 0.0;
         for (int jt = 0; jt < N; ++jt) {
-            const double d = g.axv[jt] - U;
-            const double e = g.dv * 0.5641895835477563 * exp(-d * d);
-            ts += e;
-            dts += e * 2.0 * d;
+            ts += (double)se[jt];
+            dts += (double)sde[jt];
         }
         const double din = g.hn * ts * g.zsum, ddin = g.hn * dts * g.zsum;
         lF[f] = tot[0] / din;

@@ -101,12 +101,13 @@ static __global__ void k_scatter_count(int nt, const ushort4 *__restrict__ pidx,
 
 // Exclusive scan of the per-node counts (one CTA of 1024 threads).
 // gate (nullable): when it is given and gate[1] is 0, the kernel does nothing.
-static __global__ void __launch_bounds__(1024) k_scatter_scan(int nvt, int T, const int *__restrict__ count,
-                                                      int *__restrict__ cursor, int *__restrict__ meta,
-                                                      const int *__restrict__ gate = nullptr)
+// Exclusive scan of the per-node counts (one CTA of 1024 threads, part: 1024
+// ints of shared memory): cursor = first position of each node's words,
+// meta = {E, C = ceil(E / T)}.
+__device__ __forceinline__ void scatter_scan_body(int nvt, int T, const int *__restrict__ count,
+                                                  int *__restrict__ cursor, int *__restrict__ meta,
+                                                  int *part)
 {
-    if (gate && !gate[1]) return;
-    __shared__ int part[1024];
     const int t = threadIdx.x, per = (nvt + 1023) / 1024;
     const int b = t * per, e = min(nvt, b + per);
     int s = 0;
@@ -128,6 +129,15 @@ static __global__ void __launch_bounds__(1024) k_scatter_scan(int nvt, int T, co
         meta[0] = part[1023];
         meta[1] = (part[1023] + T - 1) / T;
     }
+}
+
+static __global__ void __launch_bounds__(1024) k_scatter_scan(int nvt, int T, const int *__restrict__ count,
+                                                      int *__restrict__ cursor, int *__restrict__ meta,
+                                                      const int *__restrict__ gate = nullptr)
+{
+    if (gate && !gate[1]) return;
+    __shared__ int part[1024];
+    scatter_scan_body(nvt, T, count, cursor, meta, part);
 }
 
 static __global__ void k_scatter_fill(int nt, int T, const ushort4 *__restrict__ pidx,
@@ -340,7 +350,68 @@ struct Adj4 {
     const float *lam;
     float *lt;
     const ushort4 *pidx;
+    // The loss terms of the step (destination a or b of a sample), sorted by
+    // destination in runs of lmeta[1] records per thread (k_adj_fill2);
+    // lmeta[0] is their number.
+    const uint4 *lrec;
+    const int *lmeta;
 };
+
+// The adjoint's two lists of the step's terms.  The forward list: every
+// (node, sample, sign) term, as for k_cell4 (k_scatter_fill).  The loss
+// list of the transposed update: per sample with nodes (a, b, a*, b*) in the
+// shared-memory order (0xFFFF outside the grid) and weight W, one record for
+// each valid destination d in {a, b}:
+//   {a* | b* << 16, a | b << 16, W, d | (d is b) << 16}.
+// Counts, cursors and headers of the forward list come first, those of the
+// loss list nvt entries (two ints) after them.
+static __global__ void k_adj_count2(int nt, int nvt, const ushort4 *__restrict__ pidx,
+                                    int *__restrict__ count)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nt) return;
+    const ushort4 q = pidx[l];
+    if (q.x != 0xFFFF) {
+        atomicAdd(count + q.x, 1);
+        atomicAdd(count + nvt + q.x, 1);
+    }
+    if (q.y != 0xFFFF) {
+        atomicAdd(count + q.y, 1);
+        atomicAdd(count + nvt + q.y, 1);
+    }
+    if (q.z != 0xFFFF) atomicAdd(count + q.z, 1);
+    if (q.w != 0xFFFF) atomicAdd(count + q.w, 1);
+}
+static __global__ void __launch_bounds__(1024) k_adj_scan2(int nvt, int T, const int *__restrict__ count,
+                                                           int *__restrict__ cursor, int *__restrict__ meta)
+{
+    __shared__ int part[1024];
+    const int k = blockIdx.x;
+    scatter_scan_body(nvt, T, count + k * nvt, cursor + k * nvt, meta + 2 * k, part);
+}
+static __global__ void k_adj_fill2(int nt, int nvt, int T, const ushort4 *__restrict__ pidx,
+                                   const PlanA<float, uint16_t> *__restrict__ pa,
+                                   int *__restrict__ cursor, const int *__restrict__ meta,
+                                   uint32_t *__restrict__ ent, uint4 *__restrict__ rec)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nt) return;
+    const ushort4 q = pidx[l];
+    const unsigned short d[4] = {q.x, q.y, q.z, q.w};
+    const int C = meta[1], CL = meta[3];
+    const uint32_t gain = (uint32_t)q.z | ((uint32_t)q.w << 16), loss = (uint32_t)q.x | ((uint32_t)q.y << 16);
+    const uint32_t W = __float_as_uint(pa[l].W);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (d[k] == 0xFFFF) continue;
+        const int pos = atomicAdd(cursor + d[k], 1), tt = pos / C, i = pos - tt * C;
+        ent[(int64_t)i * T + tt] = ((uint32_t)d[k] << 16) | (k < 2 ? 0x8000u : 0u) | (uint32_t)l;
+        if (k < 2) {
+            const int pl = atomicAdd(cursor + nvt + d[k], 1), tl = pl / CL, il = pl - tl * CL;
+            rec[(int64_t)il * T + tl] = make_uint4(gain, loss, W, (uint32_t)d[k] | ((uint32_t)k << 16));
+        }
+    }
+}
 
 // x = G^{-1} rhs for the Gram matrix G = G0 + eps sum_j N_c,j psi_j psi_j^T
 // of the correction (P[0..13] its moment sums, as in correction_spd), by
@@ -476,37 +547,49 @@ __device__ __forceinline__ void adj4_tail(const Geo &g, const Map4 &m, int c, co
     __syncthreads();
 
     // ---- transposed Monte Carlo update --------------------------------------
+    // Each thread walks its run of the destination-sorted loss terms: the
+    // term of sample l at its node d in {a, b} adds gamma_l (1 + eps h~_p),
+    // p the other pre-collision node, to dJ/dh~_d.  A destination's sum is
+    // added plainly once the run leaves it, atomically for the run's first
+    // and last destinations (neighbouring runs may share them).
     {
         const float *Bf = reinterpret_cast<const float *>(X.B);
         const float *Af = reinterpret_cast<const float *>(S.slab4);
         float *Cf = reinterpret_cast<float *>(X.C);
-        auto one = [&](ushort4 d, float W) {
-            float gam = 0.f;
-            if (d.z != 0xFFFF) gam += Bf[d.z];
-            if (d.w != 0xFFFF) gam += Bf[d.w];
-            if (d.x != 0xFFFF) gam -= Bf[d.x];
-            if (d.y != 0xFFFF) gam -= Bf[d.y];
-            gam *= W;
-            if (gam != 0.f) {
-                const float ha = d.x != 0xFFFF ? Af[d.x] : 0.f;
-                const float hb = d.y != 0xFFFF ? Af[d.y] : 0.f;
-                if (d.x != 0xFFFF) atomicAdd(Cf + d.x, gam * (1.f + eps * hb));
-                if (d.y != 0xFFFF) atomicAdd(Cf + d.y, gam * (1.f + eps * ha));
+        const int E = X.lmeta[0], C = X.lmeta[1];
+        const int n = max(0, min(C, E - t * C));
+        int cur = -1;
+        bool first = true;
+        float acc = 0.f;
+        auto qv = [&](uint32_t i) { return i != 0xFFFFu ? Bf[i] : 0.f; };
+        auto term = [&](uint4 r) {
+            const float gam = __uint_as_float(r.z) * ((qv(r.x & 0xFFFFu) + qv(r.x >> 16)) -
+                                                      (qv(r.y & 0xFFFFu) + qv(r.y >> 16)));
+            const uint32_t p = (r.w >> 16) ? (r.y & 0xFFFFu) : (r.y >> 16);
+            const float hp = p != 0xFFFFu ? Af[p] : 0.f;
+            const int d = (int)(r.w & 0xFFFFu);
+            if (d != cur) {
+                if (cur >= 0) {
+                    if (first) atomicAdd(Cf + cur, acc);
+                    else Cf[cur] += acc;
+                    first = false;
+                }
+                cur = d;
+                acc = 0.f;
             }
+            acc = fmaf(gam, fmaf(eps, hp, 1.f), acc);
         };
-        int l = t;
-        for (; l + 7 * T < g.nt; l += 8 * T) {
-            ushort4 d[8];
-            float W[8];
+        const uint4 *rp = X.lrec + t;
+        int i = 0;
+        for (; i + 3 < n; i += 4) {
+            uint4 r[4];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                d[u] = X.pidx[l + u * T];
-                W[u] = pa[l + u * T].W;
-            }
+            for (int u = 0; u < 4; ++u) r[u] = rp[(int64_t)(i + u) * T];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) one(d[u], W[u]);
+            for (int u = 0; u < 4; ++u) term(r[u]);
         }
-        for (; l < g.nt; l += T) one(X.pidx[l], pa[l].W);
+        for (; i < n; ++i) term(rp[(int64_t)i * T]);
+        if (cur >= 0) atomicAdd(Cf + cur, acc);
     }
     __syncthreads();
 
@@ -908,15 +991,28 @@ static __global__ void __launch_bounds__(1024) k_adj_stream4(Geo g, const float 
     const int jy = q / nq, jz0 = 4 * (q % nq);
     const float vy = sv[jy], ay = say[jy];
     const float dcoef = (float)(wD * 2.0 / g.nx);
-    for (int c = blockIdx.x; c < g.nr; c += gridDim.x) {
+    for (int kc = blockIdx.x; kc < g.nr; kc += gridDim.x) {
+        const int c = cell_of(g, kc);
         const int ix = c % g.nx, iy = c / g.nx;
         const float4 *own = reinterpret_cast<const float4 *>(lt) + (int64_t)c * plane;
         float4 *dst = reinterpret_cast<float4 *>(lam_out) + (int64_t)c * plane;
         // Downwind y neighbour of this thread's row (v_y > 0: above).
-        const bool yd = jy >= half ? iy < g.ny - 1 : iy > 0;
         const float4 *ys = own + (jy >= half ? (int64_t)g.nx : -(int64_t)g.nx) * plane;
-        const bool edge = ix == 0 || ix == g.nx - 1 || iy == 0 || iy == g.ny - 1;
+        if (ix > 0 && ix < g.nx - 1 && iy > 0 && iy < g.ny - 1) {
+            // Interior cell: both downwind neighbours are cells.
+            const float4 *xr = own + plane, *xl = own - plane;
 #pragma unroll 4
+            for (int jx = jxs; jx < N; jx += jstep) {
+                const int o = jx * Q + q;
+                const float ax = sax[jx];
+                const float4 l0 = own[o], lx = jx >= half ? xr[o] : xl[o], ly = ys[o];
+                const float c0 = 1.f - ax - ay;
+                dst[o] = make_float4(c0 * l0.x + ax * lx.x + ay * ly.x, c0 * l0.y + ax * lx.y + ay * ly.y,
+                                     c0 * l0.z + ax * lx.z + ay * ly.z, c0 * l0.w + ax * lx.w + ay * ly.w);
+            }
+            continue;
+        }
+        const bool yd = jy >= half ? iy < g.ny - 1 : iy > 0;
         for (int jx = jxs; jx < N; jx += jstep) {
             const int o = jx * Q + q;
             const float ax = sax[jx];
@@ -930,22 +1026,20 @@ static __global__ void __launch_bounds__(1024) k_adj_stream4(Geo g, const float 
             r.y = c0 * l0.y + ax * lx.y + ay * ly.y;
             r.z = c0 * l0.z + ax * lx.z + ay * ly.z;
             r.w = c0 * l0.w + ax * lx.w + ay * ly.w;
-            if (edge) {
-                const float vx = sv[jx];
-                float ex = 0.f;
-                if (ix == 0 && vx < 0.f) ex -= (float)lF[iy] * vx;
-                if (ix == g.nx - 1 && vx > 0.f) ex += (float)lF[g.ny + iy] * vx;
-                if (iy == 0 && vy < 0.f) ex -= (float)lF[2 * g.ny + ix] * vy;
-                float dl = 0.f;
-                if (iy == g.ny - 1 && vy > 0.f) {
-                    ex += (float)lF[2 * g.ny + g.nx + ix] * vy;
-                    dl = dcoef * vx * vy;
-                }
-                const float wxy = sA[jx] * sA[jy];
-                float *rr = &r.x;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) rr[i] += (ex + dl) * wxy * sA[jz0 + i];
+            const float vx = sv[jx];
+            float ex = 0.f;
+            if (ix == 0 && vx < 0.f) ex -= (float)lF[iy] * vx;
+            if (ix == g.nx - 1 && vx > 0.f) ex += (float)lF[g.ny + iy] * vx;
+            if (iy == 0 && vy < 0.f) ex -= (float)lF[2 * g.ny + ix] * vy;
+            float dl = 0.f;
+            if (iy == g.ny - 1 && vy > 0.f) {
+                ex += (float)lF[2 * g.ny + g.nx + ix] * vy;
+                dl = dcoef * vx * vy;
             }
+            const float wxy = sA[jx] * sA[jy];
+            float *rr = &r.x;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) rr[i] += (ex + dl) * wxy * sA[jz0 + i];
             dst[o] = r;
         }
     }
@@ -970,6 +1064,7 @@ __global__ void __launch_bounds__(MAXT, 1024 / MAXT)
 k_adj_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ ghost,
             const ushort4 *__restrict__ pidx, const PlanA<float, uint16_t> *__restrict__ pa,
             const uint32_t *__restrict__ ent, const int *__restrict__ meta,
+            const uint4 *__restrict__ lrec, const int *__restrict__ lmeta,
             const float *__restrict__ lam, float *__restrict__ lt,
             unsigned long long *__restrict__ stats)
 {
@@ -986,6 +1081,8 @@ k_adj_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restric
         X.lam = lam;
         X.lt = lt;
         X.pidx = pidx;
+        X.lrec = lrec;
+        X.lmeta = lmeta;
         if (gin) S.gw = reinterpret_cast<float *>(X.C);
     }
     cell4_setup(g, S);

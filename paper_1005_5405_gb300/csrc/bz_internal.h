@@ -42,8 +42,9 @@ struct bz_adj_scratch {
     // the destination-sorted scatter list of the step, the quad mapping.
     bool fast;
     void *pidx16, *pa16;
-    int *sc_count, *sc_cursor, *sc_meta;
-    uint32_t *sc_ent;
+    int *sc_count, *sc_cursor, *sc_meta;   // counts and cursors of both lists, 2 x nvt;
+    uint32_t *sc_ent;                      // headers: forward list, then the loss list
+    uint4 *lrec;         // the loss-term records of the transposed update
     int map[3];          // Q, K, J
 };
 
