@@ -275,10 +275,16 @@ bz_status bz_profile(bz_handle *h, int32_t enable);
 bz_status bz_profile_read(bz_handle *h, double ms[4], int64_t launches[4]);
 
 /* Phase trace of the FP32 per-cell kernel, recorded while bz_profile(h, 2)
- * is on: SM clock (clock64) at the 9 phase barriers (cell start, after
- * streaming, gather, N = w h~, scatter, correction sums, solve, write-back,
- * cell end) of the first 8 cells of CTA 0 in the latest launch.  out: at
- * least 72 int64, host; row-major [cell][phase].  BZ_ESTATE if not enabled. */
+ * is on: SM clock (clock64) at up to 9 phase points of the first 8 work
+ * items of CTA 0 in the latest launch.  For the quad kernel (kernel variant
+ * 1) an item is a cell and the points are: cell start, after streaming,
+ * gather, N = w h~, scatter, correction sums, solve, write-back, cell end.
+ * For the active-node kernel (variant 2) an item is an iteration of its two
+ * roles and the points are: iteration start, streaming done, collision
+ * terms done, their sums done, write-back done, correction and moments of
+ * the group two back done (the first two from a streaming thread, the next
+ * three from a collision thread).  out: at least 72 int64, host; row-major
+ * [item][point].  BZ_ESTATE if not enabled. */
 bz_status bz_phase_clocks(bz_handle *h, int64_t *out, int32_t n);
 
 /* ---------------------------------------------------------------------

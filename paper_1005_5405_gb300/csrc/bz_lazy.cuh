@@ -410,8 +410,8 @@ struct LzArgs {
 // (kLzStages stages x {own, x source, y source} x streaming threads, 16 bytes
 // each), the active-node bit mask, its word prefixes and the node list.
 struct LzHead {
-    float fpart[2][kLzMaxG][kLzRoleWarps][32];   // warp partials of the F sums, per group buffer
-    float dpart[kLzMaxG][kLzRoleWarps][32];      // warp partials of the D sums
+    float fpart[3][kLzMaxG][kLzRoleWarps][32];   // warp partials of the F sums, per group (it mod 3)
+    float dpart[2][kLzMaxG][kLzRoleWarps][32];   // warp partials of the D sums, per group (it mod 2)
     float4 ta[kLzMaxN];                          // -ax, -ax, A, A
     float4 tv12[kLzMaxN];                        // v, v, v^2, v^2
     float4 tv34[kLzMaxN];                        // v^3, v^3, v^4, v^4
@@ -862,10 +862,11 @@ __device__ __forceinline__ void lz_role_bar(int id)
 
 // One CTA of 512 threads per SM, two roles working on consecutive groups of
 // G cells: warps 0-7 stream group i (Eq. streaming2D, the power sums, the
-// active nodes to one compact array) while warps 8-15 apply the collision
-// terms, the correction and the write-back of group i - 1 from the other
-// compact array.  Streaming is bound by HBM and the collision terms by
-// shared memory, so the two overlap.
+// active nodes to one compact array) and then solve the correction and the
+// moments of group i - 2, while warps 8-15 apply the collision terms, their
+// sums and the write-back of group i - 1 from the other compact array.
+// Streaming is bound by HBM and the collision terms by shared memory, so
+// the two overlap.
 //
 // NV: the velocity axis length as a compile-time constant (0: read g.nv at
 // run time).  Streaming thread t < S = K N^2/4 owns node quad q = t mod
@@ -931,7 +932,7 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
 
     // Iteration it: the streaming warps take this CTA's group it, the
     // collision warps its group it - 1.
-    for (int it = 0; it <= nmine; ++it) {
+    for (int it = 0; it <= nmine + 1; ++it) {
         const bool clk = a.clk && blockIdx.x == 0 && it < kClkCells;
         if (clk && t == 0) a.clk[it * kClkPhases + 0] = clock64();
         if (streamer) {
@@ -1040,12 +1041,34 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
                             lz_mono_from_powers(si, H.v[jy], H.v[4 * qz + i], Msum);
                         }
                     }
-                    H.fpart[buf][k][warp][lane] = lz_warp_reduce_scatter(Msum);
+                    H.fpart[it % 3][k][warp][lane] = lz_warp_reduce_scatter(Msum);
                 }
                 lz_cp_wait_all();
             }
             if (clk && t == 0) a.clk[it * kClkPhases + 1] = clock64();
-        } else if (it >= 1) {
+            // One warp per cell of group it - 2: totals over the warps, then the
+            // correction and the moments.
+            if (it >= 2) {
+                const int grp = blockIdx.x + (it - 2) * gridDim.x, fb = (it - 2) % 3, db = it & 1;
+                const int k = warp, kc = grp * G + k;
+                if (k < G && kc < g.nr) {
+                    if (lane < kLzMono) {
+                        float f = 0.f, d = 0.f;
+#pragma unroll
+                        for (int w = 0; w < kLzRoleWarps; ++w) {
+                            f += H.fpart[fb][k][w][lane];
+                            d += H.dpart[db][k][w][lane];
+                        }
+                        H.fpart[fb][k][0][lane] = f;
+                        H.dpart[db][k][0][lane] = d;
+                    }
+                    __syncwarp();
+                    if (lane == 0)
+                        lz_finish(g, a, cell_of(g, kc), H.fpart[fb][k][0], H.dpart[db][k][0], &fallback);
+                }
+            }
+            if (clk && t == 0) a.clk[it * kClkPhases + 5] = clock64();
+        } else if (it >= 1 && it <= nmine) {
             const int tc = t - kLzRoleT, wc = warp - kLzRoleWarps, buf = (it - 1) & 1;
             char *Ab = smem_raw + kLzAOff + buf * so.abytes;
             float *Af = reinterpret_cast<float *>(Ab);
@@ -1133,43 +1156,21 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
                     }
                 }
                 const float2 r = lz_warp_reduce_scatter2(D2);
-                H.dpart[k2][wc][lane] = r.x;
-                H.dpart[k2 + 1][wc][lane] = r.y;
+                H.dpart[buf][k2][wc][lane] = r.x;
+                H.dpart[buf][k2 + 1][wc][lane] = r.y;
             }
-            lz_role_bar(2);
             if (clk && tc == 0) a.clk[it * kClkPhases + 3] = clock64();
-            // One warp per cell of the group: totals over the warps, then the
-            // correction and the moments; meanwhile the other collision warps
-            // write h_c = h~ + dN / w of the active nodes.
-            if (wc < ncell) {
-                const int k = wc;
-                if (lane < kLzMono) {
-                    float f = 0.f, d = 0.f;
+            // ---- h_c = h~ + dN / w on the active nodes ----------------------
+            for (int mm = tc; mm < M; mm += kLzRoleT) {
+                const int j = sact[mm], jxy = j / N;
+                const int jx = jxy / N, jyy = jxy - jx * N, jz = j - jxy * N;
+                const float iw = H.IA[jx] * H.IA[jyy] * H.IA[jz];
 #pragma unroll
-                    for (int w = 0; w < kLzRoleWarps; ++w) {
-                        f += H.fpart[buf][k][w][lane];
-                        d += H.dpart[k][w][lane];
-                    }
-                    H.fpart[buf][k][0][lane] = f;
-                    H.dpart[k][0][lane] = d;
-                }
-                __syncwarp();
-                if (lane == 0)
-                    lz_finish(g, a, cg[k], H.fpart[buf][k][0], H.dpart[k][0], &fallback);
-            } else {
-                const int nw = kLzRoleT - 32 * ncell;
-                for (int mm = tc - 32 * ncell; mm < M; mm += nw) {
-                    const int j = sact[mm], jxy = j / N;
-                    const int jx = jxy / N, jyy = jxy - jx * N, jz = j - jxy * N;
-                    const float iw = H.IA[jx] * H.IA[jyy] * H.IA[jz];
-#pragma unroll
-                    for (int k = 0; k < G; ++k)
-                        if (k < ncell)
-                            a.hout[(int64_t)cg[k] * nvt + j] = fmaf(Bf[mm * G + k], iw, Af[mm * G + k]);
-                }
+                for (int k = 0; k < G; ++k)
+                    if (k < ncell)
+                        a.hout[(int64_t)cg[k] * nvt + j] = fmaf(Bf[mm * G + k], iw, Af[mm * G + k]);
             }
             if (clk && tc == 0) a.clk[it * kClkPhases + 4] = clock64();
-            if (clk && tc == 0) a.clk[it * kClkPhases + 5] = clock64();
         }
         __syncthreads();
     }
