@@ -1081,7 +1081,7 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
             // ---- Monte Carlo terms (Eq. monteCarloInt) ----------------------
             // The increments start from zero; the zero entry M of h~ stands for
             // nodes outside the grid, and cells missing from a short group hold 0.
-            for (int i = tc; i < (M + 1) * G; i += kLzRoleT) Bf[i] = 0.f;
+            for (int i = tc; i < M + 1; i += kLzRoleT) lz_set_zero(Bv[i]);
             if (tc < G) Af[M * G + tc] = 0.f;
             if (ncell < G)
                 for (int i = tc; i < M * G; i += kLzRoleT)
@@ -1138,7 +1138,8 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
             lz_role_bar(2);
             if (clk && tc == 0) a.clk[it * kClkPhases + 2] = clock64();
 
-            // ---- sums of the collision increment, two cells at a time -------
+            // ---- sums of the collision increment and h_c = h~ + dN / w on the
+            // active nodes, two cells at a time -------------------------------
 #pragma unroll
             for (int k2 = 0; k2 < G; k2 += 2) {
                 float2 D2[32];
@@ -1149,10 +1150,14 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
                         const int j = sact[mm], jxy = j / N;
                         const int jx = jxy / N, jyy = jxy - jx * N, jz = j - jxy * N;
                         const float2 d = *reinterpret_cast<const float2 *>(Bf + mm * G + k2);
+                        const float2 h = *reinterpret_cast<const float2 *>(Af + mm * G + k2);
                         const float x = H.v[jx], x2 = x * x;
                         const float2 sp[5] = {d, lz_mul2(d, lz_dup(x)), lz_mul2(d, lz_dup(x2)),
                                               lz_mul2(d, lz_dup(x2 * x)), lz_mul2(d, lz_dup(x2 * x2))};
                         lz_mono_from_powers2(sp, H.v[jyy], H.v[jz], D2);
+                        const float iw = H.IA[jx] * H.IA[jyy] * H.IA[jz];
+                        a.hout[(int64_t)cg[k2] * nvt + j] = fmaf(d.x, iw, h.x);
+                        if (k2 + 1 < ncell) a.hout[(int64_t)cg[k2 + 1] * nvt + j] = fmaf(d.y, iw, h.y);
                     }
                 }
                 const float2 r = lz_warp_reduce_scatter2(D2);
@@ -1160,16 +1165,6 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
                 H.dpart[buf][k2 + 1][wc][lane] = r.y;
             }
             if (clk && tc == 0) a.clk[it * kClkPhases + 3] = clock64();
-            // ---- h_c = h~ + dN / w on the active nodes ----------------------
-            for (int mm = tc; mm < M; mm += kLzRoleT) {
-                const int j = sact[mm], jxy = j / N;
-                const int jx = jxy / N, jyy = jxy - jx * N, jz = j - jxy * N;
-                const float iw = H.IA[jx] * H.IA[jyy] * H.IA[jz];
-#pragma unroll
-                for (int k = 0; k < G; ++k)
-                    if (k < ncell)
-                        a.hout[(int64_t)cg[k] * nvt + j] = fmaf(Bf[mm * G + k], iw, Af[mm * G + k]);
-            }
             if (clk && tc == 0) a.clk[it * kClkPhases + 4] = clock64();
         }
         __syncthreads();
