@@ -125,6 +125,7 @@ struct bz_handle {
     uint32_t *lz_mask = nullptr;
     uint2 *lz_rec = nullptr;
     int lz_mcap = 0, lz_G = 0, lz_T = 0, lz_grid = 0, lz_mprobe = 0;
+    int lz_cmax = 0, lz_order_tpb = 0;     // bank-aware ordering of the term runs (1: on)
     size_t lz_smem = 0;
     float lz_e0[bzk::kLzX] = {};
 };
@@ -477,6 +478,12 @@ bz_status configure_lazy(bz_handle *H)
     }
     if (!ok) return BZ_OK;
     H->lz_mcap = mcap;
+    // Bank-aware ordering of the term runs: one thread per run with its
+    // records staged in shared memory.
+    H->lz_cmax = ((4 * nt + bzk::kLzRoleT - 1) / bzk::kLzRoleT + 7) / 8 * 8;
+    H->lz_order_tpb = bzk::lz_order_smem(H->lz_cmax) <= (size_t)H->smem_optin ? 1 : 0;
+    if (getenv("BZ_LAZY_NOORDER")) H->lz_order_tpb = 0;
+    if (H->lz_order_tpb > 0) BZ_CUDA(bz_allow_max_smem(bzk::k_lz_order, H->smem_optin));
     BZ_TRY(dalloc(&H->lz_count, sizeof(int) * (size_t)nvt));
     BZ_TRY(dalloc(&H->lz_cursor, sizeof(int) * (size_t)nvt));
     BZ_TRY(dalloc(&H->lz_rowend, sizeof(int) * (size_t)nvt));
@@ -538,6 +545,13 @@ bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true)
                                           H->lz_cursor, H->lz_rowend, H->lz_meta, H->lz_rec,
                                           H->lz_dest0);
         BZ_LAUNCHED(H);
+        if (H->lz_order_tpb > 0) {
+            bzk::k_lz_order<<<(bzk::kLzRoleT + bzk::kLzOrderWarps - 1) / bzk::kLzOrderWarps,
+                              bzk::kLzOrderWarps * 32, bzk::lz_order_smem(H->lz_cmax), s>>>(
+                bzk::kLzRoleT, H->lz_G == 4 ? 8 : 16, H->lz_G == 4 ? 4 : 3, H->lz_cmax, H->lz_meta,
+                H->lz_rec);
+            BZ_LAUNCHED(H);
+        }
     }
     {
         ProfScope ps(H, 2, s);

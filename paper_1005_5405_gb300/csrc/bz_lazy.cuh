@@ -241,6 +241,94 @@ __global__ void k_lz_lfill(int nt, int T, int osh, const ushort4 *__restrict__ q
     }
 }
 
+// Bank-aware order of the term records.  A collision thread reads the two
+// operands of its term with two 16-byte (G = 4) or 8-byte (G = 2) shared
+// loads; the loads of a warp are served nb = 8 (or 16) lanes at a time, and
+// lanes whose entries fall in the same bank group of the nb (entry index mod
+// nb) are served one after the other.  Within each destination segment of a
+// run the terms may come in any order, and the two operands of a term may be
+// swapped (the product is symmetric).  Position i of run tt has the target
+// group (i + tt) mod nb, so the targets of the nb lanes of a group differ at
+// every step; each term goes to the next free position whose target is the
+// group of one of its operands (that one read first), the others fill the
+// positions left.  One warp per run, its records staged in shared memory,
+// one lane per destination segment (nothing happens if a run is longer than
+// cmax).
+constexpr int kLzOrderWarps = 8;   // runs per CTA of k_lz_order (one warp each)
+__host__ __device__ inline size_t lz_order_smem(int cmax)
+{
+    return (sizeof(uint2) + sizeof(int)) * (size_t)kLzOrderWarps * (cmax + 1) + sizeof(int) * 16 * kLzOrderWarps * 32;
+}
+
+static __global__ void __launch_bounds__(kLzOrderWarps * 32)
+k_lz_order(int T, int nb, int osh, int cmax, const int *__restrict__ meta, uint2 *__restrict__ rec)
+{
+    extern __shared__ uint2 sbuf_raw[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tt = blockIdx.x * kLzOrderWarps + w;
+    const int C = meta[3];
+    if (tt >= T || C > cmax || meta[1]) return;
+    // Per warp: the run's records, its segment starts, and per lane the next
+    // free position of each target group.
+    uint2 *b = sbuf_raw + (size_t)w * (cmax + 1);
+    int *seg = reinterpret_cast<int *>(sbuf_raw + (size_t)kLzOrderWarps * (cmax + 1)) + w * (cmax + 1);
+    int *cur = reinterpret_cast<int *>(sbuf_raw + (size_t)kLzOrderWarps * (cmax + 1)) +
+               kLzOrderWarps * (cmax + 1) + threadIdx.x * 16;
+    for (int i = lane; i < C; i += 32) b[i] = rec[(int64_t)i * T + tt];
+    __syncwarp();
+    // Segments: up to a destination's last term or the run's end, before
+    // the padding (zero records, left as they are).
+    if (lane == 0) {
+        int n = 0, i = 0;
+        while (i < C && !(b[i].x == 0u && b[i].y == 0u)) {
+            seg[n++] = i;
+            int e = i;                      // the segment's last position (< C)
+            while (e + 1 < C && !(b[e].x & 1u) && !(b[e + 1].x == 0u && b[e + 1].y == 0u)) ++e;
+            i = e + 1;
+        }
+        seg[n] = i;
+        seg[cmax] = n;
+    }
+    __syncwarp();
+    const int nseg = seg[cmax], om = nb - 1;
+    for (int sg = lane; sg < nseg; sg += 32) {
+        const int s0 = seg[sg], s1 = seg[sg + 1] - 1;
+        const uint32_t last = b[s1].x & 1u;
+        for (int k = 0; k < nb; ++k) cur[k] = s0 + ((k - s0 - tt) & om);
+        int left = 0;                       // terms placed at no group position
+        for (int j = s0; j <= s1; ++j) {
+            uint2 r = b[j];
+            const int ga = (int)(((r.x & 0xFFFCu) >> osh) & (uint32_t)om);
+            const int gb = (int)(((r.x >> 16) >> osh) & (uint32_t)om);
+            const int pa = cur[ga], pb = cur[gb];
+            int p = -1;
+            if (pa <= s1 && (pa <= pb || pb > s1)) {
+                p = pa;
+                cur[ga] = pa + nb;
+            } else if (pb <= s1) {
+                p = pb;
+                cur[gb] = pb + nb;
+                r.x = (r.x >> 16) | ((r.x & 0xFFFCu) << 16);     // the operand on target first
+            }
+            r.x &= ~1u;
+            if (p < 0) {
+                b[s0 + left++] = r;                             // slots before j are free
+                continue;
+            }
+            if (p == s1) r.x |= last;
+            rec[(int64_t)p * T + tt] = r;
+        }
+        // The unplaced terms fill the positions no term took, in order.
+        int q = 0;
+        for (int k = 0; k < nb && q < left; ++k)
+            for (int p = cur[k]; p <= s1 && q < left; p += nb) {
+                uint2 r = b[s0 + q++];
+                if (p == s1) r.x |= last;
+                rec[(int64_t)p * T + tt] = r;
+            }
+    }
+}
+
 // ---------------------------------------------------------------------
 // Fallback when a step has more active nodes than mcap: the k_cell4 plan is
 // derived from the logical one, the input is corrected in place and mu_out
