@@ -126,6 +126,9 @@ struct bz_handle {
     uint2 *lz_rec = nullptr;
     int lz_mcap = 0, lz_G = 0, lz_T = 0, lz_grid = 0, lz_mprobe = 0;
     int lz_cmax = 0, lz_order_tpb = 0;     // bank-aware ordering of the term runs (1: on)
+    int lz_chunk = 0;                      // positions per chunk of the ordering
+    cudaStream_t lz_side = nullptr;        // the sample plan runs here, beside the walls
+    cudaEvent_t lz_fork = nullptr, lz_join = nullptr;
     size_t lz_smem = 0;
     float lz_e0[bzk::kLzX] = {};
 };
@@ -478,12 +481,19 @@ bz_status configure_lazy(bz_handle *H)
     }
     if (!ok) return BZ_OK;
     H->lz_mcap = mcap;
-    // Bank-aware ordering of the term runs: one thread per run with its
-    // records staged in shared memory.
+    // Bank-aware ordering of the term runs: one warp per phase group of
+    // runs, with their records staged in shared memory.
     H->lz_cmax = ((4 * nt + bzk::kLzRoleT - 1) / bzk::kLzRoleT + 7) / 8 * 8;
-    H->lz_order_tpb = bzk::lz_order_smem(H->lz_cmax) <= (size_t)H->smem_optin ? 1 : 0;
-    if (getenv("BZ_LAZY_NOORDER")) H->lz_order_tpb = 0;
-    if (H->lz_order_tpb > 0) BZ_CUDA(bz_allow_max_smem(bzk::k_lz_order, H->smem_optin));
+    {
+        const int nb = H->lz_G == 4 ? 8 : 16;
+        H->lz_chunk = std::min(H->lz_cmax, 64);
+        if (const char *c = getenv("BZ_LAZY_ORDER_CHUNK")) H->lz_chunk = std::max(8, std::min(H->lz_cmax, atoi(c)));
+        H->lz_order_tpb = H->lz_chunk <= 32767 &&
+                          bzk::lz_order_smem(H->lz_chunk, nb) <= (size_t)H->smem_optin ? 1 : 0;
+        if (getenv("BZ_LAZY_NOORDER")) H->lz_order_tpb = 0;
+        if (H->lz_order_tpb > 0)
+            BZ_CUDA(bz_allow_max_smem(nb == 8 ? bzk::k_lz_order<8> : bzk::k_lz_order<16>, H->smem_optin));
+    }
     BZ_TRY(dalloc(&H->lz_count, sizeof(int) * (size_t)nvt));
     BZ_TRY(dalloc(&H->lz_cursor, sizeof(int) * (size_t)nvt));
     BZ_TRY(dalloc(&H->lz_rowend, sizeof(int) * (size_t)nvt));
@@ -502,6 +512,15 @@ bz_status configure_lazy(bz_handle *H)
                     acc += axA[jx] * axA[jy] * axA[jz] * lz_monomial(k, axv[jx], axv[jy], axv[jz]);
         H->lz_e0[k] = (float)acc;
     }
+    {
+        // The plan is a chain of small latency-bound kernels: its blocks go
+        // first when the walls' blocks leave room.
+        int least = 0, greatest = 0;
+        BZ_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        BZ_CUDA(cudaStreamCreateWithPriority(&H->lz_side, cudaStreamNonBlocking, greatest));
+    }
+    BZ_CUDA(cudaEventCreateWithFlags(&H->lz_fork, cudaEventDisableTiming));
+    BZ_CUDA(cudaEventCreateWithFlags(&H->lz_join, cudaEventDisableTiming));
     H->lazy = true;
     return BZ_OK;
 }
@@ -509,7 +528,10 @@ bz_status configure_lazy(bz_handle *H)
 // One fused step on the active-node path: walls (applying the input's
 // pending corrections), the sample set, its compact form and scatter list,
 // the per-cell kernel, and the k_cell4 fallback that runs only when the step
-// has more active nodes than the compact arrays hold.
+// has more active nodes than the compact arrays hold.  The sample plan
+// depends on the step counter only, so it runs on a side stream while the
+// walls run (after everything before the step on s: the last step's kernel
+// reads the plan's buffers), and the per-cell kernel waits for both.
 bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true)
 {
     const Geo &g = H->g;
@@ -518,41 +540,49 @@ bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true)
     const int in = H->cur, out = in ^ 1;
     float *hin = (float *)H->h[in];
     float *hout = (float *)H->h[out];
+    BZ_CUDA(cudaEventRecord(H->lz_fork, s));
+    BZ_CUDA(cudaStreamWaitEvent(H->lz_side, H->lz_fork, 0));
+    const int pb = 256, pg = (g.nt + pb - 1) / pb;
+    {
+        const cudaStream_t sp = H->lz_side;
+        ProfScope ps(H, 1, sp);
+        bzk::k_plan<float, int><<<pg, pb, 0, sp>>>(gl, H->d_step, H->lz_idx, H->lz_pa, nullptr,
+                                                  H->stats);
+        BZ_LAUNCHED(H);
+        bzk::k_lz_mark<<<pg, pb, 0, sp>>>(g.nt, H->lz_idx, H->lz_flag);
+        BZ_LAUNCHED(H);
+        bzk::k_lz_scan<<<1, 1024, 0, sp>>>(g.nvt, H->lz_mcap, H->lz_flag, H->lz_cidx, H->lz_act,
+                                          H->lz_mask, H->lz_wpre, H->lz_meta, H->stats);
+        BZ_LAUNCHED(H);
+        bzk::k_lz_remap<<<pg, pb, 0, sp>>>(g.nt, H->lz_idx, H->lz_cidx, H->lz_qc, H->lz_count);
+        BZ_LAUNCHED(H);
+        bzk::k_lz_lscan<<<1, 1024, 0, sp>>>(bzk::kLzRoleT, H->lz_G == 4 ? 4 : 3, H->lz_count,
+                                           H->lz_cursor, H->lz_rowend,
+                                           H->lz_meta, H->lz_rec, H->lz_dest0);
+        BZ_LAUNCHED(H);
+        bzk::k_lz_lfill<<<pg, pb, 0, sp>>>(g.nt, bzk::kLzRoleT, H->lz_G == 4 ? 4 : 3, H->lz_qc, H->lz_pa,
+                                          H->lz_cursor, H->lz_rowend, H->lz_meta, H->lz_rec,
+                                          H->lz_dest0);
+        BZ_LAUNCHED(H);
+        if (H->lz_order_tpb > 0) {
+            const int nch = (H->lz_cmax + H->lz_chunk - 1) / H->lz_chunk;
+            if (H->lz_G == 4)
+                bzk::k_lz_order<8><<<dim3(bzk::kLzRoleT / 8, nch), 32, bzk::lz_order_smem(H->lz_chunk, 8), sp>>>(
+                    bzk::kLzRoleT, H->lz_cmax, H->lz_chunk, H->lz_meta, H->lz_rec);
+            else
+                bzk::k_lz_order<16><<<dim3(bzk::kLzRoleT / 16, nch), 32, bzk::lz_order_smem(H->lz_chunk, 16), sp>>>(
+                    bzk::kLzRoleT, H->lz_cmax, H->lz_chunk, H->lz_meta, H->lz_rec);
+            BZ_LAUNCHED(H);
+        }
+    }
+    BZ_CUDA(cudaEventRecord(H->lz_join, H->lz_side));
     {
         ProfScope ps(H, 0, s);
         bzk::k_walls<float><<<g.nfaces, 256, 0, s>>>(g, H->d_step, hin, (float *)H->ghost, H->nw,
                                                      nullptr, H->mu[in]);
         BZ_LAUNCHED(H);
     }
-    const int pb = 256, pg = (g.nt + pb - 1) / pb;
-    {
-        ProfScope ps(H, 1, s);
-        bzk::k_plan<float, int><<<pg, pb, 0, s>>>(gl, H->d_step, H->lz_idx, H->lz_pa, nullptr,
-                                                  H->stats);
-        BZ_LAUNCHED(H);
-        bzk::k_lz_mark<<<pg, pb, 0, s>>>(g.nt, H->lz_idx, H->lz_flag);
-        BZ_LAUNCHED(H);
-        bzk::k_lz_scan<<<1, 1024, 0, s>>>(g.nvt, H->lz_mcap, H->lz_flag, H->lz_cidx, H->lz_act,
-                                          H->lz_mask, H->lz_wpre, H->lz_meta, H->stats);
-        BZ_LAUNCHED(H);
-        bzk::k_lz_remap<<<pg, pb, 0, s>>>(g.nt, H->lz_idx, H->lz_cidx, H->lz_qc, H->lz_count);
-        BZ_LAUNCHED(H);
-        bzk::k_lz_lscan<<<1, 1024, 0, s>>>(bzk::kLzRoleT, H->lz_G == 4 ? 4 : 3, H->lz_count,
-                                           H->lz_cursor, H->lz_rowend,
-                                           H->lz_meta, H->lz_rec, H->lz_dest0);
-        BZ_LAUNCHED(H);
-        bzk::k_lz_lfill<<<pg, pb, 0, s>>>(g.nt, bzk::kLzRoleT, H->lz_G == 4 ? 4 : 3, H->lz_qc, H->lz_pa,
-                                          H->lz_cursor, H->lz_rowend, H->lz_meta, H->lz_rec,
-                                          H->lz_dest0);
-        BZ_LAUNCHED(H);
-        if (H->lz_order_tpb > 0) {
-            bzk::k_lz_order<<<(bzk::kLzRoleT + bzk::kLzOrderWarps - 1) / bzk::kLzOrderWarps,
-                              bzk::kLzOrderWarps * 32, bzk::lz_order_smem(H->lz_cmax), s>>>(
-                bzk::kLzRoleT, H->lz_G == 4 ? 8 : 16, H->lz_G == 4 ? 4 : 3, H->lz_cmax, H->lz_meta,
-                H->lz_rec);
-            BZ_LAUNCHED(H);
-        }
-    }
+    BZ_CUDA(cudaStreamWaitEvent(s, H->lz_join, 0));
     {
         ProfScope ps(H, 2, s);
         bzk::LzArgs a{};
@@ -783,6 +813,9 @@ void release(bz_handle *H)
     for (auto &g : H->graph)
         if (g) cudaGraphExecDestroy(g);
     if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
+    if (H->lz_side) cudaStreamDestroy(H->lz_side);
+    if (H->lz_fork) cudaEventDestroy(H->lz_fork);
+    if (H->lz_join) cudaEventDestroy(H->lz_join);
     void *ptrs[] = {H->d_step, H->sc_count, H->sc_cursor, H->sc_meta, H->sc_ent, H->prof_clk, H->h[0], H->h[1], H->ht, H->pidx, H->pa, H->ghost, H->nw, H->shear,
                     H->mom, H->gw_global, H->stats, H->flag, H->axv, H->axA, H->profile};
     for (void *p : ptrs)

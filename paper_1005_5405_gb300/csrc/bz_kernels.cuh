@@ -408,37 +408,48 @@ __device__ __forceinline__ void walls_face(const Geo &g, int64_t step, const R *
     const R ns = (R)F.nsign;
     // Outgoing flux sum_{v_n<0} |v_n| w_j h_j and, on the lid, the cell part
     // of the shear, sum_{v_y>0} w_j v_x v_y h_j (per-thread sums in the state
-    // precision, combined in double).
+    // precision, combined in double).  Threads take the pairs of the other
+    // two axes (z fastest, so their loads are adjacent) and loop over the
+    // normal axis, skipping its incoming half.
     R acc[2] = {R(0), R(0)};
-    for (int j = threadIdx.x; j < g.nvt; j += blockDim.x) {
-        int jx = j / N2, jy = (j / N) % N, jz = j % N;
-        R vx = sv[jx], vy = sv[jy];
-        R vn = (F.nax == 0 ? vx : vy) * ns;
-        if (vn < R(0)) {
-            R w = sA[jx] * sA[jy] * sA[jz];
-            R hv = hc[j];
+    const R eps = (R)g.eps;
+    for (int q = threadIdx.x; q < N2; q += blockDim.x) {
+        const int qa = q / N, jz = q - qa * N;   // (jy, jz) on side walls, (jx, jz) on bottom and lid
+        const R vz = sv[jz], Az = sA[jz], va = sv[qa], Aa = sA[qa];
+        const int64_t base = F.nax == 0 ? (int64_t)q : (int64_t)qa * N2 + jz;
+        const int64_t stride = F.nax == 0 ? N2 : N;
+        for (int jn = 0; jn < N; ++jn) {
+            const R vnn = sv[jn];
+            const R vn = vnn * ns;
+            if (!(vn < R(0))) continue;
+            const R vx = F.nax == 0 ? vnn : va, vy = F.nax == 0 ? va : vnn;
+            const R w = sA[jn] * Aa * Az;
+            R hv = hc[base + jn * stride];
             if (mu) {
-                const R vz = sv[jz];
-                const R kap = m5[0] + m5[1] * vx + m5[2] * vy + m5[3] * vz +
-                              m5[4] * (vx * vx + vy * vy + vz * vz);
-                hv = hv + (R(1) + (R)g.eps * hv) * kap;
+                const R kap = m5[0] + m5[1] * vx + m5[2] * vy + m5[3] * vz + m5[4] * (vx * vx + vy * vy + vz * vz);
+                hv = hv + (R(1) + eps * hv) * kap;
             }
             acc[0] -= vn * w * hv;
             if (lid) acc[1] += w * vx * vy * hv;
         }
     }
     block_reduce<2, R>(acc, red, tot);
-    if (threadIdx.x == 0) {
-        // D_in = sum_{v_n>0} v_n dV Phi_w(v_j), separable in the three axes.
+    if (threadIdx.x < 32) {
+        // D_in = sum_{v_n>0} v_n dV Phi_w(v_j), separable in the three axes
+        // (the tangential factor summed by one warp).
         double tsum = 0.0;
-        for (int jt = 0; jt < N; ++jt) {
-            double d = g.axv[jt] - F.U;
+        for (int jt = threadIdx.x; jt < N; jt += 32) {
+            const double d = g.axv[jt] - F.U;
             tsum += (g.axd ? g.axd[jt] : g.dv) * 0.5641895835477563 * exp(-d * d);
         }
-        double din = g.hn * tsum * g.zsum;
-        double nw = (g.cout + g.eps * tot[0]) / din;
-        *snw = nw;
-        if (nw_out) nw_out[f] = nw;
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) tsum += __shfl_xor_sync(0xFFFFFFFFu, tsum, o);
+        if (threadIdx.x == 0) {
+            const double din = g.hn * tsum * g.zsum;
+            const double nw = (g.cout + g.eps * tot[0]) / din;
+            *snw = nw;
+            if (nw_out) nw_out[f] = nw;
+        }
     }
     __syncthreads();
     const double nw = *snw, lnw = log(nw), U = F.U;
@@ -448,16 +459,21 @@ __device__ __forceinline__ void walls_face(const Geo &g, int64_t step, const R *
         double gh = expm1(lnw + 2.0 * vt * U - U * U) / g.eps;
         ghost[f * N + jt] = (R)gh;
     }
-    if (lid && shear && threadIdx.x == 0) {
-        // Emitted part: sum over v_y < 0 of w v_x v_y h_w(jx), separable.
+    if (lid && shear && threadIdx.x < 32) {
+        // Emitted part: sum over v_y < 0 of w v_x v_y h_w(jx), separable
+        // (each factor summed by one warp).
         double sx = 0.0, sy = 0.0;
-        for (int jx = 0; jx < N; ++jx) {
-            double gh = expm1(lnw + 2.0 * g.axv[jx] * U - U * U) / g.eps;
+        for (int jx = threadIdx.x; jx < N; jx += 32) {
+            const double gh = expm1(lnw + 2.0 * g.axv[jx] * U - U * U) / g.eps;
             sx += g.axA[jx] * g.axv[jx] * gh;
+            if (g.axv[jx] < 0.0) sy += g.axA[jx] * g.axv[jx];
         }
-        for (int jy = 0; jy < N; ++jy)
-            if (g.axv[jy] < 0.0) sy += g.axA[jy] * g.axv[jy];
-        shear[f - 2 * g.ny - g.nx] = 2.0 * (tot[1] + sx * sy * g.zsum);
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            sx += __shfl_xor_sync(0xFFFFFFFFu, sx, o);
+            sy += __shfl_xor_sync(0xFFFFFFFFu, sy, o);
+        }
+        if (threadIdx.x == 0) shear[f - 2 * g.ny - g.nx] = 2.0 * (tot[1] + sx * sy * g.zsum);
     }
     __syncthreads();
 }

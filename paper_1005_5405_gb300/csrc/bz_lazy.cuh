@@ -38,6 +38,8 @@
 
 #include "bz_cell4.cuh"
 
+#include <type_traits>
+
 namespace bzk {
 
 constexpr int kLzMono = 26;        // monomial sums per cell
@@ -243,90 +245,193 @@ __global__ void k_lz_lfill(int nt, int T, int osh, const ushort4 *__restrict__ q
 
 // Bank-aware order of the term records.  A collision thread reads the two
 // operands of its term with two 16-byte (G = 4) or 8-byte (G = 2) shared
-// loads; the loads of a warp are served nb = 8 (or 16) lanes at a time, and
-// lanes whose entries fall in the same bank group of the nb (entry index mod
-// nb) are served one after the other.  Within each destination segment of a
-// run the terms may come in any order, and the two operands of a term may be
-// swapped (the product is symmetric).  Position i of run tt has the target
-// group (i + tt) mod nb, so the targets of the nb lanes of a group differ at
-// every step; each term goes to the next free position whose target is the
-// group of one of its operands (that one read first), the others fill the
-// positions left.  One warp per run, its records staged in shared memory,
-// one lane per destination segment (nothing happens if a run is longer than
-// cmax).
-constexpr int kLzOrderWarps = 8;   // runs per CTA of k_lz_order (one warp each)
-__host__ __device__ inline size_t lz_order_smem(int cmax)
+// loads.  The loads of a warp are served NB = 8 (or 16) lanes at a time, one
+// wavefront per distinct entry in the busiest of the NB bank groups (entry
+// index mod NB), so the NB runs that one phase reads together are ordered
+// jointly.  Terms move only inside their destination segment of a run, and
+// the two operands of a term may be swapped (the product is symmetric).
+// Position by position, the runs choose in order of how few choices they
+// have left (the one with the fewest remaining terms in its segment first;
+// padding, which reads entry 0, before all): each takes the remaining term
+// of its segment, and the operand order, whose first and second operands
+// meet the fewest bank groups already holding another entry at that
+// position.  A run decides position p once it has decided p - 1 and every
+// run before it at p has decided p.  The positions are cut into chunks
+// ordered independently (a segment that crosses a chunk's end is cut
+// there).  One warp per phase group and chunk: NB runs x 32 / NB lanes that
+// scan a run's choices.  Nothing happens if a run is longer than cmax.
+__host__ __device__ inline size_t lz_order_smem(int chunk, int nb)
 {
-    return (sizeof(uint2) + sizeof(int)) * (size_t)kLzOrderWarps * (cmax + 1) + sizeof(int) * 16 * kLzOrderWarps * 32;
+    // records (rows padded to an odd length), taken entries, segment ends,
+    // run order masks, decided masks
+    const size_t m = nb == 8 ? 1 : 2;
+    return (size_t)nb * (chunk + 1) * sizeof(uint2) + (size_t)chunk * nb * (sizeof(uint32_t) + sizeof(uint16_t) + m) +
+           (size_t)chunk * m + 32;
 }
 
-static __global__ void __launch_bounds__(kLzOrderWarps * 32)
-k_lz_order(int T, int nb, int osh, int cmax, const int *__restrict__ meta, uint2 *__restrict__ rec)
+// w[g] of a register row, g < NB (a tree of selects).
+template <int NB> __device__ __forceinline__ uint32_t lz_row_get(const uint32_t (&w)[NB], uint32_t g)
 {
-    extern __shared__ uint2 sbuf_raw[];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tt = blockIdx.x * kLzOrderWarps + w;
-    const int C = meta[3];
-    if (tt >= T || C > cmax || meta[1]) return;
-    // Per warp: the run's records, its segment starts, and per lane the next
-    // free position of each target group.
-    uint2 *b = sbuf_raw + (size_t)w * (cmax + 1);
-    int *seg = reinterpret_cast<int *>(sbuf_raw + (size_t)kLzOrderWarps * (cmax + 1)) + w * (cmax + 1);
-    int *cur = reinterpret_cast<int *>(sbuf_raw + (size_t)kLzOrderWarps * (cmax + 1)) +
-               kLzOrderWarps * (cmax + 1) + threadIdx.x * 16;
-    for (int i = lane; i < C; i += 32) b[i] = rec[(int64_t)i * T + tt];
+    uint32_t t[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) t[k] = w[k];
+#pragma unroll
+    for (int sft = NB / 2; sft >= 1; sft >>= 1)
+#pragma unroll
+        for (int k = 0; k < sft; ++k) t[k] = (g & sft) ? t[k + sft] : t[k];
+    return t[0];
+}
+
+template <int NB>
+__global__ void __launch_bounds__(32) k_lz_order(int T, int cmax, int chunk, const int *__restrict__ meta,
+                                                 uint2 *__restrict__ rec)
+{
+    static_assert(NB == 8 || NB == 16, "phase width");
+    constexpr int H = 32 / NB;                       // lanes per run
+    constexpr int OSH = NB == 8 ? 4 : 3;             // log2 of the entry size
+    constexpr uint16_t kNone = 0xFFFF;
+    using Mask = typename std::conditional<NB == 8, uint8_t, uint16_t>::type;
+    extern __shared__ __align__(16) unsigned char osm[];
+    const int lane = threadIdx.x, l = lane / H, h = lane - l * H;
+    const int tt = blockIdx.x * NB + l;
+    const int C = meta[3], c0 = blockIdx.y * chunk;
+    if (C > cmax || meta[1] || blockIdx.x * NB + NB > T || c0 >= C) return;
+    const int L = min(chunk, C - c0), SP = chunk + 1;
+    uint2 *b = reinterpret_cast<uint2 *>(osm);                   // [NB][SP] working copies of the runs
+    uint32_t *u = reinterpret_cast<uint32_t *>(b + NB * SP);     // [chunk][NB] entries taken: first | second << 16
+    uint16_t *seg = reinterpret_cast<uint16_t *>(u + chunk * NB); // [NB][chunk] segment end | last << 15
+    Mask *bm = reinterpret_cast<Mask *>(seg + NB * chunk);       // [NB][chunk] runs that choose before this one
+    Mask *dec = bm + NB * chunk;                                // [chunk] runs that have decided p
+    for (int i = lane; i < NB * L; i += 32) {
+        const int r = i / L, p = i - r * L;
+        b[r * SP + p] = rec[(int64_t)(c0 + p) * T + blockIdx.x * NB + r];
+    }
+    for (int i = lane; i < NB * L; i += 32) u[i] = 0xFFFFFFFFu;
     __syncwarp();
-    // Segments: up to a destination's last term or the run's end, before
-    // the padding (zero records, left as they are).
-    if (lane == 0) {
-        int n = 0, i = 0;
-        while (i < C && !(b[i].x == 0u && b[i].y == 0u)) {
-            seg[n++] = i;
-            int e = i;                      // the segment's last position (< C)
-            while (e + 1 < C && !(b[e].x & 1u) && !(b[e + 1].x == 0u && b[e + 1].y == 0u)) ++e;
+    // Segments: up to a destination's last term or the chunk's end, before
+    // the padding (zero records).
+    if (h == 0) {
+        const uint2 *br = b + l * SP;
+        uint16_t *se = seg + l * chunk;
+        int i = 0;
+        while (i < L && !(br[i].x == 0u && br[i].y == 0u)) {
+            int e = i;                                // the segment's last position (< L)
+            while (e + 1 < L && !(br[e].x & 1u) && !(br[e + 1].x == 0u && br[e + 1].y == 0u)) ++e;
+            const uint16_t v = (uint16_t)(e | (br[e].x & 1u) << 15);
+            for (int p = i; p <= e; ++p) se[p] = v;
             i = e + 1;
         }
-        seg[n] = i;
-        seg[cmax] = n;
+        for (int p = i; p < L; ++p) se[p] = kNone;
     }
     __syncwarp();
-    const int nseg = seg[cmax], om = nb - 1;
-    for (int sg = lane; sg < nseg; sg += 32) {
-        const int s0 = seg[sg], s1 = seg[sg + 1] - 1;
-        const uint32_t last = b[s1].x & 1u;
-        for (int k = 0; k < nb; ++k) cur[k] = s0 + ((k - s0 - tt) & om);
-        int left = 0;                       // terms placed at no group position
-        for (int j = s0; j <= s1; ++j) {
-            uint2 r = b[j];
-            const int ga = (int)(((r.x & 0xFFFCu) >> osh) & (uint32_t)om);
-            const int gb = (int)(((r.x >> 16) >> osh) & (uint32_t)om);
-            const int pa = cur[ga], pb = cur[gb];
-            int p = -1;
-            if (pa <= s1 && (pa <= pb || pb > s1)) {
-                p = pa;
-                cur[ga] = pa + nb;
-            } else if (pb <= s1) {
-                p = pb;
-                cur[gb] = pb + nb;
-                r.x = (r.x >> 16) | ((r.x & 0xFFFCu) << 16);     // the operand on target first
-            }
-            r.x &= ~1u;
-            if (p < 0) {
-                b[s0 + left++] = r;                             // slots before j are free
-                continue;
-            }
-            if (p == s1) r.x |= last;
-            rec[(int64_t)p * T + tt] = r;
+    // Per position: the order of the runs (remaining choices, then run
+    // index); padding is decided from the start and reads entry 0.
+    for (int p = lane; p < L; p += 32) {
+        int sz[NB];
+        Mask d = 0;
+#pragma unroll
+        for (int r = 0; r < NB; ++r) {
+            const uint16_t v = seg[r * chunk + p];
+            sz[r] = v == kNone ? 0 : (v & 0x7FFF) - p + 1;
+            if (v == kNone) d |= (Mask)(1u << r);
         }
-        // The unplaced terms fill the positions no term took, in order.
-        int q = 0;
-        for (int k = 0; k < nb && q < left; ++k)
-            for (int p = cur[k]; p <= s1 && q < left; p += nb) {
-                uint2 r = b[s0 + q++];
-                if (p == s1) r.x |= last;
-                rec[(int64_t)p * T + tt] = r;
-            }
+        if (d) u[p * NB] = 0u;
+        dec[p] = d;
+#pragma unroll
+        for (int r = 0; r < NB; ++r) {
+            Mask m = 0;
+#pragma unroll
+            for (int r2 = 0; r2 < NB; ++r2)
+                if (sz[r2] < sz[r] || (sz[r2] == sz[r] && r2 < r)) m |= (Mask)(1u << r2);
+            bm[r * chunk + p] = m;
+        }
     }
+    __syncwarp();
+    uint2 *bl = b + l * SP;
+    const uint16_t *sl = seg + l * chunk;
+    const Mask *bml = bm + l * chunk;
+    int p = 0;                                        // this run's next position in the chunk
+    uint16_t sv = L > 0 ? sl[0] : kNone;              // its segment: end | last << 15, kNone: padding
+    // Every step some run is ready (the first, at the smallest undecided
+    // position, in that position's order), so NB * L steps always suffice.
+    for (int step = 0; step < NB * L; ++step) {
+        const bool active = p < L && sv != kNone;
+        if (!__any_sync(0xFFFFFFFFu, active)) break;
+        bool ready = false;
+        Mask dp = 0;
+        if (active) {
+            const Mask need = bml[p];
+            dp = dec[p];
+            ready = (Mask)(dp & need) == need;
+        }
+        __syncwarp();                                 // the reads above precede this step's writes
+        uint32_t best = 0xFFFFFFFFu;                  // cost << 24 | swap << 23 | position
+        const int s1 = sv & 0x7FFF;
+        uint32_t w[NB];
+        if (ready) {
+            const uint4 *ur = reinterpret_cast<const uint4 *>(u + p * NB);
+#pragma unroll
+            for (int k = 0; k < NB / 4; ++k) {
+                const uint4 q = ur[k];
+                w[4 * k] = q.x;
+                w[4 * k + 1] = q.y;
+                w[4 * k + 2] = q.z;
+                w[4 * k + 3] = q.w;
+            }
+            for (int j0 = p + h; j0 <= s1; j0 += 4 * H) {
+                uint32_t xs[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) xs[k] = j0 + k * H <= s1 ? bl[j0 + k * H].x : 0u;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int j = j0 + k * H;
+                    if (j > s1) break;
+                    const uint32_t ea = (xs[k] & 0xFFFCu) >> OSH, eb = (xs[k] >> 16) >> OSH;
+                    const uint32_t wa = lz_row_get<NB>(w, ea & (NB - 1)), wb = lz_row_get<NB>(w, eb & (NB - 1));
+                    const uint32_t a1 = wa & 0xFFFFu, a2 = wa >> 16, b1 = wb & 0xFFFFu, b2 = wb >> 16;
+                    const uint32_t cn = (a1 != kNone && a1 != ea) + (b2 != kNone && b2 != eb);
+                    const uint32_t cs = (b1 != kNone && b1 != eb) + (a2 != kNone && a2 != ea);
+                    const uint32_t key = cs < cn ? (cs << 24 | 1u << 23 | (uint32_t)j) : (cn << 24 | (uint32_t)j);
+                    best = min(best, key);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 1; o < H; o <<= 1) best = min(best, __shfl_xor_sync(0xFFFFFFFFu, best, o));
+        if (ready && h == 0) {
+            const int j = (int)(best & 0xFFFFu);
+            uint2 r = bl[j];
+            const uint2 front = bl[p];
+            r.x &= ~1u;
+            if (best >> 23 & 1u) r.x = (r.x >> 16) | ((r.x & 0xFFFCu) << 16);
+            if (p == s1) r.x |= (uint32_t)(sv >> 15);
+            rec[(int64_t)(c0 + p) * T + tt] = r;
+            bl[j] = front;                            // the front term fills the hole
+            const uint32_t e1 = (r.x & 0xFFFCu) >> OSH, e2 = (r.x >> 16) >> OSH;
+            const uint32_t g1 = e1 & (NB - 1), g2 = e2 & (NB - 1);
+            uint32_t v1 = lz_row_get<NB>(w, g1);
+            if ((v1 & 0xFFFFu) == kNone) v1 = (v1 & 0xFFFF0000u) | e1;
+            uint32_t v2 = g2 == g1 ? v1 : lz_row_get<NB>(w, g2);
+            if ((v2 >> 16) == kNone) v2 = (v2 & 0xFFFFu) | e2 << 16;
+            u[p * NB + g1] = g2 == g1 ? v2 : v1;
+            if (g2 != g1) u[p * NB + g2] = v2;
+            dec[p] = (Mask)(dp | (1u << l));
+        }
+        __syncwarp();
+        if (ready) {
+            ++p;
+            if (p > s1) sv = p < L ? sl[p] : kNone;
+        }
+    }
+    // Positions left undecided (none when the loop ran out normally) keep
+    // their remaining terms, with the destination bit at the segment end.
+    if (h == 0)
+        for (; p < L && sl[p] != kNone; ++p) {
+            uint2 r = bl[p];
+            r.x &= ~1u;
+            if (p == (sl[p] & 0x7FFF)) r.x |= (uint32_t)(sl[p] >> 15);
+            rec[(int64_t)(c0 + p) * T + tt] = r;
+        }
 }
 
 // ---------------------------------------------------------------------
