@@ -546,7 +546,8 @@ bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true)
     {
         const cudaStream_t sp = H->lz_side;
         ProfScope ps(H, 1, sp);
-        bzk::k_plan<float, int><<<pg, pb, 0, sp>>>(gl, H->d_step, H->lz_idx, H->lz_pa, nullptr,
+        // 64-thread blocks spread the FP64 sampling over every SM.
+        bzk::k_plan<float, int><<<(g.nt + 63) / 64, 64, 0, sp>>>(gl, H->d_step, H->lz_idx, H->lz_pa, nullptr,
                                                   H->stats);
         BZ_LAUNCHED(H);
         bzk::k_lz_mark<<<pg, pb, 0, sp>>>(g.nt, H->lz_idx, H->lz_flag);

@@ -86,6 +86,9 @@ static __global__ void k_lz_mark(int nt, const int4 *__restrict__ idx, int *__re
 // Compact numbering of the marked nodes (ascending node order), one CTA of
 // 1024 threads: cidx[j] = m, act[m] = j, the bit mask of marked nodes and, per
 // 32-node word, the compact index of its first marked node.  Clears the flags.
+// Each warp forms 32 mask words from coalesced flag loads (one ballot per
+// word), lane k keeping word k; warp and block scans of the word counts
+// give the compact indices.
 // stats (nullable): [5] counts steps whose active set exceeded mcap.
 static __global__ void __launch_bounds__(1024) k_lz_scan(int nvt, int mcap, int *__restrict__ flag,
                                                  int *__restrict__ cidx, int *__restrict__ act,
@@ -93,44 +96,62 @@ static __global__ void __launch_bounds__(1024) k_lz_scan(int nvt, int mcap, int 
                                                  int *__restrict__ meta,
                                                  unsigned long long *__restrict__ stats = nullptr)
 {
-    __shared__ int part[1024];
-    const int t = threadIdx.x, nw = nvt / 32, per = (nw + 1023) / 1024;
-    const int w0 = min(nw, t * per), w1 = min(nw, w0 + per);
-    int cnt = 0;
-    for (int w = w0; w < w1; ++w) {
+    __shared__ int wsum[32];
+    __shared__ int btot;
+    const int t = threadIdx.x, lane = t & 31, wp = t >> 5, nw = nvt / 32;
+    int carry = 0;
+    for (int b0 = 0; b0 < nw; b0 += 1024) {
+        const int base = b0 + wp * 32;                // this warp's 32 words
         uint32_t bits = 0;
-        for (int b = 0; b < 32; ++b) bits |= (flag[w * 32 + b] ? 1u : 0u) << b;
-        mask[w] = bits;
-        cnt += __popc(bits);
-    }
-    part[t] = cnt;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-        const int v = t >= off ? part[t - off] : 0;
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            const int w = base + k;
+            const bool set = w < nw && flag[w * 32 + lane] != 0;
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, set);
+            if (lane == k) bits = bal;
+        }
+        const int w = base + lane, cnt = __popc(bits);
+        int inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        if (lane == 31) wsum[wp] = inc;
         __syncthreads();
-        part[t] += v;
+        if (wp == 0) {
+            const int x0 = wsum[lane];
+            int x = x0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xFFFFFFFFu, x, o);
+                if (lane >= o) x += v;
+            }
+            wsum[lane] = x - x0;
+            if (lane == 31) btot = x;
+        }
         __syncthreads();
-    }
-    int run = part[t] - cnt;
-    for (int w = w0; w < w1; ++w) {
-        const uint32_t bits = mask[w];
-        wpre[w] = run;
-        for (int b = 0; b < 32; ++b) {
-            const int j = w * 32 + b;
-            if (bits >> b & 1u) {
+        int run = carry + wsum[wp] + inc - cnt;
+        carry += btot;
+        __syncthreads();                              // wsum and btot are reused
+        if (w < nw) {
+            mask[w] = bits;
+            wpre[w] = run;
+            for (uint32_t bb = bits; bb; bb &= bb - 1) {
+                const int j = w * 32 + __ffs(bb) - 1;
                 cidx[j] = run;
                 act[run] = j;
+                flag[j] = 0;
                 ++run;
             }
-            flag[j] = 0;
         }
     }
-    if (t == 1023) {
-        meta[0] = part[1023];
-        meta[1] = part[1023] > mcap ? 1 : 0;
+    if (t == 0) {
+        meta[0] = carry;
+        meta[1] = carry > mcap ? 1 : 0;
         if (stats) {
-            if (part[1023] > mcap) atomicAdd(stats + 5, 1ull);
-            stats[6] = (unsigned long long)part[1023];
+            if (carry > mcap) atomicAdd(stats + 5, 1ull);
+            stats[6] = (unsigned long long)carry;
         }
     }
 }
@@ -269,19 +290,6 @@ __host__ __device__ inline size_t lz_order_smem(int chunk, int nb)
            (size_t)chunk * m + 32;
 }
 
-// w[g] of a register row, g < NB (a tree of selects).
-template <int NB> __device__ __forceinline__ uint32_t lz_row_get(const uint32_t (&w)[NB], uint32_t g)
-{
-    uint32_t t[NB];
-#pragma unroll
-    for (int k = 0; k < NB; ++k) t[k] = w[k];
-#pragma unroll
-    for (int sft = NB / 2; sft >= 1; sft >>= 1)
-#pragma unroll
-        for (int k = 0; k < sft; ++k) t[k] = (g & sft) ? t[k + sft] : t[k];
-    return t[0];
-}
-
 template <int NB>
 __global__ void __launch_bounds__(32) k_lz_order(int T, int cmax, int chunk, const int *__restrict__ meta,
                                                  uint2 *__restrict__ rec)
@@ -302,8 +310,9 @@ __global__ void __launch_bounds__(32) k_lz_order(int T, int cmax, int chunk, con
     uint16_t *seg = reinterpret_cast<uint16_t *>(u + chunk * NB); // [NB][chunk] segment end | last << 15
     Mask *bm = reinterpret_cast<Mask *>(seg + NB * chunk);       // [NB][chunk] runs that choose before this one
     Mask *dec = bm + NB * chunk;                                // [chunk] runs that have decided p
-    for (int i = lane; i < NB * L; i += 32) {
-        const int r = i / L, p = i - r * L;
+#pragma unroll 4
+    for (int i = lane; i < NB * L; i += 32) {       // the NB runs of a position are adjacent in rec
+        const int p = i / NB, r = i - p * NB;
         b[r * SP + p] = rec[(int64_t)(c0 + p) * T + blockIdx.x * NB + r];
     }
     for (int i = lane; i < NB * L; i += 32) u[i] = 0xFFFFFFFFu;
@@ -367,28 +376,23 @@ __global__ void __launch_bounds__(32) k_lz_order(int T, int cmax, int chunk, con
         __syncwarp();                                 // the reads above precede this step's writes
         uint32_t best = 0xFFFFFFFFu;                  // cost << 24 | swap << 23 | position
         const int s1 = sv & 0x7FFF;
-        uint32_t w[NB];
+        const uint32_t *row = u + p * NB;            // entries taken at p, by group
         if (ready) {
-            const uint4 *ur = reinterpret_cast<const uint4 *>(u + p * NB);
-#pragma unroll
-            for (int k = 0; k < NB / 4; ++k) {
-                const uint4 q = ur[k];
-                w[4 * k] = q.x;
-                w[4 * k + 1] = q.y;
-                w[4 * k + 2] = q.z;
-                w[4 * k + 3] = q.w;
-            }
             for (int j0 = p + h; j0 <= s1; j0 += 4 * H) {
-                uint32_t xs[4];
+                uint32_t xs[4], wa[4], wb[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) xs[k] = j0 + k * H <= s1 ? bl[j0 + k * H].x : 0u;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
+                    wa[k] = row[(xs[k] >> OSH) & (NB - 1)];
+                    wb[k] = row[(xs[k] >> (16 + OSH)) & (NB - 1)];
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
                     const int j = j0 + k * H;
                     if (j > s1) break;
-                    const uint32_t ea = (xs[k] & 0xFFFCu) >> OSH, eb = (xs[k] >> 16) >> OSH;
-                    const uint32_t wa = lz_row_get<NB>(w, ea & (NB - 1)), wb = lz_row_get<NB>(w, eb & (NB - 1));
-                    const uint32_t a1 = wa & 0xFFFFu, a2 = wa >> 16, b1 = wb & 0xFFFFu, b2 = wb >> 16;
+                    const uint32_t ea = (xs[k] & 0xFFFCu) >> OSH, eb = xs[k] >> (16 + OSH);
+                    const uint32_t a1 = wa[k] & 0xFFFFu, a2 = wa[k] >> 16, b1 = wb[k] & 0xFFFFu, b2 = wb[k] >> 16;
                     const uint32_t cn = (a1 != kNone && a1 != ea) + (b2 != kNone && b2 != eb);
                     const uint32_t cs = (b1 != kNone && b1 != eb) + (a2 != kNone && a2 != ea);
                     const uint32_t key = cs < cn ? (cs << 24 | 1u << 23 | (uint32_t)j) : (cn << 24 | (uint32_t)j);
@@ -407,11 +411,11 @@ __global__ void __launch_bounds__(32) k_lz_order(int T, int cmax, int chunk, con
             if (p == s1) r.x |= (uint32_t)(sv >> 15);
             rec[(int64_t)(c0 + p) * T + tt] = r;
             bl[j] = front;                            // the front term fills the hole
-            const uint32_t e1 = (r.x & 0xFFFCu) >> OSH, e2 = (r.x >> 16) >> OSH;
+            const uint32_t e1 = (r.x & 0xFFFCu) >> OSH, e2 = r.x >> (16 + OSH);
             const uint32_t g1 = e1 & (NB - 1), g2 = e2 & (NB - 1);
-            uint32_t v1 = lz_row_get<NB>(w, g1);
+            uint32_t v1 = row[g1];
             if ((v1 & 0xFFFFu) == kNone) v1 = (v1 & 0xFFFF0000u) | e1;
-            uint32_t v2 = g2 == g1 ? v1 : lz_row_get<NB>(w, g2);
+            uint32_t v2 = g2 == g1 ? v1 : row[g2];
             if ((v2 >> 16) == kNone) v2 = (v2 & 0xFFFFu) | e2 << 16;
             u[p * NB + g1] = g2 == g1 ? v2 : v1;
             if (g2 != g1) u[p * NB + g2] = v2;
@@ -1109,6 +1113,7 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
         swpre[w] = (uint16_t)a.wpre[w];
     }
     for (int m = t; m < M; m += kLzThreads) sact[m] = (uint16_t)a.act[m];
+    for (int i = t; i < 2 * kLzMaxG * kLzRoleWarps * 32; i += kLzThreads) (&H.dpart[0][0][0][0])[i] = 0.f;
     __syncthreads();
 
     // A streaming thread's quad.
@@ -1258,11 +1263,14 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
                     __syncwarp();
                     if (lane == 0)
                         lz_finish(g, a, cell_of(g, kc), H.fpart[fb][k][0], H.dpart[db][k][0], &fallback);
+                    __syncwarp();
+                    // The slots take the increment sums of a later group (atomically).
+                    for (int i = lane; i < kLzRoleWarps * 32; i += 32) (&H.dpart[db][k][0][0])[i] = 0.f;
                 }
             }
             if (clk && t == 0) a.clk[it * kClkPhases + 5] = clock64();
         } else if (it >= 1 && it <= nmine) {
-            const int tc = t - kLzRoleT, wc = warp - kLzRoleWarps, buf = (it - 1) & 1;
+            const int tc = t - kLzRoleT, buf = (it - 1) & 1;
             char *Ab = smem_raw + kLzAOff + buf * so.abytes;
             float *Af = reinterpret_cast<float *>(Ab);
             int ncell = 0, cg[G];
@@ -1328,18 +1336,29 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
                     lz_atomic_add(Bv + st.dest, st.acc);
                 }
             }
-            lz_role_bar(2);
             if (clk && tc == 0) a.clk[it * kClkPhases + 2] = clock64();
-
-            // ---- sums of the collision increment and h_c = h~ + dN / w on the
-            // active nodes, two cells at a time -------------------------------
+        }
+        // ---- sums of the collision increment and h_c = h~ + dN / w on the
+        // active nodes of group it - 1, two cells at a time, by both roles
+        // (the increments are complete after the barrier; each warp adds its
+        // partial sums to the slots of warp (warp mod 8)).
+        if (it >= 1 && it <= nmine) {
+            __syncthreads();
+            const int buf = (it - 1) & 1, u = t ^ kLzRoleT;
+            const float *Af = reinterpret_cast<const float *>(smem_raw + kLzAOff + buf * so.abytes);
+            int ncell = 0, cg[G];
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                cg[k] = H.cell[buf][k].x;
+                ncell += cg[k] >= 0 ? 1 : 0;
+            }
 #pragma unroll
             for (int k2 = 0; k2 < G; k2 += 2) {
                 float2 D2[32];
 #pragma unroll
                 for (int r = 0; r < 32; ++r) D2[r] = lz_zero2();
                 if (k2 < ncell) {
-                    for (int mm = tc; mm < M; mm += kLzRoleT) {
+                    for (int mm = u; mm < M; mm += kLzThreads) {
                         const int j = sact[mm], jxy = j / N;
                         const int jx = jxy / N, jyy = jxy - jx * N, jz = j - jxy * N;
                         const float2 d = *reinterpret_cast<const float2 *>(Bf + mm * G + k2);
@@ -1354,11 +1373,11 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
                     }
                 }
                 const float2 r = lz_warp_reduce_scatter2(D2);
-                H.dpart[buf][k2][wc][lane] = r.x;
-                H.dpart[buf][k2 + 1][wc][lane] = r.y;
+                atomicAdd(&H.dpart[buf][k2][warp & (kLzRoleWarps - 1)][lane], r.x);
+                atomicAdd(&H.dpart[buf][k2 + 1][warp & (kLzRoleWarps - 1)][lane], r.y);
             }
-            if (clk && tc == 0) a.clk[it * kClkPhases + 3] = clock64();
-            if (clk && tc == 0) a.clk[it * kClkPhases + 4] = clock64();
+            if (clk && t == kLzRoleT) a.clk[it * kClkPhases + 3] = clock64();
+            if (clk && t == kLzRoleT) a.clk[it * kClkPhases + 4] = clock64();
         }
         __syncthreads();
     }
