@@ -154,43 +154,56 @@ bz_status launch(bz_adj_scratch *a, const bzk::Geo &g0, int64_t step, const R *h
     };
     bzk::k_set_step<<<1, 1, 0, s>>>(a->step, step);
     cudaError_t e = check();
-    // Forward quantities of step n: wall densities and ghosts of h^n, the samples.
-    if (e == cudaSuccess) {
-        bzk::k_walls<R><<<g.nfaces, 256, 0, s>>>(g, a->step, hn, (R *)a->ghost, a->nw, nullptr);
-        e = check();
-    }
     const int pb = 256, pg = (g.nt + pb - 1) / pb;
     bool fast = false;
     if constexpr (sizeof(R) == 4) fast = a->fast;
+    // The fast path's plan depends on the step only: it runs on the side
+    // stream while the walls run (after everything before it on s).
+    const cudaStream_t sp = fast ? a->side : s;
+    if (fast && e == cudaSuccess) e = cudaEventRecord(a->fork, s);
+    if (fast && e == cudaSuccess) e = cudaStreamWaitEvent(sp, a->fork, 0);
     if (fast) {
         // FP32 quad kernel: plan in the shared-memory order and the
-        // destination-sorted scatter list, as the forward step builds them.
+        // destination-sorted scatter list, as the forward step builds them
+        // (64-thread blocks spread the FP64 sampling over every SM).
         bzk::Geo gs = g;
         gs.swz = 1;
         const ushort4 *pi = (const ushort4 *)a->pidx16;
         if (e == cudaSuccess) {
-            bzk::k_plan<float, uint16_t><<<pg, pb, 0, s>>>(
+            bzk::k_plan<float, uint16_t><<<(g.nt + 63) / 64, 64, 0, sp>>>(
                 gs, a->step, (ushort4 *)a->pidx16, (bzk::PlanA<float, uint16_t> *)a->pa16,
                 nullptr, nullptr);
             e = check();
         }
         // The forward list and the loss list of the transposed update.
-        if (e == cudaSuccess) e = cudaMemsetAsync(a->sc_count, 0, sizeof(int) * 2 * g.nvt, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(a->sc_count, 0, sizeof(int) * 2 * g.nvt, sp);
         if (e == cudaSuccess) {
-            bzk::k_adj_count2<<<pg, pb, 0, s>>>(g.nt, g.nvt, pi, a->sc_count);
+            bzk::k_adj_count2<<<pg, pb, 0, sp>>>(g.nt, g.nvt, pi, a->sc_count);
             e = check();
         }
         if (e == cudaSuccess) {
-            bzk::k_adj_scan2<<<2, 1024, 0, s>>>(g.nvt, a->threads, a->sc_count, a->sc_cursor,
-                                                a->sc_meta);
+            bzk::k_adj_scan2<<<2, 1024, 0, sp>>>(g.nvt, a->threads, a->sc_count, a->sc_cursor,
+                                                 a->sc_meta);
             e = check();
         }
         if (e == cudaSuccess) {
-            bzk::k_adj_fill2<<<pg, pb, 0, s>>>(g.nt, g.nvt, a->threads, pi,
-                                               (const bzk::PlanA<float, uint16_t> *)a->pa16,
-                                               a->sc_cursor, a->sc_meta, a->sc_ent, a->lrec);
+            bzk::k_adj_fill2<<<pg, pb, 0, sp>>>(g.nt, g.nvt, a->threads, pi,
+                                                (const bzk::PlanA<float, uint16_t> *)a->pa16,
+                                                a->sc_cursor, a->sc_meta, a->sc_ent, a->lrec);
             e = check();
         }
+        if (e == cudaSuccess) e = cudaEventRecord(a->join, sp);
+    }
+    // Forward quantities of step n: wall densities and ghosts of h^n.
+    if (e == cudaSuccess) {
+        bzk::k_walls<R><<<g.nfaces, 256, 0, s>>>(g, a->step, hn, (R *)a->ghost, a->nw, nullptr);
+        e = check();
+    }
+    if (fast && e == cudaSuccess) e = cudaStreamWaitEvent(s, a->join, 0);
+    if (fast) {
+        const ushort4 *pi = (const ushort4 *)a->pidx16;
+        bzk::Geo gs = g;
+        gs.swz = 1;
         if (e == cudaSuccess) {
             const bzk::Map4 m{a->map[0], a->map[1], a->map[2]};
             if (a->threads <= 512)
@@ -207,8 +220,8 @@ bz_status launch(bz_adj_scratch *a, const bzk::Geo &g0, int64_t step, const R *h
         }
     } else {
         if (e == cudaSuccess) {
-            bzk::k_plan<R, int><<<pg, pb, 0, s>>>(g, a->step, a->pidx,
-                                                  (bzk::PlanA<R, int> *)a->pa, nullptr, nullptr);
+            bzk::k_plan<R, int><<<(g.nt + 63) / 64, 64, 0, s>>>(g, a->step, a->pidx,
+                                                                (bzk::PlanA<R, int> *)a->pa, nullptr, nullptr);
             e = check();
         }
         if (e == cudaSuccess) {
@@ -255,6 +268,15 @@ bz_status bz_adj_prepare(bz_adj_scratch *a, const bzk::Geo &g, int dtype, int ns
     if (st == BZ_OK && !t.fast)
         st = dtype == BZ_F64 ? setup_generic<double>(&t, g, nsm, optin)
                              : setup_generic<float>(&t, g, nsm, optin);
+    if (st == BZ_OK && t.fast) {
+        // A chain of small latency-bound kernels: highest priority.
+        int least = 0, greatest = 0;
+        cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&t.side, cudaStreamNonBlocking, greatest);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.join, cudaEventDisableTiming);
+        if (e != cudaSuccess) st = cuda_err(e, "adjoint side stream");
+    }
     if (st != BZ_OK) {
         bz_adj_release(&t);
         return st;
@@ -281,5 +303,8 @@ void bz_adj_release(bz_adj_scratch *a)
                     a->lrec};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (a->side) cudaStreamDestroy(a->side);
+    if (a->fork) cudaEventDestroy(a->fork);
+    if (a->join) cudaEventDestroy(a->join);
     *a = bz_adj_scratch{};
 }

@@ -463,7 +463,9 @@ bz_status configure_lazy(bz_handle *H)
     // whose shared memory fits.
     H->lz_T = bzk::kLzThreads;
     bool ok = false;
+    const char *force_g = getenv("BZ_LAZY_G");
     for (int G : {4, 2}) {
+        if (force_g && atoi(force_g) != G) continue;
         // Term records address a compact array with 16-bit byte offsets.
         if ((size_t)mcap * 4 * G > 65535) continue;
         const size_t smem = bzk::lz_offsets(nvt, mcap, G).end;
@@ -488,7 +490,14 @@ bz_status configure_lazy(bz_handle *H)
         const int nb = H->lz_G == 4 ? 8 : 16;
         H->lz_chunk = std::min(H->lz_cmax, 64);
         if (const char *c = getenv("BZ_LAZY_ORDER_CHUNK")) H->lz_chunk = std::max(8, std::min(H->lz_cmax, atoi(c)));
-        H->lz_order_tpb = H->lz_chunk <= 32767 &&
+        // The order saves shared-memory replays on every CTA iteration (about
+        // 3 us per iteration at 320 positions on a GB300) and costs a chain of
+        // about 2 x 64 dependent decisions (about 50 us): it runs when the
+        // iterations per CTA times the run length reach 6144.
+        const int64_t iters = ((int64_t)(g.nr + H->lz_G - 1) / H->lz_G + H->lz_grid - 1) / H->lz_grid;
+        H->lz_order_tpb = H->lz_chunk <= 32767 && iters * H->lz_cmax >= 6144 &&
+                          bzk::lz_order_smem(H->lz_chunk, nb) <= (size_t)H->smem_optin ? 1 : 0;
+        if (const char *o = getenv("BZ_LAZY_ORDER")) H->lz_order_tpb = atoi(o) != 0 && H->lz_chunk <= 32767 &&
                           bzk::lz_order_smem(H->lz_chunk, nb) <= (size_t)H->smem_optin ? 1 : 0;
         if (getenv("BZ_LAZY_NOORDER")) H->lz_order_tpb = 0;
         if (H->lz_order_tpb > 0)

@@ -46,6 +46,9 @@ struct bz_adj_scratch {
     uint32_t *sc_ent;                      // headers: forward list, then the loss list
     uint4 *lrec;         // the loss-term records of the transposed update
     int map[3];          // Q, K, J
+    // The fast path's plan runs on a side stream beside the forward walls.
+    cudaStream_t side;
+    cudaEvent_t fork, join;
 };
 
 // Allocates the scratch and sets up the kernels on the first call.

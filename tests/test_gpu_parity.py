@@ -117,16 +117,29 @@ def test_collide_matches_oracle(p, kernel):
     assert np.allclose(mom_g, mom_o, rtol=1e-4, atol=1e-6 * (1 + np.abs(mom_o).max()))
 
 
-@pytest.fixture(params=["auto", "overflow", "cell4", "t512", "generic"])
+@pytest.fixture(params=["auto", "ordered", "ordered_g2", "unordered", "overflow", "cell4", "t512",
+                        "generic"])
 def kernel(request, monkeypatch):
     """Run a test with the library's own choice of per-cell kernel (the FP32
-    active-node kernel with deferred correction where it applies), with that
-    kernel's compact arrays capped below the step's active-node count (every
-    step then takes the k_cell4 fallback on the device), with the FP32
-    4-node-vector kernel (BZ_KERNEL=cell4) in its 1024- and 512-thread shapes,
-    and with the generic kernel."""
-    for k in ("BZ_KERNEL", "BZ_CELL_THREADS", "BZ_LAZY_MCAP"):
+    active-node kernel with deferred correction where it applies); with that
+    kernel's term runs in the joint bank-aware order (forced on, in chunks of
+    16 or 24 positions, for groups of four cells and of two), and with no
+    order; with that kernel's compact arrays capped below the step's
+    active-node count (every step then takes the k_cell4 fallback on the
+    device); with the FP32 4-node-vector kernel (BZ_KERNEL=cell4) in its
+    1024- and 512-thread shapes; and with the generic kernel."""
+    for k in ("BZ_KERNEL", "BZ_CELL_THREADS", "BZ_LAZY_MCAP", "BZ_LAZY_ORDER", "BZ_LAZY_NOORDER",
+              "BZ_LAZY_ORDER_CHUNK", "BZ_LAZY_G"):
         monkeypatch.delenv(k, raising=False)
+    if request.param == "ordered":
+        monkeypatch.setenv("BZ_LAZY_ORDER", "1")
+        monkeypatch.setenv("BZ_LAZY_ORDER_CHUNK", "16")
+    elif request.param == "ordered_g2":
+        monkeypatch.setenv("BZ_LAZY_ORDER", "1")
+        monkeypatch.setenv("BZ_LAZY_ORDER_CHUNK", "24")
+        monkeypatch.setenv("BZ_LAZY_G", "2")
+    elif request.param == "unordered":
+        monkeypatch.setenv("BZ_LAZY_NOORDER", "1")
     if request.param == "generic":
         monkeypatch.setenv("BZ_KERNEL", "generic")
     elif request.param == "cell4":
