@@ -325,16 +325,29 @@ __global__ void k_adj_walls(Geo g, const int64_t *__restrict__ stepp, const R *_
     R a0 = R(0), a1 = R(0);        // sum lg r, sum lg r v_x
     const int per = blockDim.x / N, jz = threadIdx.x % N;
     if ((int)threadIdx.x < per * N) {
-        for (int row = threadIdx.x / N; row < N2; row += per) {
-            const int jx = row / N, jy = row - jx * N;
-            const R vx = sv[jx], vy = sv[jy];
-            const R vn = (F.nax == 0 ? vx : vy) * (R)F.nsign;
-            if (vn > R(0)) {
-                R lg = vn * rcdx * L[row * N + jz];
-                if (dcoef != R(0)) lg += dcoef * sA[jx] * sA[jy] * sA[jz] * vx * vy;
-                const R lr = lg * rt[jx];
-                a0 += lr;
-                a1 += lr * vx;
+        // Eight rows at a time: their loads are in flight together.
+        for (int row0 = threadIdx.x / N; row0 < N2; row0 += 8 * per) {
+            R ls[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int row = row0 + k * per, jx = row / N, jy = row - jx * N;
+                const bool in = row < N2 && (F.nax == 0 ? sv[jx] : sv[jy]) * (R)F.nsign > R(0);
+                ls[k] = in ? L[row * N + jz] : R(0);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int row = row0 + k * per;
+                if (row >= N2) break;
+                const int jx = row / N, jy = row - jx * N;
+                const R vx = sv[jx], vy = sv[jy];
+                const R vn = (F.nax == 0 ? vx : vy) * (R)F.nsign;
+                if (vn > R(0)) {
+                    R lg = vn * rcdx * ls[k];
+                    if (dcoef != R(0)) lg += dcoef * sA[jx] * sA[jy] * sA[jz] * vx * vy;
+                    const R lr = lg * rt[jx];
+                    a0 += lr;
+                    a1 += lr * vx;
+                }
             }
         }
     }

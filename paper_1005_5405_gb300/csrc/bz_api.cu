@@ -128,7 +128,7 @@ struct bz_handle {
     int lz_cmax = 0, lz_order_tpb = 0;     // bank-aware ordering of the term runs (1: on)
     int lz_chunk = 0;                      // positions per chunk of the ordering
     cudaStream_t lz_side = nullptr;        // the sample plan runs here, beside the walls
-    cudaEvent_t lz_fork = nullptr, lz_join = nullptr;
+    cudaEvent_t lz_fork = nullptr, lz_join = nullptr, lz_mid = nullptr;
     size_t lz_smem = 0;
     float lz_e0[bzk::kLzX] = {};
 };
@@ -530,6 +530,7 @@ bz_status configure_lazy(bz_handle *H)
     }
     BZ_CUDA(cudaEventCreateWithFlags(&H->lz_fork, cudaEventDisableTiming));
     BZ_CUDA(cudaEventCreateWithFlags(&H->lz_join, cudaEventDisableTiming));
+    BZ_CUDA(cudaEventCreateWithFlags(&H->lz_mid, cudaEventDisableTiming));
     H->lazy = true;
     return BZ_OK;
 }
@@ -575,6 +576,9 @@ bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true)
                                           H->lz_dest0);
         BZ_LAUNCHED(H);
         if (H->lz_order_tpb > 0) {
+            // The walls start now, beside the order (one warp per SM, bound by
+            // latency) rather than beside the bandwidth-hungry plan kernels.
+            BZ_CUDA(cudaEventRecord(H->lz_mid, sp));
             const int nch = (H->lz_cmax + H->lz_chunk - 1) / H->lz_chunk;
             if (H->lz_G == 4)
                 bzk::k_lz_order<8><<<dim3(bzk::kLzRoleT / 8, nch), 32, bzk::lz_order_smem(H->lz_chunk, 8), sp>>>(
@@ -586,6 +590,7 @@ bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true)
         }
     }
     BZ_CUDA(cudaEventRecord(H->lz_join, H->lz_side));
+    if (H->lz_order_tpb > 0) BZ_CUDA(cudaStreamWaitEvent(s, H->lz_mid, 0));
     {
         ProfScope ps(H, 0, s);
         bzk::k_walls<float><<<g.nfaces, 256, 0, s>>>(g, H->d_step, hin, (float *)H->ghost, H->nw,
@@ -826,6 +831,7 @@ void release(bz_handle *H)
     if (H->lz_side) cudaStreamDestroy(H->lz_side);
     if (H->lz_fork) cudaEventDestroy(H->lz_fork);
     if (H->lz_join) cudaEventDestroy(H->lz_join);
+    if (H->lz_mid) cudaEventDestroy(H->lz_mid);
     void *ptrs[] = {H->d_step, H->sc_count, H->sc_cursor, H->sc_meta, H->sc_ent, H->prof_clk, H->h[0], H->h[1], H->ht, H->pidx, H->pa, H->ghost, H->nw, H->shear,
                     H->mom, H->gw_global, H->stats, H->flag, H->axv, H->axA, H->profile};
     for (void *p : ptrs)

@@ -418,19 +418,31 @@ __device__ __forceinline__ void walls_face(const Geo &g, int64_t step, const R *
         const R vz = sv[jz], Az = sA[jz], va = sv[qa], Aa = sA[qa];
         const int64_t base = F.nax == 0 ? (int64_t)q : (int64_t)qa * N2 + jz;
         const int64_t stride = F.nax == 0 ? N2 : N;
-        for (int jn = 0; jn < N; ++jn) {
-            const R vnn = sv[jn];
-            const R vn = vnn * ns;
-            if (!(vn < R(0))) continue;
-            const R vx = F.nax == 0 ? vnn : va, vy = F.nax == 0 ? va : vnn;
-            const R w = sA[jn] * Aa * Az;
-            R hv = hc[base + jn * stride];
-            if (mu) {
-                const R kap = m5[0] + m5[1] * vx + m5[2] * vy + m5[3] * vz + m5[4] * (vx * vx + vy * vy + vz * vz);
-                hv = hv + (R(1) + eps * hv) * kap;
+        // Eight planes at a time: their loads are in flight together.
+        for (int jn0 = 0; jn0 < N; jn0 += 8) {
+            R hs[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int jn = jn0 + k;
+                hs[k] = jn < N && sv[jn] * ns < R(0) ? hc[base + jn * stride] : R(0);
             }
-            acc[0] -= vn * w * hv;
-            if (lid) acc[1] += w * vx * vy * hv;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int jn = jn0 + k;
+                if (jn >= N) break;
+                const R vnn = sv[jn];
+                const R vn = vnn * ns;
+                if (!(vn < R(0))) continue;
+                const R vx = F.nax == 0 ? vnn : va, vy = F.nax == 0 ? va : vnn;
+                const R w = sA[jn] * Aa * Az;
+                R hv = hs[k];
+                if (mu) {
+                    const R kap = m5[0] + m5[1] * vx + m5[2] * vy + m5[3] * vz + m5[4] * (vx * vx + vy * vy + vz * vz);
+                    hv = hv + (R(1) + eps * hv) * kap;
+                }
+                acc[0] -= vn * w * hv;
+                if (lid) acc[1] += w * vx * vy * hv;
+            }
         }
     }
     block_reduce<2, R>(acc, red, tot);
@@ -452,7 +464,9 @@ __device__ __forceinline__ void walls_face(const Geo &g, int64_t step, const R *
         }
     }
     __syncthreads();
-    const double nw = *snw, lnw = log(nw), U = F.U;
+    // ln n_w only in the threads that emit ghosts or sum the lid shear.
+    const double nw = *snw, U = F.U;
+    const double lnw = (int)threadIdx.x < N || threadIdx.x < 32 ? log(nw) : 0.0;
     for (int jt = threadIdx.x; jt < N; jt += blockDim.x) {
         double vt = g.axv[jt];
         // n_w Phi_w / Phi0 - 1 = expm1(ln n_w + 2 v_t U - U^2)
