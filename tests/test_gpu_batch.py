@@ -34,15 +34,20 @@ def _warm(p, seed):
     return workloads.warm_state(p, seed=seed).astype(np.float32)
 
 
-@pytest.mark.parametrize("mode", ["persistent", "fanout"])
+@pytest.mark.parametrize("mode", ["persistent", "fanout", "fanout_ordered"])
 def test_batch_matches_single_instances_and_oracle(monkeypatch, mode):
     """Both schedules: the persistent per-cell kernels over all instances,
-    and the fan-out graph of the instances' own active-node steps."""
-    if mode == "fanout":
+    and the fan-out graph of the instances' own active-node steps (each with
+    its sample plan on its own second stream), also with the joint term order
+    forced on in every instance and in the single-instance handles."""
+    monkeypatch.delenv("BZ_LAZY_ORDER", raising=False)
+    if mode.startswith("fanout"):
         monkeypatch.setenv("BZ_BATCH_MODE", "fanout")
+    if mode == "fanout_ordered":
+        monkeypatch.setenv("BZ_LAZY_ORDER", "1")
     ps = _problems()
     b = binding.Batch(ps)
-    assert (b.schedule()["fanout_branches"] > 0) == (mode == "fanout")
+    assert (b.schedule()["fanout_branches"] > 0) == mode.startswith("fanout")
     singles = []
     for i, p in enumerate(ps):
         h0 = _warm(p, 40 + i)
