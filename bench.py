@@ -282,8 +282,8 @@ def run_ours(args):
     launches = cav.stats()[4] - launches0
     ms_max = max_over_ranks(ms, world, "cuda")
 
-    # Free streaming alone (walls + upwind stencil, Eq. streaming2D): the
-    # BASELINE's separate streaming target.  Timed by the library's events
+    # Free streaming alone (walls + upwind stencil, Eq. streaming2D), which
+    # has its own roofline target.  Timed by the library's events
     # around each streaming-kernel launch.
     barrier()
     cav.profile(True)
