@@ -288,34 +288,36 @@ bz_status bz_profile_read(bz_handle *h, double ms[4], int64_t launches[4]);
 bz_status bz_phase_clocks(bz_handle *h, int64_t *out, int32_t n);
 
 /* ---------------------------------------------------------------------
- * Collision step without device allocation.  The paper has no counterpart:
- * this entry point exists for callers that cannot call cudaMalloc, such as
- * applications whose device memory is owned entirely by their own pool
- * allocator, and latency-critical loops in which cudaMalloc/cudaFree would
- * synchronise the device.
+ * Collision step without device allocation.  The paper has no counterpart.
+ * This entry point is for callers that cannot call cudaMalloc: applications
+ * whose device memory is all owned by their own pool allocator and that
+ * forbid allocation while they run, and latency-critical loops in which a
+ * cudaMalloc or cudaFree would synchronise the device.
  *
- * Applies the relaxation of step `step` (the shared Monte Carlo sample set of
- * that step, the Jacobi collision update, the conservation correction; Eqs.
- * monteCarloInt, collision_step, rinorm_a, correzione) to the caller's state
- * h_in and writes the result to h_out and, when mom is non-NULL, the moments
- * of the result to mom (nx*ny*11 doubles, as bz_moments).  h_in and h_out
- * are device arrays of nx*ny*nv^3 elements of params->dtype in the layout
- * above and must not overlap.  walls are not needed; params->eps must be
- * given (> 0); cfl and kcoll keep their defaults at 0.  The result equals
- * bz_step_ex(h, 1, BZ_DO_COLLIDE, ...) on a handle holding h_in at `step`, up
- * to floating-point summation order.
+ * It computes what bz_step_ex(h, 1, BZ_DO_COLLIDE, ...) computes on a handle
+ * holding h_in at step `step` (the step's shared Monte Carlo sample set, the
+ * collision update and the conservation correction, no streaming), up to
+ * floating-point summation order, and writes the result to h_out and, when
+ * mom is non-NULL, its moments to mom (nx*ny*11 doubles, as bz_moments).
+ * h_in and h_out are caller-owned device arrays of nx*ny*nv^3 elements of
+ * params->dtype in the layout above; their byte ranges must not overlap
+ * (BZ_EINVAL).  No walls are needed; params->eps must be given (> 0); cfl and
+ * kcoll keep their defaults at 0; uniform grids and the shared sample set
+ * only (BZ_EUNSUPPORTED otherwise).
  *
  * It calls no cudaMalloc, cudaFree or allocating library routine.  Its only
- * scratch (the sample set and the per-axis velocity tables) is a file-scope
- * device array of BZ_NOALLOC_SCRATCH_BYTES that every GPU which loads the
- * library keeps until the process exits; hence n_pairs <= BZ_NOALLOC_MAX_PAIRS
- * (larger values return BZ_EINVAL), and the per-sample products must fit in
- * shared memory next to the velocity slab (else BZ_EUNSUPPORTED).  The first
- * call on a device looks up the device address of that array (with the device
- * current) and should come before any stream capture.  All calls share the
- * array and it keeps the last call's contents: calls that overlap on the GPU
- * (on different streams or devices' shared use) race and give wrong results;
- * serialise them.  Asynchronous on `stream`; errors as elsewhere. */
+ * scratch (the sample set, the per-axis velocity tables and the step number)
+ * is a file-scope device array of BZ_NOALLOC_SCRATCH_BYTES, which every GPU
+ * that loads the library holds until the process exits.  Hence n_pairs <=
+ * BZ_NOALLOC_MAX_PAIRS (larger values return BZ_EINVAL), and the velocity slab
+ * and the per-sample products must fit one block's shared memory (else
+ * BZ_EUNSUPPORTED).  The first call on a device looks up the device address of
+ * that array, with the device current, and should come before any stream
+ * capture.  Every call on a device uses the same array, which keeps the last
+ * call's contents: calls on one device that overlap in time (on different
+ * streams) race and give wrong results, so serialise them; calls on different
+ * devices use different arrays.  Asynchronous on `stream`; errors as
+ * elsewhere. */
 #define BZ_NOALLOC_MAX_PAIRS 65536
 #define BZ_NOALLOC_SCRATCH_BYTES ((2u << 20) + 4096u)
 bz_status bz_collide_noalloc(const bz_space *space, const bz_vel *vel, const bz_params *params,

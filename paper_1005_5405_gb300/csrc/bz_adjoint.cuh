@@ -200,8 +200,12 @@ k_adj_cell(Geo g, const R *__restrict__ hin, const R *__restrict__ ghost,
             acc[12] += vz * (s2 + q * s0);
             acc[13] += s4 + R(2) * q * s2 + q * q * s0;
         }
-#pragma unroll
-        for (int k = 0; k < 5; ++k) acc[14 + k] = pre[k];
+        // The thread's share of the increment sums D (post minus pre).
+        acc[14] = acc[0] - pre[0];
+        acc[15] = acc[1] - pre[1];
+        acc[16] = acc[2] - pre[2];
+        acc[17] = acc[3] - pre[3];
+        acc[18] = (acc[4] + acc[5] + acc[6]) - pre[4];
         block_reduce<19, R>(acc, S.red, S.tot);
         if (t == 0) {
             for (int k = 0; k < 19; ++k) S.P[k] = S.tot[k];
@@ -284,7 +288,7 @@ k_adj_cell(Geo g, const R *__restrict__ hin, const R *__restrict__ ghost,
         for (int j = t; j < nvt; j += T) dst[j] = S.C[j];
         __syncthreads();
     }
-    if (fallback && stats) atomicAdd(stats + 3, 1ull);
+    if (fallback && stats) atomicAdd(stats + 3, (unsigned long long)fallback);
 }
 
 // Per face: the sensitivities of its ghost values, gathered from dJ/dh~ of

@@ -542,7 +542,10 @@ bz_status configure_lazy(bz_handle *H)
 // depends on the step counter only, so it runs on a side stream while the
 // walls run (after everything before the step on s: the last step's kernel
 // reads the plan's buffers), and the per-cell kernel waits for both.
-bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true)
+// nostream: the relaxation alone (BZ_DO_COLLIDE), h~ = h; the walls still
+// run so that the ghost values the kernel reads (times a zero Courant
+// number) are those of the state.
+bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true, bool nostream = false)
 {
     const Geo &g = H->g;
     Geo gl = g;
@@ -616,6 +619,8 @@ bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true)
         a.mcap = H->lz_mcap;
         for (int k = 0; k < bzk::kLzX; ++k) a.e0[k] = H->lz_e0[k];
         a.clk = H->prof_clk;
+        a.stats = H->stats;
+        a.nostream = nostream ? 1 : 0;
         if (H->lz_G == 4) launch_lz_kernel<4>(H, a, s);
         else launch_lz_kernel<2>(H, a, s);
         BZ_LAUNCHED(H);
@@ -642,15 +647,17 @@ bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true)
         // The input now holds corrected values: its pending corrections go.
         bzk::k_lz_clear<<<H->nsm, 256, 0, s>>>(H->lz_meta, H->mu[in], (int64_t)g.nr * 8);
         BZ_LAUNCHED(H);
-        const int grid = H->grid4f;
-        if (H->maxt4 == 512)
-            bzk::k_cell4<true, 512><<<grid, H->threads4, H->smem4, s>>>(
-                g, H->map, hin, (const float *)H->ghost, pa16, H->sc_ent, H->sc_meta, hout, H->mom,
-                H->stats, nullptr, H->lz_meta);
-        else
-            bzk::k_cell4<true, 1024><<<grid, H->threads4, H->smem4, s>>>(
-                g, H->map, hin, (const float *)H->ghost, pa16, H->sc_ent, H->sc_meta, hout, H->mom,
-                H->stats, nullptr, H->lz_meta);
+        const int grid = nostream ? H->grid4c : H->grid4f;
+#define BZ_C4G(F, M)                                                                              \
+    bzk::k_cell4<F, M><<<grid, H->threads4, H->smem4, s>>>(g, H->map, hin, (const float *)H->ghost, \
+                                                          pa16, H->sc_ent, H->sc_meta, hout, H->mom, \
+                                                          H->stats, nullptr, H->lz_meta)
+        if (H->maxt4 == 512) {
+            if (nostream) BZ_C4G(false, 512); else BZ_C4G(true, 512);
+        } else {
+            if (nostream) BZ_C4G(false, 1024); else BZ_C4G(true, 1024);
+        }
+#undef BZ_C4G
         BZ_LAUNCHED(H);
     }
     if (!advance_step) return BZ_OK;           // a repeatable trial of the step
@@ -665,8 +672,11 @@ bz_status launch_step(bz_handle *H, cudaStream_t s, bool fused, bool do_stream, 
 {
     using V4 = typename bzk::Idx4<I>::type;
     using PA = bzk::PlanA<R, I>;
-    if constexpr (sizeof(R) == 4)
+    if constexpr (sizeof(R) == 4) {
         if (fused && H->lazy) return launch_lazy(H, s);
+        // The relaxation alone on the active-node kernel (no streaming).
+        if (!fused && do_collide && !do_stream && H->lazy) return launch_lazy(H, s, true, true);
+    }
     // Every other path reads and writes corrected states.
     BZ_TRY(materialize_if_lazy(H, H->cur, s));
     BZ_TRY(drop_lazy(H, H->cur ^ 1, s));
@@ -849,6 +859,107 @@ void release(bz_handle *H)
 
 }  // namespace
 
+// The discretisation of a problem statement (Sec. 3, Sec. 5.1): grids, time
+// step, collision prefactor, eps, wall constants and the equilibrium Gram
+// matrix.  walls may be NULL (lid at rest; eps must then be given).
+void bz_discretise(const bz_space *space, const bz_vel *vel, const bz_walls *walls,
+                   const bz_params *params, bzk::Geo &g, bz_grid_tables &tb)
+{
+    const int N = vel->nv;
+    g.nx = space->nx;
+    g.ny = space->ny;
+    g.nv = N;
+    g.nvt = N * N * N;
+    g.nr = g.nx * g.ny;
+    g.nfaces = 2 * g.nx + 2 * g.ny;
+    g.nt = (int)params->n_pairs;
+    g.vmax = vel->vmax;
+    g.dv = (2.0 * vel->vmax) / (double)N;
+    g.dx = (1.0 / space->kn) / (double)g.nx;
+    g.dy = (1.0 / space->kn) / (double)g.ny;
+    const double cfl = params->cfl > 0.0 ? params->cfl : 0.5;
+    // Grids (Sec. 3, Sec. 5.1), uniform or stretched.
+    const bool sv = vel->rv > 0.0 && vel->rv < 1.0;
+    std::vector<double> &edges = tb.edges, &axv = tb.axv, &axw = tb.axw, &axA = tb.axA;
+    edges.assign(N + 1, 0.0);
+    axv.assign(N, 0.0);
+    axw.assign(N, 0.0);
+    if (sv) {
+        // Half-axis widths d0, d0 q, d0 q^2, ... (q = 1/rv) from the origin
+        // outward summing to vmax; edges mirrored about 0.
+        const int m = N / 2;
+        const double q = 1.0 / vel->rv;
+        const double d0 = g.vmax * (q - 1.0) / (std::pow(q, (double)m) - 1.0);
+        for (int k = 0; k <= N; ++k) {
+            const int i = k >= m ? k - m : m - k;
+            const double e = d0 * (std::pow(q, (double)i) - 1.0) / (q - 1.0);
+            edges[k] = k >= m ? e : -e;
+        }
+        for (int j = 0; j < N; ++j) {
+            axv[j] = 0.5 * (edges[j] + edges[j + 1]);
+            axw[j] = edges[j + 1] - edges[j];
+        }
+    } else {
+        for (int j = 0; j < N; ++j) {
+            axv[j] = -g.vmax + ((double)j + 0.5) * g.dv;
+            axw[j] = g.dv;
+        }
+    }
+    // Spatial widths: shrinking by r per cell toward the refined end(s).
+    auto widths = [](int n, bool both_ends, double r, double L) {
+        std::vector<double> w(n, L / n);
+        if (!(r > 0.0 && r < 1.0)) return w;
+        auto dist = [&](int k) { return both_ends ? std::min(k, n - 1 - k) : n - 1 - k; };
+        double sum = 0.0;
+        for (int k = 0; k < n; ++k) sum += std::pow(1.0 / r, (double)dist(k));
+        for (int k = 0; k < n; ++k) w[k] = L * std::pow(1.0 / r, (double)dist(k)) / sum;
+        return w;
+    };
+    tb.cdx = widths(g.nx, true, space->rx, 1.0 / space->kn);
+    tb.cdy = widths(g.ny, false, space->ry, 1.0 / space->kn);
+    double hmin = tb.cdx[0];
+    for (double w : tb.cdx) hmin = std::min(hmin, w);
+    for (double w : tb.cdy) hmin = std::min(hmin, w);
+    const double vtop = axv[N - 1];
+    g.dt = cfl * hmin / vtop;
+    const double kcoll =
+        params->kcoll > 0.0 ? params->kcoll : 5.0 * 1.016034 / 16.0 * std::sqrt(2.0 / M_PI);
+    g.cw = M_PI * kcoll * g.dt / (double)g.nt;
+    const double lu0 = walls ? walls->lid_u0 : 0.0, lamp = walls ? walls->lid_amp : 0.0;
+    g.eps = params->eps > 0.0 ? params->eps
+                              : lid_eps(lu0, lamp, walls ? walls->lid_profile : nullptr, g.nx);
+    g.seed = params->seed;
+    g.instance = params->instance;
+    g.lid_u0 = lu0;
+    g.lid_amp = lamp;
+    g.lid_period = walls ? walls->lid_period : 0.0;
+    g.strip = g.nx >= 16 ? 8 : g.nx;
+    // Per-axis weight factors (w_j = A_x A_y A_z) and the wall flux constants.
+    axA.assign(N, 0.0);
+    for (int j = 0; j < N; ++j)
+        axA[j] = axw[j] * (1.0 / std::sqrt(M_PI)) * std::exp(-axv[j] * axv[j]);
+    double hn = 0.0, zsum = 0.0;
+    for (int j = 0; j < N; ++j) {
+        zsum += axA[j];
+        if (axv[j] > 0.0) hn += axv[j] * axA[j];
+    }
+    g.hn = hn;
+    g.zsum = zsum;
+    g.cout = hn * zsum * zsum;
+    // Gram matrix of the equilibrium, sum_j w_j psi_a psi_b.
+    for (int a = 0; a < 25; ++a) g.G0[a] = 0.0;
+    for (int jx = 0; jx < N; ++jx)
+        for (int jy = 0; jy < N; ++jy)
+            for (int jz = 0; jz < N; ++jz) {
+                double w = axA[jx] * axA[jy] * axA[jz];
+                double p[5] = {1.0, axv[jx], axv[jy], axv[jz],
+                               axv[jx] * axv[jx] + axv[jy] * axv[jy] + axv[jz] * axv[jz]};
+                for (int a = 0; a < 5; ++a)
+                    for (int b = 0; b < 5; ++b) g.G0[a * 5 + b] += w * p[a] * p[b];
+            }
+    for (int a = 0; a < 25; ++a) g.G0f[a] = (float)g.G0[a];
+}
+
 extern "C" {
 
 const char *bz_last_error(void) { return g_last_error.c_str(); }
@@ -899,100 +1010,17 @@ bz_status bz_create(const bz_space *space, const bz_vel *vel, const bz_walls *wa
     };
     Geo &g = H->g;
     const int N = vel->nv;
-    g.nx = space->nx;
-    g.ny = space->ny;
-    g.nv = N;
-    g.nvt = N * N * N;
-    g.nr = g.nx * g.ny;
-    g.nfaces = 2 * g.nx + 2 * g.ny;
-    g.nt = (int)params->n_pairs;
-    g.vmax = vel->vmax;
-    g.dv = (2.0 * vel->vmax) / (double)N;
-    g.dx = (1.0 / space->kn) / (double)g.nx;
-    g.dy = (1.0 / space->kn) / (double)g.ny;
-    const double cfl = params->cfl > 0.0 ? params->cfl : 0.5;
-    // Grids (Sec. 3, Sec. 5.1), uniform or stretched.
+    bz_grid_tables tb;
+    bz_discretise(space, vel, walls, params, g, tb);
+    if (const char *fb = getenv("BZ_SOLVE_FALLBACK")) g.solve_fb = atoi(fb) != 0 ? 1 : 0;
     const bool sv = vel->rv > 0.0 && vel->rv < 1.0;
     const bool sxg = space->rx > 0.0 && space->rx < 1.0, syg = space->ry > 0.0 && space->ry < 1.0;
     H->stretched = sv || sxg || syg;
-    std::vector<double> edges(N + 1), axv(N), axw(N);
-    if (sv) {
-        // Half-axis widths d0, d0 q, d0 q^2, ... (q = 1/rv) from the origin
-        // outward summing to vmax; edges mirrored about 0.
-        const int m = N / 2;
-        const double q = 1.0 / vel->rv;
-        const double d0 = g.vmax * (q - 1.0) / (std::pow(q, (double)m) - 1.0);
-        for (int k = 0; k <= N; ++k) {
-            const int i = k >= m ? k - m : m - k;
-            const double e = d0 * (std::pow(q, (double)i) - 1.0) / (q - 1.0);
-            edges[k] = k >= m ? e : -e;
-        }
-        for (int j = 0; j < N; ++j) {
-            axv[j] = 0.5 * (edges[j] + edges[j + 1]);
-            axw[j] = edges[j + 1] - edges[j];
-        }
-    } else {
-        for (int j = 0; j < N; ++j) {
-            axv[j] = -g.vmax + ((double)j + 0.5) * g.dv;
-            axw[j] = g.dv;
-        }
-    }
-    // Spatial widths: shrinking by r per cell toward the refined end(s).
-    auto widths = [](int n, bool both_ends, double r, double L) {
-        std::vector<double> w(n, L / n);
-        if (!(r > 0.0 && r < 1.0)) return w;
-        auto dist = [&](int k) { return both_ends ? std::min(k, n - 1 - k) : n - 1 - k; };
-        double sum = 0.0;
-        for (int k = 0; k < n; ++k) sum += std::pow(1.0 / r, (double)dist(k));
-        for (int k = 0; k < n; ++k) w[k] = L * std::pow(1.0 / r, (double)dist(k)) / sum;
-        return w;
-    };
-    const std::vector<double> cdx = widths(g.nx, true, space->rx, 1.0 / space->kn);
-    const std::vector<double> cdy = widths(g.ny, false, space->ry, 1.0 / space->kn);
-    double hmin = cdx[0];
-    for (double w : cdx) hmin = std::min(hmin, w);
-    for (double w : cdy) hmin = std::min(hmin, w);
-    const double vtop = axv[N - 1];
-    g.dt = cfl * hmin / vtop;
-    const double kcoll =
-        params->kcoll > 0.0 ? params->kcoll : 5.0 * 1.016034 / 16.0 * std::sqrt(2.0 / M_PI);
-    g.cw = M_PI * kcoll * g.dt / (double)g.nt;
-    g.eps = params->eps > 0.0 ? params->eps
-                              : lid_eps(walls->lid_u0, walls->lid_amp, walls->lid_profile, g.nx);
-    g.seed = params->seed;
-    g.instance = params->instance;
-    g.lid_u0 = walls->lid_u0;
-    g.lid_amp = walls->lid_amp;
-    g.lid_period = walls->lid_period;
-    g.strip = g.nx >= 16 ? 8 : g.nx;
     H->dtype = params->dtype;
     H->esz = params->dtype == BZ_F64 ? 8 : 4;
     H->per_cell = params->sample_mode == BZ_PER_CELL;
-
-    // Per-axis weight factors (w_j = A_x A_y A_z) and the wall flux constants.
-    std::vector<double> axA(N);
-    for (int j = 0; j < N; ++j)
-        axA[j] = axw[j] * (1.0 / std::sqrt(M_PI)) * std::exp(-axv[j] * axv[j]);
-    double hn = 0.0, zsum = 0.0;
-    for (int j = 0; j < N; ++j) {
-        zsum += axA[j];
-        if (axv[j] > 0.0) hn += axv[j] * axA[j];
-    }
-    g.hn = hn;
-    g.zsum = zsum;
-    g.cout = hn * zsum * zsum;
-    // Gram matrix of the equilibrium, sum_j w_j psi_a psi_b.
-    for (int a = 0; a < 25; ++a) g.G0[a] = 0.0;
-    for (int jx = 0; jx < N; ++jx)
-        for (int jy = 0; jy < N; ++jy)
-            for (int jz = 0; jz < N; ++jz) {
-                double w = axA[jx] * axA[jy] * axA[jz];
-                double p[5] = {1.0, axv[jx], axv[jy], axv[jz],
-                               axv[jx] * axv[jx] + axv[jy] * axv[jy] + axv[jz] * axv[jz]};
-                for (int a = 0; a < 5; ++a)
-                    for (int b = 0; b < 5; ++b) g.G0[a * 5 + b] += w * p[a] * p[b];
-            }
-    for (int a = 0; a < 25; ++a) g.G0f[a] = (float)g.G0[a];
+    const std::vector<double> &edges = tb.edges, &axv = tb.axv, &axw = tb.axw, &axA = tb.axA;
+    const std::vector<double> &cdx = tb.cdx, &cdy = tb.cdy;
 
     cudaError_t e = cudaGetDevice(&H->dev);
     if (e != cudaSuccess) {

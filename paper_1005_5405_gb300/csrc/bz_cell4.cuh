@@ -159,11 +159,22 @@ static __global__ void k_scatter_fill(int nt, int T, const ushort4 *__restrict__
     }
 }
 
-// G mu = -(post - pre) (Eqs. rinorm_a, correzione) solved in registers by
-// Gaussian elimination without pivoting, which is stable for the symmetric
-// positive definite Gram matrix; false if a pivot is not positive.
+// G mu = -D (Eqs. rinorm_a, correzione): the correction restores the
+// conserved moments of h~, so its right-hand side is minus the conserved
+// moments of the collision increment, D_a = sum_j psi_a (N_c,j - N_j), taken
+// directly from the increment sums (never as the difference of the large
+// post- and pre-collision sums).  P[0..13] are the moment sums of N_c over
+// 1, vx, vy, vz, vx2, vy2, vz2, vxvy, vxvz, vyvz, vx v2, vy v2, vz v2, v4
+// (they give G = G0 + eps sum_j N_c psi psi^T) and P[14..18] the increment
+// sums D over 1, vx, vy, vz, v2.  Solved in registers by Gaussian
+// elimination without pivoting (stable for the symmetric positive definite
+// Gram matrix), then one step of iterative refinement whose residual
+// -D - G mu is evaluated exactly with error-free products and sums and
+// rounded once, so mu is as accurate as the FP32 entries of G and D allow.
+// False if a pivot is not positive.
 __device__ __forceinline__ bool correction_spd(const Geo &g, const float *P, float *mu)
 {
+    if (g.solve_fb) return false;
     const float e = (float)g.eps;
     const float p4 = P[4] + P[5] + P[6];
     const float m[5][5] = {
@@ -172,35 +183,63 @@ __device__ __forceinline__ bool correction_spd(const Geo &g, const float *P, flo
         {P[2], P[7], P[5], P[9], P[11]},
         {P[3], P[8], P[9], P[6], P[12]},
         {p4, P[10], P[11], P[12], P[13]}};
-    const float post[5] = {P[0], P[1], P[2], P[3], p4};
-    float A[5][6];
+    float A[5][5], U[5][5], L[5][5], ip[5], b[5], x[5];
 #pragma unroll
     for (int a = 0; a < 5; ++a) {
 #pragma unroll
-        for (int b = 0; b < 5; ++b) A[a][b] = g.G0f[a * 5 + b] + e * m[a][b];
-        A[a][5] = -(post[a] - P[14 + a]);
+        for (int c = 0; c < 5; ++c) A[a][c] = U[a][c] = g.G0f[a * 5 + c] + e * m[a][c];
+        b[a] = -P[14 + a];
     }
 #pragma unroll
     for (int kk = 0; kk < 5; ++kk) {
-        const float piv = A[kk][kk];
+        const float piv = U[kk][kk];
         if (!(piv > 0.f)) return false;
-        const float ip = 1.f / piv;
+        ip[kk] = 1.f / piv;
 #pragma unroll
         for (int i = kk + 1; i < 5; ++i) {
-            const float f = A[i][kk] * ip;
+            L[i][kk] = U[i][kk] * ip[kk];
 #pragma unroll
-            for (int j = kk + 1; j < 6; ++j) A[i][j] -= f * A[kk][j];
+            for (int j = kk + 1; j < 5; ++j) U[i][j] -= L[i][kk] * U[kk][j];
         }
     }
+    // x = U^-1 L^-1 r, for the right-hand side and then the residual.
+    auto lu_solve = [&](float (&r)[5], float (&y)[5]) {
 #pragma unroll
-    for (int i = 4; i >= 0; --i) {
-        float s = A[i][5];
+        for (int i = 0; i < 5; ++i) {
+            float s = r[i];
 #pragma unroll
-        for (int j = i + 1; j < 5; ++j) s -= A[i][j] * A[j][5];
-        A[i][5] = s / A[i][i];
+            for (int k = 0; k < i; ++k) s -= L[i][k] * r[k];
+            r[i] = s;
+        }
+#pragma unroll
+        for (int i = 4; i >= 0; --i) {
+            float s = r[i];
+#pragma unroll
+            for (int j = i + 1; j < 5; ++j) s -= U[i][j] * y[j];
+            y[i] = s * ip[i];
+        }
+    };
+    float r[5];
+#pragma unroll
+    for (int a = 0; a < 5; ++a) r[a] = b[a];
+    lu_solve(r, x);
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+        float hi = b[a], lo = 0.f;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            float p, pe, s, se;
+            two_prod(A[a][c], x[c], p, pe);
+            two_sum(hi, -p, s, se);
+            hi = s;
+            lo = __fadd_rn(lo, __fsub_rn(se, pe));
+        }
+        r[a] = __fadd_rn(hi, lo);
     }
+    float dx[5];
+    lu_solve(r, dx);
 #pragma unroll
-    for (int a = 0; a < 5; ++a) mu[a] = A[a][5];
+    for (int a = 0; a < 5; ++a) mu[a] = x[a] + dx[a];
     return true;
 }
 
@@ -229,9 +268,14 @@ __device__ __forceinline__ void block_reduce4(float (&v)[K], float *red, float *
     if (lane < K) red[warp * 32 + lane] = x[0];
     __syncthreads();
     if (threadIdx.x < K) {
-        float s = 0.f;
-        for (int w = 0; w < nwarps; ++w) s += red[w * 32 + threadIdx.x];
-        tot[threadIdx.x] = s;
+        // Compensated sum of the warp totals.
+        float s = 0.f, c = 0.f;
+        for (int w = 0; w < nwarps; ++w) {
+            float e;
+            two_sum(s, red[w * 32 + threadIdx.x], s, e);
+            c = __fadd_rn(c, e);
+        }
+        tot[threadIdx.x] = __fadd_rn(s, c);
     }
     __syncthreads();
 }
@@ -858,11 +902,13 @@ __device__ __forceinline__ void cell4_cell(const Geo &g, const Map4 &m, int c,
             acc[12] += z * (s2 + qi * s0);
             acc[13] += s4 + 2.f * qi * s2 + qi * qi * s0;
         }
-        acc[14] = p0;
-        acc[15] = p1;
-        acc[16] = vy * p0;
-        acc[17] = p3;
-        acc[18] = p4;
+        // The thread's share of the increment sums D (post minus pre over
+        // its own nodes, so only thread-sized partial sums cancel).
+        acc[14] = acc[0] - p0;
+        acc[15] = acc[1] - p1;
+        acc[16] = acc[2] - vy * p0;
+        acc[17] = acc[3] - p3;
+        acc[18] = (acc[4] + acc[5] + acc[6]) - p4;
     }
     block_reduce4<19>(acc, S.red, totf);
     stamp(5);
@@ -873,7 +919,9 @@ __device__ __forceinline__ void cell4_cell(const Geo &g, const Map4 &m, int c,
         if (!correction_spd(g, totf, muf)) {
             double m8[5], Pd[19];
             for (int a = 0; a < 19; ++a) Pd[a] = (double)totf[a];
-            correction_solve<float>(g, Pd, m8, &fallback);
+            int f2 = 0;
+            correction_solve<float>(g, Pd, m8, &f2);
+            ++fallback;
             for (int a = 0; a < 5; ++a) muf[a] = (float)m8[a];
         }
         if constexpr (ADJ)
@@ -963,7 +1011,7 @@ k_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restrict__ 
     for (int kc = blockIdx.x; kc < g.nr; kc += gridDim.x, ++ncell)
         cell4_cell<FUSED>(g, m, cell_of(g, kc), hin, ghost, pa, ent, meta, hout, mom, S,
                           fallback, clk, ncell);
-    if (fallback && stats) atomicAdd(stats + 3, 1ull);
+    if (fallback && stats) atomicAdd(stats + 3, (unsigned long long)fallback);
 }
 
 
@@ -1090,7 +1138,7 @@ k_adj_cell4(Geo g, Map4 m, const float *__restrict__ hin, const float *__restric
     for (int kc = blockIdx.x; kc < g.nr; kc += gridDim.x)
         cell4_cell<true, true>(g, m, cell_of(g, kc), hin, ghost, pa, ent, meta, nullptr, nullptr,
                                S, fallback, nullptr, 0, &X);
-    if (fallback && stats) atomicAdd(stats + 3, 1ull);
+    if (fallback && stats) atomicAdd(stats + 3, (unsigned long long)fallback);
 }
 
 }  // namespace bzk

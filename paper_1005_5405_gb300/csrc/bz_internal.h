@@ -7,12 +7,31 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace bzk {
 struct Geo;
 }
 
 // Stores the text returned by bz_last_error() on this thread.
 void bz_record_error(const char *msg);
+
+// Host tables of a discretised problem: velocity cell edges (nv + 1), node
+// velocities, cell widths and weight factors A_j = width_j pi^-1/2
+// exp(-v_j^2) per axis (nv each), and the spatial column and row widths.
+struct bz_grid_tables {
+    std::vector<double> edges, axv, axw, axA, cdx, cdy;
+};
+
+// The discretisation of a validated problem statement (Sec. 3, Sec. 5.1):
+// fills every scalar field of g (sizes, dv, dx, dy, dt from the Courant
+// number, the collision prefactor cw, eps, the Philox key, the lid motion,
+// the wall flux constants, the equilibrium Gram matrix G0) and the host
+// tables; device pointers of g are left untouched.  walls may be NULL (lid at
+// rest; params->eps must then be > 0).  The one rule for bz_create and
+// bz_collide_noalloc.
+void bz_discretise(const bz_space *space, const bz_vel *vel, const bz_walls *walls,
+                   const bz_params *params, bzk::Geo &g, bz_grid_tables &tb);
 
 // A kernel's dynamic shared-memory limit is one setting for the whole
 // process, shared by every handle that launches it: it is raised to the most

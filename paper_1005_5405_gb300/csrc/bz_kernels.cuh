@@ -45,6 +45,7 @@ struct Geo {
     float G0f[25];              // the same, rounded to float
     int swz;                    // plan node indices in the quad-rotated shared-memory order
     int strip;                  // cells are visited in column strips of this width
+    int solve_fb;               // 1: every correction solve takes its pivoted fallback (tests)
     // Stretched grids (nullptr when uniform).  axe: nv + 1 velocity cell
     // edges; axd: nv widths; sx, sy: per column / row, dx / dx_i and
     // dx / dy_j (the Courant numbers are cu(v) times these); wlid: per lid
@@ -314,6 +315,22 @@ __global__ void k_plan(Geo g, const int64_t *__restrict__ stepp,
 // ---------------------------------------------------------------------
 // Block reductions (per-thread partials -> per-warp -> double totals)
 // ---------------------------------------------------------------------
+// Error-free transformations in FP32: a + b = s + e exactly (Knuth's
+// TwoSum) and a b = p + e exactly (the product's rounding error from one
+// fused multiply-add).  Explicit rounding intrinsics keep the compiler from
+// contracting or reassociating them.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
 template <int K, typename A>
 __device__ __forceinline__ void block_reduce(A (&v)[K], double *red /* kMaxWarps*kRedSlots */,
                                              double *tot /* K */)
@@ -334,7 +351,18 @@ __device__ __forceinline__ void block_reduce(A (&v)[K], double *red /* kMaxWarps
     __syncthreads();
     if (threadIdx.x < K) {
         A s = A(0);
-        for (int w = 0; w < nwarps; ++w) s += ra[w * kRedSlots + threadIdx.x];
+        if constexpr (sizeof(A) == 4) {
+            // FP32: compensated sum of the warp partials.
+            float c = 0.f;
+            for (int w = 0; w < nwarps; ++w) {
+                float e;
+                two_sum(s, ra[w * kRedSlots + threadIdx.x], s, e);
+                c = __fadd_rn(c, e);
+            }
+            s = __fadd_rn(s, c);
+        } else {
+            for (int w = 0; w < nwarps; ++w) s += ra[w * kRedSlots + threadIdx.x];
+        }
         tot[threadIdx.x] = (double)s;
     }
     __syncthreads();
@@ -584,10 +612,10 @@ struct AxisTab {       // per-axis tables in shared memory, N entries each
 };
 
 template <typename R>
-__device__ __noinline__ void chol_or_ge(R G[5][5], R b[5], R x[5], int *fallback)
+__device__ __noinline__ void chol_or_ge(R G[5][5], R b[5], R x[5], int *fallback, bool force_ge = false)
 {
     R L[5][5];
-    bool ok = true;
+    bool ok = !force_ge;
     for (int i = 0; i < 5 && ok; ++i) {
         for (int j = 0; j <= i; ++j) {
             R s = G[i][j];
@@ -614,7 +642,7 @@ __device__ __noinline__ void chol_or_ge(R G[5][5], R b[5], R x[5], int *fallback
         }
         return;
     }
-    *fallback = 1;
+    ++*fallback;
     // Gaussian elimination with partial pivoting.
     R A[5][6];
     for (int i = 0; i < 5; ++i) {
@@ -647,8 +675,10 @@ __device__ __noinline__ void chol_or_ge(R G[5][5], R b[5], R x[5], int *fallback
 // Correction of Eqs. rinorm_a / correzione for one cell.  P holds the reduced
 // sums: P[0..13] moments of the post-collision N_c over the monomials
 // 1, vx, vy, vz, vx2, vy2, vz2, vxvy, vxvz, vyvz, vx v2, vy v2, vz v2, v4 and
-// P[14..18] the invariants 1, vx, vy, vz, v2 of the pre-collision N.  Solves
-// G mu = -(post - pre) with G = sum_j w_j (1 + eps h_c,j) psi psi^T.
+// P[14..18] the moments D of the collision increment N_c - N over the
+// invariants 1, vx, vy, vz, v2.  Solves G mu = -D (the correction restores the
+// invariants of the pre-collision N) with G = sum_j w_j (1 + eps h_c,j) psi
+// psi^T.
 template <typename R>
 __device__ __noinline__ void correction_solve(const Geo &g, const double *Pd, double *mu,
                                               int *fallback)
@@ -660,7 +690,7 @@ __device__ __noinline__ void correction_solve(const Geo &g, const double *Pd, do
     const R e = (R)g.eps;
     R post[5] = {P[0], P[1], P[2], P[3], P[4] + P[5] + P[6]};
     R rhs[5];
-    for (int a = 0; a < 5; ++a) rhs[a] = -(post[a] - P[14 + a]);
+    for (int a = 0; a < 5; ++a) rhs[a] = (R)(-Pd[14 + a]);
     const R m[5][5] = {
         {P[0], P[1], P[2], P[3], post[4]},
         {P[1], P[4], P[7], P[8], P[10]},
@@ -672,7 +702,7 @@ __device__ __noinline__ void correction_solve(const Geo &g, const double *Pd, do
         for (int b = 0; b < 5; ++b)
             M[a][b] = (sizeof(R) == 8 ? (R)g.G0[a * 5 + b] : (R)g.G0f[a * 5 + b]) + e * m[a][b];
     R x[5];
-    chol_or_ge<R>(M, rhs, x, fallback);
+    chol_or_ge<R>(M, rhs, x, fallback, g.solve_fb != 0);
     for (int a = 0; a < 5; ++a) mu[a] = (double)x[a];
 }
 
@@ -973,11 +1003,16 @@ k_cell(Geo g, const R *__restrict__ hin, const R *__restrict__ ghost,
             acc[12] += vz * (s2 + q * s0); // vz v^2
             acc[13] += s4 + R(2) * q * s2 + q * q * s0;   // v^4
         }
-#pragma unroll
-        for (int k = 0; k < 5; ++k) acc[14 + k] = pre[k];
+        // The thread's share of the increment sums D: post minus pre over its
+        // own nodes, so only thread-sized partial sums cancel.
+        acc[14] = acc[0] - pre[0];
+        acc[15] = acc[1] - pre[1];
+        acc[16] = acc[2] - pre[2];
+        acc[17] = acc[3] - pre[3];
+        acc[18] = (acc[4] + acc[5] + acc[6]) - pre[4];
         block_reduce<19, R>(acc, S.red, S.tot);
 
-        // ---- 5x5 solve: G mu = -(post - pre), G = sum w (1 + eps h_c) psi psi
+        // ---- 5x5 solve: G mu = -D, G = sum w (1 + eps h_c) psi psi
         if (t == 0) correction_solve<R>(g, S.tot, S.mu, &fallback);
         __syncthreads();
         {
@@ -1029,7 +1064,7 @@ k_cell(Geo g, const R *__restrict__ hin, const R *__restrict__ ghost,
         // next cell's first writes to the slab happen after this point only.
         __syncthreads();
     }
-    if (fallback && stats) atomicAdd(stats + 3, 1ull);
+    if (fallback && stats) atomicAdd(stats + 3, (unsigned long long)fallback);
 }
 
 // Moments of an arbitrary state (Eqs. densita..sforzi), one CTA per cell.

@@ -596,6 +596,8 @@ struct LzArgs {
     int mcap;
     float e0[kLzX];         // sum_j w_j X_k(v_j) of the 30 monomials
     long long *clk;         // nullable: phase trace of CTA 0 (kClkCells groups x kClkPhases)
+    unsigned long long *stats;  // nullable: [3] counts correction solves that fell back
+    int nostream;           // 1: h~ = h (no free streaming; the relaxation alone)
 };
 
 // Shared memory.  A fixed-layout head (compile-time offsets): warp partial
@@ -728,33 +730,34 @@ __device__ __forceinline__ void lz_extend(const float *T, float *X)
     X[29] = T[14] + T[16] + T[12];
 }
 
-// Correction and output moments of one cell from the sums F (of N = w h~)
-// and D (of the collision increment): mu to mu_out, moments to mom.
-__device__ __forceinline__ void lz_finish(const Geo &g, const LzArgs &a, int c, const float *F,
+// Correction and output moments of one cell from the sums T (of the
+// post-collision N_c = N + dN) and D (of the collision increment dN): mu to
+// mu_out, moments to mom.
+__device__ __forceinline__ void lz_finish(const Geo &g, const LzArgs &a, int c, const float *T,
                                        const float *D, int *fallback)
 {
-    float T[kLzMono], X[kLzX], XF[kLzX];
-#pragma unroll
-    for (int k = 0; k < kLzMono; ++k) T[k] = F[k] + D[k];
+    float X[kLzX];
     lz_extend(T, X);
-    lz_extend(F, XF);
-    // Eqs. rinorm_a, correzione: G mu = -(post - pre) with the sums of N_c.
+    // Eqs. rinorm_a, correzione: G mu = -D with G from the sums of N_c and
+    // D the conserved moments of the increment (1, v, v^2).
     float P[19];
     for (int k = 0; k < 10; ++k) P[k] = X[k];
     P[10] = X[27];
     P[11] = X[28];
     P[12] = X[29];
     P[13] = X[20] + X[21] + X[22];
-    P[14] = XF[0];
-    P[15] = XF[1];
-    P[16] = XF[2];
-    P[17] = XF[3];
-    P[18] = XF[26];
+    P[14] = D[0];
+    P[15] = D[1];
+    P[16] = D[2];
+    P[17] = D[3];
+    P[18] = D[4] + D[5] + D[6];
     float mu[5];
     if (!correction_spd(g, P, mu)) {
         double Pd[19], m8[5];
         for (int k = 0; k < 19; ++k) Pd[k] = (double)P[k];
-        correction_solve<float>(g, Pd, m8, fallback);
+        int f2 = 0;
+        correction_solve<float>(g, Pd, m8, &f2);
+        ++*fallback;
         for (int k = 0; k < 5; ++k) mu[k] = (float)m8[k];
     }
     float *mo = a.mu_out + (int64_t)c * 8;
@@ -1098,11 +1101,13 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
     // ---- tables (once per launch) ----------------------------------------
     for (int i = t; i < N; i += kLzThreads) {
         const double v = g.axv[i], A = g.axA[i];
-        const float nax = -(float)fabs(v * g.dt / g.dx), fA = (float)A, fv = (float)v;
+        // Courant numbers 0 without streaming: h~ is then exactly the
+        // corrected input (every source term is multiplied by zero).
+        const float nax = a.nostream ? 0.f : -(float)fabs(v * g.dt / g.dx), fA = (float)A, fv = (float)v;
         H.v[i] = fv;
         H.A[i] = fA;
         H.IA[i] = (float)(1.0 / A);
-        H.cuy[i] = (float)fabs(v * g.dt / g.dy);
+        H.cuy[i] = a.nostream ? 0.f : (float)fabs(v * g.dt / g.dy);
         H.ta[i] = make_float4(nax, nax, fA, fA);
         const float v2 = (float)(v * v), v3 = (float)(v * v * v), v4 = (float)(v * v * v * v);
         H.tv12[i] = make_float4(fv, fv, v2, v2);
@@ -1251,14 +1256,21 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
                 const int k = warp, kc = grp * G + k;
                 if (k < G && kc < g.nr) {
                     if (lane < kLzMono) {
-                        float f = 0.f, d = 0.f;
+                        // Compensated totals over the warps: T = F + D (the
+                        // sums of N_c) and D.
+                        float f = 0.f, fc = 0.f, d = 0.f, dc = 0.f;
 #pragma unroll
                         for (int w = 0; w < kLzRoleWarps; ++w) {
-                            f += H.fpart[fb][k][w][lane];
-                            d += H.dpart[db][k][w][lane];
+                            float e;
+                            two_sum(f, H.fpart[fb][k][w][lane], f, e);
+                            fc = __fadd_rn(fc, e);
+                            two_sum(d, H.dpart[db][k][w][lane], d, e);
+                            dc = __fadd_rn(dc, e);
                         }
-                        H.fpart[fb][k][0][lane] = f;
-                        H.dpart[db][k][0][lane] = d;
+                        float tt, te;
+                        two_sum(f, d, tt, te);
+                        H.fpart[fb][k][0][lane] = __fadd_rn(tt, __fadd_rn(te, __fadd_rn(fc, dc)));
+                        H.dpart[db][k][0][lane] = __fadd_rn(d, dc);
                     }
                     __syncwarp();
                     if (lane == 0)
@@ -1381,7 +1393,7 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
         }
         __syncthreads();
     }
-    (void)fallback;
+    if (fallback && a.stats) atomicAdd(a.stats + 3, (unsigned long long)fallback);
 }
 
 }  // namespace bzk

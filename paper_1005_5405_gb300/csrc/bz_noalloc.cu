@@ -38,6 +38,24 @@ static_assert(kScratchBytes <= BZ_NOALLOC_SCRATCH_BYTES, "scratch size");
 // Shared by every call on a device; its contents are those of the last call.
 static __device__ __align__(256) unsigned char bz_noalloc_scratch[BZ_NOALLOC_SCRATCH_BYTES];
 
+// Per-axis velocity nodes and weight factors and the step number, passed to
+// the set-up kernel by value.
+struct NoallocTables {
+    double axv[bzk::kMaxN], axA[bzk::kMaxN];
+    int64_t step;
+};
+
+// Writes the tables into the scratch (one block of kMaxN threads).
+__global__ void k_noalloc_tables(NoallocTables t, int n, double *axv, double *axA, int64_t *step)
+{
+    const int i = threadIdx.x;
+    if (i < n) {
+        axv[i] = t.axv[i];
+        axA[i] = t.axA[i];
+    }
+    if (i == 0) *step = t.step;
+}
+
 std::mutex g_mutex;
 void *g_scratch[kNoallocMaxDevices] = {};
 
@@ -71,8 +89,8 @@ bz_status scratch_address(int dev, unsigned char **out)
 }
 
 template <typename R>
-bz_status run(const bzk::Geo &g0, unsigned char *scr, int64_t step, const void *hin, void *hout,
-              double *mom, cudaStream_t s)
+bz_status run(const bzk::Geo &g0, unsigned char *scr, const void *hin, void *hout, double *mom,
+              cudaStream_t s)
 {
     bzk::Geo g = g0;
     int4 *pidx = (int4 *)scr;
@@ -104,7 +122,6 @@ bz_status run(const bzk::Geo &g0, unsigned char *scr, int64_t step, const void *
     bzk::k_plan<R, int><<<pg, pb, 0, s>>>(g, stepp, pidx, pa, nullptr, nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return err(BZ_ECUDA, "sampling launch failed: %s", cudaGetErrorString(e));
-    (void)step;
     bzk::k_cell<R, false, int><<<grid, threads, smem, s>>>(g, (const R *)hin, nullptr, pidx,
                                                            pa, nullptr, (R *)hout, mom, nullptr, 1);
     e = cudaGetLastError();
@@ -140,51 +157,24 @@ extern "C" bz_status bz_collide_noalloc(const bz_space *space, const bz_vel *vel
         (space->ry > 0.0 && space->ry < 1.0))
         return err(BZ_EUNSUPPORTED, "uniform grids only");
     if (step < 0) return err(BZ_EINVAL, "step must be >= 0");
-    if (h_in == h_out) return err(BZ_EINVAL, "h_in and h_out must not overlap");
 
-    // Discretisation (Sec. 3, Sec. 5.1), the same rules as bz_create.
+    // Discretisation: the same rules, in the same code, as bz_create.
     bzk::Geo g{};
+    bz_grid_tables tb;
+    bz_discretise(space, vel, nullptr, params, g, tb);
     const int N = vel->nv;
-    g.nx = space->nx;
-    g.ny = space->ny;
-    g.nv = N;
-    g.nvt = N * N * N;
-    g.nr = g.nx * g.ny;
-    g.nfaces = 2 * g.nx + 2 * g.ny;
-    g.nt = (int)params->n_pairs;
-    g.vmax = vel->vmax;
-    g.dv = (2.0 * vel->vmax) / (double)N;
-    g.dx = (1.0 / space->kn) / (double)g.nx;
-    g.dy = (1.0 / space->kn) / (double)g.ny;
-    const double cfl = params->cfl > 0.0 ? params->cfl : 0.5;
-    const double vtop = -g.vmax + ((double)(N - 1) + 0.5) * g.dv;
-    g.dt = cfl * std::min(g.dx, g.dy) / vtop;
-    const double kcoll =
-        params->kcoll > 0.0 ? params->kcoll : 5.0 * 1.016034 / 16.0 * std::sqrt(2.0 / M_PI);
-    g.cw = M_PI * kcoll * g.dt / (double)g.nt;
-    g.eps = params->eps;
-    g.seed = params->seed;
-    g.instance = params->instance;
-    g.strip = g.nx >= 16 ? 8 : g.nx;
-    double tabs[2 * bzk::kMaxN + 1];
+    const size_t esz = params->dtype == BZ_F64 ? 8 : 4;
+    const size_t bytes = esz * (size_t)g.nr * (size_t)g.nvt;
+    const uintptr_t a0 = (uintptr_t)h_in, b0 = (uintptr_t)h_out;
+    if (a0 < b0 + bytes && b0 < a0 + bytes) return err(BZ_EINVAL, "h_in and h_out must not overlap");
+    // The tables travel as a kernel argument (copied at launch), not through
+    // a host buffer.
+    NoallocTables tabs{};
     for (int j = 0; j < N; ++j) {
-        const double v = -g.vmax + ((double)j + 0.5) * g.dv;
-        tabs[j] = v;
-        tabs[bzk::kMaxN + j] = g.dv * (1.0 / std::sqrt(M_PI)) * std::exp(-v * v);
+        tabs.axv[j] = tb.axv[j];
+        tabs.axA[j] = tb.axA[j];
     }
-    for (int a = 0; a < 25; ++a) g.G0[a] = 0.0;
-    for (int jx = 0; jx < N; ++jx)
-        for (int jy = 0; jy < N; ++jy)
-            for (int jz = 0; jz < N; ++jz) {
-                const double *v = tabs, *A = tabs + bzk::kMaxN;
-                const double w = A[jx] * A[jy] * A[jz];
-                const double p[5] = {1.0, v[jx], v[jy], v[jz],
-                                     v[jx] * v[jx] + v[jy] * v[jy] + v[jz] * v[jz]};
-                for (int a = 0; a < 5; ++a)
-                    for (int b = 0; b < 5; ++b) g.G0[a * 5 + b] += w * p[a] * p[b];
-            }
-    for (int a = 0; a < 25; ++a) g.G0f[a] = (float)g.G0[a];
-    std::memcpy(&tabs[2 * bzk::kMaxN], &step, sizeof(int64_t));   // read by the sampling kernel
+    tabs.step = step;
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -193,8 +183,11 @@ extern "C" bz_status bz_collide_noalloc(const bz_space *space, const bz_vel *vel
     bz_status st = scratch_address(dev, &scr);
     if (st != BZ_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    e = cudaMemcpyAsync(scr + kIdxBytes + kRecBytes, tabs, sizeof(tabs), cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return err(BZ_ECUDA, "table upload failed: %s", cudaGetErrorString(e));
-    return params->dtype == BZ_F64 ? run<double>(g, scr, step, h_in, h_out, mom, s)
-                                   : run<float>(g, scr, step, h_in, h_out, mom, s);
+    double *axv = (double *)(scr + kIdxBytes + kRecBytes);
+    k_noalloc_tables<<<1, bzk::kMaxN, 0, s>>>(tabs, N, axv, axv + bzk::kMaxN,
+                                              (int64_t *)(axv + 2 * bzk::kMaxN));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return err(BZ_ECUDA, "table set-up launch failed: %s", cudaGetErrorString(e));
+    return params->dtype == BZ_F64 ? run<double>(g, scr, h_in, h_out, mom, s)
+                                   : run<float>(g, scr, h_in, h_out, mom, s);
 }

@@ -1,11 +1,13 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances: node selection is integer work and must agree exactly (samples
-whose velocity lies within 1e-9 dv of a cell face may legitimately differ,
-since libm and CUDA's log/cos/sin may differ by an ulp; both sides flag them).
-Floating point: max |f_gpu - f_oracle| / max f <= 1e-5 per step with
-f = Phi0 (1 + eps h); macroscopic fields within 1e-4 of their range after
-200 steps.
+Tolerances: node selection is integer work and must agree exactly, with no
+exception (both sides flag samples whose velocity lies within 1e-9 dv of a
+cell face, where an ulp of difference between libm and CUDA's log/cos/sin
+could move a node; none may differ either).  Floating point: max |f_gpu -
+f_oracle| / max f <= 1e-5 per step with f = Phi0 (1 + eps h), the oracle
+restarted from the GPU's state before every step (so the bound does not grow
+with the step count); macroscopic fields within 1e-4 of their range after
+200 steps of both sides running on their own.
 """
 import os
 import subprocess
@@ -76,15 +78,17 @@ def test_sample_plan_matches_oracle(nv, vmax, nt, dtype):
     p = workloads.small(nx=2, ny=2, nv=nv, vmax=vmax, nt=nt, seed=3, dtype=dtype)
     cav = binding.Cavity(p)
     o = oracle.Oracle(**p.kwargs())
+    flagged = 0
     for step in (0, 1, 57):
         idx, W = cav.sample_plan(step)
         s = o.samples(step)
         same = (idx == s["idx"]).all(1)
-        bad = ~same & (s["near_face"] == 0)
-        assert bad.sum() == 0, np.nonzero(bad)
+        flagged += int((s["near_face"] != 0).sum())
+        assert same.all(), (np.nonzero(~same), s["near_face"][~same])
         # s = v_r.k suffers cancellation, so ulp-level differences of libm and
         # CUDA cos/sin/log show up relative to the largest weight only
         assert np.max(np.abs(W - s["W"])) <= 1e-12 * np.max(s["W"])
+    print(f"node selection: 0 mismatches in {3 * nt} samples, {flagged} near a face")
 
 
 # ---------------------------------------------------------------- sub-steps
@@ -159,11 +163,12 @@ def test_fused_step_matches_oracle(p, kernel):
         assert cav.get_info().kernel_variant == 0
     if kernel in ("cell4", "t512"):
         assert cav.get_info().kernel_variant in (0, 1)
-    h_o = h0
+    h_g = h0
     for n in range(3):
         cav.step(1)
-        h_o, mom_o = o.step(h_o, n)
-        assert f_metric(o, state(cav), h_o) < 1e-5 * (n + 1)
+        h_o, mom_o = o.step(h_g, n)           # the oracle restarts from the GPU state
+        h_g = state(cav)
+        assert f_metric(o, h_g, h_o) < 1e-5, n
     mom_g = cav.moments().cpu().numpy()
     assert np.allclose(mom_g, mom_o, rtol=1e-4, atol=1e-5 * (1 + np.abs(mom_o).max()))
 
@@ -249,11 +254,63 @@ def test_200_steps_fp32_v24():
         assert np.max(np.abs(mom_g[:, k] - mom_o[:, k])) <= 1e-4 * rng_, k
 
 
+@pytest.mark.parametrize("nv,vmax,nt,nxy,kn,order", [(32, 5.0, 20000, 12, 0.05 * 256 / 12, "1"),
+                                                      (24, 4.5, 10000, 8, 0.1 * 64 / 8, None)],
+                         ids=["v32_ordered", "v24"])
+def test_200_steps_warm_start_hot_path(monkeypatch, nv, vmax, nt, nxy, kn, order):
+    """The benchmark's path (FP32 active-node kernel with deferred correction;
+    at 32^3 with the joint bank-aware term order forced on) run for 200 steps
+    from a seeded warm state, so the collision integral is non-zero from the
+    first step, against the oracle running the same 200 steps on its own:
+    density, velocity and temperature within 1e-4 of their range.  The cells
+    have the size of the 256^2 (32^3) and 64^2 (24^3) cavities."""
+    if order:
+        monkeypatch.setenv("BZ_LAZY_ORDER", order)
+    p = workloads.small(nx=nxy, ny=nxy, nv=nv, vmax=vmax, nt=nt, seed=3, kn=kn, lid_u0=0.0,
+                        lid_amp=0.05, lid_period=50.0)
+    cav, o, h0 = make(p, seed=7)
+    assert cav.get_info().kernel_variant == 2
+    cav.step(200)
+    h_o, mom_o = o.run(h0, 200)
+    mom_g = cav.moments().cpu().numpy()
+    for k in range(5):
+        rng_ = np.abs(mom_o[:, k]).max()
+        err = np.max(np.abs(mom_g[:, k] - mom_o[:, k])) / rng_
+        print(f"moment {k}: {err:.2e} of its range after 200 steps")
+        assert err <= 1e-4, k
+    st = cav.stats()
+    assert st[5] == 0          # no step overflowed the compact arrays
+
+
+def _lz_traversal(nx, ny, G, grid, b):
+    """Cells the active-node kernel's CTA b visits, in order: groups b, b +
+    grid, ... of G cells in the column-strip cell order (strips of 8 columns,
+    row by row inside a strip)."""
+    S = 8 if nx >= 16 else nx
+    full = nx // S
+
+    def cell_of(k):
+        if k < full * S * ny:
+            s_, r = divmod(k, S * ny)
+            return (r // S) * nx + s_ * S + r % S
+        R = nx - full * S
+        kk = k - full * S * ny
+        return (kk // R) * nx + full * S + kk % R
+
+    nr = nx * ny
+    ngroups = (nr + G - 1) // G
+    return [cell_of(grp * G + t) for grp in range(b, ngroups, grid) for t in range(G)
+            if grp * G + t < nr]
+
+
 def test_full_size_cavity256_v32_sampled_cells():
     """256x256 cells x 32^3 velocities, FP32, 2x10^4 samples: the launch
     configuration of the benchmark.  One step from a seeded warm state; the
-    oracle recomputes sampled cells one by one from their input slabs."""
+    oracle recomputes, one by one from their input slabs, every cell of the
+    lid row and of the left wall column, and every cell that the first and the
+    last CTA of the active-node kernel visit (one CTA per SM)."""
     import torch
+    from concurrent.futures import ThreadPoolExecutor
     p = workloads.cavity256_v32()
     rng = np.random.default_rng(7)
     coef = torch.from_numpy(0.3 * rng.standard_normal((p.nr, 6)).astype(np.float32)).cuda()
@@ -266,6 +323,7 @@ def test_full_size_cavity256_v32_sampled_cells():
     g = torch.Generator(device="cuda").manual_seed(7)
     h0 += 0.01 * torch.randn(h0.shape, generator=g, device="cuda")
     cav = binding.Cavity(p)
+    assert cav.get_info().kernel_variant == 2
     cav.set_state(h0, step=3)
     cav.step(1)
     out, step = cav.get_state()
@@ -273,18 +331,32 @@ def test_full_size_cavity256_v32_sampled_cells():
     mom = cav.moments().cpu().numpy()
     o = oracle.Oracle(**p.kwargs())
     nx, ny = p.nx, p.ny
-    cells = [0, nx - 1, (ny - 1) * nx, nx * ny - 1, nx // 2, (ny - 1) * nx + nx // 3,
-             (ny // 2) * nx, (ny // 2) * nx + nx - 1] + list(rng.integers(0, nx * ny, 6))
-    for c in cells:
-        c = int(c)
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    grid = min((p.nr + 3) // 4, nsm)
+    cells = set(range((ny - 1) * nx, ny * nx)) | set(range(0, nx * ny, nx))
+    cells |= set(_lz_traversal(nx, ny, 4, grid, 0)) | set(_lz_traversal(nx, ny, 4, grid, grid - 1))
+    cells = sorted(cells)
+    need = sorted({cc for c in cells for cc in (c, c - 1, c + 1, c - nx, c + nx) if 0 <= cc < p.nr})
+    pos = {cc: i for i, cc in enumerate(need)}
+    slabs = h0[torch.tensor(need, device="cuda")].double().cpu().numpy()
+    got_all = out[torch.tensor(cells, device="cuda")].double().cpu().numpy()
+
+    def one(c):
         ix, iy = c % nx, c // nx
-        sl = lambda cc: h0[cc].double().cpu().numpy()
-        ref, m = o.step_cell(c, sl(c), sl(c - 1) if ix > 0 else None,
-                             sl(c + 1) if ix < nx - 1 else None, sl(c - nx) if iy > 0 else None,
-                             sl(c + nx) if iy < ny - 1 else None, step=3)
-        got = out[c].double().cpu().numpy()
-        assert f_metric(o, got, ref) < 1e-5, c
+        sl = lambda cc: slabs[pos[cc]]
+        return o.step_cell(c, sl(c), sl(c - 1) if ix > 0 else None,
+                           sl(c + 1) if ix < nx - 1 else None, sl(c - nx) if iy > 0 else None,
+                           sl(c + nx) if iy < ny - 1 else None, step=3)
+
+    with ThreadPoolExecutor(max_workers=min(32, os.cpu_count() or 4)) as ex:
+        refs = list(ex.map(one, cells))
+    worst = 0.0
+    for k, (c, (ref, m)) in enumerate(zip(cells, refs)):
+        err = f_metric(o, got_all[k], ref)
+        worst = max(worst, err)
+        assert err < 1e-5, c
         assert np.allclose(mom[c], m, rtol=1e-4, atol=1e-5 * (1 + np.abs(m).max())), c
+    print(f"full-size step: {len(cells)} cells checked, worst f error {worst:.2e}")
 
 
 # ---------------------------------------------------------------- API
@@ -332,25 +404,37 @@ def test_deferred_correction_is_applied_by_every_reader():
                         lid_u0=0.1)
     cav, o, h0 = make(p)
     assert cav.get_info().kernel_variant == 2
-    h_o = h0
-    for n in range(3):
-        h_o, mom_o = o.step(h_o, n)
+    # cav takes three steps, each reading the pending corrections its
+    # predecessor left; ref takes the same steps with its state read (and so
+    # corrected in place) after two, and the oracle takes the third step
+    # from that state.
+    ref_cav, _, _ = make(p)
+    ref_cav.step(2)
+    h2 = state(ref_cav)
+    ref_cav.step(1)
     cav.step(3)
+    assert f_metric(o, state(ref_cav), state(cav)) < 1e-6
+    cav, _, _ = make(p)
+    cav.step(3)
+    h_o, mom_o = o.step(h2, 2)
     d = cav.lid_shear().cpu().numpy()
     ref = o.lid_shear(h_o, 3)
     assert np.allclose(d, ref, rtol=1e-4, atol=1e-5 * np.abs(ref).max())
     mom = cav.moments().cpu().numpy()
     assert np.allclose(mom, mom_o, rtol=1e-4, atol=1e-5 * (1 + np.abs(mom_o).max()))
-    assert f_metric(o, state(cav), h_o) < 3e-5
+    h_g = state(cav)
+    assert f_metric(o, h_g, h_o) < 1e-5
     # a split step after lazy steps, then fused steps again
     cav.step_ex(1, binding.BZ_SPLIT)
-    h_o, _ = o.step(h_o, 3)
-    assert f_metric(o, state(cav), h_o) < 4e-5
-    cav.step(2)
-    for n in (4, 5):
-        h_o, mom_o = o.step(h_o, n)
+    h_o, _ = o.step(h_g, 3)
+    h_g = state(cav)
+    assert f_metric(o, h_g, h_o) < 1e-5
+    cav.step(1)
+    h4 = state(cav)
+    cav.step(1)
+    h_o, mom_o = o.step(h4, 5)
     snap, st = cav.get_state()
-    assert st == 6 and f_metric(o, snap.double().cpu().numpy(), h_o) < 6e-5
+    assert st == 6 and f_metric(o, snap.double().cpu().numpy(), h_o) < 1e-5
     c2 = binding.Cavity(p)
     c2.set_state(snap.clone(), step=st)
     c2.step(1)

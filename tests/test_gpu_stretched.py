@@ -38,9 +38,7 @@ def test_sample_plan_on_stretched_velocity_cells(p):
     o = oracle.Oracle(**p.kwargs())
     idx, W = cav.sample_plan(3)
     ref = o.samples(3)
-    ok = ref["near_face"] == 0
-    assert ok.mean() > 0.99
-    assert np.array_equal(idx[ok], ref["idx"][ok])
+    assert np.array_equal(idx, ref["idx"])
     assert np.allclose(W, ref["W"], rtol=0, atol=1e-12 * np.abs(ref["W"]).max())
 
 
@@ -55,11 +53,12 @@ def test_streaming_with_per_cell_widths(p):
 @pytest.mark.parametrize("p", CASES, ids=IDS)
 def test_fused_steps_on_stretched_grids(p):
     cav, o, h0 = make(p)
-    h_o = h0
+    h_g = h0
     for n in range(3):
         cav.step(1)
-        h_o, mom_o = o.step(h_o, n)
-        assert f_metric(o, state(cav), h_o) < (1e-10 if p.dtype == "f64" else 1e-5) * (n + 1)
+        h_o, mom_o = o.step(h_g, n)           # the oracle restarts from the GPU state
+        h_g = state(cav)
+        assert f_metric(o, h_g, h_o) < (1e-10 if p.dtype == "f64" else 1e-5), n
     mom_g = cav.moments().cpu().numpy()
     assert np.allclose(mom_g, mom_o, rtol=1e-4, atol=1e-5 * (1 + np.abs(mom_o).max()))
 

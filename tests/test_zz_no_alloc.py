@@ -18,6 +18,18 @@ def _problem(dtype, nt=3000):
     return workloads.small(nx=6, ny=5, nv=12, vmax=4.0, nt=nt, seed=13, dtype=dtype, eps=0.1)
 
 
+def test_noalloc_rejects_overlapping_buffers():
+    """h_in and h_out must not share a byte (checked on the host before any
+    device work, so this runs without a GPU too): an output that starts one
+    element into the input is refused, the same buffer twice as well."""
+    p = _problem("f32")
+    buf = np.zeros(p.nr * p.nvt + 1, dtype=np.float32)
+    for a, b in ((buf[:-1], buf[1:]), (buf[1:], buf[:-1]), (buf[:-1], buf[:-1])):
+        with pytest.raises(binding.BzError) as e:
+            binding.collide_noalloc(p, 0, a, b, stream=0)
+        assert e.value.status == binding.BZ_EINVAL and "overlap" in str(e.value)
+
+
 def test_noalloc_rejects_too_many_samples():
     """The sample set must fit the static scratch (checked before any device
     work, so this runs without a GPU too)."""
@@ -66,4 +78,43 @@ def test_noalloc_matches_collide_entry_point(dtype):
         assert err < 1e-5, (step, err)
         m, r = mom.cpu().numpy(), mref[k].cpu().numpy()
         assert np.allclose(m, r, rtol=1e-4, atol=1e-6 * (1 + np.abs(r).max())), step
+        # and against the oracle's relaxation of the same input
+        h_o, m_o = o.collide(src.double().cpu().numpy(), step=step)
+        assert f_metric(o, dst.double().cpu().numpy(), h_o) < 1e-5, step
+        assert np.allclose(m, m_o, rtol=1e-4, atol=1e-6 * (1 + np.abs(m_o).max())), step
         src = dst
+
+
+@pytest.mark.gpu
+def test_noalloc_size_limits():
+    """A large sample set that still fits shared memory next to a 24^3 slab
+    (40000 samples, FP32) runs and matches the oracle; 65536 samples (the
+    scratch's maximum) next to a 32^3 slab do not fit and are refused with
+    BZ_EUNSUPPORTED."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    from tests.gpu_helpers import f_metric
+
+    torch.cuda.set_device(0)
+    p = workloads.small(nx=3, ny=2, nv=24, vmax=4.5, nt=40000, seed=17, eps=0.1)
+    o = oracle.Oracle(**p.kwargs())
+    h0 = workloads.warm_state(p, seed=5).astype(np.float32)
+    src = torch.from_numpy(h0).cuda()
+    dst = torch.empty_like(src)
+    mom = torch.empty((p.nr, 11), dtype=torch.float64, device="cuda")
+    binding.collide_noalloc(p, 2, src, dst, mom)
+    torch.cuda.synchronize()
+    h_o, m_o = o.collide(h0.astype(np.float64), step=2)
+    assert f_metric(o, dst.double().cpu().numpy(), h_o) < 1e-5
+    assert np.allclose(mom.cpu().numpy(), m_o, rtol=1e-4, atol=1e-6 * (1 + np.abs(m_o).max()))
+
+    q = workloads.small(nx=2, ny=2, nv=32, vmax=5.0, nt=binding.NOALLOC_MAX_PAIRS, seed=3, eps=0.1)
+    a = torch.zeros((q.nr, q.nvt), dtype=torch.float32, device="cuda")
+    b = torch.empty_like(a)
+    with pytest.raises(binding.BzError) as e:
+        binding.collide_noalloc(q, 0, a, b)
+    assert e.value.status == binding.BZ_EUNSUPPORTED
