@@ -171,8 +171,10 @@ static __global__ void k_scatter_fill(int nt, int T, const ushort4 *__restrict__
 // Gram matrix), then one step of iterative refinement whose residual
 // -D - G mu is evaluated exactly with error-free products and sums and
 // rounded once, so mu is as accurate as the FP32 entries of G and D allow.
-// False if a pivot is not positive.
-__device__ __forceinline__ bool correction_spd(const Geo &g, const float *P, float *mu)
+// False if a pivot is not positive.  lane >= 0: all 32 lanes of a warp call
+// it with the same P and their lane index, and lane a < 5 evaluates row a of
+// the residual (the rest is the same on every lane).
+__device__ __forceinline__ bool correction_spd(const Geo &g, const float *P, float *mu, int lane = -1)
 {
     if (g.solve_fb) return false;
     const float e = (float)g.eps;
@@ -223,18 +225,36 @@ __device__ __forceinline__ bool correction_spd(const Geo &g, const float *P, flo
 #pragma unroll
     for (int a = 0; a < 5; ++a) r[a] = b[a];
     lu_solve(r, x);
-#pragma unroll
-    for (int a = 0; a < 5; ++a) {
-        float hi = b[a], lo = 0.f;
+    // Row a of b - A x, exactly, rounded once.
+    auto residual = [&](const float (&Ar)[5], float ba) {
+        float hi = ba, lo = 0.f;
 #pragma unroll
         for (int c = 0; c < 5; ++c) {
             float p, pe, s, se;
-            two_prod(A[a][c], x[c], p, pe);
+            two_prod(Ar[c], x[c], p, pe);
             two_sum(hi, -p, s, se);
             hi = s;
             lo = __fadd_rn(lo, __fsub_rn(se, pe));
         }
-        r[a] = __fadd_rn(hi, lo);
+        return __fadd_rn(hi, lo);
+    };
+    if (lane < 0) {
+#pragma unroll
+        for (int a = 0; a < 5; ++a) r[a] = residual(A[a], b[a]);
+    } else {
+        float Ar[5], ba = 0.f;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) Ar[c] = 0.f;
+#pragma unroll
+        for (int a = 0; a < 5; ++a)
+            if (lane == a) {
+#pragma unroll
+                for (int c = 0; c < 5; ++c) Ar[c] = A[a][c];
+                ba = b[a];
+            }
+        const float ra = residual(Ar, ba);
+#pragma unroll
+        for (int a = 0; a < 5; ++a) r[a] = __shfl_sync(0xFFFFFFFFu, ra, a);
     }
     float dx[5];
     lu_solve(r, dx);

@@ -49,7 +49,7 @@ constexpr int kLzThreads = 2 * kLzRoleT;
 constexpr int kLzRoleWarps = kLzRoleT / 32;
 constexpr int kLzMaxG = 4;         // cells per CTA group
 constexpr int kLzMaxN = 32;        // velocity nodes per axis (N^2 / 4 <= kLzRoleT)
-constexpr int kLzStages = 4;       // streaming stages staged per thread
+constexpr int kLzStages = 5;       // streaming stages staged per thread
 
 // meta layout: [0] M, [1] overflow (M > mcap), [2] E (terms of the step),
 // [3] C (terms per thread).
@@ -732,10 +732,12 @@ __device__ __forceinline__ void lz_extend(const float *T, float *X)
 
 // Correction and output moments of one cell from the sums T (of the
 // post-collision N_c = N + dN) and D (of the collision increment dN): mu to
-// mu_out, moments to mom.
+// mu_out, moments to mom.  Called by all 32 lanes of a warp (the lanes share
+// the residual of the solve); lane 0 stores.
 __device__ __forceinline__ void lz_finish(const Geo &g, const LzArgs &a, int c, const float *T,
                                        const float *D, int *fallback)
 {
+    const int lane = threadIdx.x & 31;
     float X[kLzX];
     lz_extend(T, X);
     // Eqs. rinorm_a, correzione: G mu = -D with G from the sums of N_c and
@@ -752,14 +754,15 @@ __device__ __forceinline__ void lz_finish(const Geo &g, const LzArgs &a, int c, 
     P[17] = D[3];
     P[18] = D[4] + D[5] + D[6];
     float mu[5];
-    if (!correction_spd(g, P, mu)) {
+    if (!correction_spd(g, P, mu, lane)) {
         double Pd[19], m8[5];
         for (int k = 0; k < 19; ++k) Pd[k] = (double)P[k];
         int f2 = 0;
         correction_solve<float>(g, Pd, m8, &f2);
-        ++*fallback;
+        if (lane == 0) ++*fallback;
         for (int k = 0; k < 5; ++k) mu[k] = (float)m8[k];
     }
+    if (lane != 0) return;
     float *mo = a.mu_out + (int64_t)c * 8;
     for (int k = 0; k < 5; ++k) mo[k] = mu[k];
     // Moments of h^{n+1}: sum w h phi = sum N_c phi + sum_a mu_a (E0 + eps sum N_c psi_a phi).
@@ -998,11 +1001,12 @@ __device__ __forceinline__ void lz_stream_stage(uint32_t sl, int jx, int j0, int
     }
 }
 
-// g = ha + hb + eps ha hb per cell, acc += w g (Eq. monteCarloInt: the
-// sample's product, signed and weighted for its destination).
+// g = ha + hb + eps ha hb per cell, as ha + hb (1 + eps ha), and acc += w g
+// (Eq. monteCarloInt: the sample's product, signed and weighted for its
+// destination).
 __device__ __forceinline__ void lz_term(float2 ha, float2 hb, float2 eps2, float2 w2, float2 &acc)
 {
-    const float2 g = lz_fma2(lz_mul2(eps2, ha), hb, lz_add2(ha, hb));
+    const float2 g = lz_fma2(hb, lz_fma2(eps2, ha, lz_dup(1.f)), ha);
     acc = lz_fma2(w2, g, acc);
 }
 __device__ __forceinline__ void lz_term(float4 ha, float4 hb, float2 eps2, float2 w2, float4 &acc)
@@ -1273,8 +1277,7 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
                         H.dpart[db][k][0][lane] = __fadd_rn(d, dc);
                     }
                     __syncwarp();
-                    if (lane == 0)
-                        lz_finish(g, a, cell_of(g, kc), H.fpart[fb][k][0], H.dpart[db][k][0], &fallback);
+                    lz_finish(g, a, cell_of(g, kc), H.fpart[fb][k][0], H.dpart[db][k][0], &fallback);
                     __syncwarp();
                     // The slots take the increment sums of a later group (atomically).
                     for (int i = lane; i < kLzRoleWarps * 32; i += 32) (&H.dpart[db][k][0][0])[i] = 0.f;
