@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--config", default="cavity256_v32")
+    ap.add_argument("--repeats", type=int, default=5,
+                    help="timed blocks of --steps steps (adjoint128_v20, batch64)")
     return ap.parse_args()
 
 
@@ -446,7 +448,9 @@ def run_batch(args):
 def run_adjoint(args):
     """The adjoint step (bz_adjoint_step) against the forward step on the
     128x128 cavity with a 20^3 velocity grid (per-face lid speeds), and the
-    whole checkpointed backward pass of an M-step rollout per step."""
+    whole checkpointed backward pass of an M-step rollout per step.  The
+    forward and adjoint steps are timed in `repeats` alternating blocks of
+    `steps` steps each; the line reports the median ratio and its spread."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -469,14 +473,18 @@ def run_adjoint(args):
 
     for _ in range(args.warmup):
         cav.step(1)
-    t_fwd = timed(lambda i: cav.step(1), args.steps)
     h = cav.get_state()[0].clone()
     lam = torch.randn_like(h) * 1e-3
     g = torch.zeros(p.nx, dtype=torch.float64, device="cuda")
     for i in range(args.warmup):
         cav.adjoint_step(i, h, lam, lam, g, 0.1)
-    t_adj = timed(lambda i: cav.adjoint_step(100 + i, h, lam, lam, g, 0.1), args.steps)
-    M, every = args.steps, max(1, args.steps // 2)
+    fwd, adj = [], []
+    for r in range(args.repeats):
+        fwd.append(timed(lambda i: cav.step(1), args.steps))
+        adj.append(timed(lambda i: cav.adjoint_step(100 + i, h, lam, lam, g, 0.1), args.steps))
+    ratios = sorted(a / f for a, f in zip(adj, fwd))
+    t_fwd, t_adj = statistics.median(fwd), statistics.median(adj)
+    M, every = min(args.steps, 50), max(1, min(args.steps, 50) // 2)
     prof = torch.tensor(p.lid_profile, dtype=torch.float64, requires_grad=True)
     x0 = h0.clone().requires_grad_(True)
     torch.cuda.synchronize()
@@ -489,13 +497,18 @@ def run_adjoint(args):
     t2 = time.perf_counter()
     line = {
         "metric": "adjoint step time / forward step time (128^2 x 20^3 FP32 cavity)",
-        "value": t_adj / t_fwd, "unit": "ratio", "n_gpus": 1, "steps": args.steps,
+        "value": statistics.median(ratios), "unit": "ratio", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_adj * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "adjoint128_v20", "nx": p.nx, "ny": p.ny, "nv": p.nv,
-                   "samples_per_step": p.nt, "l2": "state 524 MB > L2, no flush"},
+                   "samples_per_step": p.nt, "l2": "state 524 MB > L2, no flush",
+                   "repeats": args.repeats},
+        "ratio_median": statistics.median(ratios), "ratio_min": ratios[0], "ratio_max": ratios[-1],
+        "ratios": [round(x, 4) for x in ratios],
         "forward_ms_per_step": t_fwd * 1e3,
         "adjoint_ms_per_step": t_adj * 1e3,
+        "forward_ms_each": [round(x * 1e3, 4) for x in fwd],
+        "adjoint_ms_each": [round(x * 1e3, 4) for x in adj],
         "rollout": {"steps": M, "checkpoint_every": every,
                     "forward_ms_per_step": (t1 - t0) / M * 1e3,
                     "backward_ms_per_step": (t2 - t1) / M * 1e3,

@@ -264,7 +264,6 @@ bz_status configure_cell4(bz_handle *H)
     H->fast = false;
     if (force && strcmp(force, "generic") == 0) return BZ_OK;
     if (H->per_cell) return BZ_OK;         // the shared-set kernels only
-    if (H->stretched) return BZ_OK;        // uniform grids only
     if (H->dtype != BZ_F32 || !H->idx16 || N % 4 != 0 || N < 12) return BZ_OK;
     if (g.nt > 32768) return BZ_OK;                 // 15-bit sample index in the scatter list
     if (bzk::cell4_smem_bytes(N, g.nvt, g.nt) > (size_t)H->smem_optin) return BZ_OK;
@@ -368,34 +367,37 @@ double lz_monomial(int k, double x, double y, double z)
 }
 
 // Velocity axes with a kernel specialised on their length (the others run
-// the kernel that reads it at run time).
-int lz_nv_key(int nv) { return nv == 32 || nv == 20 ? nv : 0; }
+// the kernel that reads it at run time); stretched grids take the run-time
+// length with per-cell Courant factors.
+int lz_nv_key(const bz_handle *H) { return H->stretched ? -1 : (H->g.nv == 32 || H->g.nv == 20 ? H->g.nv : 0); }
 
-template <int G, int NV>
+template <int G, int NV, bool SX>
 bz_status setup_lz_one(bz_handle *H, size_t smem, int *occ)
 {
-    BZ_CUDA(bz_allow_max_smem(bzk::k_lz<G, NV>, H->smem_optin));
-    BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, bzk::k_lz<G, NV>, H->lz_T, smem));
+    BZ_CUDA(bz_allow_max_smem(bzk::k_lz<G, NV, SX>, H->smem_optin));
+    BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, bzk::k_lz<G, NV, SX>, H->lz_T, smem));
     return BZ_OK;
 }
 
 template <int G>
 bz_status setup_lz_kernel(bz_handle *H, size_t smem, int *occ)
 {
-    switch (lz_nv_key(H->g.nv)) {
-    case 32: return setup_lz_one<G, 32>(H, smem, occ);
-    case 20: return setup_lz_one<G, 20>(H, smem, occ);
-    default: return setup_lz_one<G, 0>(H, smem, occ);
+    switch (lz_nv_key(H)) {
+    case 32: return setup_lz_one<G, 32, false>(H, smem, occ);
+    case 20: return setup_lz_one<G, 20, false>(H, smem, occ);
+    case -1: return setup_lz_one<G, 0, true>(H, smem, occ);
+    default: return setup_lz_one<G, 0, false>(H, smem, occ);
     }
 }
 
 template <int G>
 void launch_lz_kernel(bz_handle *H, const bzk::LzArgs &a, cudaStream_t s)
 {
-    switch (lz_nv_key(H->g.nv)) {
-    case 32: bzk::k_lz<G, 32><<<H->lz_grid, H->lz_T, H->lz_smem, s>>>(H->g, a); break;
-    case 20: bzk::k_lz<G, 20><<<H->lz_grid, H->lz_T, H->lz_smem, s>>>(H->g, a); break;
-    default: bzk::k_lz<G, 0><<<H->lz_grid, H->lz_T, H->lz_smem, s>>>(H->g, a); break;
+    switch (lz_nv_key(H)) {
+    case 32: bzk::k_lz<G, 32, false><<<H->lz_grid, H->lz_T, H->lz_smem, s>>>(H->g, a); break;
+    case 20: bzk::k_lz<G, 20, false><<<H->lz_grid, H->lz_T, H->lz_smem, s>>>(H->g, a); break;
+    case -1: bzk::k_lz<G, 0, true><<<H->lz_grid, H->lz_T, H->lz_smem, s>>>(H->g, a); break;
+    default: bzk::k_lz<G, 0, false><<<H->lz_grid, H->lz_T, H->lz_smem, s>>>(H->g, a); break;
     }
 }
 
@@ -621,6 +623,10 @@ bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true, bo
         a.clk = H->prof_clk;
         a.stats = H->stats;
         a.nostream = nostream ? 1 : 0;
+        // Below 32^3 velocities the streaming of a group takes longer than
+        // its collision terms: the collision warps start the increment sums.
+        a.early_tail = g.nv < 32 ? 1 : 0;
+        if (const char *et = getenv("BZ_LAZY_EARLY_TAIL")) a.early_tail = atoi(et) != 0 ? 1 : 0;
         if (H->lz_G == 4) launch_lz_kernel<4>(H, a, s);
         else launch_lz_kernel<2>(H, a, s);
         BZ_LAUNCHED(H);

@@ -330,10 +330,12 @@ static __global__ void __launch_bounds__(1024) k_stream4(Geo g, const float *__r
     const float ry = (float)(g.dx / g.dy);
     const int q = threadIdx.x % Q, jxs = threadIdx.x / Q, jstep = blockDim.x / Q;
     const int jy = q / nq;
-    const float ay = fabsf(scu[jy] * ry);
     for (int kc = blockIdx.x; kc < g.nr; kc += gridDim.x) {
         const int c = cell_of(g, kc);
         const int ix = c % g.nx, iy = c / g.nx;
+        // Courant factors of this cell (its own widths on stretched grids).
+        const float fx = g.sx ? (float)g.sx[ix] : 1.f, fy = g.sy ? (float)g.sy[iy] : ry;
+        const float ay = fabsf(scu[jy]) * fy;
         const float4 *own = reinterpret_cast<const float4 *>(hin) + (int64_t)c * plane;
         float4 *dst = reinterpret_cast<float4 *>(hout) + (int64_t)c * plane;
         if (ix > 0 && ix < g.nx - 1 && iy > 0 && iy < g.ny - 1) {
@@ -343,7 +345,7 @@ static __global__ void __launch_bounds__(1024) k_stream4(Geo g, const float *__r
             for (int jx = jxs; jx < N; jx += jstep) {
                 const int o = jx * Q + q;
                 const float4 hx = jx < half ? xr[o] : xl[o];
-                dst[o] = upwind4(own[o], hx, ys[o], fabsf(scu[jx]), ay);
+                dst[o] = upwind4(own[o], hx, ys[o], fabsf(scu[jx]) * fx, ay);
             }
         } else {
             for (int jx = jxs; jx < N; jx += jstep) {
@@ -356,7 +358,7 @@ static __global__ void __launch_bounds__(1024) k_stream4(Geo g, const float *__r
                                        : f4(ghost[(2 * g.ny + g.nx + ix) * N + jx]);
                 else
                     hy = iy > 0 ? own[o - (int64_t)g.nx * plane] : f4(ghost[(2 * g.ny + ix) * N + jx]);
-                dst[o] = upwind4(own[o], hx, hy, fabsf(scu[jx]), ay);
+                dst[o] = upwind4(own[o], hx, hy, fabsf(scu[jx]) * fx, ay);
             }
         }
     }
@@ -728,7 +730,9 @@ __device__ __forceinline__ void cell4_cell(const Geo &g, const Map4 &m, int c,
     // ---- slab <- h~ ------------------------------------------------------
     if (active) {
         if (FUSED) {
-            const float cuy = S.cu[jy] * ry, ay = fabsf(cuy);
+            // Courant factors of this cell (its own widths on stretched grids).
+            const float fx = g.sx ? (float)g.sx[ix] : 1.f, fy = g.sy ? (float)g.sy[iy] : ry;
+            const float cuy = S.cu[jy] * fy, ay = fabsf(cuy);
             const int64_t plane = (int64_t)nvt / 4;
             if (ix > 0 && ix < g.nx - 1 && iy > 0 && iy < g.ny - 1) {
                 // Interior cell: all upwind sources are neighbour slabs.
@@ -740,13 +744,13 @@ __device__ __forceinline__ void cell4_cell(const Geo &g, const Map4 &m, int c,
                 for (int jx = jx0; jx < e; ++jx) {
                     const int o = jx * Q4 + q;
                     const float4 h0 = own4[o], hx = xr[o], hy = ys[o];
-                    S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]), ay);
+                    S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]) * fx, ay);
                 }
 #pragma unroll 4
                 for (int jx = b; jx < jx1; ++jx) {
                     const int o = jx * Q4 + q;
                     const float4 h0 = own4[o], hx = xl[o], hy = ys[o];
-                    S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]), ay);
+                    S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]) * fx, ay);
                 }
             } else {
                 const float4 *ys = nullptr;
@@ -767,7 +771,7 @@ __device__ __forceinline__ void cell4_cell(const Geo &g, const Map4 &m, int c,
                     else             // v_x > 0: left neighbour or left-wall ghost
                         hx = ix > 0 ? own4[o - plane] : f4(ghost[iy * N + jy]);
                     const float4 hy = ys ? ys[o] : f4(yg[jx]);
-                    S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]), ay);
+                    S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]) * fx, ay);
                 }
             }
         } else {

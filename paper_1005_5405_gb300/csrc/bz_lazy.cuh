@@ -598,6 +598,7 @@ struct LzArgs {
     long long *clk;         // nullable: phase trace of CTA 0 (kClkCells groups x kClkPhases)
     unsigned long long *stats;  // nullable: [3] counts correction solves that fell back
     int nostream;           // 1: h~ = h (no free streaming; the relaxation alone)
+    int early_tail;         // 1: the collision warps start the increment sums at once
 };
 
 // Shared memory.  A fixed-layout head (compile-time offsets): warp partial
@@ -608,7 +609,7 @@ struct LzArgs {
 // increments, the per-thread staging slots of the streaming prefetch
 // (kLzStages stages x {own, x source, y source} x streaming threads, 16 bytes
 // each), the active-node bit mask, its word prefixes and the node list.
-struct LzHead {
+struct alignas(128) LzHead {
     float fpart[3][kLzMaxG][kLzRoleWarps][32];   // warp partials of the F sums, per group (it mod 3)
     float dpart[2][kLzMaxG][kLzRoleWarps][32];   // warp partials of the D sums, per group (it mod 2)
     float4 ta[kLzMaxN];                          // -ax, -ax, A, A
@@ -619,6 +620,7 @@ struct LzHead {
     float2 tcy[kLzMaxG][2][kLzMaxN];             // ca of the cell below (0) and above (1), duplicated
     float mus[kLzMaxG][5][8];                    // mu of own, right, left, below, above (0 outside)
     int4 cell[2][kLzMaxG];                       // c, ix, iy of a group's cells (c < 0: none), per buffer
+    int tail_next;                               // next chunk of the increment sums to claim
 };
 constexpr uint32_t kLzAOff = (sizeof(LzHead) + 15) & ~(size_t)15;
 
@@ -950,18 +952,19 @@ struct LzAcc {
 
 // One streaming stage of one cell (Eq. streaming2D with the deferred
 // correction applied to its sources): h~ to dst, the power sums, and the
-// active nodes of the quad to the compact array (component k of G).
-template <int G>
+// active nodes of the quad to the compact array (component k of G).  SX:
+// stretched cells, the x Courant numbers times the cell's factor fx2.
+template <int G, bool SX>
 __device__ __forceinline__ void lz_stream_stage(uint32_t sl, int jx, int j0, int k, const LzHead &H,
                                                 const float4 *tcx, const float2 *tcy, LzAcc &c,
                                                 float4 *dst, const uint32_t *smask, const uint16_t *swpre,
-                                                float *Af, float2 eps2, float2 one2, float2 nay2)
+                                                float *Af, float2 eps2, float2 one2, float2 nay2, float2 fx2)
 {
     const float4 h0 = lz_lds4(sl), hx = lz_lds4(sl + kLzSrcStride), hy = lz_lds4(sl + 2 * kLzSrcStride);
     const float4 cx4 = tcx[jx];
     const float2 cy2 = tcy[jx];
     const float4 ta = H.ta[jx];
-    const float2 nax2 = lz_lo(ta), A2 = lz_hi(ta);
+    const float2 nax2 = SX ? lz_mul2(lz_lo(ta), fx2) : lz_lo(ta), A2 = lz_hi(ta);
     const float4 v12 = H.tv12[jx], v34 = H.tv34[jx];
     const float2 h0p[2] = {lz_lo(h0), lz_hi(h0)}, hxp[2] = {lz_lo(hx), lz_hi(hx)},
                  hyp[2] = {lz_lo(hy), lz_hi(hy)};
@@ -1063,6 +1066,17 @@ __device__ __forceinline__ void lz_role_bar(int id)
 {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(kLzRoleT) : "memory");
 }
+// Named barrier 3 over all threads: the collision role arrives without
+// waiting once its terms are complete; the streaming role waits for that.
+__device__ __forceinline__ void lz_terms_done_arrive()
+{
+    asm volatile("bar.arrive 3, %0;" ::"n"(kLzThreads) : "memory");
+}
+__device__ __forceinline__ void lz_terms_done_wait()
+{
+    asm volatile("bar.sync 3, %0;" ::"n"(kLzThreads) : "memory");
+}
+constexpr int kLzTailChunk = 256;  // active nodes per claimed chunk of the increment sums
 
 // One CTA of 512 threads per SM, two roles working on consecutive groups of
 // G cells: warps 0-7 stream group i (Eq. streaming2D, the power sums, the
@@ -1073,10 +1087,11 @@ __device__ __forceinline__ void lz_role_bar(int id)
 // the two overlap.
 //
 // NV: the velocity axis length as a compile-time constant (0: read g.nv at
-// run time).  Streaming thread t < S = K N^2/4 owns node quad q = t mod
+// run time).  SX: stretched cells (per-column and per-row Courant factors
+// g.sx, g.sy).  Streaming thread t < S = K N^2/4 owns node quad q = t mod
 // (N^2/4) (four consecutive jz at one (jx, jy)) of jx-plane t div (N^2/4) of
 // every stage; a stage covers K planes and a cell J = N / K stages.
-template <int G, int NV>
+template <int G, int NV, bool SX>
 __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
 {
     using V = typename LzVec<G>::T;
@@ -1111,7 +1126,7 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
         H.v[i] = fv;
         H.A[i] = fA;
         H.IA[i] = (float)(1.0 / A);
-        H.cuy[i] = a.nostream ? 0.f : (float)fabs(v * g.dt / g.dy);
+        H.cuy[i] = a.nostream ? 0.f : (float)fabs(v * g.dt / (SX ? g.dx : g.dy));
         H.ta[i] = make_float4(nax, nax, fA, fA);
         const float v2 = (float)(v * v), v3 = (float)(v * v * v), v4 = (float)(v * v * v * v);
         H.tv12[i] = make_float4(fv, fv, v2, v2);
@@ -1211,6 +1226,12 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
                     const float4 *tcx = H.tcx[k];
                     const float2 *tcy = H.tcy[k][yup ? 0 : 1];
                     float4 *dst = hout4 + (int64_t)cells[k].x * plane4 + t;
+                    // Courant factors of this cell on stretched grids.
+                    float2 fx2 = one2, nay2k = nay2;
+                    if (SX) {
+                        fx2 = lz_dup((float)g.sx[cells[k].y]);
+                        nay2k = lz_dup(-H.cuy[jy] * (float)g.sy[cells[k].z]);
+                    }
                     int jx = pl, j0 = 4 * t;
 #pragma unroll 1
                     for (int st = 0; st < J; ++st) {
@@ -1220,8 +1241,8 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
                         lz_prefetch(pf, qd, g, a, cells, hin_t, ncell);
                         lz_cp_wait_stage();
                         if (streams)
-                            lz_stream_stage<G>(cslot, jx, j0, k, H, tcx, tcy, ac, dst, smask, swpre, Af, eps2,
-                                               one2, nay2);
+                            lz_stream_stage<G, SX>(cslot, jx, j0, k, H, tcx, tcy, ac, dst, smask, swpre, Af,
+                                                   eps2, one2, nay2k, fx2);
                         cslot += kLzSlotStride;
                         if (cslot == qd.ring_end) cslot = ring0;
                         jx += P4;
@@ -1299,6 +1320,7 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
             // nodes outside the grid, and cells missing from a short group hold 0.
             for (int i = tc; i < M + 1; i += kLzRoleT) lz_set_zero(Bv[i]);
             if (tc < G) Af[M * G + tc] = 0.f;
+            if (tc == 0) H.tail_next = 0;
             if (ncell < G)
                 for (int i = tc; i < M * G; i += kLzRoleT)
                     if (i % G >= ncell) Af[i] = 0.f;
@@ -1352,14 +1374,30 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
                 }
             }
             if (clk && tc == 0) a.clk[it * kClkPhases + 2] = clock64();
+            if (NV != 32 && a.early_tail) {
+                // The increments are complete once every collision thread is here.
+                lz_role_bar(2);
+                lz_terms_done_arrive();
+            }
         }
         // ---- sums of the collision increment and h_c = h~ + dN / w on the
-        // active nodes of group it - 1, two cells at a time, by both roles
-        // (the increments are complete after the barrier; each warp adds its
-        // partial sums to the slots of warp (warp mod 8)).
+        // active nodes of group it - 1, two cells at a time.  Either all
+        // warps after a CTA barrier, each with a fixed share of the nodes and
+        // its partial sums added to the slots of warp (warp mod 8); or
+        // (early tail, for when the collision terms take less time than the
+        // streaming; never at 32^3 velocities) the collision warps as soon as
+        // their terms are complete and the streaming warps once they are
+        // done, every warp claiming chunks of kLzTailChunk nodes of one cell
+        // pair at a time (pair 0 first) and adding its partial sums of a pair
+        // to the slots when it moves on.
         if (it >= 1 && it <= nmine) {
-            __syncthreads();
-            const int buf = (it - 1) & 1, u = t ^ kLzRoleT;
+            const bool early = NV != 32 && a.early_tail;
+            if (early) {
+                if (streamer) lz_terms_done_wait();
+            } else {
+                __syncthreads();
+            }
+            const int buf = (it - 1) & 1;
             const float *Af = reinterpret_cast<const float *>(smem_raw + kLzAOff + buf * so.abytes);
             int ncell = 0, cg[G];
 #pragma unroll
@@ -1367,13 +1405,57 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
                 cg[k] = H.cell[buf][k].x;
                 ncell += cg[k] >= 0 ? 1 : 0;
             }
+            if (!early) {
+                const int u = t ^ kLzRoleT;
 #pragma unroll
-            for (int k2 = 0; k2 < G; k2 += 2) {
+                for (int k2 = 0; k2 < G; k2 += 2) {
+                    float2 D2[32];
+#pragma unroll
+                    for (int r = 0; r < 32; ++r) D2[r] = lz_zero2();
+                    if (k2 < ncell) {
+                        for (int mm = u; mm < M; mm += kLzThreads) {
+                            const int j = sact[mm], jxy = j / N;
+                            const int jx = jxy / N, jyy = jxy - jx * N, jz = j - jxy * N;
+                            const float2 d = *reinterpret_cast<const float2 *>(Bf + mm * G + k2);
+                            const float2 h = *reinterpret_cast<const float2 *>(Af + mm * G + k2);
+                            const float x = H.v[jx], x2 = x * x;
+                            const float2 sp[5] = {d, lz_mul2(d, lz_dup(x)), lz_mul2(d, lz_dup(x2)),
+                                                  lz_mul2(d, lz_dup(x2 * x)), lz_mul2(d, lz_dup(x2 * x2))};
+                            lz_mono_from_powers2(sp, H.v[jyy], H.v[jz], D2);
+                            const float iw = H.IA[jx] * H.IA[jyy] * H.IA[jz];
+                            a.hout[(int64_t)cg[k2] * nvt + j] = fmaf(d.x, iw, h.x);
+                            if (k2 + 1 < ncell) a.hout[(int64_t)cg[k2 + 1] * nvt + j] = fmaf(d.y, iw, h.y);
+                        }
+                    }
+                    const float2 r = lz_warp_reduce_scatter2(D2);
+                    atomicAdd(&H.dpart[buf][k2][warp & (kLzRoleWarps - 1)][lane], r.x);
+                    atomicAdd(&H.dpart[buf][k2 + 1][warp & (kLzRoleWarps - 1)][lane], r.y);
+                }
+            } else {
+                const int npair = (ncell + 1) / 2, per = (M + kLzTailChunk - 1) / kLzTailChunk;
+                const int nchunk = npair * per;
                 float2 D2[32];
 #pragma unroll
                 for (int r = 0; r < 32; ++r) D2[r] = lz_zero2();
-                if (k2 < ncell) {
-                    for (int mm = u; mm < M; mm += kLzThreads) {
+                int kcur = -1;
+                for (;;) {
+                    int ch = 0;
+                    if (lane == 0) ch = atomicAdd(&H.tail_next, 1);
+                    ch = __shfl_sync(0xFFFFFFFFu, ch, 0);
+                    const int k2 = ch < nchunk ? 2 * (ch / per) : -1;
+                    if (k2 != kcur) {
+                        if (kcur >= 0) {
+                            const float2 r = lz_warp_reduce_scatter2(D2);
+                            atomicAdd(&H.dpart[buf][kcur][warp & (kLzRoleWarps - 1)][lane], r.x);
+                            atomicAdd(&H.dpart[buf][kcur + 1][warp & (kLzRoleWarps - 1)][lane], r.y);
+#pragma unroll
+                            for (int r2 = 0; r2 < 32; ++r2) D2[r2] = lz_zero2();
+                        }
+                        kcur = k2;
+                    }
+                    if (k2 < 0) break;
+                    const int m0 = (ch - (k2 / 2) * per) * kLzTailChunk, m1 = min(M, m0 + kLzTailChunk);
+                    for (int mm = m0 + lane; mm < m1; mm += 32) {
                         const int j = sact[mm], jxy = j / N;
                         const int jx = jxy / N, jyy = jxy - jx * N, jz = j - jxy * N;
                         const float2 d = *reinterpret_cast<const float2 *>(Bf + mm * G + k2);
@@ -1387,9 +1469,6 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
                         if (k2 + 1 < ncell) a.hout[(int64_t)cg[k2 + 1] * nvt + j] = fmaf(d.y, iw, h.y);
                     }
                 }
-                const float2 r = lz_warp_reduce_scatter2(D2);
-                atomicAdd(&H.dpart[buf][k2][warp & (kLzRoleWarps - 1)][lane], r.x);
-                atomicAdd(&H.dpart[buf][k2 + 1][warp & (kLzRoleWarps - 1)][lane], r.y);
             }
             if (clk && t == kLzRoleT) a.clk[it * kClkPhases + 3] = clock64();
             if (clk && t == kLzRoleT) a.clk[it * kClkPhases + 4] = clock64();

@@ -121,20 +121,24 @@ def test_collide_matches_oracle(p, kernel):
     assert np.allclose(mom_g, mom_o, rtol=1e-4, atol=1e-6 * (1 + np.abs(mom_o).max()))
 
 
-@pytest.fixture(params=["auto", "ordered", "ordered_g2", "unordered", "overflow", "cell4", "t512",
-                        "generic"])
+@pytest.fixture(params=["auto", "ordered", "ordered_g2", "unordered", "joint_tail", "overflow", "cell4",
+                        "t512", "generic"])
 def kernel(request, monkeypatch):
     """Run a test with the library's own choice of per-cell kernel (the FP32
     active-node kernel with deferred correction where it applies); with that
     kernel's term runs in the joint bank-aware order (forced on, in chunks of
     16 or 24 positions, for groups of four cells and of two), and with no
-    order; with that kernel's compact arrays capped below the step's
+    order; with the increment sums after a CTA barrier instead of started
+    early by the collision warps (the default below 32^3 velocities); with
+    that kernel's compact arrays capped below the step's
     active-node count (every step then takes the k_cell4 fallback on the
     device); with the FP32 4-node-vector kernel (BZ_KERNEL=cell4) in its
     1024- and 512-thread shapes; and with the generic kernel."""
     for k in ("BZ_KERNEL", "BZ_CELL_THREADS", "BZ_LAZY_MCAP", "BZ_LAZY_ORDER", "BZ_LAZY_NOORDER",
-              "BZ_LAZY_ORDER_CHUNK", "BZ_LAZY_G"):
+              "BZ_LAZY_ORDER_CHUNK", "BZ_LAZY_G", "BZ_LAZY_EARLY_TAIL"):
         monkeypatch.delenv(k, raising=False)
+    if request.param == "joint_tail":
+        monkeypatch.setenv("BZ_LAZY_EARLY_TAIL", "0")
     if request.param == "ordered":
         monkeypatch.setenv("BZ_LAZY_ORDER", "1")
         monkeypatch.setenv("BZ_LAZY_ORDER_CHUNK", "16")
