@@ -940,6 +940,8 @@ void bz_discretise(const bz_space *space, const bz_vel *vel, const bz_walls *wal
     g.lid_amp = lamp;
     g.lid_period = walls ? walls->lid_period : 0.0;
     g.strip = g.nx >= 16 ? 8 : g.nx;
+    g.epsf = (float)g.eps;
+    g.ryf = (float)(g.dx / g.dy);
     // Per-axis weight factors (w_j = A_x A_y A_z) and the wall flux constants.
     axA.assign(N, 0.0);
     for (int j = 0; j < N; ++j)

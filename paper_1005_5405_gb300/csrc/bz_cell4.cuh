@@ -177,7 +177,7 @@ static __global__ void k_scatter_fill(int nt, int T, const ushort4 *__restrict__
 __device__ __forceinline__ bool correction_spd(const Geo &g, const float *P, float *mu, int lane = -1)
 {
     if (g.solve_fb) return false;
-    const float e = (float)g.eps;
+    const float e = g.epsf;
     const float p4 = P[4] + P[5] + P[6];
     const float m[5][5] = {
         {P[0], P[1], P[2], P[3], p4},
@@ -481,12 +481,13 @@ static __global__ void k_adj_fill2(int nt, int nvt, int T, const ushort4 *__rest
 
 // x = G^{-1} rhs for the Gram matrix G = G0 + eps sum_j N_c,j psi_j psi_j^T
 // of the correction (P[0..13] its moment sums, as in correction_spd), by
-// elimination without pivoting; pivoted elimination if a pivot is not
-// positive (fallback set).
+// elimination without pivoting (in registers; stable for the symmetric
+// positive definite G); Cholesky, then pivoted elimination, if a pivot is not
+// positive (fallback counted).
 static __device__ __noinline__ void gram_solve(const Geo &g, const float *P, const float *rhs, float *x,
                                         int *fallback)
 {
-    const float e = (float)g.eps;
+    const float e = g.epsf;
     const float p4 = P[4] + P[5] + P[6];
     const float m[5][5] = {
         {P[0], P[1], P[2], P[3], p4},
@@ -494,12 +495,37 @@ static __device__ __noinline__ void gram_solve(const Geo &g, const float *P, con
         {P[2], P[7], P[5], P[9], P[11]},
         {P[3], P[8], P[9], P[6], P[12]},
         {p4, P[10], P[11], P[12], P[13]}};
-    float G[5][5], b[5];
+    float G[5][5], U[5][5], b[5], y[5];
+    bool ok = !g.solve_fb;
+#pragma unroll
     for (int a = 0; a < 5; ++a) {
-        for (int c = 0; c < 5; ++c) G[a][c] = g.G0f[a * 5 + c] + e * m[a][c];
-        b[a] = rhs[a];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) G[a][c] = U[a][c] = g.G0f[a * 5 + c] + e * m[a][c];
+        b[a] = y[a] = rhs[a];
     }
-    chol_or_ge<float>(G, b, x, fallback);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        ok = ok && U[k][k] > 0.f;
+        const float ip = 1.f / U[k][k];
+#pragma unroll
+        for (int i = k + 1; i < 5; ++i) {
+            const float f = U[i][k] * ip;
+#pragma unroll
+            for (int j = k + 1; j < 5; ++j) U[i][j] -= f * U[k][j];
+            y[i] -= f * y[k];
+        }
+    }
+    if (ok) {
+#pragma unroll
+        for (int i = 4; i >= 0; --i) {
+            float s = y[i];
+#pragma unroll
+            for (int j = i + 1; j < 5; ++j) s -= U[i][j] * x[j];
+            x[i] = s / U[i][i];
+        }
+        return;
+    }
+    chol_or_ge<float>(G, b, x, fallback, g.solve_fb != 0);
 }
 
 // Adjoint part of one cell (after the forward recompute of cell4_cell in
@@ -515,7 +541,7 @@ __device__ __forceinline__ void adj4_tail(const Geo &g, const Map4 &m, int c, co
                                           float *muf, int &fallback)
 {
     const int N = g.nv, nvt = g.nvt, T = blockDim.x, t = threadIdx.x;
-    const float eps = (float)g.eps;
+    const float eps = g.epsf;
     float *totf = reinterpret_cast<float *>(S.tot);
     const int Q = m.Q, nq = N / 4, q = t % Q, kchunk = t / Q;
     const bool active = kchunk < m.K;
@@ -687,7 +713,7 @@ __device__ __forceinline__ void cell4_cell(const Geo &g, const Map4 &m, int c,
         if (clk && blockIdx.x == 0 && t == 0 && ncell < kClkCells)
             clk[ncell * kClkPhases + ph] = clock64();
     };
-    const float eps = (float)g.eps;
+    const float eps = g.epsf;
     float *totf = reinterpret_cast<float *>(S.tot);
     // Quad of this thread.
     const int Q = m.Q, nq = N / 4;
@@ -711,7 +737,7 @@ __device__ __forceinline__ void cell4_cell(const Geo &g, const Map4 &m, int c,
         for (int i_ = 0; i_ < 4; ++i_) qq[i_] = vy * vy + vz[i_] * vz[i_];          \
     }                                                                                \
     (void)IAyz; (void)Ayz; (void)qq; (void)vz
-    const float ry = (float)(g.dx / g.dy);
+    const float ry = g.ryf;
     const int half = N / 2;
     const int Q4 = Q;   // float4 stride of one jx-plane
     // Shared-memory position of this thread's quad in plane jx: quads of a row
@@ -937,19 +963,26 @@ __device__ __forceinline__ void cell4_cell(const Geo &g, const Map4 &m, int c,
     block_reduce4<19>(acc, S.red, totf);
     stamp(5);
 
-    // ---- correction solve (thread 0) and per-cell tables --------------------
+    // ---- correction solve (warp 0, which shares the residual of the
+    // refinement) and per-cell tables --------------------------------------
     float *muf = reinterpret_cast<float *>(S.mu);
-    if (t == 0) {
-        if (!correction_spd(g, totf, muf)) {
-            double m8[5], Pd[19];
-            for (int a = 0; a < 19; ++a) Pd[a] = (double)totf[a];
-            int f2 = 0;
-            correction_solve<float>(g, Pd, m8, &f2);
-            ++fallback;
-            for (int a = 0; a < 5; ++a) muf[a] = (float)m8[a];
+    if (t < 32) {
+        float mu5[5];
+        const bool ok = correction_spd(g, totf, mu5, t);
+        if (t == 0) {
+            if (ok) {
+                for (int a = 0; a < 5; ++a) muf[a] = mu5[a];
+            } else {
+                double m8[5], Pd[19];
+                for (int a = 0; a < 19; ++a) Pd[a] = (double)totf[a];
+                int f2 = 0;
+                correction_solve<float>(g, Pd, m8, &f2);
+                ++fallback;
+                for (int a = 0; a < 5; ++a) muf[a] = (float)m8[a];
+            }
+            if constexpr (ADJ)
+                for (int a = 0; a < 14; ++a) X->P[a] = totf[a];
         }
-        if constexpr (ADJ)
-            for (int a = 0; a < 14; ++a) X->P[a] = totf[a];
     }
     __syncthreads();
     const float mu0 = muf[0], mux = muf[1], muy = muf[2], muz = muf[3], mu4 = muf[4];

@@ -32,6 +32,7 @@ struct Geo {
     int nx, ny, nv, nvt, nr, nfaces;
     int nt;                     // Monte Carlo samples per step
     double vmax, dv, dt, dx, dy, eps, cw;   // cw = pi K dt / Nt
+    float epsf, ryf;            // eps and dx / dy rounded to float (no FP64 per cell)
     uint32_t seed, instance;
     double lid_u0, lid_amp, lid_period;
     const double *lid_profile;  // device, nx, or nullptr

@@ -500,7 +500,7 @@ static __global__ void k_lz_materialize(Geo g, const int *__restrict__ skip_unle
     __shared__ float smu[8];
     const int N = g.nv, nq = N / 4, Q = N * N / 4;
     for (int i = threadIdx.x; i < N; i += blockDim.x) sv[i] = (float)g.axv[i];
-    const float eps = (float)g.eps;
+    const float eps = g.epsf;
     const int64_t plane = g.nvt / 4;
     for (int c = blockIdx.x; c < g.nr; c += gridDim.x) {
         __syncthreads();
@@ -768,7 +768,7 @@ __device__ __forceinline__ void lz_finish(const Geo &g, const LzArgs &a, int c, 
     float *mo = a.mu_out + (int64_t)c * 8;
     for (int k = 0; k < 5; ++k) mo[k] = mu[k];
     // Moments of h^{n+1}: sum w h phi = sum N_c phi + sum_a mu_a (E0 + eps sum N_c psi_a phi).
-    const float eps = (float)g.eps;
+    const float eps = g.epsf;
     float m10[10];
 #pragma unroll
     for (int b = 0; b < 10; ++b) {
@@ -1112,7 +1112,7 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
     uint32_t *smask = reinterpret_cast<uint32_t *>(smem_raw + so.mask);
     uint16_t *swpre = reinterpret_cast<uint16_t *>(smem_raw + so.wpre);
     uint16_t *sact = reinterpret_cast<uint16_t *>(smem_raw + so.act);
-    const float eps = (float)g.eps;
+    const float eps = g.epsf;
     const float2 eps2 = lz_dup(eps), one2 = lz_dup(1.f);
     const int lane = t & 31, warp = t >> 5;
     const bool streamer = t < kLzRoleT;
