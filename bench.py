@@ -384,9 +384,10 @@ def run_ours(args):
 
 
 def run_batch(args):
-    """64 uneven cavity instances: the batched persistent launch (autotuned
-    schedule, one CUDA graph per step) against the same instances stepped as
-    64 single-instance handles, one launch sequence after another."""
+    """64 uneven cavity instances: the batched step (autotuned schedule, one
+    CUDA graph per step) against the same instances stepped as 64
+    single-instance handles, one launch sequence after another.  Both are
+    timed in `repeats` blocks of `steps` steps; the line reports medians."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -402,11 +403,17 @@ def run_batch(args):
     batch.step(args.warmup)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    batch.step(args.steps)
-    e1.record()
-    torch.cuda.synchronize()
-    t_batch = e0.elapsed_time(e1) / 1e3
+
+    def block(fn):
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    tb = [block(lambda: batch.step(1)) for _ in range(args.repeats)]
     sched = batch.schedule()
     batch.close()
     torch.cuda.empty_cache()
@@ -419,14 +426,13 @@ def run_batch(args):
     for _ in range(args.warmup):
         for c in singles:
             c.step(1)
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(args.steps):
+
+    def all_singles():
         for c in singles:
             c.step(1)
-    e1.record()
-    torch.cuda.synchronize()
-    t_single = e0.elapsed_time(e1) / 1e3
+
+    ts = [block(all_singles) for _ in range(args.repeats)]
+    t_batch, t_single = statistics.median(tb), statistics.median(ts)
     n = len(ps)
     line = {
         "metric": "instance steps/s (64 uneven cavities, FP32)", "value": n * args.steps / t_batch,
@@ -435,10 +441,12 @@ def run_batch(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batch64", "instances": n, "nodes": nodes,
                    "samples_per_step": ps[0].nt, "schedule": sched, "tuner_choice": choice,
-                   "tuner_ms_per_step": tune_ms},
+                   "tuner_ms_per_step": tune_ms, "repeats": args.repeats},
         "node_updates_per_s": nodes * args.steps / t_batch,
+        "batch_ms_per_step_each": [round(x / args.steps * 1e3, 4) for x in tb],
         "back_to_back": {"value": n * args.steps / t_single, "unit": "instance-steps/s",
                          "ms_per_step": t_single / args.steps * 1e3,
+                         "ms_per_step_each": [round(x / args.steps * 1e3, 4) for x in ts],
                          "how": "64 single-instance handles, one bz_step(1) each per step"},
         "speedup_vs_back_to_back": t_single / t_batch,
     }
