@@ -1505,7 +1505,7 @@ struct bz_batch {
     // Fan-out mode: every instance's own step (the active-node kernels) on
     // `branches` forked streams, the whole step captured as one multi-branch
     // graph; one graph per parity pattern of the instances' steps.
-    int mode = 0;                           // 0 persistent kernels, 1 fan-out
+    int mode = 0;                           // 0 persistent kernels, 1 fan-out, 2 persistent active-node
     int branches = 1;
     bool fan_ok = false;                    // every instance runs the active-node path
     std::vector<cudaStream_t> br;
@@ -1513,6 +1513,20 @@ struct bz_batch {
     std::vector<int> owner;                 // branch of each instance
     cudaGraphExec_t fgraph[2] = {nullptr, nullptr};
     std::vector<int> fkey[2];
+    // Persistent active-node mode: every instance's active-node step, one
+    // launch per kernel class (bz_batch.cuh, kbl_*), the per-cell kernel as
+    // persistent CTAs over segments of the instances' cell groups.
+    bool lz_ok = false;
+    bzk::LzInst *d_lzinst = nullptr;
+    int4 *d_segs = nullptr;
+    int *d_next = nullptr;                  // one claim counter per velocity grid
+    int nseg = 0;
+    size_t lz_smem = 0;
+    struct LzClass { int nv, seg0, nseg; size_t smem; };
+    std::vector<LzClass> lz_classes;        // the segments of each velocity grid
+    cudaStream_t lz_side = nullptr;         // the sample plans run here, beside the walls
+    cudaEvent_t lz_fork = nullptr, lz_join = nullptr;
+    cudaGraphExec_t graph2 = nullptr;
 };
 
 namespace {
@@ -1529,6 +1543,13 @@ bzk::Map4 map_for(int N, int maxt)
 void batch_free(bz_batch *B)
 {
     if (B->graph) cudaGraphExecDestroy(B->graph);
+    if (B->graph2) cudaGraphExecDestroy(B->graph2);
+    void *lzp[] = {B->d_lzinst, B->d_segs, B->d_next};
+    for (void *p : lzp)
+        if (p) cudaFree(p);
+    if (B->lz_side) cudaStreamDestroy(B->lz_side);
+    if (B->lz_fork) cudaEventDestroy(B->lz_fork);
+    if (B->lz_join) cudaEventDestroy(B->lz_join);
     for (auto &g : B->fgraph)
         if (g) cudaGraphExecDestroy(g);
     for (cudaStream_t st : B->br) cudaStreamDestroy(st);
@@ -1610,7 +1631,7 @@ bz_status batch_set_mode(bz_batch *B, int mode, cudaStream_t s)
     for (int i = 0; i < B->n; ++i) {
         bz_handle *h = B->inst[i];
         const size_t mb = sizeof(float) * 8 * (size_t)h->g.nr;
-        if (mode == 0) {
+        if (B->mode != 0) {       // leaving a mode whose states carry pending corrections
             const int b = (int)(B->step[i] & 1);
             bzk::k_lz_materialize<<<std::min(h->g.nr, h->nsm * 8), 256, 0, s>>>(
                 h->g, nullptr, (const float *)h->h[b], h->mu[b], (float *)h->h[b], nullptr);
@@ -1628,7 +1649,7 @@ bz_status batch_set_mode(bz_batch *B, int mode, cudaStream_t s)
 // (the value is unchanged) before instance i's state is read.
 bz_status batch_correct_in_place(bz_batch *B, int i, cudaStream_t s)
 {
-    if (B->mode != 1) return BZ_OK;
+    if (B->mode == 0) return BZ_OK;
     bz_handle *h = B->inst[i];
     const int b = (int)(B->step[i] & 1);
     bzk::k_lz_materialize<<<std::min(h->g.nr, h->nsm * 8), 256, 0, s>>>(
@@ -1724,6 +1745,156 @@ bz_status batch_launch(bz_batch *B, cudaStream_t s, bool advance)
 }  // namespace
 
 extern "C" {
+
+// One step of every instance in the persistent active-node mode (advance =
+// false: a repeatable recomputation of the current step).
+bz_status lz_batch_launch(bz_batch *B, cudaStream_t s, bool advance)
+{
+    const int pb = 256, sg = (B->tot_samples + pb - 1) / pb;
+    // The sample plans depend on the step counters only: they run on a side
+    // stream beside the walls (after everything before the step on s).
+    BZ_CUDA(cudaEventRecord(B->lz_fork, s));
+    BZ_CUDA(cudaStreamWaitEvent(B->lz_side, B->lz_fork, 0));
+    const cudaStream_t sp = B->lz_side;
+    bzk::kbl_plan<<<sg, pb, 0, sp>>>(B->d_lzinst, B->d_samp_pre, B->n);
+    bzk::kbl_scan<<<B->n, 1024, 0, sp>>>(B->d_lzinst);
+    bzk::kbl_remap<<<sg, pb, 0, sp>>>(B->d_lzinst, B->d_samp_pre, B->n);
+    bzk::kbl_lscan<<<B->n, 1024, 0, sp>>>(B->d_lzinst);
+    bzk::kbl_lfill<<<sg, pb, 0, sp>>>(B->d_lzinst, B->d_samp_pre, B->n);
+    BZ_CUDA(cudaEventRecord(B->lz_join, sp));
+    bzk::kbl_walls<<<B->tot_faces, 256, 0, s>>>(B->d_lzinst, B->d_face_pre, B->n);
+    BZ_CUDA(cudaMemsetAsync(B->d_next, 0, sizeof(int) * B->lz_classes.size(), s));
+    BZ_CUDA(cudaStreamWaitEvent(s, B->lz_join, 0));
+    for (size_t k = 0; k < B->lz_classes.size(); ++k) {
+        const auto &c = B->lz_classes[k];
+        const int4 *sg4 = B->d_segs + c.seg0;
+        int *nx = B->d_next + k;
+        switch (c.nv) {
+        case 24: bzk::kbl_lz<24><<<B->nsm, bzk::kLzThreads, c.smem, s>>>(B->d_lzinst, sg4, c.nseg, nx); break;
+        case 20: bzk::kbl_lz<20><<<B->nsm, bzk::kLzThreads, c.smem, s>>>(B->d_lzinst, sg4, c.nseg, nx); break;
+        case 16: bzk::kbl_lz<16><<<B->nsm, bzk::kLzThreads, c.smem, s>>>(B->d_lzinst, sg4, c.nseg, nx); break;
+        default: bzk::kbl_lz<0><<<B->nsm, bzk::kLzThreads, c.smem, s>>>(B->d_lzinst, sg4, c.nseg, nx); break;
+        }
+    }
+    // The 4-node-vector fallback of instances that overflowed (no work otherwise).
+    bzk::kbl_fb_plan<<<sg, pb, 0, s>>>(B->d_lzinst, B->d_samp_pre, B->n);
+    bzk::kbl_fb_scan<<<B->n, 1024, 0, s>>>(B->d_lzinst, 512);
+    bzk::kbl_fb_fill<<<sg, pb, 0, s>>>(B->d_lzinst, B->d_samp_pre, B->n, 512);
+    bzk::kbl_fb_materialize<<<std::min(B->tot_cells, B->nsm * 8), 256, 0, s>>>(B->d_lzinst, B->d_cell_pre,
+                                                                              B->n);
+    bzk::kbl_fb_cell4<<<B->nsm, 512, B->smem, s>>>(B->d_lzinst, B->d_cell_pre, B->n);
+    if (advance) bzk::kbl_advance<<<(B->n + 127) / 128, 128, 0, s>>>(B->d_lzinst, B->n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(BZ_ECUDA, "batch launch failed: %s", cudaGetErrorString(e));
+    return BZ_OK;
+}
+
+// Set-up of the persistent active-node mode (lz_ok stays false when an
+// instance does not run the active-node kernel with groups of four cells).
+bz_status lz_batch_prepare(bz_batch *B)
+{
+    B->lz_ok = false;
+    for (bz_handle *h : B->inst)
+        if (!h->lazy || h->lz_G != 4) return BZ_OK;
+    const int n = B->n;
+    std::vector<bzk::LzInst> li(n);
+    size_t smem = 0;
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) {
+        bz_handle *h = B->inst[i];
+        bzk::LzInst &b = li[i];
+        b.g = h->g;
+        b.step = h->d_step;
+        for (int p = 0; p < 2; ++p) {
+            b.h[p] = (float *)h->h[p];
+            b.mu[p] = h->mu[p];
+        }
+        b.ghost = (float *)h->ghost;
+        b.nw = h->nw;
+        b.idx = h->lz_idx;
+        b.pa = h->lz_pa;
+        b.qc = h->lz_qc;
+        b.flag = h->lz_flag;
+        b.cidx = h->lz_cidx;
+        b.count = h->lz_count;
+        b.cursor = h->lz_cursor;
+        b.rowend = h->lz_rowend;
+        b.map = map_for(h->g.nv, 512);
+        b.pidx16 = (ushort4 *)h->pidx;
+        b.pa16 = (bzk::PlanA<float, uint16_t> *)h->pa;
+        b.sc_count = h->sc_count;
+        b.sc_cursor = h->sc_cursor;
+        b.sc_meta = h->sc_meta;
+        b.sc_ent = h->sc_ent;
+        for (int p = 0; p < 2; ++p) {
+            bzk::LzArgs &a = b.a[p];
+            a = bzk::LzArgs{};
+            a.hin = b.h[p];
+            a.mu_in = b.mu[p];
+            a.ghost = b.ghost;
+            a.hout = b.h[p ^ 1];
+            a.mu_out = b.mu[p ^ 1];
+            a.mom = h->mom;
+            a.rec = h->lz_rec;
+            a.dest0 = h->lz_dest0;
+            a.meta = h->lz_meta;
+            a.mask = h->lz_mask;
+            a.wpre = h->lz_wpre;
+            a.act = h->lz_act;
+            a.mcap = h->lz_mcap;
+            for (int k = 0; k < bzk::kLzX; ++k) a.e0[k] = h->lz_e0[k];
+            a.stats = h->stats;
+            a.early_tail = h->g.nv < 32 ? 1 : 0;
+        }
+        smem = std::max(smem, (size_t)bzk::lz_offsets(h->g.nvt, h->lz_mcap, 4).end);
+        order[i] = i;
+    }
+    // Segments of about 32 groups: R strided lanes r, r + R, ... of each
+    // instance's groups, the instances with the largest velocity grids (the
+    // costliest groups) first.
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return B->inst[x]->g.nv > B->inst[y]->g.nv;
+    });
+    std::vector<int4> segs;
+    B->lz_classes.clear();
+    for (int i : order) {
+        const int nv = B->inst[i]->g.nv;
+        const int key = nv == 24 || nv == 20 || nv == 16 ? nv : 0;
+        if (B->lz_classes.empty() || B->lz_classes.back().nv != key)
+            B->lz_classes.push_back({key, (int)segs.size(), 0, 0});
+        auto &c = B->lz_classes.back();
+        c.smem = std::max(c.smem, (size_t)bzk::lz_offsets(B->inst[i]->g.nvt, B->inst[i]->lz_mcap, 4).end);
+        const int ng = (B->inst[i]->g.nr + 3) / 4, R = std::max(1, (ng + 31) / 32);
+        for (int r = 0; r < R && r < ng; ++r) segs.push_back(make_int4(i, r, (ng - 1 - r) / R + 1, R));
+        c.nseg = (int)segs.size() - c.seg0;
+    }
+    bz_handle *h0 = B->inst[0];
+    BZ_CUDA(bz_allow_max_smem(bzk::kbl_lz<24>, h0->smem_optin));
+    BZ_CUDA(bz_allow_max_smem(bzk::kbl_lz<20>, h0->smem_optin));
+    BZ_CUDA(bz_allow_max_smem(bzk::kbl_lz<16>, h0->smem_optin));
+    BZ_CUDA(bz_allow_max_smem(bzk::kbl_lz<0>, h0->smem_optin));
+    BZ_CUDA(bz_allow_max_smem(bzk::kbl_fb_cell4, h0->smem_optin));
+    int occ = 0, occ4 = 0;
+    BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bzk::kbl_lz<0>, bzk::kLzThreads, smem));
+    BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ4, bzk::kbl_fb_cell4, 512, B->smem));
+    if (occ < 1 || occ4 < 1) return BZ_OK;
+    BZ_TRY(dalloc(&B->d_lzinst, sizeof(bzk::LzInst) * n));
+    BZ_TRY(dalloc(&B->d_segs, sizeof(int4) * segs.size()));
+    BZ_TRY(dalloc(&B->d_next, sizeof(int) * B->lz_classes.size()));
+    BZ_CUDA(cudaMemcpy(B->d_lzinst, li.data(), sizeof(bzk::LzInst) * n, cudaMemcpyHostToDevice));
+    BZ_CUDA(cudaMemcpy(B->d_segs, segs.data(), sizeof(int4) * segs.size(), cudaMemcpyHostToDevice));
+    {
+        int least = 0, greatest = 0;
+        BZ_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        BZ_CUDA(cudaStreamCreateWithPriority(&B->lz_side, cudaStreamNonBlocking, greatest));
+        BZ_CUDA(cudaEventCreateWithFlags(&B->lz_fork, cudaEventDisableTiming));
+        BZ_CUDA(cudaEventCreateWithFlags(&B->lz_join, cudaEventDisableTiming));
+    }
+    B->nseg = (int)segs.size();
+    B->lz_smem = smem;
+    B->lz_ok = true;
+    return BZ_OK;
+}
 
 bz_status bz_batch_create(int32_t n, const bz_space *spaces, const bz_vel *vels,
                           const bz_walls *walls, const bz_params *params, bz_batch **out)
@@ -1829,12 +2000,16 @@ bz_status bz_batch_create(int32_t n, const bz_space *spaces, const bz_vel *vels,
         return bail(BZ_ECUDA);
     }
     assign_branches(B, 4);
-    if (const char *m = getenv("BZ_BATCH_MODE"))
-        if (strcmp(m, "fanout") == 0 && B->fan_ok) {
-            st = batch_set_mode(B, 1, nullptr);
+    st = lz_batch_prepare(B);
+    if (st != BZ_OK) return bail(st);
+    if (const char *m = getenv("BZ_BATCH_MODE")) {
+        const int want = strcmp(m, "fanout") == 0 && B->fan_ok ? 1 : (strcmp(m, "lz") == 0 && B->lz_ok ? 2 : 0);
+        if (want) {
+            st = batch_set_mode(B, want, nullptr);
             if (st == BZ_OK) st = cudaDeviceSynchronize() == cudaSuccess ? BZ_OK : BZ_ECUDA;
             if (st != BZ_OK) return bail(st);
         }
+    }
     *out = B;
     return BZ_OK;
 }
@@ -1853,6 +2028,37 @@ bz_status bz_batch_step(bz_batch *B, int32_t nsteps, void *stream)
     if (!B) return fail(BZ_EINVAL, "batch is NULL");
     if (nsteps < 0) return fail(BZ_EINVAL, "nsteps must be >= 0");
     cudaStream_t s = (cudaStream_t)stream;
+    if (B->mode == 2) {
+        if (nsteps > 0 && graphs_enabled() && !B->graph2) {
+            BZ_CUDA(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal));
+            bz_status st = lz_batch_launch(B, B->cap, true);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamEndCapture(B->cap, &graph);
+            if (st != BZ_OK) {
+                if (graph) cudaGraphDestroy(graph);
+                return st;
+            }
+            if (e != cudaSuccess) return fail(BZ_ECUDA, "batch capture failed: %s", cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&B->graph2, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return fail(BZ_ECUDA, "batch graph: %s", cudaGetErrorString(e));
+        }
+        for (int32_t k = 0; k < nsteps; ++k) {
+            if (B->graph2 && graphs_enabled()) BZ_CUDA(cudaGraphLaunch(B->graph2, s));
+            else BZ_TRY(lz_batch_launch(B, s, true));
+        }
+        for (int i = 0; i < B->n; ++i) {
+            bz_handle *h = B->inst[i];
+            B->step[i] += nsteps;
+            h->step = B->step[i];
+            h->cur = (int)(h->step & 1);
+            if (nsteps > 0) {
+                h->lazy_buf[h->cur] = true;
+                h->mom_valid = true;
+            }
+        }
+        return BZ_OK;
+    }
     if (B->mode == 1) {
         for (int32_t k = 0; k < nsteps; ++k) {
             if (graphs_enabled()) {
@@ -1955,6 +2161,7 @@ bz_status bz_batch_tune(bz_batch *B, int32_t trial_steps, void *stream, int32_t 
             }
     if (B->fan_ok)
         for (int nb : {1, 2, 4, 8}) cands.push_back({1, 0, 0, 0, nb});
+    if (B->lz_ok) cands.push_back({2, 0, 0, 0, 0});
     cudaEvent_t e0, e1;
     BZ_CUDA(cudaEventCreate(&e0));
     BZ_CUDA(cudaEventCreate(&e1));
@@ -1969,6 +2176,17 @@ bz_status bz_batch_tune(bz_batch *B, int32_t trial_steps, void *stream, int32_t 
                 cudaEventRecord(e0, s);
                 bool ok = true;
                 for (int r = 0; r < trial_steps && ok; ++r) ok = batch_launch(B, s, false) == BZ_OK;
+                cudaEventRecord(e1, s);
+                float f = 0.f;
+                if (ok && cudaEventSynchronize(e1) == cudaSuccess &&
+                    cudaEventElapsedTime(&f, e0, e1) == cudaSuccess)
+                    t = f / trial_steps;
+            }
+        } else if (k.mode == 2) {
+            if (batch_set_mode(B, 2, s) == BZ_OK && lz_batch_launch(B, s, false) == BZ_OK) {
+                cudaEventRecord(e0, s);
+                bool ok = true;
+                for (int r = 0; r < trial_steps && ok; ++r) ok = lz_batch_launch(B, s, false) == BZ_OK;
                 cudaEventRecord(e1, s);
                 float f = 0.f;
                 if (ok && cudaEventSynchronize(e1) == cudaSuccess &&
@@ -2013,7 +2231,7 @@ bz_status bz_batch_tune(bz_batch *B, int32_t trial_steps, void *stream, int32_t 
     BZ_TRY(batch_set_mode(B, k.mode, s));
     if (k.mode == 0) {
         BZ_TRY(batch_apply(B, k.maxt, k.cps, k.strip));
-    } else {
+    } else if (k.mode == 1) {
         assign_branches(B, k.branches);
         drop_fan_graphs(B);
     }
@@ -2027,7 +2245,7 @@ bz_status bz_batch_schedule(const bz_batch *B, int32_t out[4])
     out[0] = B->maxt;
     out[1] = B->grid;
     out[2] = B->strip;
-    out[3] = B->mode == 1 ? B->branches : 0;
+    out[3] = B->mode == 1 ? B->branches : (B->mode == 2 ? -1 : 0);
     return BZ_OK;
 }
 

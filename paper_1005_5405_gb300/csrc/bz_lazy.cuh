@@ -90,11 +90,10 @@ static __global__ void k_lz_mark(int nt, const int4 *__restrict__ idx, int *__re
 // word), lane k keeping word k; warp and block scans of the word counts
 // give the compact indices.
 // stats (nullable): [5] counts steps whose active set exceeded mcap.
-static __global__ void __launch_bounds__(1024) k_lz_scan(int nvt, int mcap, int *__restrict__ flag,
-                                                 int *__restrict__ cidx, int *__restrict__ act,
-                                                 uint32_t *__restrict__ mask, int *__restrict__ wpre,
-                                                 int *__restrict__ meta,
-                                                 unsigned long long *__restrict__ stats = nullptr)
+__device__ __forceinline__ void lz_scan_block(int nvt, int mcap, int *__restrict__ flag, int *__restrict__ cidx,
+                                              int *__restrict__ act, uint32_t *__restrict__ mask,
+                                              int *__restrict__ wpre, int *__restrict__ meta,
+                                              unsigned long long *__restrict__ stats)
 {
     __shared__ int wsum[32];
     __shared__ int btot;
@@ -155,14 +154,20 @@ static __global__ void __launch_bounds__(1024) k_lz_scan(int nvt, int mcap, int 
         }
     }
 }
+static __global__ void __launch_bounds__(1024) k_lz_scan(int nvt, int mcap, int *__restrict__ flag,
+                                                 int *__restrict__ cidx, int *__restrict__ act,
+                                                 uint32_t *__restrict__ mask, int *__restrict__ wpre,
+                                                 int *__restrict__ meta,
+                                                 unsigned long long *__restrict__ stats = nullptr)
+{
+    lz_scan_block(nvt, mcap, flag, cidx, act, mask, wpre, meta, stats);
+}
 
 // Compact node indices (a, b, a*, b*) of every sample, and the number of
 // terms per destination.
-static __global__ void k_lz_remap(int nt, const int4 *__restrict__ idx, const int *__restrict__ cidx,
-                           ushort4 *__restrict__ qc, int *__restrict__ count)
+__device__ __forceinline__ void lz_remap_one(int l, const int4 *__restrict__ idx, const int *__restrict__ cidx,
+                                             ushort4 *__restrict__ qc, int *__restrict__ count)
 {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= nt) return;
     const int4 q = idx[l];
     const int d[4] = {q.x >= 0 ? cidx[q.x] : -1, q.y >= 0 ? cidx[q.y] : -1,
                       q.z >= 0 ? cidx[q.z] : -1, q.w >= 0 ? cidx[q.w] : -1};
@@ -170,6 +175,12 @@ static __global__ void k_lz_remap(int nt, const int4 *__restrict__ idx, const in
 #pragma unroll
     for (int r = 0; r < 4; ++r)
         if (d[r] >= 0) atomicAdd(count + d[r], 1);
+}
+static __global__ void k_lz_remap(int nt, const int4 *__restrict__ idx, const int *__restrict__ cidx,
+                           ushort4 *__restrict__ qc, int *__restrict__ count)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l < nt) lz_remap_one(l, idx, cidx, qc, count);
 }
 
 // Exclusive scan of the term counts over the M destinations (cursor = first
@@ -179,11 +190,9 @@ static __global__ void k_lz_remap(int nt, const int4 *__restrict__ idx, const in
 // one term of weight 0 (at the zero entry M, entries of 1 << osh bytes), so
 // that every destination has a row and a run steps to the next destination
 // at each row end.  One CTA of 1024 threads.
-static __global__ void __launch_bounds__(1024) k_lz_lscan(int T, int osh, int *__restrict__ count,
-                                                         int *__restrict__ cursor,
-                                                         int *__restrict__ rowend,
-                                                         int *__restrict__ meta, uint2 *__restrict__ rec,
-                                                         int *__restrict__ dest0)
+__device__ __forceinline__ void lz_lscan_block(int T, int osh, int *__restrict__ count, int *__restrict__ cursor,
+                                               int *__restrict__ rowend, int *__restrict__ meta,
+                                               uint2 *__restrict__ rec, int *__restrict__ dest0)
 {
     __shared__ int part[1024];
     const int t = threadIdx.x, M = meta[0], per = (M + 1023) / 1024;
@@ -227,6 +236,14 @@ static __global__ void __launch_bounds__(1024) k_lz_lscan(int T, int osh, int *_
         meta[3] = C;
     }
 }
+static __global__ void __launch_bounds__(1024) k_lz_lscan(int T, int osh, int *__restrict__ count,
+                                                         int *__restrict__ cursor,
+                                                         int *__restrict__ rowend,
+                                                         int *__restrict__ meta, uint2 *__restrict__ rec,
+                                                         int *__restrict__ dest0)
+{
+    lz_lscan_block(T, osh, count, cursor, rowend, meta, rec, dest0);
+}
 
 // The term records, sorted by destination: position p of the sorted order
 // goes to thread p / C, slot i = p mod C, stored at rec[i T + p / C] so that
@@ -239,13 +256,12 @@ static __global__ void __launch_bounds__(1024) k_lz_lscan(int T, int osh, int *_
 // a or b).  dest0[tt] is the destination of thread tt's first term.
 // Nothing is written when the step overflowed (the kernel does not run then).
 template <typename PA>
-__global__ void k_lz_lfill(int nt, int T, int osh, const ushort4 *__restrict__ qc,
-                           const PA *__restrict__ pa, int *__restrict__ cursor,
-                           const int *__restrict__ rowend, const int *__restrict__ meta,
-                           uint2 *__restrict__ rec, int *__restrict__ dest0)
+__device__ __forceinline__ void lz_lfill_one(int l, int T, int osh, const ushort4 *__restrict__ qc,
+                                             const PA *__restrict__ pa, int *__restrict__ cursor,
+                                             const int *__restrict__ rowend, const int *__restrict__ meta,
+                                             uint2 *__restrict__ rec, int *__restrict__ dest0)
 {
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= nt || meta[1]) return;
+    if (meta[1]) return;
     const int M = meta[0], C = meta[3];
     const ushort4 q = qc[l];
     const int d[4] = {idx_of(q.x), idx_of(q.y), idx_of(q.z), idx_of(q.w)};
@@ -262,6 +278,15 @@ __global__ void k_lz_lfill(int nt, int T, int osh, const ushort4 *__restrict__ q
         rec[(int64_t)i * T + tt] = make_uint2(x | last, __float_as_uint(r < 2 ? -W : W));
         if (i == 0) dest0[tt] = d[r];
     }
+}
+template <typename PA>
+__global__ void k_lz_lfill(int nt, int T, int osh, const ushort4 *__restrict__ qc,
+                           const PA *__restrict__ pa, int *__restrict__ cursor,
+                           const int *__restrict__ rowend, const int *__restrict__ meta,
+                           uint2 *__restrict__ rec, int *__restrict__ dest0)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l < nt) lz_lfill_one(l, T, osh, qc, pa, cursor, rowend, meta, rec, dest0);
 }
 
 // Bank-aware order of the term records.  A collision thread reads the two
@@ -443,14 +468,11 @@ __global__ void __launch_bounds__(32) k_lz_order(int T, int cmax, int chunk, con
 // derived from the logical one, the input is corrected in place and mu_out
 // is cleared (k_cell4 writes corrected states).  All return at once otherwise.
 // ---------------------------------------------------------------------
-static __global__ void k_lz_fb_plan(int nt, int N, const int *__restrict__ meta,
-                             const int4 *__restrict__ idx, const PlanA<float, int> *__restrict__ pa,
-                             ushort4 *__restrict__ pidx16, PlanA<float, uint16_t> *__restrict__ pa16,
-                             int *__restrict__ count)
+__device__ __forceinline__ void lz_fb_plan_one(int l, int N, const int4 *__restrict__ idx,
+                                               const PlanA<float, int> *__restrict__ pa,
+                                               ushort4 *__restrict__ pidx16, PlanA<float, uint16_t> *__restrict__ pa16,
+                                               int *__restrict__ count)
 {
-    if (!meta[1]) return;
-    const int l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= nt) return;
     const int4 q = idx[l];
     int o[4] = {q.x, q.y, q.z, q.w};
     const int nq = N / 4;
@@ -470,6 +492,15 @@ static __global__ void k_lz_fb_plan(int nt, int N, const int *__restrict__ meta,
     if (u.y != 0xFFFF) atomicAdd(count + u.y, 1);
     if (u.z != 0xFFFF) atomicAdd(count + u.z, 1);
     if (u.w != 0xFFFF) atomicAdd(count + u.w, 1);
+}
+static __global__ void k_lz_fb_plan(int nt, int N, const int *__restrict__ meta,
+                             const int4 *__restrict__ idx, const PlanA<float, int> *__restrict__ pa,
+                             ushort4 *__restrict__ pidx16, PlanA<float, uint16_t> *__restrict__ pa16,
+                             int *__restrict__ count)
+{
+    if (!meta[1]) return;
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l < nt) lz_fb_plan_one(l, N, idx, pa, pidx16, pa16, count);
 }
 
 // Clears n floats when gate[1] is set (the pending corrections of a state
@@ -1091,11 +1122,15 @@ constexpr int kLzTailChunk = 256;  // active nodes per claimed chunk of the incr
 // g.sx, g.sy).  Streaming thread t < S = K N^2/4 owns node quad q = t mod
 // (N^2/4) (four consecutive jz at one (jx, jy)) of jx-plane t div (N^2/4) of
 // every stage; a stage covers K planes and a cell J = N / K stages.
+//
+// lz_run runs the pipeline of one CTA over the groups grp0, grp0 + gstride,
+// ... (nmine of them) of one problem; the kernel k_lz gives CTA b the groups
+// b, b + gridDim.x, ...
 template <int G, int NV, bool SX>
-__global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
+__device__ __forceinline__ void lz_run(const Geo &g, const LzArgs &a, char *smem_raw, int grp0, int gstride,
+                                       int nmine)
 {
     using V = typename LzVec<G>::T;
-    extern __shared__ __align__(16) char smem_raw[];
     if (a.meta[1]) return;                        // too many active nodes: k_cell4 runs
     const int N = NV ? NV : g.nv;
     const int N2 = N * N, nvt = N2 * N, t = threadIdx.x;
@@ -1148,18 +1183,16 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
     const float2 nay2 = lz_dup(-H.cuy[jy]);
     const float4 *hin4 = reinterpret_cast<const float4 *>(a.hin);
     float4 *hout4 = reinterpret_cast<float4 *>(a.hout);
-    const int ngroups = (g.nr + G - 1) / G;
-    const int nmine = blockIdx.x < ngroups ? (ngroups - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     int fallback = 0;
 
     // Iteration it: the streaming warps take this CTA's group it, the
     // collision warps its group it - 1.
     for (int it = 0; it <= nmine + 1; ++it) {
-        const bool clk = a.clk && blockIdx.x == 0 && it < kClkCells;
+        const bool clk = a.clk && grp0 == 0 && it < kClkCells;
         if (clk && t == 0) a.clk[it * kClkPhases + 0] = clock64();
         if (streamer) {
             if (it < nmine) {
-                const int grp = blockIdx.x + it * gridDim.x, buf = it & 1;
+                const int grp = grp0 + it * gstride, buf = it & 1;
                 float *Af = reinterpret_cast<float *>(smem_raw + kLzAOff + buf * so.abytes);
                 if (t < G) {
                     const int kc = grp * G + t;
@@ -1277,7 +1310,7 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
             // One warp per cell of group it - 2: totals over the warps, then the
             // correction and the moments.
             if (it >= 2) {
-                const int grp = blockIdx.x + (it - 2) * gridDim.x, fb = (it - 2) % 3, db = it & 1;
+                const int grp = grp0 + (it - 2) * gstride, fb = (it - 2) % 3, db = it & 1;
                 const int k = warp, kc = grp * G + k;
                 if (k < G && kc < g.nr) {
                     if (lane < kLzMono) {
@@ -1476,6 +1509,15 @@ __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
         __syncthreads();
     }
     if (fallback && a.stats) atomicAdd(a.stats + 3, (unsigned long long)fallback);
+}
+
+template <int G, int NV, bool SX>
+__global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
+{
+    extern __shared__ __align__(16) char smem_raw[];
+    const int ngroups = (g.nr + G - 1) / G;
+    const int nmine = blockIdx.x < ngroups ? (ngroups - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    lz_run<G, NV, SX>(g, a, smem_raw, blockIdx.x, gridDim.x, nmine);
 }
 
 }  // namespace bzk

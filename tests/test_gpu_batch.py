@@ -34,20 +34,32 @@ def _warm(p, seed):
     return workloads.warm_state(p, seed=seed).astype(np.float32)
 
 
-@pytest.mark.parametrize("mode", ["persistent", "fanout", "fanout_ordered"])
+@pytest.mark.parametrize("mode", ["persistent", "fanout", "fanout_ordered", "lz", "lz_overflow"])
 def test_batch_matches_single_instances_and_oracle(monkeypatch, mode):
-    """Both schedules: the persistent per-cell kernels over all instances,
-    and the fan-out graph of the instances' own active-node steps (each with
-    its sample plan on its own second stream), also with the joint term order
-    forced on in every instance and in the single-instance handles."""
-    monkeypatch.delenv("BZ_LAZY_ORDER", raising=False)
+    """Every schedule: the persistent 4-node-vector kernels over all
+    instances; the fan-out graph of the instances' own active-node steps
+    (each with its sample plan on its own second stream), also with the joint
+    term order forced on in every instance and in the single-instance
+    handles; the persistent active-node kernels over all instances, also with
+    every instance's compact arrays capped below its active nodes (every step
+    then takes the gated 4-node-vector fallback).  Three steps without a
+    read, then one step at a time against the oracle restarted from the
+    batch's state."""
+    for k in ("BZ_LAZY_ORDER", "BZ_LAZY_MCAP", "BZ_BATCH_MODE"):
+        monkeypatch.delenv(k, raising=False)
     if mode.startswith("fanout"):
         monkeypatch.setenv("BZ_BATCH_MODE", "fanout")
+    if mode.startswith("lz"):
+        monkeypatch.setenv("BZ_BATCH_MODE", "lz")
     if mode == "fanout_ordered":
         monkeypatch.setenv("BZ_LAZY_ORDER", "1")
+    if mode == "lz_overflow":
+        monkeypatch.setenv("BZ_LAZY_MCAP", "8")
     ps = _problems()
     b = binding.Batch(ps)
-    assert (b.schedule()["fanout_branches"] > 0) == mode.startswith("fanout")
+    expect = {"persistent": 0, "lz": -1, "lz_overflow": -1}.get(mode)
+    branches = b.schedule()["fanout_branches"]
+    assert branches == expect if expect is not None else branches > 0
     singles = []
     for i, p in enumerate(ps):
         h0 = _warm(p, 40 + i)
@@ -60,14 +72,17 @@ def test_batch_matches_single_instances_and_oracle(monkeypatch, mode):
         cav.step(3)
         hb, st = b.get_state(i)
         assert st == 5
-        hb = hb.double().cpu().numpy()
-        assert f_metric(o, hb, state(cav)) < 1e-6, i
-        ref = h0
-        for n in range(2, 5):
-            ref, mom = o.step(ref, n)
-        assert f_metric(o, hb, ref) < 3e-5, i
-        assert np.allclose(b.moments(i).cpu().numpy(), mom, rtol=1e-4,
-                           atol=1e-5 * (1 + np.abs(mom).max())), i
+        assert f_metric(o, hb.double().cpu().numpy(), state(cav)) < 1e-6, i
+    for n in range(5, 7):
+        prev = [b.get_state(i)[0].double().cpu().numpy() for i in range(len(ps))]
+        b.step(1)
+        for i, (cav, o, _) in enumerate(singles):
+            ref, mom = o.step(prev[i], n)
+            hb, st = b.get_state(i)
+            assert st == n + 1
+            assert f_metric(o, hb.double().cpu().numpy(), ref) < 1e-5, (i, n)
+            assert np.allclose(b.moments(i).cpu().numpy(), mom, rtol=1e-4,
+                               atol=1e-5 * (1 + np.abs(mom).max())), (i, n)
 
 
 def test_tuner_keeps_state_and_graph_replay_is_exact(monkeypatch):
@@ -83,8 +98,10 @@ def test_tuner_keeps_state_and_graph_replay_is_exact(monkeypatch):
         assert st == 0 and bool((h == before[i]).all())
     sched = b.schedule()
     assert sched["threads"] in (512, 1024) and sched["strip"] in (4, 8, 16)
-    assert sched["fanout_branches"] in (0, 1, 2, 4, 8)
-    assert len(ms) == 13                 # 9 persistent schedules + 4 fan-out widths
+    assert sched["fanout_branches"] in (-1, 0, 1, 2, 4, 8)
+    # 9 persistent 4-node schedules + 4 fan-out widths + the persistent
+    # active-node schedule
+    assert len(ms) == 14
     b.step(4)
     monkeypatch.setenv("BZ_GRAPH", "0")
     c = binding.Batch(ps)
