@@ -731,8 +731,12 @@ bz_status launch_step(bz_handle *H, cudaStream_t s, bool fused, bool do_stream, 
                     const int Q = g.nv * g.nv / 4;
                     const int blk = Q * std::max(1, 512 / Q);
                     const int g4 = std::min(g.nr, H->nsm * std::max(1, 2048 / blk));
-                    bzk::k_stream4<<<g4, blk, 0, s>>>(g, (const float *)hin, (const float *)H->ghost,
-                                                      (float *)dst);
+                    if (H->stretched)
+                        bzk::k_stream4<true><<<g4, blk, 0, s>>>(g, (const float *)hin, (const float *)H->ghost,
+                                                                (float *)dst);
+                    else
+                        bzk::k_stream4<false><<<g4, blk, 0, s>>>(g, (const float *)hin, (const float *)H->ghost,
+                                                                 (float *)dst);
                 } else {
                     bzk::k_stream<R><<<grid, 256, 0, s>>>(g, hin, (const R *)H->ghost, dst);
                 }

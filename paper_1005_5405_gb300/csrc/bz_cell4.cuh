@@ -316,7 +316,9 @@ __device__ __forceinline__ float4 upwind4(float4 h0, float4 hx, float4 hy, float
 // Free streaming alone (Eq. streaming2D) for FP32 states with a multiple-of-4
 // velocity axis: each thread moves 16-byte quads of four jz nodes, one CTA
 // per cell at a time in the strip order, interior cells without branches.
-static __global__ void __launch_bounds__(1024) k_stream4(Geo g, const float *__restrict__ hin,
+// SX: stretched cells (the cell's own widths scale its Courant numbers).
+template <bool SX>
+__global__ void __launch_bounds__(1024) k_stream4(Geo g, const float *__restrict__ hin,
                                                   const float *__restrict__ ghost,
                                                   float *__restrict__ hout)
 {
@@ -330,12 +332,15 @@ static __global__ void __launch_bounds__(1024) k_stream4(Geo g, const float *__r
     const float ry = (float)(g.dx / g.dy);
     const int q = threadIdx.x % Q, jxs = threadIdx.x / Q, jstep = blockDim.x / Q;
     const int jy = q / nq;
+    float ay = fabsf(scu[jy] * ry), fx = 1.f;
     for (int kc = blockIdx.x; kc < g.nr; kc += gridDim.x) {
         const int c = cell_of(g, kc);
         const int ix = c % g.nx, iy = c / g.nx;
-        // Courant factors of this cell (its own widths on stretched grids).
-        const float fx = g.sx ? (float)g.sx[ix] : 1.f, fy = g.sy ? (float)g.sy[iy] : ry;
-        const float ay = fabsf(scu[jy]) * fy;
+        if (SX) {
+            // Courant factors of this cell: its own widths.
+            fx = (float)g.sx[ix];
+            ay = fabsf(scu[jy]) * (float)g.sy[iy];
+        }
         const float4 *own = reinterpret_cast<const float4 *>(hin) + (int64_t)c * plane;
         float4 *dst = reinterpret_cast<float4 *>(hout) + (int64_t)c * plane;
         if (ix > 0 && ix < g.nx - 1 && iy > 0 && iy < g.ny - 1) {
@@ -345,7 +350,7 @@ static __global__ void __launch_bounds__(1024) k_stream4(Geo g, const float *__r
             for (int jx = jxs; jx < N; jx += jstep) {
                 const int o = jx * Q + q;
                 const float4 hx = jx < half ? xr[o] : xl[o];
-                dst[o] = upwind4(own[o], hx, ys[o], fabsf(scu[jx]) * fx, ay);
+                dst[o] = upwind4(own[o], hx, ys[o], SX ? fabsf(scu[jx]) * fx : fabsf(scu[jx]), ay);
             }
         } else {
             for (int jx = jxs; jx < N; jx += jstep) {
@@ -358,7 +363,7 @@ static __global__ void __launch_bounds__(1024) k_stream4(Geo g, const float *__r
                                        : f4(ghost[(2 * g.ny + g.nx + ix) * N + jx]);
                 else
                     hy = iy > 0 ? own[o - (int64_t)g.nx * plane] : f4(ghost[(2 * g.ny + ix) * N + jx]);
-                dst[o] = upwind4(own[o], hx, hy, fabsf(scu[jx]) * fx, ay);
+                dst[o] = upwind4(own[o], hx, hy, SX ? fabsf(scu[jx]) * fx : fabsf(scu[jx]), ay);
             }
         }
     }
@@ -766,17 +771,30 @@ __device__ __forceinline__ void cell4_cell(const Geo &g, const Map4 &m, int c,
                                              : own4 + (int64_t)g.nx * plane;
                 const float4 *xr = own4 + plane, *xl = own4 - plane;
                 const int e = min(jx1, half), b = max(jx0, half);
+                if (!g.sx) {
 #pragma unroll 4
-                for (int jx = jx0; jx < e; ++jx) {
-                    const int o = jx * Q4 + q;
-                    const float4 h0 = own4[o], hx = xr[o], hy = ys[o];
-                    S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]) * fx, ay);
-                }
+                    for (int jx = jx0; jx < e; ++jx) {
+                        const int o = jx * Q4 + q;
+                        const float4 h0 = own4[o], hx = xr[o], hy = ys[o];
+                        S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]), ay);
+                    }
 #pragma unroll 4
-                for (int jx = b; jx < jx1; ++jx) {
-                    const int o = jx * Q4 + q;
-                    const float4 h0 = own4[o], hx = xl[o], hy = ys[o];
-                    S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]) * fx, ay);
+                    for (int jx = b; jx < jx1; ++jx) {
+                        const int o = jx * Q4 + q;
+                        const float4 h0 = own4[o], hx = xl[o], hy = ys[o];
+                        S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]), ay);
+                    }
+                } else {
+                    for (int jx = jx0; jx < e; ++jx) {
+                        const int o = jx * Q4 + q;
+                        const float4 h0 = own4[o], hx = xr[o], hy = ys[o];
+                        S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]) * fx, ay);
+                    }
+                    for (int jx = b; jx < jx1; ++jx) {
+                        const int o = jx * Q4 + q;
+                        const float4 h0 = own4[o], hx = xl[o], hy = ys[o];
+                        S.slab4[phys(jx)] = upwind4(h0, hx, hy, fabsf(S.cu[jx]) * fx, ay);
+                    }
                 }
             } else {
                 const float4 *ys = nullptr;
