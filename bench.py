@@ -527,9 +527,10 @@ def run_adjoint(args):
 
 
 def run_percell(args):
-    """Per-cell sample sets (every cell draws its own 10^4 samples, FP64
-    kinematics and node selection inside the per-cell kernel) against the
-    shared set on the same 64x64 cavity with a 24^3 velocity grid."""
+    """Per-cell sample sets (every cell draws its own 10^4 samples inside the
+    per-cell kernel: FP32 kinematics, FP64 redraw of the samples near a
+    velocity-cell face) against the shared set on the same 64x64 cavity with
+    a 24^3 velocity grid."""
     import dataclasses
     import torch
     import __graft_entry__

@@ -198,6 +198,17 @@ bz_status bz_stats(bz_handle *h, int64_t out[8]);
  * For parity checks; the step path keeps its own copy in device scratch. */
 bz_status bz_sample_plan(bz_handle *h, int64_t step, int32_t *idx, double *W, void *stream);
 
+/* The sample set of cell `cell` (0 <= cell < nx*ny, row-major) at step `step`
+ * as the BZ_PER_CELL step draws it (Sec. 4.2 with the cell index in the
+ * sampler's counter): same layout and units as bz_sample_plan.  For FP32
+ * handles the sampler's arithmetic is FP32 except near a velocity-cell face,
+ * where the sample is drawn again in double, so idx equals the double-
+ * precision node selection and W carries FP32 error (a few 1e-6 of
+ * |v1 - v| in |(v1 - v).k|).  Valid whatever the handle's sample mode.
+ * BZ_EINVAL on a NULL pointer, a negative step or a cell out of range. */
+bz_status bz_sample_plan_cell(bz_handle *h, int64_t step, int32_t cell, int32_t *idx, double *W,
+                              void *stream);
+
 /* Adjoint of one time step with its Monte Carlo sample set fixed.  With the
  * samples of step n fixed, the step h^n -> h^{n+1} (upwind streaming with
  * diffuse walls, Eqs. streaming2D and bcMax; the Jacobi Monte Carlo update,

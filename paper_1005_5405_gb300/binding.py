@@ -80,6 +80,7 @@ _SIGNATURES = {
     "bz_get_info": [_H, C.POINTER(bz_info)],
     "bz_stats": [_H, C.POINTER(C.c_int64)],
     "bz_sample_plan": [_H, C.c_int64, _V, _V, _V],
+    "bz_sample_plan_cell": [_H, C.c_int64, C.c_int32, _V, _V, _V],
     "bz_philox": [C.c_uint32, C.c_uint32, _V, C.c_int64, _V],
     "bz_adjoint_step": [_H, C.c_int64, _V, _V, _V, _V, C.c_double, _V],
     "bz_profile": [_H, C.c_int32],
@@ -265,6 +266,15 @@ class Cavity:
         W = np.zeros(self.p.nt, dtype=np.float64)
         check(load().bz_sample_plan(self.h, step, idx.ctypes.data, W.ctypes.data,
                                     _stream_ptr(None)), "bz_sample_plan")
+        return idx, W
+
+    def sample_plan_cell(self, step: int, cell: int):
+        """bz_sample_plan_cell: the sample set of one cell as the per-cell
+        step draws it ((nt, 4) node indices, (nt,) weights W)."""
+        idx = np.zeros((self.p.nt, 4), dtype=np.int32)
+        W = np.zeros(self.p.nt, dtype=np.float64)
+        check(load().bz_sample_plan_cell(self.h, step, cell, idx.ctypes.data, W.ctypes.data,
+                                         _stream_ptr(None)), "bz_sample_plan_cell")
         return idx, W
 
 

@@ -946,6 +946,9 @@ void bz_discretise(const bz_space *space, const bz_vel *vel, const bz_walls *wal
     g.strip = g.nx >= 16 ? 8 : g.nx;
     g.epsf = (float)g.eps;
     g.ryf = (float)(g.dx / g.dy);
+    g.vmaxf = (float)g.vmax;
+    g.idvf = (float)(1.0 / g.dv);
+    g.cwf = (float)g.cw;
     // Per-axis weight factors (w_j = A_x A_y A_z) and the wall flux constants.
     axA.assign(N, 0.0);
     for (int j = 0; j < N; ++j)
@@ -1399,6 +1402,38 @@ bz_status bz_sample_plan(bz_handle *H, int64_t step, int32_t *idx, double *W, vo
     cudaFree(dw);
     cudaFree(dstep);
     if (e != cudaSuccess) return fail(BZ_ECUDA, "sample plan failed: %s", cudaGetErrorString(e));
+    H->launches++;
+    return BZ_OK;
+}
+
+bz_status bz_sample_plan_cell(bz_handle *H, int64_t step, int32_t cell, int32_t *idx, double *W,
+                              void *stream)
+{
+    if (!H || !idx || !W) return fail(BZ_EINVAL, "NULL argument");
+    if (step < 0) return fail(BZ_EINVAL, "step must be >= 0");
+    if (cell < 0 || cell >= H->g.nr) return fail(BZ_EINVAL, "cell %d outside [0, %d)", cell, H->g.nr);
+    cudaStream_t s = (cudaStream_t)stream;
+    const Geo &g = H->g;
+    int4 *di = nullptr;
+    double *dw = nullptr;
+    BZ_TRY(dalloc(&di, sizeof(int4) * (size_t)g.nt));
+    bz_status st = dalloc(&dw, sizeof(double) * (size_t)g.nt);
+    if (st != BZ_OK) {
+        cudaFree(di);
+        return st;
+    }
+    const int pb = 256, pg = (g.nt + pb - 1) / pb;
+    if (H->dtype == BZ_F64)
+        bzk::k_plan_cell<double><<<pg, pb, 0, s>>>(g, step, (uint32_t)cell, di, dw);
+    else
+        bzk::k_plan_cell<float><<<pg, pb, 0, s>>>(g, step, (uint32_t)cell, di, dw);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(idx, di, sizeof(int4) * (size_t)g.nt, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(W, dw, sizeof(double) * (size_t)g.nt, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(di);
+    cudaFree(dw);
+    if (e != cudaSuccess) return fail(BZ_ECUDA, "per-cell sample plan failed: %s", cudaGetErrorString(e));
     H->launches++;
     return BZ_OK;
 }

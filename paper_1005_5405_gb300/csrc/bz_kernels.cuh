@@ -33,6 +33,7 @@ struct Geo {
     int nt;                     // Monte Carlo samples per step
     double vmax, dv, dt, dx, dy, eps, cw;   // cw = pi K dt / Nt
     float epsf, ryf;            // eps and dx / dy rounded to float (no FP64 per cell)
+    float vmaxf, idvf, cwf;     // vmax, 1 / dv and cw rounded to float (FP32 sampling)
     uint32_t seed, instance;
     double lid_u0, lid_amp, lid_period;
     const double *lid_profile;  // device, nx, or nullptr
@@ -207,6 +208,128 @@ __device__ __forceinline__ SampleOut draw_sample(const Geo &g, int64_t step, uin
     o.outside = (o.idx[0] < 0) | (o.idx[1] < 0) | (o.idx[2] < 0) | (o.idx[3] < 0);
     o.W = __dmul_rn(g.cw, fabs(s));
     return o;
+}
+
+// The same sample in FP32, for FP32 states on uniform velocity grids.  The
+// coordinates that pick nodes are computed in FP32 with a bounded error: the
+// uniforms and k_z are rounded once from their integers, -ln u near u = 1
+// comes from the exact complement 1 - u, sin(theta) = 2 sqrt(u (1 - u)), and
+// the angles 2 pi u are split into a float part for sincospif and an exact
+// remainder added to first order.  With CUDA's 1-ulp bounds for logf, log1pf
+// and sincospif this keeps every coordinate of v and v1 within 1.3e-6 of its
+// exact value and every coordinate of v* and v1* within 2.4e-5 (|v| < 4.8 by
+// the Box-Muller radius at the smallest uniform).  A coordinate closer to a
+// cell face than about four times its bound (kFastMarginA / kFastMarginB, in
+// velocity units, plus the rounding of the cell coordinate itself) sets
+// *redo: the caller draws that sample again with draw_sample.  Every other
+// sample selects exactly the nodes of the FP64 computation.  W = cw |s|
+// carries the FP32 error of s (at most 1.6e-5 absolute).
+constexpr float kFastMarginA = 6e-6f;    // v, v1
+constexpr float kFastMarginB = 1e-4f;    // v*, v1*
+
+// u = (x + 1/2) 2^-32 with a single rounding to float.
+__device__ __forceinline__ float u01f(uint32_t x)
+{
+    return __fmaf_rn((float)(x & 255u) + 0.5f, 0x1p-32f, (float)(x >> 8) * 0x1p-24f);
+}
+// -ln u for u = (x + 1/2) 2^-32 (near u = 1 from 1 - u = (~x + 1/2) 2^-32).
+__device__ __forceinline__ float neglog_u01f(uint32_t x)
+{
+    if (x < 0x80000000u) return -logf(u01f(x));
+    return -log1pf(-u01f(~x));
+}
+// (sin, cos) of 2 pi u for u = (x + 1/2) 2^-32: with x read as a signed
+// integer the angle is pi t, t = (x + 1/2) 2^-31 in [-1, 1), split exactly
+// into th = (x >> 8) 2^-23 and the remainder tl < 1.2e-7, whose rotation is
+// added to first order (the dropped term is below 1e-13).
+__device__ __forceinline__ void sincos_2pi_u01f(uint32_t x, float *sv, float *cv)
+{
+    const int32_t xs = (int32_t)x;
+    const float th = (float)(xs >> 8) * 0x1p-23f;
+    const float d = ((float)(xs & 255) + 0.5f) * (0x1p-31f * 3.14159265358979f);
+    float s, c;
+    sincospif(th, &s, &c);
+    *sv = __fmaf_rn(c, d, s);
+    *cv = __fmaf_rn(-s, d, c);
+}
+// Cell of one coordinate on a uniform axis (-1 outside the box); *near when
+// the coordinate lies within m cell widths of a face.
+__device__ __forceinline__ int node_axis_fast(float v, float vmax, float idv, int n, float m, bool *near)
+{
+    const float t = __fmul_rn(__fadd_rn(v, vmax), idv);
+    const float fl = floorf(t), fr = t - fl;
+    if (fr < m || fr > 1.f - m) *near = true;
+    if (!(t >= 0.f) || fl >= (float)n) return -1;
+    return (int)fl;
+}
+
+__device__ __forceinline__ SampleOut draw_sample_fast(const Geo &g, int64_t step, uint32_t cellword,
+                                                      uint32_t l, bool *redo)
+{
+    const uint2 key = make_uint2(g.seed, g.instance);
+    const uint4 a = philox4x32_10(make_uint4(l, (uint32_t)step, cellword, 0u), key);
+    const uint4 b = philox4x32_10(make_uint4(l, (uint32_t)step, cellword, 1u), key);
+    const float r0 = sqrtf(neglog_u01f(a.x)), r1 = sqrtf(neglog_u01f(a.z)), r2 = sqrtf(neglog_u01f(b.x));
+    float s0, c0, s1, c1, s2, c2, sp, cp;
+    sincos_2pi_u01f(a.y, &s0, &c0);
+    sincos_2pi_u01f(a.w, &s1, &c1);
+    sincos_2pi_u01f(b.y, &s2, &c2);
+    sincos_2pi_u01f(b.w, &sp, &cp);
+    const float v[3] = {r0 * c0, r0 * s0, r1 * c1};
+    const float v1[3] = {r1 * s1, r2 * c2, r2 * s2};
+    // k_z = 1 - 2u = (y + 1/2) 2^-31 with y = 2^31 - 1 - x (exact in int32);
+    // sin(theta) = sqrt(1 - k_z^2) = 2 sqrt(u (1 - u)).
+    const int32_t ys = (int32_t)(0x7FFFFFFFu - b.z);
+    const float kz = __fmaf_rn((float)(ys & 255) + 0.5f, 0x1p-31f, (float)(ys >> 8) * 0x1p-23f);
+    const float st = 2.f * sqrtf(u01f(b.z) * u01f(~b.z));
+    const float k[3] = {st * cp, st * sp, kz};
+    const float s = (v1[0] - v[0]) * k[0] + (v1[1] - v[1]) * k[1] + (v1[2] - v[2]) * k[2];
+    const float vmax = g.vmaxf, idv = g.idvf, mt = 2.4e-7f * (float)g.nv;
+    const float ma = kFastMarginA * idv + mt, mb = kFastMarginB * idv + mt;
+    const int n = g.nv;
+    bool near = false;
+    auto node = [&](float x, float y, float z, float m) {
+        const int i = node_axis_fast(x, vmax, idv, n, m, &near),
+                  j = node_axis_fast(y, vmax, idv, n, m, &near),
+                  q = node_axis_fast(z, vmax, idv, n, m, &near);
+        return (i < 0 || j < 0 || q < 0) ? -1 : (i * n + j) * n + q;
+    };
+    SampleOut o;
+    o.idx[0] = node(v[0], v[1], v[2], ma);
+    o.idx[1] = node(v1[0], v1[1], v1[2], ma);
+    o.idx[2] = node(v[0] + s * k[0], v[1] + s * k[1], v[2] + s * k[2], mb);
+    o.idx[3] = node(v1[0] - s * k[0], v1[1] - s * k[1], v1[2] - s * k[2], mb);
+    *redo = near;
+    o.near = 0;
+    o.outside = (o.idx[0] < 0) | (o.idx[1] < 0) | (o.idx[2] < 0) | (o.idx[3] < 0);
+    o.W = (double)(g.cwf * fabsf(s));
+    return o;
+}
+
+// The sampler the per-cell kernels use for states of type R: FP32 with an
+// FP64 redraw near a face (uniform grids, FP32 states), else FP64.
+template <typename R>
+__device__ __forceinline__ SampleOut draw_sample_cell(const Geo &g, int64_t step, uint32_t cell,
+                                                      uint32_t l)
+{
+    if (sizeof(R) == 4 && !g.axe) {
+        bool redo;
+        const SampleOut o = draw_sample_fast(g, step, cell, l, &redo);
+        if (!redo) return o;
+    }
+    return draw_sample(g, step, cell, l);
+}
+
+// The sample set of one cell as the per-cell kernels draw it, for
+// inspection: idx[l] in logical node order, W[l].
+template <typename R>
+__global__ void k_plan_cell(Geo g, int64_t step, uint32_t cell, int4 *__restrict__ idx, double *__restrict__ W)
+{
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= g.nt) return;
+    const SampleOut o = draw_sample_cell<R>(g, step, cell, (uint32_t)l);
+    idx[l] = make_int4(o.idx[0], o.idx[1], o.idx[2], o.idx[3]);
+    W[l] = o.W;
 }
 
 // Node indices of a sample (v, v1, v*, v1*).  Grids with fewer than 65535
@@ -871,24 +994,29 @@ k_cell(Geo g, const R *__restrict__ hin, const R *__restrict__ ghost,
             const R *src = hin + (int64_t)c * nvt;
             for (int j = t; j < nvt; j += T) S.slab[j] = src[j];
         }
+        if (PC && t == 0) reinterpret_cast<int *>(S.red)[0] = 0;     // redraw queue
         __syncthreads();
 
         // ---- phase A: g_l W_l from the pre-collision values (Jacobi) -------
         // Plan entries are loaded four at a time to keep L2 requests in flight.
         if constexpr (PC) {
             // The cell's own samples (Sec. 4.2 / Algorithm 2 with the cell in
-            // the Philox counter): kinematics and node selection in FP64.
-            for (int l0 = 0; l0 < g.nt; l0 += T) {
-                const int l = l0 + t;
-                const bool act = l < g.nt;
-                SampleOut o = {};
-                if (act) {
-                    o = draw_sample(g, step, (uint32_t)c, (uint32_t)l);
-                    sidx[l] = Idx4<I>::make(o.idx);
-                    const R ha = o.idx[0] >= 0 ? S.slab[o.idx[0]] : R(0);
-                    const R hb = o.idx[1] >= 0 ? S.slab[o.idx[1]] : R(0);
-                    gw[l] = (ha + hb + eps * ha * hb) * (R)o.W;
-                }
+            // the Philox counter), node selection equal to the FP64
+            // computation's.  FP32 states on uniform grids draw in FP32; a
+            // sample near a velocity-cell face is queued in the reduction
+            // scratch (idle until the increment sums) and drawn again in
+            // FP64 after the loop by all threads, so the warps stay together
+            // (a full queue redraws in place).
+            const bool fast = sizeof(R) == 4 && !g.axe;
+            int *rq = reinterpret_cast<int *>(S.red);
+            const int rcap = kMaxWarps * kRedSlots * 2 - 1;
+            auto put = [&](int l, const SampleOut &o) {
+                sidx[l] = Idx4<I>::make(o.idx);
+                const R ha = o.idx[0] >= 0 ? S.slab[o.idx[0]] : R(0);
+                const R hb = o.idx[1] >= 0 ? S.slab[o.idx[1]] : R(0);
+                gw[l] = (ha + hb + eps * ha * hb) * (R)o.W;
+            };
+            auto count = [&](bool act, const SampleOut &o) {
                 if (stats) {
                     const unsigned mo = __ballot_sync(0xFFFFFFFFu, act && o.outside);
                     const unsigned mn = __ballot_sync(0xFFFFFFFFu, act && o.near);
@@ -896,6 +1024,40 @@ k_cell(Geo g, const R *__restrict__ hin, const R *__restrict__ ghost,
                         if (mo) atomicAdd(stats + 1, (unsigned long long)__popc(mo));
                         if (mn) atomicAdd(stats + 2, (unsigned long long)__popc(mn));
                     }
+                }
+            };
+            for (int l0 = 0; l0 < g.nt; l0 += T) {
+                const int l = l0 + t;
+                bool act = l < g.nt;
+                SampleOut o = {};
+                if (act) {
+                    bool redo = true;
+                    if (fast) o = draw_sample_fast(g, step, (uint32_t)c, (uint32_t)l, &redo);
+                    if (redo) {
+                        const int k = fast ? atomicAdd(rq, 1) : rcap;
+                        if (k < rcap) {
+                            rq[1 + k] = l;
+                            act = false;
+                        } else {
+                            o = draw_sample(g, step, (uint32_t)c, (uint32_t)l);
+                        }
+                    }
+                    if (act) put(l, o);
+                }
+                count(act, o);
+            }
+            if (fast) {
+                __syncthreads();
+                const int nq = min(rq[0], rcap);
+                for (int i0 = 0; i0 < nq; i0 += T) {
+                    const bool act = i0 + t < nq;
+                    SampleOut o = {};
+                    if (act) {
+                        const int l = rq[1 + i0 + t];
+                        o = draw_sample(g, step, (uint32_t)c, (uint32_t)l);
+                        put(l, o);
+                    }
+                    count(act, o);
                 }
             }
         } else {

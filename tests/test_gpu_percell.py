@@ -29,9 +29,13 @@ CASES = [
     workloads.small(nx=3, ny=3, nv=8, vmax=2.0, nt=1500, seed=23, dtype="f32", per_cell=True),
 ]
 IDS = ["f64_12", "f32_16", "outbox_8"]
+# a velocity box of width 0.02 with 8 nodes: most samples lie outside, and
+# about 40 % of them come within the FP32 sampler's margin of a cell face,
+# more than its redraw queue holds (the rest are redrawn in place)
+TINY = workloads.small(nx=2, ny=2, nv=8, vmax=0.01, nt=4000, seed=24, dtype="f32", per_cell=True)
 
 
-@pytest.mark.parametrize("p", CASES, ids=IDS)
+@pytest.mark.parametrize("p", CASES + [TINY], ids=IDS + ["tiny_box"])
 def test_per_cell_fused_step_matches_oracle(p):
     cav, o, h0 = make(p)
     assert cav.get_info().kernel_variant == 0
@@ -87,3 +91,41 @@ def test_per_cell_adjoint_is_unsupported():
     with pytest.raises(binding.BzError) as e:
         cav.adjoint_step(0, h, h.clone())
     assert e.value.status == binding.BZ_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("nv,vmax,nt,dtype", [(24, 4.5, 40000, "f32"), (32, 5.0, 40000, "f32"),
+                                              (8, 2.0, 20000, "f32"), (8, 0.01, 4000, "f32"),
+                                              (12, 4.0, 2000, "f64")])
+def test_per_cell_sample_plan_matches_oracle(nv, vmax, nt, dtype):
+    """Every cell's own sample set as the per-cell step draws it: the node
+    indices equal the oracle's FP64 selection for every sample (FP32 handles
+    draw in FP32 and redraw in FP64 near a face), and W = cw |s| is within
+    the FP32 error of s (2e-5 cw absolute; 1e-12 relative for FP64)."""
+    p = workloads.small(nx=3, ny=2, nv=nv, vmax=vmax, nt=nt, seed=31, dtype=dtype, per_cell=True)
+    cav = binding.Cavity(p)
+    o = oracle.Oracle(**p.kwargs())
+    prev = None
+    for step, cell in [(0, 0), (1, 5), (57, 3), (57, 4)]:
+        idx, W = cav.sample_plan_cell(step, cell)
+        s = o.samples(step, cellword=cell)
+        same = (idx == s["idx"]).all(1)
+        assert same.all(), (np.nonzero(~same), s["near_face"][~same])
+        cw = float(np.max(s["W"]) / np.max(np.abs(s["s"])))
+        err = np.abs(W - s["W"])
+        if dtype == "f32":
+            assert np.max(err) <= 2e-5 * cw + 1e-7 * np.max(s["W"])
+        else:
+            assert np.max(err) <= 1e-12 * np.max(s["W"])
+        if prev is not None:
+            assert not np.array_equal(idx, prev)      # the cells draw different sets
+        prev = idx
+    print(f"per-cell sampler: 0 node mismatches in {4 * nt} samples")
+
+
+def test_per_cell_sample_plan_rejects_bad_arguments():
+    p = CASES[1]
+    cav = binding.Cavity(p)
+    for step, cell in [(-1, 0), (0, -1), (0, p.nr)]:
+        with pytest.raises(binding.BzError) as e:
+            cav.sample_plan_cell(step, cell)
+        assert e.value.status == binding.BZ_EINVAL
