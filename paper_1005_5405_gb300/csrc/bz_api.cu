@@ -944,6 +944,7 @@ void bz_discretise(const bz_space *space, const bz_vel *vel, const bz_walls *wal
     g.lid_amp = lamp;
     g.lid_period = walls ? walls->lid_period : 0.0;
     g.strip = g.nx >= 16 ? 8 : g.nx;
+    g.redraw_cap = -1;
     g.epsf = (float)g.eps;
     g.ryf = (float)(g.dx / g.dy);
     g.vmaxf = (float)g.vmax;
@@ -1028,6 +1029,7 @@ bz_status bz_create(const bz_space *space, const bz_vel *vel, const bz_walls *wa
     bz_grid_tables tb;
     bz_discretise(space, vel, walls, params, g, tb);
     if (const char *fb = getenv("BZ_SOLVE_FALLBACK")) g.solve_fb = atoi(fb) != 0 ? 1 : 0;
+    if (const char *rc = getenv("BZ_REDRAW_CAP")) g.redraw_cap = atoi(rc) >= 0 ? atoi(rc) : -1;
     const bool sv = vel->rv > 0.0 && vel->rv < 1.0;
     const bool sxg = space->rx > 0.0 && space->rx < 1.0, syg = space->ry > 0.0 && space->ry < 1.0;
     H->stretched = sv || sxg || syg;

@@ -48,6 +48,7 @@ struct Geo {
     int swz;                    // plan node indices in the quad-rotated shared-memory order
     int strip;                  // cells are visited in column strips of this width
     int solve_fb;               // 1: every correction solve takes its pivoted fallback (tests)
+    int redraw_cap;             // per-cell FP32 sampling: FP64 redraw queue entries (-1: all)
     // Stretched grids (nullptr when uniform).  axe: nv + 1 velocity cell
     // edges; axd: nv widths; sx, sy: per column / row, dx / dx_i and
     // dx / dy_j (the Courant numbers are cu(v) times these); wlid: per lid
@@ -1009,7 +1010,8 @@ k_cell(Geo g, const R *__restrict__ hin, const R *__restrict__ ghost,
             // (a full queue redraws in place).
             const bool fast = sizeof(R) == 4 && !g.axe;
             int *rq = reinterpret_cast<int *>(S.red);
-            const int rcap = kMaxWarps * kRedSlots * 2 - 1;
+            const int rcap = g.redraw_cap < 0 ? kMaxWarps * kRedSlots * 2 - 1
+                                              : min(g.redraw_cap, kMaxWarps * kRedSlots * 2 - 1);
             auto put = [&](int l, const SampleOut &o) {
                 sidx[l] = Idx4<I>::make(o.idx);
                 const R ha = o.idx[0] >= 0 ? S.slab[o.idx[0]] : R(0);

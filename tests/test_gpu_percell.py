@@ -29,13 +29,9 @@ CASES = [
     workloads.small(nx=3, ny=3, nv=8, vmax=2.0, nt=1500, seed=23, dtype="f32", per_cell=True),
 ]
 IDS = ["f64_12", "f32_16", "outbox_8"]
-# a velocity box of width 0.02 with 8 nodes: most samples lie outside, and
-# about 40 % of them come within the FP32 sampler's margin of a cell face,
-# more than its redraw queue holds (the rest are redrawn in place)
-TINY = workloads.small(nx=2, ny=2, nv=8, vmax=0.01, nt=4000, seed=24, dtype="f32", per_cell=True)
 
 
-@pytest.mark.parametrize("p", CASES + [TINY], ids=IDS + ["tiny_box"])
+@pytest.mark.parametrize("p", CASES, ids=IDS)
 def test_per_cell_fused_step_matches_oracle(p):
     cav, o, h0 = make(p)
     assert cav.get_info().kernel_variant == 0
@@ -57,6 +53,34 @@ def test_per_cell_collide_matches_oracle(p):
     assert f_metric(o, state(cav), h_o) < (1e-10 if p.dtype == "f64" else 1e-5)
 
 
+def test_per_cell_redraw_queue_capacity_changes_nothing(monkeypatch):
+    """The FP32 per-cell sampler queues the samples near a face for an FP64
+    redraw after its loop; with the queue cut to 0 or 5 entries they are
+    redrawn in place instead.  The samples are the same either way: each
+    run matches the oracle step by step, the runs agree to the rounding of
+    the shared-memory atomics, and the out-of-box and face-proximity counters
+    are equal."""
+    p = workloads.small(nx=4, ny=4, nv=24, vmax=4.5, nt=8000, seed=26, dtype="f32",
+                        per_cell=True, eps=0.1)
+    out = {}
+    for cap in (None, "0", "5"):
+        if cap is None:
+            monkeypatch.delenv("BZ_REDRAW_CAP", raising=False)
+        else:
+            monkeypatch.setenv("BZ_REDRAW_CAP", cap)
+        cav, o, h0 = make(p, seed=27)
+        h_g = h0
+        for n in range(3):
+            cav.step(1)
+            h_o, _ = o.step(h_g, n)
+            h_g = state(cav)
+            assert f_metric(o, h_g, h_o) < 1e-5, (cap, n)
+        out[cap] = (h_g, list(cav.stats()[1:3]))
+    for cap in ("0", "5"):
+        assert f_metric(o, out[cap][0], out[None][0]) < 1e-6, cap
+        assert out[cap][1] == out[None][1], cap
+
+
 def test_per_cell_sets_differ_from_the_shared_set():
     """The same problem with the shared set gives a different result (the
     samples differ), while both conserve mass exactly."""
@@ -72,9 +96,13 @@ def test_per_cell_sets_differ_from_the_shared_set():
     assert np.allclose((ha * w).sum(axis=1), (h0 * w).sum(axis=1), atol=1e-5)
 
 
-def test_per_cell_out_of_box_counter():
+@pytest.mark.parametrize("cap", [None, "3"])
+def test_per_cell_out_of_box_counter(monkeypatch, cap):
     """Samples with a node outside the box are counted cell by cell: the
-    count equals the oracle's over every cell's own set."""
+    count equals the oracle's over every cell's own set (also when the FP64
+    redraw queue holds 3 samples and the rest are redrawn in place)."""
+    if cap is not None:
+        monkeypatch.setenv("BZ_REDRAW_CAP", cap)
     p = CASES[2]
     cav, o, h0 = make(p)
     cav.step(1)
@@ -100,8 +128,11 @@ def test_per_cell_sample_plan_matches_oracle(nv, vmax, nt, dtype):
     """Every cell's own sample set as the per-cell step draws it: the node
     indices equal the oracle's FP64 selection for every sample (FP32 handles
     draw in FP32 and redraw in FP64 near a face), and W = cw |s| is within
-    the FP32 error of s (2e-5 cw absolute; 1e-12 relative for FP64)."""
-    p = workloads.small(nx=3, ny=2, nv=nv, vmax=vmax, nt=nt, seed=31, dtype=dtype, per_cell=True)
+    the FP32 error of s (2e-5 cw absolute; 1e-12 relative for FP64).  The
+    handles use the shared set: the per-cell sampler does not depend on the
+    mode, and 4x10^4 per-cell samples would not fit the per-cell kernel's
+    shared memory."""
+    p = workloads.small(nx=3, ny=2, nv=nv, vmax=vmax, nt=nt, seed=31, dtype=dtype)
     cav = binding.Cavity(p)
     o = oracle.Oracle(**p.kwargs())
     prev = None
@@ -117,8 +148,8 @@ def test_per_cell_sample_plan_matches_oracle(nv, vmax, nt, dtype):
         else:
             assert np.max(err) <= 1e-12 * np.max(s["W"])
         if prev is not None:
-            assert not np.array_equal(idx, prev)      # the cells draw different sets
-        prev = idx
+            assert not np.array_equal(W, prev)        # the cells draw different sets
+        prev = W
     print(f"per-cell sampler: 0 node mismatches in {4 * nt} samples")
 
 
