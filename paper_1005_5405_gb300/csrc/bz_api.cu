@@ -126,6 +126,7 @@ struct bz_handle {
     uint2 *lz_rec = nullptr;
     int lz_mcap = 0, lz_G = 0, lz_T = 0, lz_grid = 0, lz_mprobe = 0;
     int lz_cmax = 0, lz_order_tpb = 0;     // bank-aware ordering of the term runs (1: on)
+    bool lz_tma = false;                   // streaming sources by bulk copies (G = 4 only)
     int lz_chunk = 0;                      // positions per chunk of the ordering
     cudaStream_t lz_side = nullptr;        // the sample plan runs here, beside the walls
     cudaEvent_t lz_fork = nullptr, lz_join = nullptr, lz_mid = nullptr;
@@ -371,17 +372,20 @@ double lz_monomial(int k, double x, double y, double z)
 // length with per-cell Courant factors.
 int lz_nv_key(const bz_handle *H) { return H->stretched ? -1 : (H->g.nv == 32 || H->g.nv == 20 ? H->g.nv : 0); }
 
-template <int G, int NV, bool SX>
+template <int G, int NV, bool SX, bool TMA = false>
 bz_status setup_lz_one(bz_handle *H, size_t smem, int *occ)
 {
-    BZ_CUDA(bz_allow_max_smem(bzk::k_lz<G, NV, SX>, H->smem_optin));
-    BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, bzk::k_lz<G, NV, SX>, H->lz_T, smem));
+    BZ_CUDA(bz_allow_max_smem(bzk::k_lz<G, NV, SX, TMA>, H->smem_optin));
+    BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, bzk::k_lz<G, NV, SX, TMA>, H->lz_T, smem));
     return BZ_OK;
 }
 
 template <int G>
 bz_status setup_lz_kernel(bz_handle *H, size_t smem, int *occ)
 {
+    if (G == 4 && H->lz_tma && lz_nv_key(H) >= 0)
+        return lz_nv_key(H) == 32 ? setup_lz_one<4, 32, false, true>(H, smem, occ)
+                                  : setup_lz_one<4, 0, false, true>(H, smem, occ);
     switch (lz_nv_key(H)) {
     case 32: return setup_lz_one<G, 32, false>(H, smem, occ);
     case 20: return setup_lz_one<G, 20, false>(H, smem, occ);
@@ -393,6 +397,13 @@ bz_status setup_lz_kernel(bz_handle *H, size_t smem, int *occ)
 template <int G>
 void launch_lz_kernel(bz_handle *H, const bzk::LzArgs &a, cudaStream_t s)
 {
+    if (G == 4 && H->lz_tma && lz_nv_key(H) >= 0) {
+        if (lz_nv_key(H) == 32)
+            bzk::k_lz<4, 32, false, true><<<H->lz_grid, H->lz_T, H->lz_smem, s>>>(H->g, a);
+        else
+            bzk::k_lz<4, 0, false, true><<<H->lz_grid, H->lz_T, H->lz_smem, s>>>(H->g, a);
+        return;
+    }
     switch (lz_nv_key(H)) {
     case 32: bzk::k_lz<G, 32, false><<<H->lz_grid, H->lz_T, H->lz_smem, s>>>(H->g, a); break;
     case 20: bzk::k_lz<G, 20, false><<<H->lz_grid, H->lz_T, H->lz_smem, s>>>(H->g, a); break;
@@ -460,6 +471,7 @@ bz_status configure_lazy(bz_handle *H)
     // independent node hits); a step above the capacity runs the fallback.
     int mcap = std::min(nvt, (mmax + mmax / 20 + 64 + 31) / 32 * 32);
     if (const char *mc = getenv("BZ_LAZY_MCAP")) mcap = std::max(1, std::min(nvt, atoi(mc)));
+    if (const char *tm = getenv("BZ_LAZY_TMA")) H->lz_tma = atoi(tm) != 0;
 
     // One CTA of two 256-thread roles per SM; the largest group of cells
     // whose shared memory fits.
@@ -622,6 +634,11 @@ bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true, bo
         for (int k = 0; k < bzk::kLzX; ++k) a.e0[k] = H->lz_e0[k];
         a.clk = H->prof_clk;
         a.stats = H->stats;
+        a.err = H->stats + 8;
+        // BZ_LAZY_TMA_TIMEOUT_TEST=1: CTA 0 expects 16 bytes more than its
+        // first bulk copies bring, so its first wait runs out (tests of the
+        // bounded waits; the step's result is then invalid).
+        if (const char *tt = getenv("BZ_LAZY_TMA_TIMEOUT_TEST")) a.tx_excess = atoi(tt) != 0 ? 16 : 0;
         a.nostream = nostream ? 1 : 0;
         // Below 32^3 velocities the streaming of a group takes longer than
         // its collision terms: the collision warps start the increment sums.
@@ -1063,7 +1080,7 @@ bz_status bz_create(const bz_space *space, const bz_vel *vel, const bz_walls *wa
     BZ_STEP(dalloc(&H->nw, sizeof(double) * g.nfaces));
     BZ_STEP(dalloc(&H->shear, sizeof(double) * (g.nx + 1)));
     BZ_STEP(dalloc(&H->mom, sizeof(double) * 11 * (size_t)g.nr));
-    BZ_STEP(dalloc(&H->stats, sizeof(unsigned long long) * 8));
+    BZ_STEP(dalloc(&H->stats, sizeof(unsigned long long) * 9));
     BZ_STEP(dalloc(&H->flag, sizeof(int)));
     BZ_STEP(dalloc(&H->axv, sizeof(double) * N));
     BZ_STEP(dalloc(&H->axA, sizeof(double) * N));
@@ -1114,7 +1131,7 @@ bz_status bz_create(const bz_space *space, const bz_vel *vel, const bz_walls *wa
     }
     if (e == cudaSuccess) e = cudaMemset(H->h[0], 0, nodes * H->esz);
     if (e == cudaSuccess) e = cudaMemset(H->h[1], 0, nodes * H->esz);
-    if (e == cudaSuccess) e = cudaMemset(H->stats, 0, sizeof(unsigned long long) * 8);
+    if (e == cudaSuccess) e = cudaMemset(H->stats, 0, sizeof(unsigned long long) * 9);
     if (e == cudaSuccess) e = cudaMemset(H->d_step, 0, sizeof(int64_t));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&H->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -1356,13 +1373,18 @@ bz_status bz_get_info(const bz_handle *H, bz_info *o)
 bz_status bz_stats(bz_handle *H, int64_t out[8])
 {
     if (!H || !out) return fail(BZ_EINVAL, "NULL argument");
-    unsigned long long d[8];
+    unsigned long long d[9];
     BZ_CUDA(cudaDeviceSynchronize());
     BZ_CUDA(cudaMemcpy(d, H->stats, sizeof(d), cudaMemcpyDeviceToHost));
     for (int i = 0; i < 8; ++i) out[i] = (int64_t)d[i];
     out[0] = H->step;
     out[4] = H->launches;
     out[7] = H->lz_mcap;
+    if (d[8]) {
+        // Reported once: the flag is cleared for the steps that follow.
+        BZ_CUDA(cudaMemset(H->stats + 8, 0, sizeof(unsigned long long)));
+        return fail(BZ_ETIMEOUT, "a bounded device wait of the active-node kernel gave up");
+    }
     return BZ_OK;
 }
 

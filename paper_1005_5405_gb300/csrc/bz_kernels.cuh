@@ -33,7 +33,6 @@ struct Geo {
     int nt;                     // Monte Carlo samples per step
     double vmax, dv, dt, dx, dy, eps, cw;   // cw = pi K dt / Nt
     float epsf, ryf;            // eps and dx / dy rounded to float (no FP64 per cell)
-    float vmaxf, idvf, cwf;     // vmax, 1 / dv and cw rounded to float (FP32 sampling)
     uint32_t seed, instance;
     double lid_u0, lid_amp, lid_period;
     const double *lid_profile;  // device, nx, or nullptr
@@ -48,7 +47,6 @@ struct Geo {
     int swz;                    // plan node indices in the quad-rotated shared-memory order
     int strip;                  // cells are visited in column strips of this width
     int solve_fb;               // 1: every correction solve takes its pivoted fallback (tests)
-    int redraw_cap;             // per-cell FP32 sampling: FP64 redraw queue entries (-1: all)
     // Stretched grids (nullptr when uniform).  axe: nv + 1 velocity cell
     // edges; axd: nv widths; sx, sy: per column / row, dx / dx_i and
     // dx / dy_j (the Courant numbers are cu(v) times these); wlid: per lid
@@ -56,6 +54,8 @@ struct Geo {
     const double *axe, *axd;
     const double *sx, *sy;
     const double *wlid;
+    float vmaxf, idvf, cwf;     // vmax, 1 / dv and cw rounded to float (FP32 sampling)
+    int redraw_cap;             // per-cell FP32 sampling: FP64 redraw queue entries (-1: all)
 };
 
 // Visiting order of the cells by the persistent per-cell kernels: column

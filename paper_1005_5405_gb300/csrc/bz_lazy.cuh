@@ -50,6 +50,7 @@ constexpr int kLzRoleWarps = kLzRoleT / 32;
 constexpr int kLzMaxG = 4;         // cells per CTA group
 constexpr int kLzMaxN = 32;        // velocity nodes per axis (N^2 / 4 <= kLzRoleT)
 constexpr int kLzStages = 5;       // streaming stages staged per thread
+constexpr unsigned long long kLzWaitNs = 1000000000ull;   // an mbarrier wait gives up after 1 s
 
 // meta layout: [0] M, [1] overflow (M > mcap), [2] E (terms of the step),
 // [3] C (terms per thread).
@@ -614,6 +615,73 @@ __device__ __forceinline__ void lz_cp_wait_stage()
     asm volatile("cp.async.wait_group %0;" ::"n"(kLzStages - 1) : "memory");
 }
 
+// Bulk copies global -> shared through the tensor-memory-access unit
+// (cp.async.bulk, completion counted in bytes on an mbarrier) and the
+// mbarrier operations of the streaming ring.  Every wait is bounded: each
+// poll returns within the hardware's own suspend limit, and after kLzWaitNs
+// of the global timer the wait gives up and returns false.
+__device__ __forceinline__ void lz_mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void lz_mbar_init_fence()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void lz_mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void lz_mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool lz_mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+__device__ __forceinline__ unsigned long long lz_now_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool lz_mbar_wait(uint32_t bar, uint32_t parity)
+{
+    if (lz_mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = lz_now_ns();
+    while (!lz_mbar_try(bar, parity))
+        if (lz_now_ns() - t0 > kLzWaitNs) return false;
+    return true;
+}
+// A bounded wait that is skipped once any wait of the CTA has given up (the
+// CTA then finishes without waiting and reports the error).
+__device__ __forceinline__ void lz_ring_wait(uint32_t bar, uint32_t parity, int &err)
+{
+    volatile int *e = &err;
+    if (*e == 0 && !lz_mbar_wait(bar, parity)) *e = 1;
+}
+__device__ __forceinline__ void lz_bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+// Orders this thread's generic-proxy shared-memory writes before later
+// bulk copies (async proxy) into the same bytes.
+__device__ __forceinline__ void lz_fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // Everything the kernel needs besides the geometry (by value).
 struct LzArgs {
     const float *hin, *mu_in, *ghost;
@@ -630,6 +698,9 @@ struct LzArgs {
     unsigned long long *stats;  // nullable: [3] counts correction solves that fell back
     int nostream;           // 1: h~ = h (no free streaming; the relaxation alone)
     int early_tail;         // 1: the collision warps start the increment sums at once
+    unsigned long long *err;    // nullable: set to 1 when a bounded mbarrier wait gave up
+    int tx_excess;          // bulk-copy ring, CTA 0's first stage: bytes expected beyond
+                            // those copied (a wait that runs out, for tests; normally 0)
 };
 
 // Shared memory.  A fixed-layout head (compile-time offsets): warp partial
@@ -652,6 +723,9 @@ struct alignas(128) LzHead {
     float mus[kLzMaxG][5][8];                    // mu of own, right, left, below, above (0 outside)
     int4 cell[2][kLzMaxG];                       // c, ix, iy of a group's cells (c < 0: none), per buffer
     int tail_next;                               // next chunk of the increment sums to claim
+    int tma_err;                                 // a bounded wait of the bulk-copy ring gave up
+    unsigned long long bar_full[kLzStages];      // bulk-copy ring: stage landed (transaction bytes)
+    unsigned long long bar_empty[kLzStages];     // bulk-copy ring: stage read by the streaming warps
 };
 constexpr uint32_t kLzAOff = (sizeof(LzHead) + 15) & ~(size_t)15;
 
@@ -920,6 +994,7 @@ constexpr uint32_t kLzSlotStride = 3 * kLzSrcStride;      // between stage slots
 // sources are (cells, or a wall's ghost values).
 struct LzPf {
     int pk, pst;
+    int sidx;                // ring slot index of the next stage (bulk-copy ring)
     uint32_t slot;
     const char *own;         // this thread's quad of stage pst of cell pk
     int64_t yoff;            // byte offset of the y source cell
@@ -967,6 +1042,74 @@ __device__ __forceinline__ void lz_prefetch(LzPf &p, const LzQuad &q, const Geo 
     lz_cp_commit();
     p.slot += kLzSlotStride;
     if (p.slot == q.ring_end) p.slot = q.ring0;
+    if (++p.pst == q.J) {
+        p.pst = 0;
+        ++p.pk;
+    }
+}
+
+// The producer's view of the bulk-copy ring: per slot (one bit each),
+// whether a stage was issued into it whose reading has not been awaited yet,
+// the parity of the next phase of its empty barrier, and the parity of its
+// issue count.
+struct LzTmaProd {
+    uint32_t pending, epar, ipar;
+};
+
+// The same step with bulk copies: thread 0 of the role issues the stage's
+// runs once every streaming warp has read the slot's previous stage.  The
+// own and the x-source runs are S float4 each, contiguous in global memory
+// and in the slot (a stage never straddles jx = N/2).  The y source differs
+// within a plane: its rows jy < N/2 (v_y < 0) come from the cell above and
+// its rows jy >= N/2 from the cell below, so each of the stage's P4 planes
+// takes two half-plane copies.  Each thread still writes its wall ghost
+// values into its own bytes of the slot (no copy where the source lies
+// outside the cavity).
+__device__ __forceinline__ void lz_prefetch_tma(LzPf &p, const LzQuad &q, const Geo &g, const LzArgs &a,
+                                                const int4 *cells, const char *hin_t, int ncell, LzHead &H,
+                                                LzTmaProd &pr)
+{
+    if (p.pk < ncell) {
+        if (p.pst == 0) lz_pf_cell(p, q, g, a, cells, hin_t);
+        const bool left = p.pst >= q.Jh;
+        const bool xin = left ? p.xin_l : p.xin_r;
+        if (q.streams) {
+            if (!xin) lz_sts4(p.slot + kLzSrcStride, left ? p.gxl : p.gxr);
+            if (!p.yin) lz_sts4(p.slot + 2 * kLzSrcStride, __ldg(p.gy + p.pst * q.P4));
+        }
+        // After a wait gave up, nothing more is issued (the waits are skipped).
+        if (threadIdx.x == 0 && *(volatile int *)&H.tma_err == 0) {
+            const int s = p.sidx;
+            const uint32_t full = lz_saddr(&H.bar_full[s]);
+            if (pr.pending >> s & 1u) {
+                lz_ring_wait(lz_saddr(&H.bar_empty[s]), pr.epar >> s & 1u, H.tma_err);
+                pr.epar ^= 1u << s;
+            }
+            const uint32_t extra = (blockIdx.x == 0 && pr.ipar == 0u && pr.pending == 0u) ? (uint32_t)a.tx_excess : 0u;
+            pr.pending |= 1u << s;
+            pr.ipar ^= 1u << s;
+            const uint32_t sb = (uint32_t)q.sbytes;
+            const uint32_t hb = (uint32_t)(q.N * q.N) * 2u;          // half a plane (N^2/2 floats)
+            const int4 ce = cells[p.pk];
+            const bool above = ce.z < g.ny - 1, below = ce.z > 0;
+            const uint32_t ybytes = (uint32_t)q.P4 * hb * ((above ? 1u : 0u) + (below ? 1u : 0u));
+            lz_mbar_expect_tx(full, sb * (1u + (xin ? 1u : 0u)) + ybytes + extra);
+            lz_bulk_g2s(p.slot, p.own, sb, full);
+            if (xin) lz_bulk_g2s(p.slot + kLzSrcStride, left ? p.own - q.pbytes : p.own + q.pbytes, sb, full);
+            const int64_t ystep = (int64_t)g.nx * q.pbytes;
+            for (int pl = 0; pl < q.P4; ++pl) {
+                const uint32_t o = (uint32_t)pl * 2u * hb;
+                if (above) lz_bulk_g2s(p.slot + 2 * kLzSrcStride + o, p.own + ystep + o, hb, full);
+                if (below) lz_bulk_g2s(p.slot + 2 * kLzSrcStride + o + hb, p.own - ystep + o + hb, hb, full);
+            }
+        }
+        p.own += q.sbytes;
+    }
+    p.slot += kLzSlotStride;
+    if (++p.sidx == kLzStages) {
+        p.sidx = 0;
+        p.slot = q.ring0;
+    }
     if (++p.pst == q.J) {
         p.pst = 0;
         ++p.pk;
@@ -1123,10 +1266,14 @@ constexpr int kLzTailChunk = 256;  // active nodes per claimed chunk of the incr
 // (N^2/4) (four consecutive jz at one (jx, jy)) of jx-plane t div (N^2/4) of
 // every stage; a stage covers K planes and a cell J = N / K stages.
 //
+// TMA: the streaming sources arrive by bulk copies (cp.async.bulk) that
+// thread 0 of the role issues into a ring of kLzStages slots, with a full
+// and an empty mbarrier per slot, instead of per-thread cp.async.
+//
 // lz_run runs the pipeline of one CTA over the groups grp0, grp0 + gstride,
 // ... (nmine of them) of one problem; the kernel k_lz gives CTA b the groups
 // b, b + gridDim.x, ...
-template <int G, int NV, bool SX>
+template <int G, int NV, bool SX, bool TMA = false>
 __device__ __forceinline__ void lz_run(const Geo &g, const LzArgs &a, char *smem_raw, int grp0, int gstride,
                                        int nmine)
 {
@@ -1173,6 +1320,14 @@ __device__ __forceinline__ void lz_run(const Geo &g, const LzArgs &a, char *smem
     }
     for (int m = t; m < M; m += kLzThreads) sact[m] = (uint16_t)a.act[m];
     for (int i = t; i < 2 * kLzMaxG * kLzRoleWarps * 32; i += kLzThreads) (&H.dpart[0][0][0][0])[i] = 0.f;
+    if (TMA && t == 0) {
+        for (int s = 0; s < kLzStages; ++s) {
+            lz_mbar_init(lz_saddr(&H.bar_full[s]), 1);
+            lz_mbar_init(lz_saddr(&H.bar_empty[s]), kLzRoleWarps);
+        }
+        H.tma_err = 0;
+        lz_mbar_init_fence();
+    }
     __syncthreads();
 
     // A streaming thread's quad.
@@ -1184,6 +1339,8 @@ __device__ __forceinline__ void lz_run(const Geo &g, const LzArgs &a, char *smem
     const float4 *hin4 = reinterpret_cast<const float4 *>(a.hin);
     float4 *hout4 = reinterpret_cast<float4 *>(a.hout);
     int fallback = 0;
+    LzTmaProd prod{0u, 0u, 0u};                   // thread 0: the bulk-copy ring's producer state
+    uint32_t fpar = 0u;                           // parity of each slot's next full phase
 
     // Iteration it: the streaming warps take this CTA's group it, the
     // collision warps its group it - 1.
@@ -1224,7 +1381,10 @@ __device__ __forceinline__ void lz_run(const Geo &g, const LzArgs &a, char *smem
                 pf.slot = ring0;
                 const int4 *cells = H.cell[buf];
 #pragma unroll
-                for (int kk = 0; kk < kLzStages - 1; ++kk) lz_prefetch(pf, qd, g, a, cells, hin_t, ncell);
+                for (int kk = 0; kk < kLzStages - 1; ++kk) {
+                    if (TMA) lz_prefetch_tma(pf, qd, g, a, cells, hin_t, ncell, H, prod);
+                    else lz_prefetch(pf, qd, g, a, cells, hin_t, ncell);
+                }
                 lz_role_bar(1);
                 // Correction tables of the group's cells: ca(jx) = mu_0 + mu_x
                 // v_x + mu_4 v_x^2 of the own cell, the upwind x cell (right for
@@ -1247,8 +1407,13 @@ __device__ __forceinline__ void lz_run(const Geo &g, const LzArgs &a, char *smem
 
                 // ---- streaming with the deferred correction applied to its sources
                 uint32_t cslot = ring0;           // slots of the stage being used
+                int cidx = 0;                     // and their index
 #pragma unroll 1
                 for (int k = 0; k < ncell; ++k) {
+                    // A cell at a wall had ghost values written into its slots
+                    // by the threads (generic proxy) before later bulk copies.
+                    const int4 cek = cells[k];
+                    const bool wallk = TMA && (cek.y == 0 || cek.y == g.nx - 1 || cek.z == 0 || cek.z == g.ny - 1);
                     LzAcc ac;
 #pragma unroll
                     for (int p = 0; p < 2; ++p)
@@ -1271,13 +1436,32 @@ __device__ __forceinline__ void lz_run(const Geo &g, const LzArgs &a, char *smem
                         if (st == Jh) lz_bd(H.mus[k][2], H.v, jy, qz, ac.bdx);   // the left cell now
                         // The slots read last stage take the stage kLzStages - 1
                         // ahead; then this stage's copies have landed.
-                        lz_prefetch(pf, qd, g, a, cells, hin_t, ncell);
-                        lz_cp_wait_stage();
+                        if (TMA) {
+                            lz_prefetch_tma(pf, qd, g, a, cells, hin_t, ncell, H, prod);
+                            lz_ring_wait(lz_saddr(&H.bar_full[cidx]), fpar >> cidx & 1u, H.tma_err);
+                            fpar ^= 1u << cidx;
+                        } else {
+                            lz_prefetch(pf, qd, g, a, cells, hin_t, ncell);
+                            lz_cp_wait_stage();
+                        }
                         if (streams)
                             lz_stream_stage<G, SX>(cslot, jx, j0, k, H, tcx, tcy, ac, dst, smask, swpre, Af,
                                                    eps2, one2, nay2k, fx2);
+                        if (TMA) {
+                            // The warp has read the slot: release it to the producer.
+                            if (wallk) lz_fence_proxy_async();
+                            __syncwarp();
+                            if (lane == 0) lz_mbar_arrive(lz_saddr(&H.bar_empty[cidx]));
+                        }
                         cslot += kLzSlotStride;
-                        if (cslot == qd.ring_end) cslot = ring0;
+                        if (TMA) {
+                            if (++cidx == kLzStages) {
+                                cidx = 0;
+                                cslot = ring0;
+                            }
+                        } else if (cslot == qd.ring_end) {
+                            cslot = ring0;
+                        }
                         jx += P4;
                         j0 += 4 * S;
                         dst += S;
@@ -1304,7 +1488,7 @@ __device__ __forceinline__ void lz_run(const Geo &g, const LzArgs &a, char *smem
                     }
                     H.fpart[it % 3][k][warp][lane] = lz_warp_reduce_scatter(Msum);
                 }
-                lz_cp_wait_all();
+                if (!TMA) lz_cp_wait_all();
             }
             if (clk && t == 0) a.clk[it * kClkPhases + 1] = clock64();
             // One warp per cell of group it - 2: totals over the warps, then the
@@ -1509,15 +1693,23 @@ __device__ __forceinline__ void lz_run(const Geo &g, const LzArgs &a, char *smem
         __syncthreads();
     }
     if (fallback && a.stats) atomicAdd(a.stats + 3, (unsigned long long)fallback);
+    if (TMA && t == 0 && H.tma_err) {
+        // A wait gave up: report it, and wait (bounded) for the last copy
+        // issued into each slot before the CTA leaves (after the first
+        // timeout nothing more was issued).
+        if (a.err) atomicOr(a.err, 1ull);
+        for (int s = 0; s < kLzStages; ++s)
+            if (prod.pending >> s & 1u) lz_mbar_wait(lz_saddr(&H.bar_full[s]), (prod.ipar >> s & 1u) ^ 1u);
+    }
 }
 
-template <int G, int NV, bool SX>
+template <int G, int NV, bool SX, bool TMA = false>
 __global__ void __launch_bounds__(kLzThreads, 1) k_lz(Geo g, LzArgs a)
 {
     extern __shared__ __align__(16) char smem_raw[];
     const int ngroups = (g.nr + G - 1) / G;
     const int nmine = blockIdx.x < ngroups ? (ngroups - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    lz_run<G, NV, SX>(g, a, smem_raw, blockIdx.x, gridDim.x, nmine);
+    lz_run<G, NV, SX, TMA>(g, a, smem_raw, blockIdx.x, gridDim.x, nmine);
 }
 
 }  // namespace bzk

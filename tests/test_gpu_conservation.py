@@ -37,19 +37,22 @@ def _v32(nxy=6, **kw):
                            kn=0.05 * 256 / nxy, **kw)
 
 
-@pytest.fixture(params=["auto", "ordered", "early_tail", "cell4", "generic"])
+@pytest.fixture(params=["auto", "ordered", "early_tail", "tma", "cell4", "generic"])
 def kernel(request, monkeypatch):
     """The active-node kernel (the benchmark's), with the joint term order
     forced on, with the increment sums started early by the collision warps
     (below 32^3 velocities: the 32^3 kernel always sums after a barrier);
-    the 4-node-vector kernel; the generic kernel."""
+    with the streaming sources brought in by bulk copies (TMA); the
+    4-node-vector kernel; the generic kernel."""
     for k in ("BZ_KERNEL", "BZ_LAZY_ORDER", "BZ_LAZY_NOORDER", "BZ_LAZY_ORDER_CHUNK",
-              "BZ_SOLVE_FALLBACK", "BZ_LAZY_EARLY_TAIL"):
+              "BZ_SOLVE_FALLBACK", "BZ_LAZY_EARLY_TAIL", "BZ_LAZY_TMA"):
         monkeypatch.delenv(k, raising=False)
     if request.param == "ordered":
         monkeypatch.setenv("BZ_LAZY_ORDER", "1")
     elif request.param == "early_tail":
         monkeypatch.setenv("BZ_LAZY_EARLY_TAIL", "1")
+    elif request.param == "tma":
+        monkeypatch.setenv("BZ_LAZY_TMA", "1")
     elif request.param in ("cell4", "generic"):
         monkeypatch.setenv("BZ_KERNEL", request.param)
     return request.param
@@ -74,7 +77,7 @@ def test_collision_step_conserves(kernel, nv):
     else:
         p = workloads.small(nx=6, ny=5, nv=nv, vmax=4.5, nt=10000, seed=4, kn=0.8, eps=0.1)
     cav, o, h0 = make(p, seed=9)
-    if kernel in ("auto", "ordered", "early_tail"):
+    if kernel in ("auto", "ordered", "early_tail", "tma"):
         assert cav.get_info().kernel_variant == 2
     wpsi = invariants(o)
     h = cav.get_state()[0].clone()

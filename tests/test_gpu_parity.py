@@ -121,8 +121,8 @@ def test_collide_matches_oracle(p, kernel):
     assert np.allclose(mom_g, mom_o, rtol=1e-4, atol=1e-6 * (1 + np.abs(mom_o).max()))
 
 
-@pytest.fixture(params=["auto", "ordered", "ordered_g2", "unordered", "joint_tail", "overflow", "cell4",
-                        "t512", "generic"])
+@pytest.fixture(params=["auto", "ordered", "ordered_g2", "unordered", "joint_tail", "overflow", "tma",
+                        "tma_ordered", "cell4", "t512", "generic"])
 def kernel(request, monkeypatch):
     """Run a test with the library's own choice of per-cell kernel (the FP32
     active-node kernel with deferred correction where it applies); with that
@@ -132,11 +132,17 @@ def kernel(request, monkeypatch):
     early by the collision warps (the default below 32^3 velocities); with
     that kernel's compact arrays capped below the step's
     active-node count (every step then takes the k_cell4 fallback on the
-    device); with the FP32 4-node-vector kernel (BZ_KERNEL=cell4) in its
+    device); with the streaming sources brought in by bulk copies (TMA) on
+    mbarriers, with and without the term order; with the FP32 4-node-vector kernel (BZ_KERNEL=cell4) in its
     1024- and 512-thread shapes; and with the generic kernel."""
     for k in ("BZ_KERNEL", "BZ_CELL_THREADS", "BZ_LAZY_MCAP", "BZ_LAZY_ORDER", "BZ_LAZY_NOORDER",
-              "BZ_LAZY_ORDER_CHUNK", "BZ_LAZY_G", "BZ_LAZY_EARLY_TAIL"):
+              "BZ_LAZY_ORDER_CHUNK", "BZ_LAZY_G", "BZ_LAZY_EARLY_TAIL", "BZ_LAZY_TMA"):
         monkeypatch.delenv(k, raising=False)
+    if request.param in ("tma", "tma_ordered"):
+        monkeypatch.setenv("BZ_LAZY_TMA", "1")
+    if request.param == "tma_ordered":
+        monkeypatch.setenv("BZ_LAZY_ORDER", "1")
+        monkeypatch.setenv("BZ_LAZY_ORDER_CHUNK", "16")
     if request.param == "joint_tail":
         monkeypatch.setenv("BZ_LAZY_EARLY_TAIL", "0")
     if request.param == "ordered":
@@ -258,10 +264,11 @@ def test_200_steps_fp32_v24():
         assert np.max(np.abs(mom_g[:, k] - mom_o[:, k])) <= 1e-4 * rng_, k
 
 
-@pytest.mark.parametrize("nv,vmax,nt,nxy,kn,order", [(32, 5.0, 20000, 12, 0.05 * 256 / 12, "1"),
-                                                      (24, 4.5, 10000, 8, 0.1 * 64 / 8, None)],
-                         ids=["v32_ordered", "v24"])
-def test_200_steps_warm_start_hot_path(monkeypatch, nv, vmax, nt, nxy, kn, order):
+@pytest.mark.parametrize("nv,vmax,nt,nxy,kn,order,tma", [(32, 5.0, 20000, 12, 0.05 * 256 / 12, "1", "0"),
+                                                          (32, 5.0, 20000, 12, 0.05 * 256 / 12, "1", "1"),
+                                                          (24, 4.5, 10000, 8, 0.1 * 64 / 8, None, "0")],
+                         ids=["v32_ordered", "v32_ordered_tma", "v24"])
+def test_200_steps_warm_start_hot_path(monkeypatch, nv, vmax, nt, nxy, kn, order, tma):
     """The benchmark's path (FP32 active-node kernel with deferred correction;
     at 32^3 with the joint bank-aware term order forced on) run for 200 steps
     from a seeded warm state, so the collision integral is non-zero from the
@@ -270,6 +277,7 @@ def test_200_steps_warm_start_hot_path(monkeypatch, nv, vmax, nt, nxy, kn, order
     have the size of the 256^2 (32^3) and 64^2 (24^3) cavities."""
     if order:
         monkeypatch.setenv("BZ_LAZY_ORDER", order)
+    monkeypatch.setenv("BZ_LAZY_TMA", tma)
     p = workloads.small(nx=nxy, ny=nxy, nv=nv, vmax=vmax, nt=nt, seed=3, kn=kn, lid_u0=0.0,
                         lid_amp=0.05, lid_period=50.0)
     cav, o, h0 = make(p, seed=7)
