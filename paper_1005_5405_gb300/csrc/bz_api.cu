@@ -368,9 +368,10 @@ double lz_monomial(int k, double x, double y, double z)
 }
 
 // Velocity axes with a kernel specialised on their length (the others run
-// the kernel that reads it at run time); stretched grids take the run-time
-// length with per-cell Courant factors.
-int lz_nv_key(const bz_handle *H) { return H->stretched ? -1 : (H->g.nv == 32 || H->g.nv == 20 ? H->g.nv : 0); }
+// the kernel that reads it at run time); stretched grids (per-cell Courant
+// factors) have their own instances, specialised for 20 nodes per axis (the
+// paper's stretched cavities) and run-time lengths otherwise.
+int lz_nv_key(const bz_handle *H) { return H->stretched ? (H->g.nv == 20 ? -20 : -1) : (H->g.nv == 32 || H->g.nv == 20 ? H->g.nv : 0); }
 
 template <int G, int NV, bool SX, bool TMA = false>
 bz_status setup_lz_one(bz_handle *H, size_t smem, int *occ)
@@ -390,6 +391,7 @@ bz_status setup_lz_kernel(bz_handle *H, size_t smem, int *occ)
     case 32: return setup_lz_one<G, 32, false>(H, smem, occ);
     case 20: return setup_lz_one<G, 20, false>(H, smem, occ);
     case -1: return setup_lz_one<G, 0, true>(H, smem, occ);
+    case -20: return setup_lz_one<G, 20, true>(H, smem, occ);
     default: return setup_lz_one<G, 0, false>(H, smem, occ);
     }
 }
@@ -408,6 +410,7 @@ void launch_lz_kernel(bz_handle *H, const bzk::LzArgs &a, cudaStream_t s)
     case 32: bzk::k_lz<G, 32, false><<<H->lz_grid, H->lz_T, H->lz_smem, s>>>(H->g, a); break;
     case 20: bzk::k_lz<G, 20, false><<<H->lz_grid, H->lz_T, H->lz_smem, s>>>(H->g, a); break;
     case -1: bzk::k_lz<G, 0, true><<<H->lz_grid, H->lz_T, H->lz_smem, s>>>(H->g, a); break;
+    case -20: bzk::k_lz<G, 20, true><<<H->lz_grid, H->lz_T, H->lz_smem, s>>>(H->g, a); break;
     default: bzk::k_lz<G, 0, false><<<H->lz_grid, H->lz_T, H->lz_smem, s>>>(H->g, a); break;
     }
 }
