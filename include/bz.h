@@ -188,7 +188,11 @@ bz_status bz_get_info(const bz_handle *h, bz_info *out);
  * launches issued; on the active-node path (bz_info.kernel_variant 2) [5]
  * steps whose active velocity nodes exceeded the kernel's compact arrays (they
  * ran the fallback kernel), [6] active nodes of the latest step, [7] the
- * compact arrays' capacity; otherwise [5..7] are 0.  Synchronises the device. */
+ * compact arrays' capacity; otherwise [5..7] are 0.  Synchronises the device.
+ * Returns BZ_ETIMEOUT (out filled all the same) when a bounded device wait
+ * of the active-node kernel gave up since the last call (only its optional
+ * bulk-copy streaming ring waits on the device; the steps concerned are
+ * invalid); the flag is then cleared. */
 bz_status bz_stats(bz_handle *h, int64_t out[8]);
 
 /* The Monte Carlo sample set of step `step` (Sec. 4.2, Algorithm 2) as the
@@ -241,11 +245,15 @@ bz_status bz_philox(uint32_t k0, uint32_t k1, const uint32_t *ctr, int64_t n, ui
 /* ---------------------------------------------------------------------
  * Batches: many independent cavity instances (each with its own grids, Kn,
  * lid, sample count and Philox key) advanced together, every step one CUDA
- * graph launch.  Two schedules: persistent kernels (one launch per kernel
+ * graph launch.  Three schedules: persistent kernels (one launch per kernel
  * class and step over the cells of all instances, the FP32 4-node-vector
- * per-cell kernel) or fan-out (every instance's own active-node step, the
- * instances spread over up to 8 concurrent graph branches); bz_batch_tune
- * chooses.  Every instance must be FP32 with nv a multiple of 4 and >= 12,
+ * per-cell kernel); fan-out (every instance's own active-node step, the
+ * instances spread over up to 8 concurrent graph branches); persistent
+ * active-node kernels (one launch per kernel class over all instances, the
+ * active-node kernel claiming (instance, group of four cells) segments from
+ * a work list, one launch per velocity-grid size; available when every
+ * instance runs the active-node path with four cells per group).
+ * bz_batch_tune chooses.  Every instance must be FP32 with nv a multiple of 4 and >= 12,
  * at most 32768 samples per step, the shared sample set and uniform grids
  * (BZ_EUNSUPPORTED otherwise).  The batch owns its instances; instance i is
  * addressed by its index.  The state of an instance at step n lives in one of
@@ -265,14 +273,16 @@ bz_status bz_batch_moments(bz_batch *b, int32_t i, double *out, void *stream);
 /* Autotuner: times `trial_steps` recomputations of the current step (the
  * state is not advanced) for every schedule (persistent kernels: threads per
  * CTA 512 or 1024, CTAs per SM, cell-strip width 4, 8 or 16; fan-out: 1, 2, 4
- * or 8 branches, as a graph), keeps the fastest and returns its index in
- * *choice (nullable) and the milliseconds per step of every schedule in
- * ms[0..ncand) (nullable, up to 16 entries). */
+ * or 8 branches, as a graph; the persistent active-node schedule where
+ * available), keeps the fastest and returns its index in *choice (nullable)
+ * and the milliseconds per step of every schedule in ms[0..ncand) (nullable,
+ * up to 16 entries). */
 bz_status bz_batch_tune(bz_batch *b, int32_t trial_steps, void *stream, int32_t *choice,
                         double *ms, int32_t *ncand);
 /* Schedule in use: out[0..2] the persistent kernels' threads per CTA,
- * persistent CTAs and strip width; out[3] the fan-out branches (0 when the
- * persistent kernels run). */
+ * persistent CTAs and strip width; out[3] the fan-out branches, 0 when the
+ * persistent 4-node-vector kernels run and -1 when the persistent
+ * active-node kernels run. */
 bz_status bz_batch_schedule(const bz_batch *b, int32_t out[4]);
 
 /* Per-kernel timing with CUDA events recorded on the launching stream around

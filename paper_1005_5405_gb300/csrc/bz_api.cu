@@ -1592,6 +1592,11 @@ struct bz_batch {
     std::vector<LzClass> lz_classes;        // the segments of each velocity grid
     cudaStream_t lz_side = nullptr;         // the sample plans run here, beside the walls
     cudaEvent_t lz_fork = nullptr, lz_join = nullptr;
+    // The velocity grids' kernels after the first run on streams of their own,
+    // so that each starts on the SMs the previous one leaves.
+    std::vector<cudaStream_t> lz_cls_s;
+    std::vector<cudaEvent_t> lz_cls_done;
+    cudaEvent_t lz_go = nullptr;
     cudaGraphExec_t graph2 = nullptr;
 };
 
@@ -1614,6 +1619,9 @@ void batch_free(bz_batch *B)
     for (void *p : lzp)
         if (p) cudaFree(p);
     if (B->lz_side) cudaStreamDestroy(B->lz_side);
+    for (cudaStream_t x : B->lz_cls_s) cudaStreamDestroy(x);
+    for (cudaEvent_t x : B->lz_cls_done) cudaEventDestroy(x);
+    if (B->lz_go) cudaEventDestroy(B->lz_go);
     if (B->lz_fork) cudaEventDestroy(B->lz_fork);
     if (B->lz_join) cudaEventDestroy(B->lz_join);
     for (auto &g : B->fgraph)
@@ -1831,17 +1839,23 @@ bz_status lz_batch_launch(bz_batch *B, cudaStream_t s, bool advance)
     bzk::kbl_walls<<<B->tot_faces, 256, 0, s>>>(B->d_lzinst, B->d_face_pre, B->n);
     BZ_CUDA(cudaMemsetAsync(B->d_next, 0, sizeof(int) * B->lz_classes.size(), s));
     BZ_CUDA(cudaStreamWaitEvent(s, B->lz_join, 0));
-    for (size_t k = 0; k < B->lz_classes.size(); ++k) {
+    const size_t nc = B->lz_classes.size();
+    if (nc > 1) BZ_CUDA(cudaEventRecord(B->lz_go, s));
+    for (size_t k = 0; k < nc; ++k) {
         const auto &c = B->lz_classes[k];
         const int4 *sg4 = B->d_segs + c.seg0;
         int *nx = B->d_next + k;
+        const cudaStream_t sk = k == 0 ? s : B->lz_cls_s[k - 1];
+        if (k > 0) BZ_CUDA(cudaStreamWaitEvent(sk, B->lz_go, 0));
         switch (c.nv) {
-        case 24: bzk::kbl_lz<24><<<B->nsm, bzk::kLzThreads, c.smem, s>>>(B->d_lzinst, sg4, c.nseg, nx); break;
-        case 20: bzk::kbl_lz<20><<<B->nsm, bzk::kLzThreads, c.smem, s>>>(B->d_lzinst, sg4, c.nseg, nx); break;
-        case 16: bzk::kbl_lz<16><<<B->nsm, bzk::kLzThreads, c.smem, s>>>(B->d_lzinst, sg4, c.nseg, nx); break;
-        default: bzk::kbl_lz<0><<<B->nsm, bzk::kLzThreads, c.smem, s>>>(B->d_lzinst, sg4, c.nseg, nx); break;
+        case 24: bzk::kbl_lz<24><<<B->nsm, bzk::kLzThreads, c.smem, sk>>>(B->d_lzinst, sg4, c.nseg, nx); break;
+        case 20: bzk::kbl_lz<20><<<B->nsm, bzk::kLzThreads, c.smem, sk>>>(B->d_lzinst, sg4, c.nseg, nx); break;
+        case 16: bzk::kbl_lz<16><<<B->nsm, bzk::kLzThreads, c.smem, sk>>>(B->d_lzinst, sg4, c.nseg, nx); break;
+        default: bzk::kbl_lz<0><<<B->nsm, bzk::kLzThreads, c.smem, sk>>>(B->d_lzinst, sg4, c.nseg, nx); break;
         }
+        if (k > 0) BZ_CUDA(cudaEventRecord(B->lz_cls_done[k - 1], sk));
     }
+    for (size_t k = 1; k < nc; ++k) BZ_CUDA(cudaStreamWaitEvent(s, B->lz_cls_done[k - 1], 0));
     // The 4-node-vector fallback of instances that overflowed (no work otherwise).
     bzk::kbl_fb_plan<<<sg, pb, 0, s>>>(B->d_lzinst, B->d_samp_pre, B->n);
     bzk::kbl_fb_scan<<<B->n, 1024, 0, s>>>(B->d_lzinst, 512);
@@ -1955,6 +1969,15 @@ bz_status lz_batch_prepare(bz_batch *B)
         BZ_CUDA(cudaStreamCreateWithPriority(&B->lz_side, cudaStreamNonBlocking, greatest));
         BZ_CUDA(cudaEventCreateWithFlags(&B->lz_fork, cudaEventDisableTiming));
         BZ_CUDA(cudaEventCreateWithFlags(&B->lz_join, cudaEventDisableTiming));
+        BZ_CUDA(cudaEventCreateWithFlags(&B->lz_go, cudaEventDisableTiming));
+        for (size_t k = 1; k < B->lz_classes.size(); ++k) {
+            cudaStream_t x = nullptr;
+            cudaEvent_t e = nullptr;
+            BZ_CUDA(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+            B->lz_cls_s.push_back(x);
+            BZ_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            B->lz_cls_done.push_back(e);
+        }
     }
     B->nseg = (int)segs.size();
     B->lz_smem = smem;
