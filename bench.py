@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--config", default="cavity256_v32")
     ap.add_argument("--repeats", type=int, default=5,
                     help="timed blocks of --steps steps (adjoint128_v20, batch64)")
+    ap.add_argument("--phase-trace", action="store_true",
+                    help="print the per-cell kernel's phase trace (bz_phase_clocks) of one "
+                         "step of --config after --warmup steps, instead of timing")
     return ap.parse_args()
 
 
@@ -617,9 +620,34 @@ def workloads_state(p, torch):
     return workloads.warm_state_device(p, seed=7, torch=torch)
 
 
+def run_phase_trace(args):
+    """SM clock stamps at the phase points of the first work items of CTA 0
+    (bz_phase_clocks), relative to each item's start, for one step of a
+    single-cavity config from the seeded warm state."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1005_5405_gb300 import binding
+    torch.cuda.set_device(0)
+    p = problem(args.config)
+    cav = binding.Cavity(p)
+    cav.set_state(workloads_state(p, torch), step=0)
+    cav.step(args.warmup)
+    cav.profile(2)
+    cav.step(1)
+    torch.cuda.synchronize()
+    pc = cav.phase_clocks()
+    cav.profile(0)
+    rows = [[int(x - r[0]) if x else -1 for x in r] for r in pc]
+    print(json.dumps({"config": p.name, "kernel_variant": cav.get_info().kernel_variant,
+                      "cycles_from_item_start": rows}), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.phase_trace:
+        run_phase_trace(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.config == "batch64":
         run_batch(args)
