@@ -333,12 +333,11 @@ bz_status bz_phase_clocks(bz_handle *h, int64_t *out, int32_t n);
  * BZ_NOALLOC_MAX_PAIRS (larger values return BZ_EINVAL), and the velocity slab
  * and the per-sample products must fit one block's shared memory (else
  * BZ_EUNSUPPORTED).  The first call on a device looks up the device address of
- * that array, with the device current, and should come before any stream
- * capture.  Every call on a device uses the same array, which keeps the last
- * call's contents: calls on one device that overlap in time (on different
- * streams) race and give wrong results, so serialise them; calls on different
- * devices use different arrays.  Asynchronous on `stream`; errors as
- * elsewhere. */
+ * that array, with that device current.  Every call on a device uses the same
+ * array, which keeps the last call's contents: calls on one device that
+ * overlap in time (on different streams) race and give wrong results, so
+ * serialise them; calls on different devices use different arrays.
+ * Asynchronous on `stream`; errors as elsewhere. */
 #define BZ_NOALLOC_MAX_PAIRS 65536
 #define BZ_NOALLOC_SCRATCH_BYTES ((2u << 20) + 4096u)
 bz_status bz_collide_noalloc(const bz_space *space, const bz_vel *vel, const bz_params *params,
