@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "phase-space node updates/s (256^2 x 32^3 FP32 cavity step)"
 UNIT = "node-updates/s"
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0      # GB300 HBM3e, nominal (context beside the measured peak)
 
 
 def parse():
@@ -360,13 +361,17 @@ def run_ours(args):
                    "l2": f"state ({nodes * esz / 1e9:.2f} GB/buffer) exceeds L2 (129 MB); no flush needed",
                    "parallelism": f"replicas x{world}"},
         "mc_pairs_per_s": pairs,
+        # the step's N_t samples drawn and planned (sample set, active-node plan,
+        # term order) per second of those kernels
+        "sampled_pairs_per_s": p.nt / (kms[1] / max(1, kn[1]) / 1e3) if kms[1] > 0 else None,
         "kernels_ms_per_step": {"walls": kms[0] / max(1, kn[0]), "sampling": kms[1] / max(1, kn[1]),
                                 "cell": cell_ms},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(p.nr, variant),
                      "kernel": CELL_KERNELS.get(variant, ("?", None, ()))[0],
                      "algorithmic_bytes": alg_bytes, "peak_source": peak_src,
-                     "step_frac": (step_bytes / (ms_max / args.steps / 1e3) / 1e9) / peak},
+                     "step_frac": (step_bytes / (ms_max / args.steps / 1e3) / 1e9) / peak,
+                     "frac_of_nominal": achieved / NOMINAL_HBM_GBS},
         "streaming": {
             "node_updates_per_s": world * nodes / (stream_step_ms / 1e3),
             "ms_per_step": stream_step_ms, "kernel_ms": stream_kernel_ms,
