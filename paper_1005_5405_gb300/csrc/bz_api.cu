@@ -10,6 +10,7 @@
 #include "bz_cell4.cuh"
 #include "bz_batch.cuh"
 #include "bz_lazy.cuh"
+#include "bz_ahead.cuh"
 
 #include <cuda_runtime.h>
 
@@ -127,6 +128,11 @@ struct bz_handle {
     int lz_mcap = 0, lz_G = 0, lz_T = 0, lz_grid = 0, lz_mprobe = 0;
     int lz_cmax = 0, lz_order_tpb = 0;     // bank-aware ordering of the term runs (1: on)
     bool lz_tma = false;                   // streaming sources by bulk copies (G = 4 only)
+    // Plans built ahead (bz_ahead.cuh): K slots, covering steps [ahead_lo, ahead_hi).
+    int ahead_K = 0;
+    bzk::AheadPlans ahead{};
+    int64_t ahead_lo = 0, ahead_hi = 0;
+    int ahead_chunk = 0;                   // positions per chunk of their term order
     int lz_chunk = 0;                      // positions per chunk of the ordering
     cudaStream_t lz_side = nullptr;        // the sample plan runs here, beside the walls
     cudaEvent_t lz_fork = nullptr, lz_join = nullptr, lz_mid = nullptr;
@@ -510,9 +516,14 @@ bz_status configure_lazy(bz_handle *H)
         // The order saves shared-memory replays on every CTA iteration (about
         // 3 us per iteration at 320 positions on a GB300) and costs a chain of
         // about 2 x 64 dependent decisions (about 50 us): it runs when the
-        // iterations per CTA times the run length reach 6144.
+        // iterations per CTA times the run length reach 6144.  With the plans
+        // built ahead (below) it runs over whole runs, which saves about 2.5%
+        // of the kernel and costs about 63 us of GPU time per step at 2x10^4
+        // samples: it runs from 15000 on.
         const int64_t iters = ((int64_t)(g.nr + H->lz_G - 1) / H->lz_G + H->lz_grid - 1) / H->lz_grid;
-        H->lz_order_tpb = H->lz_chunk <= 32767 && iters * H->lz_cmax >= 6144 &&
+        const char *ka = getenv("BZ_LAZY_AHEAD");
+        const int64_t order_min = ka && atoi(ka) == 0 ? 6144 : 15000;
+        H->lz_order_tpb = H->lz_chunk <= 32767 && iters * H->lz_cmax >= order_min &&
                           bzk::lz_order_smem(H->lz_chunk, nb) <= (size_t)H->smem_optin ? 1 : 0;
         if (const char *o = getenv("BZ_LAZY_ORDER")) H->lz_order_tpb = atoi(o) != 0 && H->lz_chunk <= 32767 &&
                           bzk::lz_order_smem(H->lz_chunk, nb) <= (size_t)H->smem_optin ? 1 : 0;
@@ -526,6 +537,46 @@ bz_status configure_lazy(bz_handle *H)
     BZ_TRY(dalloc(&H->lz_dest0, sizeof(int) * (size_t)bzk::kLzRoleT));
     BZ_TRY(dalloc(&H->lz_rec, sizeof(uint2) * ((size_t)4 * nt + (size_t)8 * bzk::kLzRoleT)));
     BZ_CUDA(cudaMemset(H->lz_count, 0, sizeof(int) * (size_t)nvt));
+    // Plans of 32 steps built ahead at a time (BZ_LAZY_AHEAD=K sets the
+    // count, 0 builds each step's plan in the step), their term order over
+    // whole runs.
+    H->ahead_K = 32;
+    if (const char *kk = getenv("BZ_LAZY_AHEAD")) H->ahead_K = std::max(0, std::min(256, atoi(kk)));
+    if (H->ahead_K > 0) {
+        bzk::AheadPlans &A = H->ahead;
+        const int K = H->ahead_K;
+        A.K = K;
+        A.nt = nt;
+        A.nvt = nvt;
+        A.mcap = mcap;
+        A.osh = H->lz_G == 4 ? 4 : 3;
+        A.recn = (int64_t)4 * nt + (int64_t)8 * bzk::kLzRoleT;
+        const size_t k = (size_t)K;
+        BZ_TRY(dalloc(&A.idx, sizeof(int4) * k * nt));
+        BZ_TRY(dalloc(&A.pa, sizeof(bzk::PlanA<float, int>) * k * nt));
+        BZ_TRY(dalloc(&A.qc, sizeof(ushort4) * k * nt));
+        BZ_TRY(dalloc(&A.flag, sizeof(int) * k * nvt));
+        BZ_TRY(dalloc(&A.cidx, sizeof(int) * k * nvt));
+        BZ_TRY(dalloc(&A.act, sizeof(int) * k * nvt));
+        BZ_TRY(dalloc(&A.mask, sizeof(uint32_t) * k * (nvt / 32)));
+        BZ_TRY(dalloc(&A.wpre, sizeof(int) * k * (nvt / 32)));
+        BZ_TRY(dalloc(&A.meta, sizeof(int) * k * bzk::kLzMetaSize));
+        BZ_TRY(dalloc(&A.count, sizeof(int) * k * nvt));
+        BZ_TRY(dalloc(&A.cursor, sizeof(int) * k * nvt));
+        BZ_TRY(dalloc(&A.rowend, sizeof(int) * k * nvt));
+        BZ_TRY(dalloc(&A.dest0, sizeof(int) * k * bzk::kLzRoleT));
+        BZ_TRY(dalloc(&A.rec, sizeof(uint2) * k * (size_t)A.recn));
+        BZ_TRY(dalloc(&A.cnt, sizeof(unsigned long long) * 2 * k));
+        BZ_CUDA(cudaMemset(A.flag, 0, sizeof(int) * k * nvt));
+        BZ_CUDA(cudaMemset(A.count, 0, sizeof(int) * k * nvt));
+        H->ahead_lo = H->ahead_hi = 0;
+        // Built ahead, the order's chain costs little per step: whole runs.
+        const int nb = H->lz_G == 4 ? 8 : 16;
+        H->ahead_chunk = H->lz_cmax;
+        if (const char *c = getenv("BZ_LAZY_ORDER_CHUNK")) H->ahead_chunk = H->lz_chunk;
+        if (H->lz_order_tpb > 0 && bzk::lz_order_smem(H->ahead_chunk, nb) > (size_t)H->smem_optin)
+            H->ahead_chunk = H->lz_chunk;
+    }
     // Equilibrium sums of the 30 monomials (the moments of h^{n+1} need them).
     std::vector<double> axv(N), axA(N);
     BZ_CUDA(cudaMemcpy(axv.data(), g.axv, sizeof(double) * N, cudaMemcpyDeviceToHost));
@@ -562,7 +613,48 @@ bz_status configure_lazy(bz_handle *H)
 // nostream: the relaxation alone (BZ_DO_COLLIDE), h~ = h; the walls still
 // run so that the ghost values the kernel reads (times a zero Courant
 // number) are those of the state.
-bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true, bool nostream = false)
+// The plans of steps [n, n + K) built ahead into the handle's K slots on
+// stream s, unless the slots already cover [n, n + cnt).  Never called while
+// a stream is being captured (the step graphs hold only k_ahead_take).
+bz_status ensure_plans(bz_handle *H, cudaStream_t s, int64_t n, int cnt)
+{
+    if (!H->lazy || H->ahead_K == 0) return BZ_OK;
+    if (n >= H->ahead_lo && n + cnt <= H->ahead_hi) return BZ_OK;
+    const bzk::AheadPlans &A = H->ahead;
+    const int K = H->ahead_K;
+    Geo gl = H->g;
+    gl.swz = 0;
+    ProfScope ps(H, 1, s);
+    BZ_CUDA(cudaMemsetAsync(A.cnt, 0, sizeof(unsigned long long) * 2 * K, s));
+    bzk::k_ahead_plan<<<dim3((A.nt + 63) / 64, K), 64, 0, s>>>(gl, A, n);
+    BZ_LAUNCHED(H);
+    bzk::k_ahead_scan<<<K, 1024, 0, s>>>(A, n);
+    BZ_LAUNCHED(H);
+    bzk::k_ahead_remap<<<dim3((A.nt + 255) / 256, K), 256, 0, s>>>(A, n);
+    BZ_LAUNCHED(H);
+    bzk::k_ahead_lscan<<<K, 1024, 0, s>>>(A, n);
+    BZ_LAUNCHED(H);
+    bzk::k_ahead_lfill<<<dim3((A.nt + 255) / 256, K), 256, 0, s>>>(A, n);
+    BZ_LAUNCHED(H);
+    if (H->lz_order_tpb > 0) {
+        const int ch = H->ahead_chunk, nch = (H->lz_cmax + ch - 1) / ch, z0 = (int)(n % K);
+        if (H->lz_G == 4)
+            bzk::k_lz_order<8><<<dim3(bzk::kLzRoleT / 8, nch, K), 32, bzk::lz_order_smem(ch, 8), s>>>(
+                bzk::kLzRoleT, H->lz_cmax, ch, A.meta, A.rec, K, z0, A.recn);
+        else
+            bzk::k_lz_order<16><<<dim3(bzk::kLzRoleT / 16, nch, K), 32, bzk::lz_order_smem(ch, 16), s>>>(
+                bzk::kLzRoleT, H->lz_cmax, ch, A.meta, A.rec, K, z0, A.recn);
+        BZ_LAUNCHED(H);
+    }
+    H->ahead_lo = n;
+    H->ahead_hi = n + K;
+    return BZ_OK;
+}
+
+// ahead: the step's plan is copied from the slots built ahead (ensure_plans
+// covered it) instead of being built by the per-step chain.
+bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true, bool nostream = false,
+                      bool ahead = false)
 {
     const Geo &g = H->g;
     Geo gl = g;
@@ -573,7 +665,13 @@ bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true, bo
     BZ_CUDA(cudaEventRecord(H->lz_fork, s));
     BZ_CUDA(cudaStreamWaitEvent(H->lz_side, H->lz_fork, 0));
     const int pb = 256, pg = (g.nt + pb - 1) / pb;
-    {
+    if (ahead) {
+        ProfScope ps(H, 1, H->lz_side);
+        bzk::k_ahead_take<<<H->nsm, 256, 0, H->lz_side>>>(H->ahead, H->d_step, H->lz_idx, H->lz_pa, H->lz_meta,
+                                                           H->lz_mask, H->lz_wpre, H->lz_act, H->lz_rec,
+                                                           H->lz_dest0, H->stats);
+        BZ_LAUNCHED(H);
+    } else {
         const cudaStream_t sp = H->lz_side;
         ProfScope ps(H, 1, sp);
         // 64-thread blocks spread the FP64 sampling over every SM.
@@ -610,7 +708,7 @@ bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true, bo
         }
     }
     BZ_CUDA(cudaEventRecord(H->lz_join, H->lz_side));
-    if (H->lz_order_tpb > 0) BZ_CUDA(cudaStreamWaitEvent(s, H->lz_mid, 0));
+    if (!ahead && H->lz_order_tpb > 0) BZ_CUDA(cudaStreamWaitEvent(s, H->lz_mid, 0));
     {
         ProfScope ps(H, 0, s);
         bzk::k_walls<float><<<g.nfaces, 256, 0, s>>>(g, H->d_step, hin, (float *)H->ghost, H->nw,
@@ -699,9 +797,10 @@ bz_status launch_step(bz_handle *H, cudaStream_t s, bool fused, bool do_stream, 
     using V4 = typename bzk::Idx4<I>::type;
     using PA = bzk::PlanA<R, I>;
     if constexpr (sizeof(R) == 4) {
-        if (fused && H->lazy) return launch_lazy(H, s);
+        const bool ahead = H->ahead_K > 0;
+        if (fused && H->lazy) return launch_lazy(H, s, true, false, ahead);
         // The relaxation alone on the active-node kernel (no streaming).
-        if (!fused && do_collide && !do_stream && H->lazy) return launch_lazy(H, s, true, true);
+        if (!fused && do_collide && !do_stream && H->lazy) return launch_lazy(H, s, true, true, ahead);
     }
     // Every other path reads and writes corrected states.
     BZ_TRY(materialize_if_lazy(H, H->cur, s));
@@ -883,6 +982,11 @@ void release(bz_handle *H)
                   H->lz_act, H->lz_wpre, H->lz_meta, H->lz_count, H->lz_cursor, H->lz_rowend,
                   H->lz_dest0, H->lz_mask, H->lz_rec};
     for (void *p : lz)
+        if (p) cudaFree(p);
+    const bzk::AheadPlans &A = H->ahead;
+    void *ah[] = {A.idx, A.pa, A.qc, A.flag, A.cidx, A.act, A.mask, A.wpre, A.meta, A.count, A.cursor,
+                  A.rowend, A.dest0, A.rec, A.cnt};
+    for (void *p : ah)
         if (p) cudaFree(p);
     bz_adj_release(&H->adj);
 }
@@ -1236,6 +1340,7 @@ bz_status bz_step_ex(bz_handle *H, int32_t nsteps, uint32_t flags, void *stream)
         }
         if (!H->graph[H->cur]) BZ_TRY(capture_pair(H));
         for (; n + 1 < nsteps; n += 2) {
+            BZ_TRY(ensure_plans(H, s, H->step, 2));
             BZ_CUDA(cudaGraphLaunch(H->graph[H->cur], s));
             H->step += 2;
             H->launches += H->graph_launches;
@@ -1243,7 +1348,11 @@ bz_status bz_step_ex(bz_handle *H, int32_t nsteps, uint32_t flags, void *stream)
             if (H->lazy) H->lazy_buf[0] = H->lazy_buf[1] = true;
         }
     }
-    for (; n < nsteps; ++n) BZ_TRY(one_step(H, s, fused, ds, dc));
+    const bool planned = fused || (dc && !ds);   // the steps that run the active-node kernel
+    for (; n < nsteps; ++n) {
+        if (planned) BZ_TRY(ensure_plans(H, s, H->step, 1));
+        BZ_TRY(one_step(H, s, fused, ds, dc));
+    }
     return BZ_OK;
 }
 

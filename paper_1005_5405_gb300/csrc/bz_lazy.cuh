@@ -307,6 +307,9 @@ __global__ void k_lz_lfill(int nt, int T, int osh, const ushort4 *__restrict__ q
 // ordered independently (a segment that crosses a chunk's end is cut
 // there).  One warp per phase group and chunk: NB runs x 32 / NB lanes that
 // scan a run's choices.  Nothing happens if a run is longer than cmax.
+// Several plans at once: blockIdx.z selects plan slot (z0 + blockIdx.z) mod
+// zK, whose meta and records lie kLzMetaSize ints and rec_stride records
+// after those of slot 0.
 __host__ __device__ inline size_t lz_order_smem(int chunk, int nb)
 {
     // records (rows padded to an odd length), taken entries, segment ends,
@@ -318,8 +321,14 @@ __host__ __device__ inline size_t lz_order_smem(int chunk, int nb)
 
 template <int NB>
 __global__ void __launch_bounds__(32) k_lz_order(int T, int cmax, int chunk, const int *__restrict__ meta,
-                                                 uint2 *__restrict__ rec)
+                                                 uint2 *__restrict__ rec, int zK = 1, int z0 = 0,
+                                                 int64_t rec_stride = 0)
 {
+    {
+        const int zs = (z0 + (int)blockIdx.z) % zK;
+        meta += zs * kLzMetaSize;
+        rec += zs * rec_stride;
+    }
     static_assert(NB == 8 || NB == 16, "phase width");
     constexpr int H = 32 / NB;                       // lanes per run
     constexpr int OSH = NB == 8 ? 4 : 3;             // log2 of the entry size

@@ -497,3 +497,38 @@ def test_handles_of_different_sizes_coexist(monkeypatch, kernel_env):
         cav.step(1)
         h_o, _ = o.step(h0, 0)
         assert f_metric(o, state(cav), h_o) < 1e-5, p.nv
+
+
+@pytest.mark.parametrize("order", ["1", "0"])
+def test_plans_built_ahead_match_the_per_step_chain(monkeypatch, order):
+    """The sample plans built ahead in slots (BZ_LAZY_AHEAD=K, several steps
+    per launch) give the steps of the per-step chain (BZ_LAZY_AHEAD=0): the
+    same states to FP32 rounding (the term order runs over whole runs rather
+    than chunks), the same counters of out-of-box and near-face samples,
+    overflows and active nodes, across batch boundaries (K = 3), odd step
+    counts (graph pairs and single steps) and a jump of the step counter."""
+    for k in ("BZ_KERNEL", "BZ_LAZY_MCAP", "BZ_LAZY_ORDER", "BZ_LAZY_NOORDER", "BZ_LAZY_ORDER_CHUNK",
+              "BZ_LAZY_G", "BZ_LAZY_TMA"):
+        monkeypatch.delenv(k, raising=False)
+    monkeypatch.setenv("BZ_LAZY_ORDER" if order == "1" else "BZ_LAZY_NOORDER", "1")
+    p = workloads.small(nx=12, ny=12, nv=32, vmax=5.0, nt=20000, seed=3, kn=0.05 * 256 / 12,
+                        lid_u0=0.0, lid_amp=0.05, lid_period=50.0)
+    h0 = workloads.warm_state(p, seed=17).astype(np.float32)
+    o = oracle.Oracle(**p.kwargs())
+    runs = {}
+    for K in ("0", "3"):
+        monkeypatch.setenv("BZ_LAZY_AHEAD", K)
+        cav = binding.Cavity(p)
+        assert cav.get_info().kernel_variant == 2
+        cav.set_state(h0, step=0)
+        cav.step(5)
+        cav.step(2)
+        cav.step_ex(1, binding.BZ_DO_COLLIDE)
+        mid = state(cav)
+        cav.set_state(mid.astype(np.float32), step=100)
+        cav.step(4)
+        runs[K] = (state(cav), cav.stats())
+    (ha, sa), (hb, sb) = runs["0"], runs["3"]
+    assert f_metric(o, hb, ha) < 1e-6
+    assert sa[0] == sb[0] == 104
+    assert [sa[i] for i in (1, 2, 5, 6)] == [sb[i] for i in (1, 2, 5, 6)]
