@@ -126,10 +126,16 @@ bz_status prepare_fast(bz_adj_scratch *a, const bzk::Geo &g, int nsm, int optin)
                              sizeof(uint4) * ((size_t)2 * g.nt + bzk::kMaxThreads)};
     void **dst[7] = {&a->pidx16, &a->pa16, (void **)&a->sc_count, (void **)&a->sc_cursor,
                      (void **)&a->sc_meta, (void **)&a->sc_ent, (void **)&a->lrec};
+    void **dstb[7] = {&a->pidx16b, &a->pa16b, (void **)&a->sc_countb, (void **)&a->sc_cursorb,
+                      (void **)&a->sc_metab, (void **)&a->sc_entb, (void **)&a->lrecb};
     for (int k = 0; k < 7; ++k) {
         e = alloc_fault() ? cudaErrorMemoryAllocation : cudaMalloc(dst[k], bytes[k]);
+        if (e == cudaSuccess) e = cudaMalloc(dstb[k], bytes[k]);
         if (e != cudaSuccess) return cuda_err(e, "adjoint scratch allocation");
     }
+    e = cudaMalloc(&a->step2, sizeof(int64_t));
+    if (e != cudaSuccess) return cuda_err(e, "adjoint scratch allocation");
+    a->pre_step = a->last_step = -1;
     a->fast = true;
     a->threads = T;
     a->smem = smem;
@@ -138,6 +144,32 @@ bz_status prepare_fast(bz_adj_scratch *a, const bzk::Geo &g, int nsm, int optin)
     a->map[1] = K;
     a->map[2] = N / K;
     return BZ_OK;
+}
+
+// The fast path's plan of the step in *stepp into one plan set, on stream sp:
+// the 16-bit plan in the shared-memory order and the destination-sorted
+// forward and loss lists, as the forward step builds them (64-thread blocks
+// spread the FP64 sampling over every SM).
+cudaError_t fast_plan(const bzk::Geo &g, const int64_t *stepp, int threads, void *pidx16, void *pa16,
+                      int *sc_count, int *sc_cursor, int *sc_meta, uint32_t *sc_ent, uint4 *lrec,
+                      cudaStream_t sp, int *n)
+{
+    bzk::Geo gs = g;
+    gs.swz = 1;
+    const int pb = 256, pg = (g.nt + pb - 1) / pb;
+    const ushort4 *pi = (const ushort4 *)pidx16;
+    bzk::k_plan<float, uint16_t><<<(g.nt + 63) / 64, 64, 0, sp>>>(
+        gs, stepp, (ushort4 *)pidx16, (bzk::PlanA<float, uint16_t> *)pa16, nullptr, nullptr);
+    ++*n;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemsetAsync(sc_count, 0, sizeof(int) * 2 * g.nvt, sp);
+    if (e != cudaSuccess) return e;
+    bzk::k_adj_count2<<<pg, pb, 0, sp>>>(g.nt, g.nvt, pi, sc_count);
+    bzk::k_adj_scan2<<<2, 1024, 0, sp>>>(g.nvt, threads, sc_count, sc_cursor, sc_meta);
+    bzk::k_adj_fill2<<<pg, pb, 0, sp>>>(g.nt, g.nvt, threads, pi, (const bzk::PlanA<float, uint16_t> *)pa16,
+                                        sc_cursor, sc_meta, sc_ent, lrec);
+    *n += 3;
+    return cudaGetLastError();
 }
 
 template <typename R>
@@ -158,40 +190,23 @@ bz_status launch(bz_adj_scratch *a, const bzk::Geo &g0, int64_t step, const R *h
     bool fast = false;
     if constexpr (sizeof(R) == 4) fast = a->fast;
     // The fast path's plan depends on the step only: it runs on the side
-    // stream while the walls run (after everything before it on s).
+    // stream while the walls run (after everything before it on s), unless
+    // the previous call already built it there (then s waits for that).
     const cudaStream_t sp = fast ? a->side : s;
-    if (fast && e == cudaSuccess) e = cudaEventRecord(a->fork, s);
-    if (fast && e == cudaSuccess) e = cudaStreamWaitEvent(sp, a->fork, 0);
-    if (fast) {
-        // FP32 quad kernel: plan in the shared-memory order and the
-        // destination-sorted scatter list, as the forward step builds them
-        // (64-thread blocks spread the FP64 sampling over every SM).
-        bzk::Geo gs = g;
-        gs.swz = 1;
-        const ushort4 *pi = (const ushort4 *)a->pidx16;
-        if (e == cudaSuccess) {
-            bzk::k_plan<float, uint16_t><<<(g.nt + 63) / 64, 64, 0, sp>>>(
-                gs, a->step, (ushort4 *)a->pidx16, (bzk::PlanA<float, uint16_t> *)a->pa16,
-                nullptr, nullptr);
-            e = check();
-        }
-        // The forward list and the loss list of the transposed update.
-        if (e == cudaSuccess) e = cudaMemsetAsync(a->sc_count, 0, sizeof(int) * 2 * g.nvt, sp);
-        if (e == cudaSuccess) {
-            bzk::k_adj_count2<<<pg, pb, 0, sp>>>(g.nt, g.nvt, pi, a->sc_count);
-            e = check();
-        }
-        if (e == cudaSuccess) {
-            bzk::k_adj_scan2<<<2, 1024, 0, sp>>>(g.nvt, a->threads, a->sc_count, a->sc_cursor,
-                                                 a->sc_meta);
-            e = check();
-        }
-        if (e == cudaSuccess) {
-            bzk::k_adj_fill2<<<pg, pb, 0, sp>>>(g.nt, g.nvt, a->threads, pi,
-                                                (const bzk::PlanA<float, uint16_t> *)a->pa16,
-                                                a->sc_cursor, a->sc_meta, a->sc_ent, a->lrec);
-            e = check();
-        }
+    if (fast && a->pre_step == step) {
+        std::swap(a->pidx16, a->pidx16b);
+        std::swap(a->pa16, a->pa16b);
+        std::swap(a->sc_count, a->sc_countb);
+        std::swap(a->sc_cursor, a->sc_cursorb);
+        std::swap(a->sc_meta, a->sc_metab);
+        std::swap(a->sc_ent, a->sc_entb);
+        std::swap(a->lrec, a->lrecb);
+    } else if (fast) {
+        if (e == cudaSuccess) e = cudaEventRecord(a->fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sp, a->fork, 0);
+        if (e == cudaSuccess)
+            e = fast_plan(g, a->step, a->threads, a->pidx16, a->pa16, a->sc_count, a->sc_cursor, a->sc_meta,
+                          a->sc_ent, a->lrec, sp, &n);
         if (e == cudaSuccess) e = cudaEventRecord(a->join, sp);
     }
     // Forward quantities of step n: wall densities and ghosts of h^n.
@@ -217,6 +232,26 @@ bz_status launch(bz_adj_scratch *a, const bzk::Geo &g0, int64_t step, const R *h
                     (const bzk::PlanA<float, uint16_t> *)a->pa16, a->sc_ent, a->sc_meta, a->lrec,
                     a->sc_meta + 2, (const float *)lam_in, (float *)a->lt, stats);
             e = check();
+        }
+        // The plan of the step the next call is expected to take, into the
+        // other set, on the side stream once this step's cell kernel is done
+        // with its plan (it runs beside this step's walls and streaming).
+        const int64_t dir = a->last_step >= 0 && a->last_step != step ? (step > a->last_step ? 1 : -1) : -1;
+        const int64_t guess = step + dir;
+        a->last_step = step;
+        a->pre_step = -1;
+        if (guess >= 0 && e == cudaSuccess) {
+            e = cudaEventRecord(a->cell_done, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(sp, a->cell_done, 0);
+            if (e == cudaSuccess) {
+                bzk::k_set_step<<<1, 1, 0, sp>>>(a->step2, guess);
+                e = check();
+            }
+            if (e == cudaSuccess)
+                e = fast_plan(g, a->step2, a->threads, a->pidx16b, a->pa16b, a->sc_countb, a->sc_cursorb,
+                              a->sc_metab, a->sc_entb, a->lrecb, sp, &n);
+            if (e == cudaSuccess) e = cudaEventRecord(a->join, sp);
+            if (e == cudaSuccess) a->pre_step = guess;
         }
     } else {
         if (e == cudaSuccess) {
@@ -275,6 +310,7 @@ bz_status bz_adj_prepare(bz_adj_scratch *a, const bzk::Geo &g, int dtype, int ns
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&t.side, cudaStreamNonBlocking, greatest);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.join, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t.cell_done, cudaEventDisableTiming);
         if (e != cudaSuccess) st = cuda_err(e, "adjoint side stream");
     }
     if (st != BZ_OK) {
@@ -300,11 +336,13 @@ void bz_adj_release(bz_adj_scratch *a)
 {
     void *ptrs[] = {a->pidx, a->pa, a->ghost, a->lt, a->nw, a->lF, a->step,
                     a->pidx16, a->pa16, a->sc_count, a->sc_cursor, a->sc_meta, a->sc_ent,
-                    a->lrec};
+                    a->lrec, a->pidx16b, a->pa16b, a->sc_countb, a->sc_cursorb, a->sc_metab,
+                    a->sc_entb, a->lrecb, a->step2};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (a->side) cudaStreamDestroy(a->side);
     if (a->fork) cudaEventDestroy(a->fork);
     if (a->join) cudaEventDestroy(a->join);
+    if (a->cell_done) cudaEventDestroy(a->cell_done);
     *a = bz_adj_scratch{};
 }

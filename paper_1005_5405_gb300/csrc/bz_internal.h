@@ -68,6 +68,17 @@ struct bz_adj_scratch {
     // The fast path's plan runs on a side stream beside the forward walls.
     cudaStream_t side;
     cudaEvent_t fork, join;
+    // A second plan set (the b fields), built on the side stream while a
+    // step's walls and streaming run, for the step the next call is expected
+    // to take (the next in the direction of the last two calls, backward at
+    // first); pre_step is that step (-1: none), step2 its device counter.
+    void *pidx16b, *pa16b;
+    int *sc_countb, *sc_cursorb, *sc_metab;
+    uint32_t *sc_entb;
+    uint4 *lrecb;
+    int64_t *step2;
+    int64_t pre_step, last_step;
+    cudaEvent_t cell_done;
 };
 
 // Allocates the scratch and sets up the kernels on the first call.
