@@ -39,7 +39,10 @@ __device__ __forceinline__ int ahead_slot(const AheadPlans &A, int64_t step0, in
 
 // Samples of steps step0 + blockIdx.y (one thread per sample), their marks
 // on the active nodes and the per-slot counts of out-of-box and near-face
-// samples.  g: the handle's geometry in logical node order (swz = 0).
+// samples.  g: the handle's geometry in logical node order (swz = 0).  The
+// FP32 sampler of the per-cell sets draws them (uniform velocity grids; a
+// sample near a velocity-cell face is drawn again in FP64), so the node
+// indices are those of the FP64 computation and W carries FP32 rounding.
 __global__ void k_ahead_plan(Geo g, AheadPlans A, int64_t step0)
 {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
@@ -48,7 +51,7 @@ __global__ void k_ahead_plan(Geo g, AheadPlans A, int64_t step0)
     const bool act = l < A.nt;
     SampleOut o = {};
     if (act) {
-        o = draw_sample(g, step, 0xFFFFFFFFu, (uint32_t)l);
+        o = draw_sample_cell<float>(g, step, 0xFFFFFFFFu, (uint32_t)l);
         const int64_t off = (int64_t)s * A.nt + l;
         A.idx[off] = make_int4(o.idx[0], o.idx[1], o.idx[2], o.idx[3]);
         A.pa[off] = make_plan_a<float, int>(o.idx[0], o.idx[1], o.W);
