@@ -1854,8 +1854,31 @@ bz_status fan_launch(bz_batch *B, cudaStream_t s, bool advance_step)
         bz_handle *h = B->inst[i];
         h->cur = (int)(B->step[i] & 1);
         h->step = B->step[i];
-        BZ_TRY(launch_lazy(h, B->br[B->owner[i]], advance_step));
+        BZ_TRY(launch_lazy(h, B->br[B->owner[i]], advance_step, false, h->ahead_K > 0));
     }
+    for (int k = 0; k < nb; ++k) {
+        BZ_CUDA(cudaEventRecord(B->ev[1 + k], B->br[k]));
+        BZ_CUDA(cudaStreamWaitEvent(s, B->ev[1 + k], 0));
+    }
+    return BZ_OK;
+}
+
+// The plans of the instances' current steps built ahead where their slots do
+// not cover them yet (the instances step together, so they all need a batch
+// at the same steps): each instance's batch on its branch, forked from and
+// joined back to s.  Never called while a stream is being captured.
+bz_status fan_ensure(bz_batch *B, cudaStream_t s)
+{
+    bool need = false;
+    for (int i = 0; i < B->n && !need; ++i) {
+        const bz_handle *h = B->inst[i];
+        need = h->lazy && h->ahead_K > 0 && !(B->step[i] >= h->ahead_lo && B->step[i] + 1 <= h->ahead_hi);
+    }
+    if (!need) return BZ_OK;
+    const int nb = B->branches;
+    BZ_CUDA(cudaEventRecord(B->ev[0], s));
+    for (int k = 0; k < nb; ++k) BZ_CUDA(cudaStreamWaitEvent(B->br[k], B->ev[0], 0));
+    for (int i = 0; i < B->n; ++i) BZ_TRY(ensure_plans(B->inst[i], B->br[B->owner[i]], B->step[i], 1));
     for (int k = 0; k < nb; ++k) {
         BZ_CUDA(cudaEventRecord(B->ev[1 + k], B->br[k]));
         BZ_CUDA(cudaStreamWaitEvent(s, B->ev[1 + k], 0));
@@ -2259,6 +2282,7 @@ bz_status bz_batch_step(bz_batch *B, int32_t nsteps, void *stream)
     }
     if (B->mode == 1) {
         for (int32_t k = 0; k < nsteps; ++k) {
+            BZ_TRY(fan_ensure(B, s));
             if (graphs_enabled()) {
                 cudaGraphExec_t ex = nullptr;
                 BZ_TRY(fan_graph(B, &ex));
@@ -2398,7 +2422,8 @@ bz_status bz_batch_tune(bz_batch *B, int32_t trial_steps, void *stream, int32_t 
             cudaGraphExec_t ex = nullptr;
             std::vector<long long> l0(B->n);
             for (int i = 0; i < B->n; ++i) l0[i] = B->inst[i]->launches;
-            bool ok = cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            bool ok = fan_ensure(B, s) == BZ_OK &&
+                      cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             bz_status st = ok ? fan_launch(B, B->cap, false) : BZ_ECUDA;
             ok = cudaStreamEndCapture(B->cap, &graph) == cudaSuccess && ok && st == BZ_OK;
             for (int i = 0; i < B->n; ++i) B->inst[i]->launches = l0[i];
