@@ -190,9 +190,10 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def oracle_sample(p, cells_per_side=32, steps=2):
+def oracle_sample(p, cells_per_side=32, steps=2, warmup=1):
     """Time the FP64 oracle on a sub-cavity with the workload's cell size,
-    velocity grid and sample count (same work per node and per sample)."""
+    velocity grid and sample count (same work per node and per sample), after
+    `warmup` untimed steps."""
     import numpy as np
     import oracle
     from paper_1005_5405_gb300 import workloads
@@ -202,10 +203,11 @@ def oracle_sample(p, cells_per_side=32, steps=2):
                             lid_u0=p.lid_u0, lid_amp=p.lid_amp, lid_period=p.lid_period)
     o = oracle.Oracle(**sub.kwargs())
     h = np.zeros((sub.nr, sub.nvt))
-    o.step(h, 0)                       # first touch of the buffers
+    for n in range(max(1, warmup)):    # the first also touches the buffers
+        h, _ = o.step(h, n)
     t0 = time.perf_counter()
     for n in range(steps):
-        h, _ = o.step(h, n + 1)
+        h, _ = o.step(h, max(1, warmup) + n)
     dt = (time.perf_counter() - t0) / steps
     return {
         "value": sub.nodes / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
@@ -221,10 +223,11 @@ def run_reference(args):
         return
     p = problem(args.config)
     steps = max(1, min(args.steps, 3))
-    r = oracle_sample(p, 64, steps)
+    warmup = max(3, min(args.warmup, 5))
+    r = oracle_sample(p, 64, steps, warmup)
     line = {
         "impl": "reference", "metric": METRIC, "value": r["value"], "unit": UNIT,
-        "n_gpus": args.gpus, "steps": steps, "warmup": 1, "ms_per_step": r["s_per_step"] * 1e3,
+        "n_gpus": args.gpus, "steps": steps, "warmup": warmup, "ms_per_step": r["s_per_step"] * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": p.name, "nx": p.nx, "ny": p.ny, "nv": p.nv,
                                          "vmax": p.vmax, "kn": p.kn, "samples_per_step": p.nt},
