@@ -228,7 +228,8 @@ __global__ void kbl_plan(const LzInst *__restrict__ inst, const int *__restrict_
     const int i = inst_of(samp_pre, n, k);
     const LzInst &b = inst[i];
     const int l = k - samp_pre[i];
-    const SampleOut o = draw_sample(b.g, *b.step, 0xFFFFFFFFu, (uint32_t)l);
+    // FP32 sampler, FP64 redraw near a velocity-cell face: the FP64 nodes.
+    const SampleOut o = draw_sample_cell<float>(b.g, *b.step, 0xFFFFFFFFu, (uint32_t)l);
     b.idx[l] = make_int4(o.idx[0], o.idx[1], o.idx[2], o.idx[3]);
     b.pa[l] = make_plan_a<float, int>(o.idx[0], o.idx[1], o.W);
 #pragma unroll
