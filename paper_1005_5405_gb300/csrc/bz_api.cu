@@ -514,16 +514,18 @@ bz_status configure_lazy(bz_handle *H)
         H->lz_chunk = std::min(H->lz_cmax, 64);
         if (const char *c = getenv("BZ_LAZY_ORDER_CHUNK")) H->lz_chunk = std::max(8, std::min(H->lz_cmax, atoi(c)));
         // The order saves shared-memory replays on every CTA iteration (about
-        // 3 us per iteration at 320 positions on a GB300) and costs a chain of
-        // about 2 x 64 dependent decisions (about 50 us): it runs when the
-        // iterations per CTA times the run length reach 6144.  With the plans
-        // built ahead (below) it runs over whole runs, which saves about 2.5%
-        // of the kernel and costs about 63 us of GPU time per step at 2x10^4
-        // samples: it runs from 15000 on.
+        // 3 us per iteration at 320 positions on a GB300).  Built per step it
+        // costs a chain of about 2 x 64 dependent decisions (about 50 us) on
+        // the step's critical path: it runs when the iterations per CTA times
+        // the run length reach 6144.  With the plans built ahead (below) it
+        // runs over whole runs and costs GPU time in proportion to the run
+        // length (about 63 us per step at 2x10^4 samples), which pays from
+        // about 12 iterations per CTA on (measured: 64^2 cells lose 1%, 96^2
+        // and more gain 0.6-9%).
         const int64_t iters = ((int64_t)(g.nr + H->lz_G - 1) / H->lz_G + H->lz_grid - 1) / H->lz_grid;
         const char *ka = getenv("BZ_LAZY_AHEAD");
-        const int64_t order_min = ka && atoi(ka) == 0 ? 6144 : 15000;
-        H->lz_order_tpb = H->lz_chunk <= 32767 && iters * H->lz_cmax >= order_min &&
+        const bool per_step = ka && atoi(ka) == 0;
+        H->lz_order_tpb = H->lz_chunk <= 32767 && (per_step ? iters * H->lz_cmax >= 6144 : iters >= 12) &&
                           bzk::lz_order_smem(H->lz_chunk, nb) <= (size_t)H->smem_optin ? 1 : 0;
         if (const char *o = getenv("BZ_LAZY_ORDER")) H->lz_order_tpb = atoi(o) != 0 && H->lz_chunk <= 32767 &&
                           bzk::lz_order_smem(H->lz_chunk, nb) <= (size_t)H->smem_optin ? 1 : 0;
