@@ -211,7 +211,7 @@ bz_status launch(bz_adj_scratch *a, const bzk::Geo &g0, int64_t step, const R *h
     }
     // Forward quantities of step n: wall densities and ghosts of h^n.
     if (e == cudaSuccess) {
-        bzk::k_walls<R><<<g.nfaces, 256, 0, s>>>(g, a->step, hn, (R *)a->ghost, a->nw, nullptr);
+        bzk::k_walls<R><<<g.nfaces, bzk::kWallThreads, 0, s>>>(g, a->step, hn, (R *)a->ghost, a->nw, nullptr);
         e = check();
     }
     if (fast && e == cudaSuccess) e = cudaStreamWaitEvent(s, a->join, 0);

@@ -713,7 +713,7 @@ bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true, bo
     if (!ahead && H->lz_order_tpb > 0) BZ_CUDA(cudaStreamWaitEvent(s, H->lz_mid, 0));
     {
         ProfScope ps(H, 0, s);
-        bzk::k_walls<float><<<g.nfaces, 256, 0, s>>>(g, H->d_step, hin, (float *)H->ghost, H->nw,
+        bzk::k_walls<float><<<g.nfaces, bzk::kWallThreads, 0, s>>>(g, H->d_step, hin, (float *)H->ghost, H->nw,
                                                      nullptr, H->mu[in]);
         BZ_LAUNCHED(H);
     }
@@ -812,7 +812,7 @@ bz_status launch_step(bz_handle *H, cudaStream_t s, bool fused, bool do_stream, 
     R *hout = (R *)H->h[H->cur ^ 1];
     if (do_stream || fused) {
         ProfScope ps(H, 0, s);
-        bzk::k_walls<R><<<g.nfaces, 256, 0, s>>>(g, H->d_step, hin, (R *)H->ghost, H->nw, nullptr);
+        bzk::k_walls<R><<<g.nfaces, bzk::kWallThreads, 0, s>>>(g, H->d_step, hin, (R *)H->ghost, H->nw, nullptr);
         BZ_LAUNCHED(H);
     }
     if ((do_collide || fused) && !H->per_cell) {
@@ -1397,10 +1397,10 @@ bz_status bz_lid_shear(bz_handle *H, double *out, void *stream)
     cudaStream_t s = (cudaStream_t)stream;
     const Geo &g = H->g;
     if (H->dtype == BZ_F64)
-        bzk::k_walls<double><<<g.nfaces, 256, 0, s>>>(g, H->d_step, (const double *)H->h[H->cur],
+        bzk::k_walls<double><<<g.nfaces, bzk::kWallThreads, 0, s>>>(g, H->d_step, (const double *)H->h[H->cur],
                                                       (double *)H->ghost, H->nw, H->shear);
     else
-        bzk::k_walls<float><<<g.nfaces, 256, 0, s>>>(g, H->d_step, (const float *)H->h[H->cur],
+        bzk::k_walls<float><<<g.nfaces, bzk::kWallThreads, 0, s>>>(g, H->d_step, (const float *)H->h[H->cur],
                                                      (float *)H->ghost, H->nw, H->shear,
                                                      H->lazy ? H->mu[H->cur] : nullptr);
     BZ_LAUNCHED(H);
@@ -1935,7 +1935,7 @@ bz_status fan_graph(bz_batch *B, cudaGraphExec_t *out)
 bz_status batch_launch(bz_batch *B, cudaStream_t s, bool advance)
 {
     const int pb = 256;
-    bzk::kb_walls<<<B->tot_faces, 256, 0, s>>>(B->d_inst, B->d_face_pre, B->n);
+    bzk::kb_walls<<<B->tot_faces, bzk::kWallThreads, 0, s>>>(B->d_inst, B->d_face_pre, B->n);
     bzk::kb_plan<<<(B->tot_samples + pb - 1) / pb, pb, 0, s>>>(B->d_inst, B->d_samp_pre, B->n);
     bzk::kb_scatter_scan<<<B->n, 1024, 0, s>>>(B->d_inst, B->maxt);
     bzk::kb_scatter_fill<<<(B->tot_samples + pb - 1) / pb, pb, 0, s>>>(B->d_inst, B->d_samp_pre,
@@ -1970,7 +1970,7 @@ bz_status lz_batch_launch(bz_batch *B, cudaStream_t s, bool advance)
     bzk::kbl_lscan<<<B->n, 1024, 0, sp>>>(B->d_lzinst);
     bzk::kbl_lfill<<<sg, pb, 0, sp>>>(B->d_lzinst, B->d_samp_pre, B->n);
     BZ_CUDA(cudaEventRecord(B->lz_join, sp));
-    bzk::kbl_walls<<<B->tot_faces, 256, 0, s>>>(B->d_lzinst, B->d_face_pre, B->n);
+    bzk::kbl_walls<<<B->tot_faces, bzk::kWallThreads, 0, s>>>(B->d_lzinst, B->d_face_pre, B->n);
     BZ_CUDA(cudaMemsetAsync(B->d_next, 0, sizeof(int) * B->lz_classes.size(), s));
     BZ_CUDA(cudaStreamWaitEvent(s, B->lz_join, 0));
     const size_t nc = B->lz_classes.size();

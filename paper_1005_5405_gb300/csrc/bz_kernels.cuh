@@ -531,6 +531,12 @@ __device__ __forceinline__ Face face_of(const Geo &g, int f, int64_t step)
     return F;
 }
 
+// The wall kernels: one CTA of kWallThreads threads per face (with about 60
+// registers a thread, eight CTAs fit an SM, so a 256x256 cavity's 1024
+// faces run in one wave), each thread with kWallLoads loads in flight.
+constexpr int kWallThreads = 128;
+constexpr int kWallLoads = 16;
+
 // ghost[f*nv + jt]: emitted h for inflow nodes of face f, indexed by the
 // tangential velocity index (jy for side walls, jx for bottom and lid).
 // shear[ix]: x-momentum flux through lid face ix (lid faces only).
@@ -548,55 +554,68 @@ __device__ __forceinline__ void walls_face(const Geo &g, int64_t step, const R *
 {
     const Face F = face_of(g, f, step);
     const int N = g.nv, N2 = N * N;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        sA[i] = (R)g.axA[i];
-        sv[i] = (R)g.axv[i];
-    }
+    const bool lid = f >= 2 * g.ny + g.nx;
+    const R ns = (R)F.nsign;
     R m5[5] = {R(0), R(0), R(0), R(0), R(0)};
     if (mu)
         for (int k = 0; k < 5; ++k) m5[k] = (R)mu[(int64_t)F.cell * 8 + k];
+    // Per normal-axis node: the outgoing weight -v_n A(v_n) (0 for incoming
+    // nodes), the normal part of the pending correction, m_n v_n + m_4 v_n^2,
+    // and on the lid A(v_n) v_n for the shear.
+    __shared__ R s_cw[kMaxN], s_kn[kMaxN], s_cl[kMaxN];
+    const R mn = F.nax == 0 ? m5[1] : m5[2], mt = F.nax == 0 ? m5[2] : m5[1];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const R A = (R)g.axA[i], v = (R)g.axv[i];
+        sA[i] = A;
+        sv[i] = v;
+        s_cw[i] = v * ns < R(0) ? -(v * ns) * A : R(0);
+        s_kn[i] = mn * v + m5[4] * v * v;
+        s_cl[i] = A * v;
+    }
     __syncthreads();
     const R *hc = h + (int64_t)F.cell * g.nvt;
-    const bool lid = f >= 2 * g.ny + g.nx;
-    const R ns = (R)F.nsign;
     // Outgoing flux sum_{v_n<0} |v_n| w_j h_j and, on the lid, the cell part
     // of the shear, sum_{v_y>0} w_j v_x v_y h_j (per-thread sums in the state
     // precision, combined in double).  Threads take the pairs of the other
     // two axes (z fastest, so their loads are adjacent) and loop over the
-    // normal axis, skipping its incoming half.
+    // outgoing half of the normal axis only (v_n < 0: nodes below N/2 for an
+    // inward normal along +e_n, above for -e_n, the axes being symmetric).
+    // With w_j = A_n A_a A_z the sums over the normal axis are taken first.
     R acc[2] = {R(0), R(0)};
     const R eps = (R)g.eps;
+    const int lo = F.nsign > 0.0 ? 0 : N - N / 2, hi = F.nsign > 0.0 ? N / 2 : N;
     for (int q = threadIdx.x; q < N2; q += blockDim.x) {
         const int qa = q / N, jz = q - qa * N;   // (jy, jz) on side walls, (jx, jz) on bottom and lid
-        const R vz = sv[jz], Az = sA[jz], va = sv[qa], Aa = sA[qa];
+        const R vz = sv[jz], va = sv[qa], Aq = sA[qa] * sA[jz];
         const int64_t base = F.nax == 0 ? (int64_t)q : (int64_t)qa * N2 + jz;
         const int64_t stride = F.nax == 0 ? N2 : N;
-        // Eight planes at a time: their loads are in flight together.
-        for (int jn0 = 0; jn0 < N; jn0 += 8) {
-            R hs[8];
+        // The tangential part of the pending correction of these nodes.
+        const R kq = m5[0] + mt * va + m5[3] * vz + m5[4] * (va * va + vz * vz);
+        R s0 = R(0), s1 = R(0);
+        // kWallLoads planes at a time (the whole outgoing half up to 32
+        // nodes per axis): their loads are in flight together.
+        for (int jn0 = lo; jn0 < hi; jn0 += kWallLoads) {
+            R hs[kWallLoads];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
+            for (int k = 0; k < kWallLoads; ++k) {
                 const int jn = jn0 + k;
-                hs[k] = jn < N && sv[jn] * ns < R(0) ? hc[base + jn * stride] : R(0);
+                hs[k] = jn < hi ? hc[base + jn * stride] : R(0);
             }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
+            for (int k = 0; k < kWallLoads; ++k) {
                 const int jn = jn0 + k;
-                if (jn >= N) break;
-                const R vnn = sv[jn];
-                const R vn = vnn * ns;
-                if (!(vn < R(0))) continue;
-                const R vx = F.nax == 0 ? vnn : va, vy = F.nax == 0 ? va : vnn;
-                const R w = sA[jn] * Aa * Az;
+                if (jn >= hi) break;
                 R hv = hs[k];
                 if (mu) {
-                    const R kap = m5[0] + m5[1] * vx + m5[2] * vy + m5[3] * vz + m5[4] * (vx * vx + vy * vy + vz * vz);
+                    const R kap = kq + s_kn[jn];
                     hv = hv + (R(1) + eps * hv) * kap;
                 }
-                acc[0] -= vn * w * hv;
-                if (lid) acc[1] += w * vx * vy * hv;
+                s0 += s_cw[jn] * hv;
+                if (lid) s1 += s_cl[jn] * hv;
             }
         }
+        acc[0] += Aq * s0;
+        if (lid) acc[1] += Aq * va * s1;
     }
     block_reduce<2, R>(acc, red, tot);
     if (threadIdx.x < 32) {
