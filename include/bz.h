@@ -128,6 +128,12 @@ typedef struct {
     int32_t threads_per_cell, smem_bytes;  /* per-cell kernel launch shape */
     int32_t kernel_variant;  /* 0: generic per-cell kernel; 1: FP32 4-node-vector kernel;
                                 2: FP32 active-node kernel with deferred correction */
+    int32_t plan_batch;      /* active-node kernel: the sample plans of this many
+                                consecutive steps are built together, by the first step
+                                that needs a plan the last batch does not hold; 0: each
+                                step builds its own plan, or another kernel runs */
+    int64_t plan_end;        /* with plan_batch > 0: the first step the built plans do not
+                                cover (a step from there on builds the next batch) */
 } bz_info;
 
 /* Create a solver for the driven cavity.  Validates every argument
@@ -290,7 +296,11 @@ bz_status bz_batch_schedule(const bz_batch *b, int32_t out[4]);
 
 /* Per-kernel timing with CUDA events recorded on the launching stream around
  * every kernel the handle launches while enabled (enable != 0); disabling
- * keeps what was recorded.  bz_profile_read synchronises, returns per kernel
+ * keeps what was recorded.  On the active-node path the fused steps keep
+ * running as two-step CUDA graphs: enable == 1 captures one in which the
+ * per-cell kernel's launches (class 2 only) are bracketed by event record
+ * nodes, and every replay first gives those nodes fresh events.
+ * bz_profile_read synchronises, returns per kernel
  * class k (0 walls, 1 sampling, 2 per-cell step or collision, 3 streaming)
  * the summed device time ms[k] and the launch count launches[k] since the
  * last read, and clears the record.  No counterpart in the paper (its timings

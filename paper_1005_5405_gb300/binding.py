@@ -61,7 +61,8 @@ class bz_info(C.Structure):
                 ("nodes", C.c_int64), ("state_bytes", C.c_int64), ("step", C.c_int64),
                 ("nr", C.c_int32), ("nvt", C.c_int32), ("dtype", C.c_int32),
                 ("threads_per_cell", C.c_int32), ("smem_bytes", C.c_int32),
-                ("kernel_variant", C.c_int32)]
+                ("kernel_variant", C.c_int32), ("plan_batch", C.c_int32),
+                ("plan_end", C.c_int64)]
 
 
 _H = C.c_void_p

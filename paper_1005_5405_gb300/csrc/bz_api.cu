@@ -77,6 +77,18 @@ struct bz_handle {
     cudaStream_t cap_stream = nullptr;  // stream used to capture step graphs
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // two fused steps, by buffer parity
     long long graph_launches = 0;
+    // Profiled graphs: the event record nodes of each timed launch (kernel
+    // class k), found in the graph they were captured into (kept for that),
+    // which get fresh events before every replay.
+    struct ProfNode {
+        int k;
+        cudaGraphNode_t a, b;
+    };
+    cudaGraph_t gtmpl[2] = {nullptr, nullptr};
+    std::vector<ProfNode> gprof[2];
+    std::vector<cudaEvent_t> gplace;    // the events recorded while capturing
+    bool capturing = false;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> cap_ev;
     void *ht = nullptr;                 // h~ for the unfused path (lazy)
     void *pidx = nullptr;               // sample plan: node indices (16- or 32-bit)
     bool idx16 = true;
@@ -179,16 +191,20 @@ struct ProfScope {
     int k;
     cudaStream_t s;
     cudaEvent_t a = nullptr, b = nullptr;
+    // While a step graph is captured only the per-cell kernel (class 2) is
+    // timed: every event node costs the replayed step a little time.
     ProfScope(bz_handle *H_, int k_, cudaStream_t s_) : H(H_), k(k_), s(s_)
     {
-        if (H->prof && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
-            cudaEventRecord(a, s);
+        if (H->prof && (!H->capturing || k == 2) && cudaEventCreate(&a) == cudaSuccess &&
+            cudaEventCreate(&b) == cudaSuccess)
+            cudaEventRecordWithFlags(a, s, H->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
     }
     ~ProfScope()
     {
         if (a && b) {
-            cudaEventRecord(b, s);
-            H->ev[k].push_back({a, b});
+            cudaEventRecordWithFlags(b, s, H->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+            if (H->capturing) H->cap_ev.push_back({k, {a, b}});
+            else H->ev[k].push_back({a, b});
         }
     }
 };
@@ -209,6 +225,13 @@ void drop_graphs(bz_handle *H)
             cudaGraphExecDestroy(g);
             g = nullptr;
         }
+    for (int p = 0; p < 2; ++p) {
+        if (H->gtmpl[p]) cudaGraphDestroy(H->gtmpl[p]);
+        H->gtmpl[p] = nullptr;
+        H->gprof[p].clear();
+    }
+    for (cudaEvent_t e : H->gplace) cudaEventDestroy(e);
+    H->gplace.clear();
 }
 
 // Launch the FP32 fast-path cell kernel; false when the handle does not use it.
@@ -539,10 +562,35 @@ bz_status configure_lazy(bz_handle *H)
     BZ_TRY(dalloc(&H->lz_dest0, sizeof(int) * (size_t)bzk::kLzRoleT));
     BZ_TRY(dalloc(&H->lz_rec, sizeof(uint2) * ((size_t)4 * nt + (size_t)8 * bzk::kLzRoleT)));
     BZ_CUDA(cudaMemset(H->lz_count, 0, sizeof(int) * (size_t)nvt));
-    // Plans of 32 steps built ahead at a time (BZ_LAZY_AHEAD=K sets the
+    // Plans of K steps built ahead at a time (BZ_LAZY_AHEAD=K sets the
     // count, 0 builds each step's plan in the step), their term order over
-    // whole runs.
-    H->ahead_K = 32;
+    // whole runs.  The order kernel's one-warp CTAs (T / NB per plan and
+    // chunk) are bound by their shared memory to a few per SM and take about
+    // the same time in every wave.  When 32 plans need more than one wave, K
+    // fills the last wave (46 on a 152-SM GB300 at 2x10^4 samples, where the
+    // 1024 CTAs of 32 plans would leave the second wave a third full); K is
+    // kept even so that the two-step graphs never straddle a batch; at most 64.
+    {
+        const int nb = H->lz_G == 4 ? 8 : 16;
+        H->ahead_chunk = H->lz_cmax;
+        if (getenv("BZ_LAZY_ORDER_CHUNK")) H->ahead_chunk = H->lz_chunk;
+        if (H->lz_order_tpb > 0 && bzk::lz_order_smem(H->ahead_chunk, nb) > (size_t)H->smem_optin)
+            H->ahead_chunk = H->lz_chunk;
+        H->ahead_K = 32;
+        if (H->lz_order_tpb > 0) {
+            const int nch = (H->lz_cmax + H->ahead_chunk - 1) / H->ahead_chunk;
+            const int64_t per = (int64_t)(bzk::kLzRoleT / nb) * nch;       // CTAs per plan
+            int occ = 0;
+            const size_t osm = bzk::lz_order_smem(H->ahead_chunk, nb);
+            BZ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &occ, nb == 8 ? bzk::k_lz_order<8> : bzk::k_lz_order<16>, 32, osm));
+            const int64_t wave = (int64_t)occ * H->nsm;
+            if (wave > 0 && 32 * per > wave) {
+                const int64_t waves = (32 * per + wave - 1) / wave;
+                H->ahead_K = (int)std::min<int64_t>(64, waves * wave / per / 2 * 2);
+            }
+        }
+    }
     if (const char *kk = getenv("BZ_LAZY_AHEAD")) H->ahead_K = std::max(0, std::min(256, atoi(kk)));
     if (H->ahead_K > 0) {
         bzk::AheadPlans &A = H->ahead;
@@ -572,12 +620,6 @@ bz_status configure_lazy(bz_handle *H)
         BZ_CUDA(cudaMemset(A.flag, 0, sizeof(int) * k * nvt));
         BZ_CUDA(cudaMemset(A.count, 0, sizeof(int) * k * nvt));
         H->ahead_lo = H->ahead_hi = 0;
-        // Built ahead, the order's chain costs little per step: whole runs.
-        const int nb = H->lz_G == 4 ? 8 : 16;
-        H->ahead_chunk = H->lz_cmax;
-        if (const char *c = getenv("BZ_LAZY_ORDER_CHUNK")) H->ahead_chunk = H->lz_chunk;
-        if (H->lz_order_tpb > 0 && bzk::lz_order_smem(H->ahead_chunk, nb) > (size_t)H->smem_optin)
-            H->ahead_chunk = H->lz_chunk;
     }
     // Equilibrium sums of the 30 monomials (the moments of h^{n+1} need them).
     std::vector<double> axv(N), axA(N);
@@ -738,6 +780,8 @@ bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true, bo
         a.clk = H->prof_clk;
         a.stats = H->stats;
         a.err = H->stats + 8;
+        a.fb_count = H->sc_count;
+        a.fb_n = g.nvt;
         // BZ_LAZY_TMA_TIMEOUT_TEST=1: CTA 0 expects 16 bytes more than its
         // first bulk copies bring, so its first wait runs out (tests of the
         // bounded waits; the step's result is then invalid).
@@ -757,7 +801,7 @@ bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true, bo
         ProfScope ps(H, 1, s);
         const ushort4 *pi = (const ushort4 *)H->pidx;
         auto *pa16 = (bzk::PlanA<float, uint16_t> *)H->pa;
-        BZ_CUDA(cudaMemsetAsync(H->sc_count, 0, sizeof(int) * g.nvt, s));
+        // (k_lz zeroed the scatter counts if the step overflowed.)
         bzk::k_lz_fb_plan<<<pg, pb, 0, s>>>(g.nt, g.nv, H->lz_meta, H->lz_idx, H->lz_pa,
                                             (ushort4 *)H->pidx, pa16, H->sc_count);
         BZ_LAUNCHED(H);
@@ -767,11 +811,10 @@ bz_status launch_lazy(bz_handle *H, cudaStream_t s, bool advance_step = true, bo
         bzk::k_scatter_fill<<<pg, pb, 0, s>>>(g.nt, H->threads4, pi, H->sc_cursor, H->sc_meta,
                                               H->sc_ent, H->lz_meta);
         BZ_LAUNCHED(H);
+        // The input is corrected in place and its pending corrections go;
+        // the output's are cleared (k_cell4 writes corrected values).
         bzk::k_lz_materialize<<<std::min(g.nr, H->nsm * 8), 256, 0, s>>>(
-            g, H->lz_meta, hin, H->mu[in], hin, H->mu[out]);
-        BZ_LAUNCHED(H);
-        // The input now holds corrected values: its pending corrections go.
-        bzk::k_lz_clear<<<H->nsm, 256, 0, s>>>(H->lz_meta, H->mu[in], (int64_t)g.nr * 8);
+            g, H->lz_meta, hin, H->mu[in], hin, H->mu[out], H->mu[in]);
         BZ_LAUNCHED(H);
         const int grid = nostream ? H->grid4c : H->grid4f;
 #define BZ_C4G(F, M)                                                                              \
@@ -966,8 +1009,7 @@ void clear_events(bz_handle *H)
 void release(bz_handle *H)
 {
     clear_events(H);
-    for (auto &g : H->graph)
-        if (g) cudaGraphExecDestroy(g);
+    drop_graphs(H);
     if (H->cap_stream) cudaStreamDestroy(H->cap_stream);
     if (H->lz_side) cudaStreamDestroy(H->lz_side);
     if (H->lz_fork) cudaEventDestroy(H->lz_fork);
@@ -1293,11 +1335,20 @@ bz_status capture_pair(bz_handle *H)
     const long long l0 = H->launches;
     const bool mv0 = H->mom_valid;
     const bool lz0[2] = {H->lazy_buf[0], H->lazy_buf[1]};
+    // With profiling on, the timed launches' events become event record
+    // nodes of the graph (recorded as external events while capturing).
+    H->capturing = H->prof;
+    H->cap_ev.clear();
     BZ_CUDA(cudaStreamBeginCapture(H->cap_stream, cudaStreamCaptureModeThreadLocal));
     bz_status st = one_step(H, H->cap_stream, true, false, false);
     if (st == BZ_OK) st = one_step(H, H->cap_stream, true, false, false);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(H->cap_stream, &graph);
+    H->capturing = false;
+    for (auto &c : H->cap_ev) {
+        H->gplace.push_back(c.second.first);
+        H->gplace.push_back(c.second.second);
+    }
     H->graph_launches = H->launches - l0;
     H->cur = cur0;
     H->step = step0;
@@ -1312,9 +1363,64 @@ bz_status capture_pair(bz_handle *H)
     if (e != cudaSuccess) return fail(BZ_ECUDA, "step capture failed: %s", cudaGetErrorString(e));
     cudaGraphExec_t ex = nullptr;
     e = cudaGraphInstantiate(&ex, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return fail(BZ_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(BZ_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
     H->graph[cur0] = ex;
+    if (H->cap_ev.empty()) {
+        cudaGraphDestroy(graph);
+        return BZ_OK;
+    }
+    // The event record nodes of the timed launches, by the events they
+    // were captured with.  The graph stays alive: its nodes name them.
+    size_t nn = 0;
+    BZ_CUDA(cudaGraphGetNodes(graph, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    BZ_CUDA(cudaGraphGetNodes(graph, nodes.data(), &nn));
+    std::vector<std::pair<cudaEvent_t, cudaGraphNode_t>> rec;
+    for (cudaGraphNode_t n : nodes) {
+        cudaGraphNodeType t;
+        BZ_CUDA(cudaGraphNodeGetType(n, &t));
+        if (t != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev = nullptr;
+        BZ_CUDA(cudaGraphEventRecordNodeGetEvent(n, &ev));
+        rec.push_back({ev, n});
+    }
+    auto node_of = [&](cudaEvent_t ev) -> cudaGraphNode_t {
+        for (auto &r : rec)
+            if (r.first == ev) return r.second;
+        return nullptr;
+    };
+    for (auto &c : H->cap_ev) {
+        cudaGraphNode_t na = node_of(c.second.first), nb = node_of(c.second.second);
+        if (!na || !nb) {
+            H->gprof[cur0].clear();
+            cudaGraphDestroy(graph);
+            return fail(BZ_ECUDA, "profiled step capture: an event record node is missing");
+        }
+        H->gprof[cur0].push_back({c.first, na, nb});
+    }
+    if (H->gtmpl[cur0]) cudaGraphDestroy(H->gtmpl[cur0]);
+    H->gtmpl[cur0] = graph;
+    return BZ_OK;
+}
+
+// Fresh events for the timed launches of the next replay of graph p (a
+// replay records into the events its record nodes hold at launch time).
+bz_status arm_profiled_graph(bz_handle *H, int p)
+{
+    for (auto &n : H->gprof[p]) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        BZ_CUDA(cudaEventCreate(&a));
+        if (cudaEventCreate(&b) != cudaSuccess) {
+            cudaEventDestroy(a);
+            return fail(BZ_ECUDA, "cudaEventCreate failed");
+        }
+        H->ev[n.k].push_back({a, b});
+        BZ_CUDA(cudaGraphExecEventRecordNodeSetEvent(H->graph[p], n.a, a));
+        BZ_CUDA(cudaGraphExecEventRecordNodeSetEvent(H->graph[p], n.b, b));
+    }
     return BZ_OK;
 }
 
@@ -1333,7 +1439,7 @@ bz_status bz_step_ex(bz_handle *H, int32_t nsteps, uint32_t flags, void *stream)
     bool dc = (flags & BZ_DO_COLLIDE) || (flags & BZ_SPLIT);
     if (ds && dc && !H->ht) BZ_TRY(dalloc(&H->ht, H->esz * (size_t)H->g.nr * H->g.nvt));
     int32_t n = 0;
-    if (fused && nsteps >= 2 && !H->prof && graphs_enabled()) {
+    if (fused && nsteps >= 2 && graphs_enabled()) {
         // The captured steps read the buffers as they are now: bring the
         // pair into the state the steps leave it in before capturing.
         if (!H->lazy) {
@@ -1343,6 +1449,7 @@ bz_status bz_step_ex(bz_handle *H, int32_t nsteps, uint32_t flags, void *stream)
         if (!H->graph[H->cur]) BZ_TRY(capture_pair(H));
         for (; n + 1 < nsteps; n += 2) {
             BZ_TRY(ensure_plans(H, s, H->step, 2));
+            if (H->prof) BZ_TRY(arm_profiled_graph(H, H->cur));
             BZ_CUDA(cudaGraphLaunch(H->graph[H->cur], s));
             H->step += 2;
             H->launches += H->graph_launches;
@@ -1481,6 +1588,8 @@ bz_status bz_get_info(const bz_handle *H, bz_info *o)
     o->threads_per_cell = H->lazy ? H->lz_T : H->fast ? H->threads4 : H->threads;
     o->smem_bytes = (int32_t)(H->lazy ? H->lz_smem : H->fast ? H->smem4 : H->smem_cell);
     o->kernel_variant = H->lazy ? 2 : H->fast ? 1 : 0;
+    o->plan_batch = H->lazy ? H->ahead_K : 0;
+    o->plan_end = H->lazy && H->ahead_K > 0 ? H->ahead_hi : 0;
     return BZ_OK;
 }
 
@@ -1581,6 +1690,9 @@ bz_status bz_profile(bz_handle *H, int32_t enable)
     if (!H) return fail(BZ_EINVAL, "handle is NULL");
     H->prof = enable != 0;
     drop_graphs(H);
+    // The active-node path captures its profiled two-step graph now, so
+    // that a timed region that starts next does not hold the capture.
+    if (enable == 1 && H->lazy && graphs_enabled()) BZ_TRY(capture_pair(H));
     if (enable >= 2 && !H->prof_clk) {
         BZ_TRY(dalloc(&H->prof_clk, sizeof(long long) * bzk::kClkCells * bzk::kClkPhases));
         BZ_CUDA(cudaMemset(H->prof_clk, 0, sizeof(long long) * bzk::kClkCells * bzk::kClkPhases));

@@ -618,6 +618,16 @@ __device__ __forceinline__ void walls_face(const Geo &g, int64_t step, const R *
         if (lid) acc[1] += Aq * va * s1;
     }
     block_reduce<2, R>(acc, red, tot);
+    if (F.U == 0.0 && !lid) {
+        // A wall at rest: Phi_w = Phi0, so D_in = h_n z_sum^2 = c_out (the
+        // tangential sum of A is z_sum), n_w = 1 + eps F / c_out, and every
+        // emitted value is (n_w - 1) / eps = F / c_out.
+        const double gh = tot[0] / g.cout;
+        if (threadIdx.x == 0 && nw_out) nw_out[f] = 1.0 + g.eps * gh;
+        for (int jt = threadIdx.x; jt < N; jt += blockDim.x) ghost[f * N + jt] = (R)gh;
+        __syncthreads();
+        return;
+    }
     if (threadIdx.x < 32) {
         // D_in = sum_{v_n>0} v_n dV Phi_w(v_j), separable in the three axes
         // (the tangential factor summed by one warp).

@@ -336,6 +336,7 @@ __global__ void __launch_bounds__(32) k_lz_order(int T, int cmax, int chunk, con
     using Mask = typename std::conditional<NB == 8, uint8_t, uint16_t>::type;
     extern __shared__ __align__(16) unsigned char osm[];
     const int lane = threadIdx.x, l = lane / H, h = lane - l * H;
+    const unsigned rmask = ((1u << H) - 1u) << (l * H);   // the lanes of this run
     const int tt = blockIdx.x * NB + l;
     const int C = meta[3], c0 = blockIdx.y * chunk;
     if (C > cmax || meta[1] || blockIdx.x * NB + NB > T || c0 >= C) return;
@@ -413,7 +414,9 @@ __global__ void __launch_bounds__(32) k_lz_order(int T, int cmax, int chunk, con
         const int s1 = sv & 0x7FFF;
         const uint32_t *row = u + p * NB;            // entries taken at p, by group
         if (ready) {
-            for (int j0 = p + h; j0 <= s1; j0 += 4 * H) {
+            // Passes of 4 H candidates; the run's lanes take the same passes.
+            for (int jb = p; jb <= s1; jb += 4 * H) {
+                const int j0 = jb + h;
                 uint32_t xs[4], wa[4], wb[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) xs[k] = j0 + k * H <= s1 ? bl[j0 + k * H].x : 0u;
@@ -433,6 +436,11 @@ __global__ void __launch_bounds__(32) k_lz_order(int T, int cmax, int chunk, con
                     const uint32_t key = cs < cn ? (cs << 24 | 1u << 23 | (uint32_t)j) : (cn << 24 | (uint32_t)j);
                     best = min(best, key);
                 }
+                // A candidate with no conflict and no swap beats every later
+                // one (the key then orders by position): the scan stops.
+#pragma unroll
+                for (int o = 1; o < H; o <<= 1) best = min(best, __shfl_xor_sync(rmask, best, o));
+                if (best < (1u << 23)) break;
             }
         }
 #pragma unroll
@@ -513,28 +521,20 @@ static __global__ void k_lz_fb_plan(int nt, int N, const int *__restrict__ meta,
     if (l < nt) lz_fb_plan_one(l, N, idx, pa, pidx16, pa16, count);
 }
 
-// Clears n floats when gate[1] is set (the pending corrections of a state
-// that the fallback corrected in place).
-static __global__ void k_lz_clear(const int *__restrict__ gate, float *__restrict__ x, int64_t n)
-{
-    if (!gate[1]) return;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x)
-        x[i] = 0.f;
-}
-
 // The correction of a stored node value: h = h_c + (1 + eps h_c) kappa.
 __device__ __forceinline__ float lz_corr(float hc, float kappa, float eps)
 {
     return fmaf(eps * hc, kappa, hc + kappa);
 }
 
-// h <- h_c + (1 + eps h_c)(mu_c . psi_j) for every node (in place allowed);
-// mu_zero (nullable) is then cleared.  When skip_unless (nullable) points to
-// 0, does nothing.  One CTA per cell at a time; float4 over jz.
+// h <- h_c + (1 + eps h_c)(mu_c . psi_j) for every node (in place allowed:
+// hout may be hin, so neither is restrict-qualified); mu_zero (nullable) is
+// then cleared, and mu_used (nullable; may be mu) gets each cell's
+// corrections cleared once they are read.  When skip_unless (nullable)
+// points to 0, does nothing.  One CTA per cell at a time; float4 over jz.
 static __global__ void k_lz_materialize(Geo g, const int *__restrict__ skip_unless,
-                                 const float *__restrict__ hin, const float *__restrict__ mu,
-                                 float *__restrict__ hout, float *__restrict__ mu_zero)
+                                 const float *hin, const float *mu, float *hout,
+                                 float *__restrict__ mu_zero, float *mu_used = nullptr)
 {
     if (skip_unless && !skip_unless[1]) return;
     __shared__ float sv[kMaxN];
@@ -547,6 +547,7 @@ static __global__ void k_lz_materialize(Geo g, const int *__restrict__ skip_unle
         __syncthreads();
         if (threadIdx.x < 8) smu[threadIdx.x] = mu[(int64_t)c * 8 + threadIdx.x];
         __syncthreads();
+        if (mu_used && threadIdx.x < 8) mu_used[(int64_t)c * 8 + threadIdx.x] = 0.f;
         const float4 *src = reinterpret_cast<const float4 *>(hin) + (int64_t)c * plane;
         float4 *dst = reinterpret_cast<float4 *>(hout) + (int64_t)c * plane;
         for (int o = threadIdx.x; o < (int)plane; o += blockDim.x) {
@@ -710,6 +711,8 @@ struct LzArgs {
     unsigned long long *err;    // nullable: set to 1 when a bounded mbarrier wait gave up
     int tx_excess;          // bulk-copy ring, CTA 0's first stage: bytes expected beyond
                             // those copied (a wait that runs out, for tests; normally 0)
+    int *fb_count;          // nullable: counts of the fallback's scatter list, zeroed
+    int fb_n;               // (fb_n ints) when the step overflowed, before the fallback
 };
 
 // Shared memory.  A fixed-layout head (compile-time offsets): warp partial
@@ -1287,7 +1290,12 @@ __device__ __forceinline__ void lz_run(const Geo &g, const LzArgs &a, char *smem
                                        int nmine)
 {
     using V = typename LzVec<G>::T;
-    if (a.meta[1]) return;                        // too many active nodes: k_cell4 runs
+    if (a.meta[1]) {                              // too many active nodes: k_cell4 runs
+        if (a.fb_count)
+            for (int i = (int)(blockIdx.x * blockDim.x + threadIdx.x); i < a.fb_n; i += gridDim.x * blockDim.x)
+                a.fb_count[i] = 0;
+        return;
+    }
     const int N = NV ? NV : g.nv;
     const int N2 = N * N, nvt = N2 * N, t = threadIdx.x;
     const int Qd = N2 / 4, nq = N / 4, P4 = lz_planes4(N), J = N / P4, Jh = J / 2;

@@ -51,3 +51,52 @@ def test_profiled_traffic_scales_with_cells_or_is_withheld():
     else:
         assert t1 is None and t2 is None
     assert bench.profiled_traffic(1000, 0) is None
+
+
+class _FakeCavity:
+    """Stands in for binding.Cavity: a plan batch of K steps built by the
+    first step outside the last batch (pairs of steps, as the library's
+    two-step graphs take them, never straddle one when K is even)."""
+
+    def __init__(self, K, step=0):
+        self.K, self.cur, self.lo, self.hi, self.builds = K, step, 0, 0, []
+
+    def get_info(self):
+        class I:
+            pass
+        i = I()
+        i.plan_batch, i.step, i.plan_end = self.K, self.cur, self.hi if self.K else 0
+        return i
+
+    def step(self, n):
+        k = 0
+        while k < n:
+            cnt = 2 if n - k >= 2 else 1
+            if self.K and not (self.lo <= self.cur and self.cur + cnt <= self.hi):
+                self.lo, self.hi = self.cur, self.cur + self.K
+                self.builds.append(self.cur)
+            self.cur += cnt
+            k += cnt
+
+
+def test_timed_window_starts_with_a_plan_batch():
+    """After the warm-up, bench.to_plan_boundary runs the steps left in the
+    current batch, so a timed window of S steps holds ceil(S / K) batch
+    builds (S a multiple of K: exactly S / K, its share), for any warm-up."""
+    for K in (46, 32):
+        for warmup in (1, 5, 17, 46, 50):
+            cav = _FakeCavity(K)
+            cav.step(warmup)
+            extra = bench.to_plan_boundary(cav)
+            start = cav.cur
+            assert start % K == 0 and extra == start - warmup
+            for S in (2 * K, 40, 92):
+                c2 = _FakeCavity(K)
+                c2.step(start)
+                n0 = len(c2.builds)
+                c2.step(S)
+                assert len(c2.builds) - n0 == -(-S // K), (K, warmup, S)
+    # Without plans built ahead nothing is added.
+    cav = _FakeCavity(0)
+    cav.step(5)
+    assert bench.to_plan_boundary(cav) == 0 and cav.cur == 5
