@@ -261,8 +261,10 @@ bz_status bz_philox(uint32_t k0, uint32_t k1, const uint32_t *ctr, int64_t n, ui
  * active-node kernels (one launch per kernel class over all instances, the
  * active-node kernel claiming (instance, group of four cells) segments from
  * a work list, one launch per velocity-grid size; available when every
- * instance runs the active-node path with four cells per group).
- * bz_batch_tune chooses.  Every instance must be FP32 with nv a multiple of 4 and >= 12,
+ * instance runs the active-node path with four cells per group).  The two
+ * active-node schedules copy every instance's sample plans from the batches
+ * built ahead (built between steps, before the step's graph launch, when an
+ * instance's step leaves its last batch).  bz_batch_tune chooses.  Every instance must be FP32 with nv a multiple of 4 and >= 12,
  * at most 32768 samples per step, the shared sample set and uniform grids
  * (BZ_EUNSUPPORTED otherwise).  The batch owns its instances; instance i is
  * addressed by its index.  The state of an instance at step n lives in one of

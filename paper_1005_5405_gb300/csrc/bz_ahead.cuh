@@ -105,22 +105,22 @@ __global__ void k_ahead_lfill(AheadPlans A, int64_t step0)
                  A.meta + s * kLzMetaSize, A.rec + s * A.recn, A.dest0 + s * kLzRoleT);
 }
 
-// The plan of the current step (*stepp) into the arrays the step reads, and
-// its counters into the handle's statistics (as the per-step chain records
-// them: [1] out-of-box samples, [2] near-face samples, [5] overflowing
-// steps, [6] active nodes).  Grid-stride over every array.
-__global__ void k_ahead_take(AheadPlans A, const int64_t *__restrict__ stepp, int4 *__restrict__ idx,
-                             PlanA<float, int> *__restrict__ pa, int *__restrict__ meta,
-                             uint32_t *__restrict__ mask, int *__restrict__ wpre, int *__restrict__ act,
-                             uint2 *__restrict__ rec, int *__restrict__ dest0,
-                             unsigned long long *__restrict__ stats)
+// The plan of step `step` into the arrays the step reads, and its counters
+// into the handle's statistics (as the per-step chain records them: [1]
+// out-of-box samples, [2] near-face samples, [5] overflowing steps, [6]
+// active nodes).  Thread i0 of `stride` threads; the thread with i0 == 0
+// records the counters.
+__device__ __forceinline__ void ahead_take(const AheadPlans &A, int64_t step, int4 *__restrict__ idx,
+                                           PlanA<float, int> *__restrict__ pa, int *__restrict__ meta,
+                                           uint32_t *__restrict__ mask, int *__restrict__ wpre,
+                                           int *__restrict__ act, uint2 *__restrict__ rec,
+                                           int *__restrict__ dest0, unsigned long long *__restrict__ stats,
+                                           int64_t i0, int64_t stride)
 {
-    const int s = (int)(*stepp % A.K);
+    const int s = (int)(step % A.K);
     const int *sm = A.meta + s * kLzMetaSize;
     const int M = min(sm[0], A.nvt), C = sm[3];
     const int64_t t0 = (int64_t)s * A.nt, v0 = (int64_t)s * A.nvt, w0 = (int64_t)s * (A.nvt / 32);
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t i = i0; i < A.nt; i += stride) {
         idx[i] = A.idx[t0 + i];
         pa[i] = A.pa[t0 + i];
@@ -141,6 +141,18 @@ __global__ void k_ahead_take(AheadPlans A, const int64_t *__restrict__ stepp, in
         if (sm[1]) stats[5] += 1ull;
         stats[6] = (unsigned long long)sm[0];
     }
+}
+
+// The plan of the current step (*stepp) of one handle.  Grid-stride over
+// every array.
+__global__ void k_ahead_take(AheadPlans A, const int64_t *__restrict__ stepp, int4 *__restrict__ idx,
+                             PlanA<float, int> *__restrict__ pa, int *__restrict__ meta,
+                             uint32_t *__restrict__ mask, int *__restrict__ wpre, int *__restrict__ act,
+                             uint2 *__restrict__ rec, int *__restrict__ dest0,
+                             unsigned long long *__restrict__ stats)
+{
+    ahead_take(A, *stepp, idx, pa, meta, mask, wpre, act, rec, dest0, stats,
+               (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
 }  // namespace bzk

@@ -1806,6 +1806,7 @@ struct bz_batch {
     // launch per kernel class (bz_batch.cuh, kbl_*), the per-cell kernel as
     // persistent CTAs over segments of the instances' cell groups.
     bool lz_ok = false;
+    bool lz_ahead = false;                  // every instance builds its plans ahead: copy them
     bzk::LzInst *d_lzinst = nullptr;
     int4 *d_segs = nullptr;
     int *d_next = nullptr;                  // one claim counter per velocity grid
@@ -2076,11 +2077,17 @@ bz_status lz_batch_launch(bz_batch *B, cudaStream_t s, bool advance)
     BZ_CUDA(cudaEventRecord(B->lz_fork, s));
     BZ_CUDA(cudaStreamWaitEvent(B->lz_side, B->lz_fork, 0));
     const cudaStream_t sp = B->lz_side;
-    bzk::kbl_plan<<<sg, pb, 0, sp>>>(B->d_lzinst, B->d_samp_pre, B->n);
-    bzk::kbl_scan<<<B->n, 1024, 0, sp>>>(B->d_lzinst);
-    bzk::kbl_remap<<<sg, pb, 0, sp>>>(B->d_lzinst, B->d_samp_pre, B->n);
-    bzk::kbl_lscan<<<B->n, 1024, 0, sp>>>(B->d_lzinst);
-    bzk::kbl_lfill<<<sg, pb, 0, sp>>>(B->d_lzinst, B->d_samp_pre, B->n);
+    if (B->lz_ahead) {
+        // Each instance's plan copied from its slots (the batches are built
+        // ahead by the caller of this launch, outside any capture).
+        bzk::kbl_take<<<dim3(8, B->n), 256, 0, sp>>>(B->d_lzinst);
+    } else {
+        bzk::kbl_plan<<<sg, pb, 0, sp>>>(B->d_lzinst, B->d_samp_pre, B->n);
+        bzk::kbl_scan<<<B->n, 1024, 0, sp>>>(B->d_lzinst);
+        bzk::kbl_remap<<<sg, pb, 0, sp>>>(B->d_lzinst, B->d_samp_pre, B->n);
+        bzk::kbl_lscan<<<B->n, 1024, 0, sp>>>(B->d_lzinst);
+        bzk::kbl_lfill<<<sg, pb, 0, sp>>>(B->d_lzinst, B->d_samp_pre, B->n);
+    }
     BZ_CUDA(cudaEventRecord(B->lz_join, sp));
     bzk::kbl_walls<<<B->tot_faces, bzk::kWallThreads, 0, s>>>(B->d_lzinst, B->d_face_pre, B->n);
     BZ_CUDA(cudaMemsetAsync(B->d_next, 0, sizeof(int) * B->lz_classes.size(), s));
@@ -2152,6 +2159,8 @@ bz_status lz_batch_prepare(bz_batch *B)
         b.sc_cursor = h->sc_cursor;
         b.sc_meta = h->sc_meta;
         b.sc_ent = h->sc_ent;
+        b.ahead = h->ahead;
+        if (h->ahead_K == 0) b.ahead.K = 0;
         for (int p = 0; p < 2; ++p) {
             bzk::LzArgs &a = b.a[p];
             a = bzk::LzArgs{};
@@ -2228,6 +2237,11 @@ bz_status lz_batch_prepare(bz_batch *B)
     B->nseg = (int)segs.size();
     B->lz_smem = smem;
     B->lz_ok = true;
+    // With every instance's plans built ahead (the default) the step copies
+    // them (BZ_BATCH_LZ_AHEAD=0: every step builds them in the step).
+    B->lz_ahead = true;
+    for (bz_handle *h : B->inst) B->lz_ahead = B->lz_ahead && h->ahead_K > 0;
+    if (const char *e = getenv("BZ_BATCH_LZ_AHEAD")) B->lz_ahead = B->lz_ahead && atoi(e) != 0;
     return BZ_OK;
 }
 
@@ -2379,12 +2393,13 @@ bz_status bz_batch_step(bz_batch *B, int32_t nsteps, void *stream)
             if (e != cudaSuccess) return fail(BZ_ECUDA, "batch graph: %s", cudaGetErrorString(e));
         }
         for (int32_t k = 0; k < nsteps; ++k) {
+            if (B->lz_ahead) BZ_TRY(fan_ensure(B, s));
             if (B->graph2 && graphs_enabled()) BZ_CUDA(cudaGraphLaunch(B->graph2, s));
             else BZ_TRY(lz_batch_launch(B, s, true));
+            for (auto &v : B->step) v += 1;
         }
         for (int i = 0; i < B->n; ++i) {
             bz_handle *h = B->inst[i];
-            B->step[i] += nsteps;
             h->step = B->step[i];
             h->cur = (int)(h->step & 1);
             if (nsteps > 0) {
@@ -2519,7 +2534,8 @@ bz_status bz_batch_tune(bz_batch *B, int32_t trial_steps, void *stream, int32_t 
                     t = f / trial_steps;
             }
         } else if (k.mode == 2) {
-            if (batch_set_mode(B, 2, s) == BZ_OK && lz_batch_launch(B, s, false) == BZ_OK) {
+            if (batch_set_mode(B, 2, s) == BZ_OK && (!B->lz_ahead || fan_ensure(B, s) == BZ_OK) &&
+                lz_batch_launch(B, s, false) == BZ_OK) {
                 cudaEventRecord(e0, s);
                 bool ok = true;
                 for (int r = 0; r < trial_steps && ok; ++r) ok = lz_batch_launch(B, s, false) == BZ_OK;

@@ -10,7 +10,7 @@
 // step counter, so one captured step replays correctly any number of times.
 #pragma once
 
-#include "bz_lazy.cuh"
+#include "bz_ahead.cuh"
 
 namespace bzk {
 
@@ -201,7 +201,20 @@ struct LzInst {
     PlanA<float, uint16_t> *pa16;
     int *sc_count, *sc_cursor, *sc_meta;
     uint32_t *sc_ent;
+    AheadPlans ahead;            // the instance's plans built ahead (K = 0: none)
 };
+
+// The plans of every instance's current step from its slots built ahead (grid
+// row y: instance y), as k_ahead_take copies them for a single handle.
+__global__ void kbl_take(const LzInst *__restrict__ inst)
+{
+    const LzInst &b = inst[blockIdx.y];
+    const LzArgs &a = b.a[0];
+    ahead_take(b.ahead, *b.step, b.idx, b.pa, const_cast<int *>(a.meta), const_cast<uint32_t *>(a.mask),
+               const_cast<int *>(a.wpre), const_cast<int *>(a.act), const_cast<uint2 *>(a.rec),
+               const_cast<int *>(a.dest0), a.stats, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+               (int64_t)gridDim.x * blockDim.x);
+}
 
 // Walls of every face of every instance (the input's pending corrections
 // applied): one CTA per face.

@@ -34,30 +34,34 @@ def _warm(p, seed):
     return workloads.warm_state(p, seed=seed).astype(np.float32)
 
 
-@pytest.mark.parametrize("mode", ["persistent", "fanout", "fanout_ordered", "lz", "lz_overflow"])
+@pytest.mark.parametrize("mode", ["persistent", "fanout", "fanout_ordered", "lz", "lz_ordered",
+                                  "lz_per_step", "lz_overflow"])
 def test_batch_matches_single_instances_and_oracle(monkeypatch, mode):
     """Every schedule: the persistent 4-node-vector kernels over all
     instances; the fan-out graph of the instances' own active-node steps
     (each with its sample plan on its own second stream), also with the joint
     term order forced on in every instance and in the single-instance
-    handles; the persistent active-node kernels over all instances, also with
-    every instance's compact arrays capped below its active nodes (every step
-    then takes the gated 4-node-vector fallback).  Three steps without a
-    read, then one step at a time against the oracle restarted from the
-    batch's state."""
-    for k in ("BZ_LAZY_ORDER", "BZ_LAZY_MCAP", "BZ_BATCH_MODE"):
+    handles; the persistent active-node kernels over all instances, copying
+    each instance's plans built ahead (also with the term order forced on),
+    or building every instance's plan in the step, and with every instance's
+    compact arrays capped below its active nodes (every step then takes the
+    gated 4-node-vector fallback).  Three steps without a read, then one step
+    at a time against the oracle restarted from the batch's state."""
+    for k in ("BZ_LAZY_ORDER", "BZ_LAZY_MCAP", "BZ_BATCH_MODE", "BZ_BATCH_LZ_AHEAD"):
         monkeypatch.delenv(k, raising=False)
     if mode.startswith("fanout"):
         monkeypatch.setenv("BZ_BATCH_MODE", "fanout")
     if mode.startswith("lz"):
         monkeypatch.setenv("BZ_BATCH_MODE", "lz")
-    if mode == "fanout_ordered":
+    if mode in ("fanout_ordered", "lz_ordered"):
         monkeypatch.setenv("BZ_LAZY_ORDER", "1")
+    if mode == "lz_per_step":
+        monkeypatch.setenv("BZ_BATCH_LZ_AHEAD", "0")
     if mode == "lz_overflow":
         monkeypatch.setenv("BZ_LAZY_MCAP", "8")
     ps = _problems()
     b = binding.Batch(ps)
-    expect = {"persistent": 0, "lz": -1, "lz_overflow": -1}.get(mode)
+    expect = {"persistent": 0, "lz": -1, "lz_ordered": -1, "lz_per_step": -1, "lz_overflow": -1}.get(mode)
     branches = b.schedule()["fanout_branches"]
     assert branches == expect if expect is not None else branches > 0
     singles = []
