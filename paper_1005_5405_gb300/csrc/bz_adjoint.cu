@@ -267,7 +267,7 @@ bz_status launch(bz_adj_scratch *a, const bzk::Geo &g0, int64_t step, const R *h
         }
     }
     if (e == cudaSuccess) {
-        bzk::k_adj_walls<R><<<g.nfaces, 256, 0, s>>>(g, a->step, (const R *)a->lt, a->nw, a->lF,
+        bzk::k_adj_walls<R><<<g.nfaces, bzk::kWallThreads, 0, s>>>(g, a->step, (const R *)a->lt, a->nw, a->lF,
                                                      grad_lid, wD);
         e = check();
     }

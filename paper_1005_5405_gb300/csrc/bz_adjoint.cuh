@@ -324,34 +324,40 @@ __global__ void k_adj_walls(Geo g, const int64_t *__restrict__ stepp, const R *_
     __syncthreads();
     const R *L = lt + (int64_t)F.cell * g.nvt;
     const R dcoef = (R)(lid && wD != 0.0 ? wD * 2.0 / g.nx : 0.0), rcdx = (R)cdx;
-    // Thread t takes node jz = t mod N of every (t div N)-th (jx, jy) row;
-    // per-thread sums in the state's precision, the block sum in double.
+    // Thread t takes node jz = t mod N of every (t div N)-th (jx, jy) row
+    // whose normal velocity points into the cell (v_n > 0: the upper half of
+    // the normal axis for an inward normal along +e_n, the lower half for
+    // -e_n, the axes being symmetric); per-thread sums in the state's
+    // precision, the block sum in double.
     R a0 = R(0), a1 = R(0);        // sum lg r, sum lg r v_x
-    const int per = blockDim.x / N, jz = threadIdx.x % N;
+    const int per = blockDim.x / N, jz = threadIdx.x % N, H = N / 2;
+    const int jlo = F.nsign > 0.0 ? N - H : 0;
+    const int nrow = N * H;        // rows with v_n > 0
     if ((int)threadIdx.x < per * N) {
-        // Eight rows at a time: their loads are in flight together.
-        for (int row0 = threadIdx.x / N; row0 < N2; row0 += 8 * per) {
-            R ls[8];
+        // kWallLoads rows at a time: their loads are in flight together.
+        for (int r0 = threadIdx.x / N; r0 < nrow; r0 += kWallLoads * per) {
+            R ls[kWallLoads];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int row = row0 + k * per, jx = row / N, jy = row - jx * N;
-                const bool in = row < N2 && (F.nax == 0 ? sv[jx] : sv[jy]) * (R)F.nsign > R(0);
-                ls[k] = in ? L[row * N + jz] : R(0);
+            for (int k = 0; k < kWallLoads; ++k) {
+                const int r = r0 + k * per;
+                // side walls: jx in the half, jy free; bottom and lid: jy in it
+                const int a = r / H, b = r - a * H;
+                const int row = F.nax == 0 ? (jlo + r / N) * N + r % N : a * N + jlo + b;
+                ls[k] = r < nrow ? L[row * N + jz] : R(0);
             }
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int row = row0 + k * per;
-                if (row >= N2) break;
-                const int jx = row / N, jy = row - jx * N;
+            for (int k = 0; k < kWallLoads; ++k) {
+                const int r = r0 + k * per;
+                if (r >= nrow) break;
+                const int a = r / H, b = r - a * H;
+                const int jx = F.nax == 0 ? jlo + r / N : a, jy = F.nax == 0 ? r % N : jlo + b;
                 const R vx = sv[jx], vy = sv[jy];
                 const R vn = (F.nax == 0 ? vx : vy) * (R)F.nsign;
-                if (vn > R(0)) {
-                    R lg = vn * rcdx * ls[k];
-                    if (dcoef != R(0)) lg += dcoef * sA[jx] * sA[jy] * sA[jz] * vx * vy;
-                    const R lr = lg * rt[jx];
-                    a0 += lr;
-                    a1 += lr * vx;
-                }
+                R lg = vn * rcdx * ls[k];
+                if (dcoef != R(0)) lg += dcoef * sA[jx] * sA[jy] * sA[jz] * vx * vy;
+                const R lr = lg * rt[jx];
+                a0 += lr;
+                a1 += lr * vx;
             }
         }
     }
