@@ -151,10 +151,10 @@ bz_status bz_destroy(bz_handle *h);
  * wall densities from h^n (Eq. bcMax), the shared sample set (Sec. 4.2,
  * Algorithm 2), and one fused kernel that streams (Eq. streaming2D),
  * collides (Eq. collision_step), corrects (Eqs. rinorm_a, correzione) and
- * reduces the moments.  On the FP32 active-node path the sample sets of 32
- * steps are built ahead in one batch (they depend on the step number only),
- * so the step that starts a batch carries its cost.  Asynchronous on
- * `stream`. */
+ * reduces the moments.  On the FP32 active-node path the sample sets of
+ * bz_info.plan_batch steps are built ahead in one batch (they depend on the
+ * step number only), so the step that starts a batch carries its cost.
+ * Asynchronous on `stream`. */
 bz_status bz_step(bz_handle *h, int32_t nsteps, void *stream);
 
 /* Like bz_step with the sub-steps chosen by `flags` (BZ_DO_STREAM,
