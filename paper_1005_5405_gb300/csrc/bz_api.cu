@@ -542,9 +542,9 @@ bz_status configure_lazy(bz_handle *H)
         // the step's critical path: it runs when the iterations per CTA times
         // the run length reach 6144.  With the plans built ahead (below) it
         // runs over whole runs and costs GPU time in proportion to the run
-        // length (about 63 us per step at 2x10^4 samples), which pays from
-        // about 12 iterations per CTA on (measured: 64^2 cells lose 1%, 96^2
-        // and more gain 0.6-9%).
+        // length (about 45-65 us per step at 2x10^4 samples, by the batch
+        // size), which pays from about 12 iterations per CTA on (measured:
+        // 64^2 cells lose 1%, 96^2 and more gain 0.6-9%).
         const int64_t iters = ((int64_t)(g.nr + H->lz_G - 1) / H->lz_G + H->lz_grid - 1) / H->lz_grid;
         const char *ka = getenv("BZ_LAZY_AHEAD");
         const bool per_step = ka && atoi(ka) == 0;
