@@ -567,9 +567,9 @@ bz_status configure_lazy(bz_handle *H)
     // whole runs.  The order kernel's one-warp CTAs (T / NB per plan and
     // chunk) are bound by their shared memory to a few per SM and take about
     // the same time in every wave.  When 32 plans need more than one wave, K
-    // fills the last wave (46 on a 152-SM GB300 at 2x10^4 samples, where the
-    // 1024 CTAs of 32 plans would leave the second wave a third full); K is
-    // kept even so that the two-step graphs never straddle a batch; at most 64.
+    // fills the last wave; K is kept even so that the two-step graphs never
+    // straddle a batch; at most 64.  (On a 152-SM GB300 at 2x10^4 samples
+    // seven CTAs fit an SM, so the 1024 CTAs of 32 plans take one wave.)
     {
         const int nb = H->lz_G == 4 ? 8 : 16;
         H->ahead_chunk = H->lz_cmax;

@@ -310,13 +310,16 @@ __global__ void k_lz_lfill(int nt, int T, int osh, const ushort4 *__restrict__ q
 // Several plans at once: blockIdx.z selects plan slot (z0 + blockIdx.z) mod
 // zK, whose meta and records lie kLzMetaSize ints and rec_stride records
 // after those of slot 0.
+constexpr int kLzOrderWin = 64;     // positions whose taken entries are held at a time
+
 __host__ __device__ inline size_t lz_order_smem(int chunk, int nb)
 {
-    // records (rows padded to an odd length), taken entries, segment ends,
-    // run order masks, decided masks
+    // records (rows padded to an odd length), taken entries of a window of
+    // positions, segment ends, run order masks, decided masks of the window,
+    // padding masks
     const size_t m = nb == 8 ? 1 : 2;
-    return (size_t)nb * (chunk + 1) * sizeof(uint2) + (size_t)chunk * nb * (sizeof(uint32_t) + sizeof(uint16_t) + m) +
-           (size_t)chunk * m + 32;
+    return (size_t)nb * (chunk + 1) * sizeof(uint2) + (size_t)kLzOrderWin * nb * sizeof(uint32_t) +
+           (size_t)chunk * nb * (sizeof(uint16_t) + m) + (size_t)kLzOrderWin * m + (size_t)chunk * m + 32;
 }
 
 template <int NB>
@@ -332,6 +335,7 @@ __global__ void __launch_bounds__(32) k_lz_order(int T, int cmax, int chunk, con
     static_assert(NB == 8 || NB == 16, "phase width");
     constexpr int H = 32 / NB;                       // lanes per run
     constexpr int OSH = NB == 8 ? 4 : 3;             // log2 of the entry size
+    constexpr int W = kLzOrderWin;
     constexpr uint16_t kNone = 0xFFFF;
     using Mask = typename std::conditional<NB == 8, uint8_t, uint16_t>::type;
     extern __shared__ __align__(16) unsigned char osm[];
@@ -342,16 +346,19 @@ __global__ void __launch_bounds__(32) k_lz_order(int T, int cmax, int chunk, con
     if (C > cmax || meta[1] || blockIdx.x * NB + NB > T || c0 >= C) return;
     const int L = min(chunk, C - c0), SP = chunk + 1;
     uint2 *b = reinterpret_cast<uint2 *>(osm);                   // [NB][SP] working copies of the runs
-    uint32_t *u = reinterpret_cast<uint32_t *>(b + NB * SP);     // [chunk][NB] entries taken: first | second << 16
-    uint16_t *seg = reinterpret_cast<uint16_t *>(u + chunk * NB); // [NB][chunk] segment end | last << 15
+    uint32_t *u = reinterpret_cast<uint32_t *>(b + NB * SP);     // [W][NB] entries taken: first | second << 16
+    uint16_t *seg = reinterpret_cast<uint16_t *>(u + W * NB);    // [NB][chunk] segment end | last << 15
     Mask *bm = reinterpret_cast<Mask *>(seg + NB * chunk);       // [NB][chunk] runs that choose before this one
-    Mask *dec = bm + NB * chunk;                                // [chunk] runs that have decided p
+    Mask *dec = bm + NB * chunk;                                // [W] runs that have decided p
+    Mask *pad = dec + W;                                        // [chunk] runs that are padding at p
+    // Positions p live in slot p mod W of u and dec while some run has not
+    // decided them; a run decides p only while p < (the smallest undecided
+    // position) + W, which delays some decisions but changes none.
 #pragma unroll 4
     for (int i = lane; i < NB * L; i += 32) {       // the NB runs of a position are adjacent in rec
         const int p = i / NB, r = i - p * NB;
         b[r * SP + p] = rec[(int64_t)(c0 + p) * T + blockIdx.x * NB + r];
     }
-    for (int i = lane; i < NB * L; i += 32) u[i] = 0xFFFFFFFFu;
     __syncwarp();
     // Segments: up to a destination's last term or the chunk's end, before
     // the padding (zero records).
@@ -380,8 +387,7 @@ __global__ void __launch_bounds__(32) k_lz_order(int T, int cmax, int chunk, con
             sz[r] = v == kNone ? 0 : (v & 0x7FFF) - p + 1;
             if (v == kNone) d |= (Mask)(1u << r);
         }
-        if (d) u[p * NB] = 0u;
-        dec[p] = d;
+        pad[p] = d;
 #pragma unroll
         for (int r = 0; r < NB; ++r) {
             Mask m = 0;
@@ -392,27 +398,50 @@ __global__ void __launch_bounds__(32) k_lz_order(int T, int cmax, int chunk, con
         }
     }
     __syncwarp();
+    // The first window: nothing taken, padding decided (its reads are entry 0).
+    int wend = min(W, L);                             // positions below this hold their slot
+    for (int i = lane; i < wend * NB; i += 32) {
+        const int q = i / NB, g = i - q * NB;
+        u[i] = g == 0 && pad[q] ? 0u : 0xFFFFFFFFu;
+    }
+    for (int q = lane; q < wend; q += 32) dec[q] = pad[q];
+    __syncwarp();
     uint2 *bl = b + l * SP;
     const uint16_t *sl = seg + l * chunk;
     const Mask *bml = bm + l * chunk;
     int p = 0;                                        // this run's next position in the chunk
     uint16_t sv = L > 0 ? sl[0] : kNone;              // its segment: end | last << 15, kNone: padding
     // Every step some run is ready (the first, at the smallest undecided
-    // position, in that position's order), so NB * L steps always suffice.
+    // position, in that position's order; that position lies in the window),
+    // so NB * L steps always suffice.
     for (int step = 0; step < NB * L; ++step) {
         const bool active = p < L && sv != kNone;
         if (!__any_sync(0xFFFFFFFFu, active)) break;
+        // The smallest undecided position; positions up to it + W get slots.
+        const int pmin = (int)__reduce_min_sync(0xFFFFFFFFu, (unsigned)(active ? p : L));
+        const int wnew = min(pmin + W, L);
+        if (wnew > wend) {
+            // (positions below wnew - W are behind every run: not set up)
+            const int w0 = max(wend, wnew - W);
+            for (int i = lane; i < (wnew - w0) * NB; i += 32) {
+                const int q = w0 + i / NB, g = i % NB;
+                u[(q & (W - 1)) * NB + g] = g == 0 && pad[q] ? 0u : 0xFFFFFFFFu;
+            }
+            for (int q = w0 + lane; q < wnew; q += 32) dec[q & (W - 1)] = pad[q];
+            wend = wnew;
+            __syncwarp();
+        }
         bool ready = false;
         Mask dp = 0;
-        if (active) {
+        if (active && p < wend) {
             const Mask need = bml[p];
-            dp = dec[p];
+            dp = dec[p & (W - 1)];
             ready = (Mask)(dp & need) == need;
         }
         __syncwarp();                                 // the reads above precede this step's writes
         uint32_t best = 0xFFFFFFFFu;                  // cost << 24 | swap << 23 | position
         const int s1 = sv & 0x7FFF;
-        const uint32_t *row = u + p * NB;            // entries taken at p, by group
+        const uint32_t *row = u + (p & (W - 1)) * NB; // entries taken at p, by group
         if (ready) {
             // Passes of 4 H candidates; the run's lanes take the same passes.
             for (int jb = p; jb <= s1; jb += 4 * H) {
@@ -460,9 +489,10 @@ __global__ void __launch_bounds__(32) k_lz_order(int T, int cmax, int chunk, con
             if ((v1 & 0xFFFFu) == kNone) v1 = (v1 & 0xFFFF0000u) | e1;
             uint32_t v2 = g2 == g1 ? v1 : row[g2];
             if ((v2 >> 16) == kNone) v2 = (v2 & 0xFFFFu) | e2 << 16;
-            u[p * NB + g1] = g2 == g1 ? v2 : v1;
-            if (g2 != g1) u[p * NB + g2] = v2;
-            dec[p] = (Mask)(dp | (1u << l));
+            uint32_t *roww = u + (p & (W - 1)) * NB;
+            roww[g1] = g2 == g1 ? v2 : v1;
+            if (g2 != g1) roww[g2] = v2;
+            dec[p & (W - 1)] = (Mask)(dp | (1u << l));
         }
         __syncwarp();
         if (ready) {
